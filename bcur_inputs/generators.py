@@ -1,0 +1,265 @@
+"""Seeded synthetic inputs for Block CUR workloads.
+
+This module is shared by the FP64 oracle, the tests and the benchmark.  It
+only *draws* numbers: matrices with the structure of the paper's workloads,
+the Rademacher test matrix Omega of the randomized range finder, and the
+uniform variates that drive block sampling.  It holds none of the method's
+arithmetic (no leverage scores, no sampling rule, no factorisation of A).
+
+Every random stream is keyed by ``(seed, stream)`` through NumPy's
+``SeedSequence`` so that the oracle and the CUDA path see identical inputs.
+
+Workload recipes (all synthetic stand-ins; the paper's EDA and Arcene data
+are not available):
+
+* ``small_lowrank``  -- the paper's synthetic family A = U V with iid
+  Gaussian factors (Sec. 4.2), plus iid Gaussian noise.
+* ``haar_spectrum`` -- A = U diag(sigma) V^T with Haar-random orthonormal
+  factors and a power-law spectrum, plus iid Gaussian noise.
+* ``ar1_mixture``   -- a biometric-like signal (Sec. 4.1 stand-in): k
+  AR(1) time series of unit stationary variance mixed by an m x k Gaussian
+  loading matrix, plus iid Gaussian noise.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+# Stream identifiers.  Each consumer of randomness draws from its own stream
+# so that changing one (e.g. the number of blocks sampled) never shifts
+# another.
+STREAM_MATRIX = 1
+STREAM_OMEGA = 2
+STREAM_UCOL = 3
+STREAM_UROW = 4
+STREAM_SHAPES = 5
+STREAM_ARRIVALS = 6
+
+
+def rng(seed: int, stream: int) -> np.random.Generator:
+    """Counter-free, reproducible generator for ``(seed, stream)``."""
+    return np.random.default_rng(np.random.SeedSequence([int(seed), int(stream)]))
+
+
+# ----------------------------------------------------------------------------
+# Matrices
+# ----------------------------------------------------------------------------
+
+def small_lowrank(m: int, n: int, rank: int, noise: float, seed: int) -> np.ndarray:
+    """A = G1 (m x rank) . G2 (rank x n) + noise . N(0,1), FP64."""
+    g = rng(seed, STREAM_MATRIX)
+    g1 = g.standard_normal((m, rank))
+    g2 = g.standard_normal((rank, n))
+    a = g1 @ g2
+    if noise:
+        a = a + noise * g.standard_normal((m, n))
+    return a
+
+
+def haar_orthonormal(g: np.random.Generator, n: int, r: int) -> np.ndarray:
+    """n x r matrix with Haar-distributed orthonormal columns.
+
+    QR of a Gaussian matrix with the diagonal-sign correction of Mezzadri
+    (2007), which makes the distribution exactly Haar.
+    """
+    z = g.standard_normal((n, r))
+    q, rr = np.linalg.qr(z)
+    d = np.sign(np.diag(rr))
+    d[d == 0] = 1.0
+    return q * d
+
+
+def haar_spectrum(m: int, n: int, rank: int, decay: float, noise: float, seed: int) -> np.ndarray:
+    """A = U diag(i^-decay) V^T + noise . N(0,1) (host, FP64; small sizes)."""
+    g = rng(seed, STREAM_MATRIX)
+    u = haar_orthonormal(g, m, rank)
+    v = haar_orthonormal(g, n, rank)
+    sig = np.arange(1, rank + 1, dtype=np.float64) ** (-decay)
+    a = (u * sig) @ v.T
+    if noise:
+        a = a + noise * g.standard_normal((m, n))
+    return a
+
+
+def haar_spectrum_device(m: int, n: int, rank: int, decay: float, noise: float, seed: int,
+                         device="cuda", dtype=None):
+    """Same recipe as :func:`haar_spectrum`, drawn on a torch device.
+
+    Used for the 32768 x 32768 workload, which is too large to draw on the
+    host for every run.  The factors are formed in FP64 and the sum is cast
+    to ``dtype`` (default float32) in row panels to bound peak memory.
+    """
+    import torch
+
+    dtype = dtype or torch.float32
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + STREAM_MATRIX)
+
+    def haar(rows: int) -> "torch.Tensor":
+        z = torch.randn(rows, rank, generator=gen, device=device, dtype=torch.float64)
+        q, rr = torch.linalg.qr(z)
+        d = torch.sign(torch.diagonal(rr))
+        d[d == 0] = 1.0
+        return q * d
+
+    u = haar(m)
+    v = haar(n)
+    sig = torch.arange(1, rank + 1, device=device, dtype=torch.float64) ** (-decay)
+    us = (u * sig)
+    a = torch.empty(m, n, device=device, dtype=dtype)
+    panel = 2048
+    for i0 in range(0, m, panel):
+        i1 = min(m, i0 + panel)
+        blk = us[i0:i1] @ v.T
+        if noise:
+            blk += noise * torch.randn(i1 - i0, n, generator=gen, device=device, dtype=torch.float64)
+        a[i0:i1] = blk.to(dtype)
+    return a
+
+
+def ar1_mixture(m: int, n: int, k: int, phi: float, noise: float, seed: int) -> np.ndarray:
+    """Biometric-like matrix: L (m x k, N(0,1)/sqrt(k)) . X (k x n AR(1)) + noise.
+
+    Each row of X follows x_t = phi x_{t-1} + sqrt(1 - phi^2) e_t with
+    x_0 ~ N(0,1), so every series has unit stationary variance.
+    """
+    g = rng(seed, STREAM_MATRIX)
+    load = g.standard_normal((m, k)) / math.sqrt(k)
+    e = g.standard_normal((k, n))
+    x = np.empty((k, n))
+    x[:, 0] = e[:, 0]
+    c = math.sqrt(1.0 - phi * phi)
+    for t in range(1, n):
+        x[:, t] = phi * x[:, t - 1] + c * e[:, t]
+    a = load @ x
+    if noise:
+        a = a + noise * g.standard_normal((m, n))
+    return a
+
+
+# ----------------------------------------------------------------------------
+# Random variates the method consumes
+# ----------------------------------------------------------------------------
+
+def rademacher(n: int, l: int, seed: int) -> np.ndarray:
+    """Omega (n x l) with iid +-1 entries, FP64 (exact in every precision)."""
+    g = rng(seed, STREAM_OMEGA)
+    return (g.integers(0, 2, size=(n, l), dtype=np.int8).astype(np.float64) * 2.0 - 1.0)
+
+
+def uniforms(count: int, seed: int, stream: int) -> np.ndarray:
+    """``count`` doubles uniform on [0, 1) with 53 random bits each."""
+    return rng(seed, stream).random(count)
+
+
+# ----------------------------------------------------------------------------
+# Block partitions
+# ----------------------------------------------------------------------------
+
+def uniform_blocks(n: int, s: int) -> np.ndarray:
+    """Offsets of contiguous blocks of ``s`` indices; G = ceil(n/s), last may be short."""
+    G = -(-n // s)
+    off = np.minimum(np.arange(G + 1, dtype=np.int64) * s, n)
+    return off
+
+
+def blocks_to_sample(k: int, s: int, G: int) -> int:
+    """Number of blocks per side for the batched workloads: min(ceil(2k/s)+1, ceil(G/2))."""
+    return int(min(-(-2 * k // s) + 1, -(-G // 2)))
+
+
+# ----------------------------------------------------------------------------
+# Workload descriptions
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    """One Block CUR problem: a matrix recipe plus the method's parameters."""
+    name: str
+    m: int
+    n: int
+    k: int
+    p: int
+    q: int
+    col_off: np.ndarray
+    row_off: np.ndarray
+    g_col: int
+    g_row: int
+    seed: int
+    storage: str = "f64"          # "f64" or "f32"
+    replacement: bool = False
+    recipe: dict = field(default_factory=dict)
+
+    @property
+    def l(self) -> int:
+        return self.k + self.p
+
+    def matrix(self) -> np.ndarray:
+        """The stored matrix (host), in its storage precision."""
+        r = self.recipe
+        kind = r["kind"]
+        if kind == "small_lowrank":
+            a = small_lowrank(self.m, self.n, r["rank"], r["noise"], self.seed)
+        elif kind == "haar_spectrum":
+            a = haar_spectrum(self.m, self.n, r["rank"], r["decay"], r["noise"], self.seed)
+        elif kind == "ar1_mixture":
+            a = ar1_mixture(self.m, self.n, r["rank"], r["phi"], r["noise"], self.seed)
+        else:
+            raise ValueError(kind)
+        return a.astype(np.float32) if self.storage == "f32" else a
+
+    def omega(self) -> np.ndarray:
+        return rademacher(self.n, self.l, self.seed)
+
+    def u_col(self) -> np.ndarray:
+        return uniforms(self.g_col, self.seed, STREAM_UCOL)
+
+    def u_row(self) -> np.ndarray:
+        return uniforms(self.g_row, self.seed, STREAM_UROW)
+
+
+def plain_fp64_512x1024(seed: int = 0) -> Problem:
+    """512 x 1024 rank-10 Gaussian product + 0.01 noise; 32 column / 16 row blocks of 32."""
+    return Problem("plain_fp64_512x1024", 512, 1024, k=10, p=10, q=2,
+                   col_off=uniform_blocks(1024, 32), row_off=uniform_blocks(512, 32),
+                   g_col=8, g_row=6, seed=seed, storage="f64",
+                   recipe=dict(kind="small_lowrank", rank=10, noise=0.01))
+
+
+def fp32_32768(seed: int = 1, k: int = 50, p: int = 10, q: int = 2) -> Problem:
+    """32768^2 Haar rank-200 spectrum i^-1.5 + 1e-4 noise; 64+64 blocks of 512; 16+16 sampled."""
+    n = 32768
+    return Problem("fp32_32768", n, n, k=k, p=p, q=q,
+                   col_off=uniform_blocks(n, 512), row_off=uniform_blocks(n, 512),
+                   g_col=16, g_row=16, seed=seed, storage="f32",
+                   recipe=dict(kind="haar_spectrum", rank=200, decay=1.5, noise=1e-4))
+
+
+def scaled_haar(m: int, n: int, s: int, k: int, p: int, q: int, g_col: int, g_row: int,
+                seed: int, storage: str = "f32", rank: int = 200, noise: float = 1e-4) -> Problem:
+    """The Haar-spectrum recipe at an arbitrary (smaller) size, for parity tests."""
+    return Problem(f"haar_{m}x{n}_s{s}", m, n, k=k, p=p, q=q,
+                   col_off=uniform_blocks(n, s), row_off=uniform_blocks(m, s),
+                   g_col=g_col, g_row=g_row, seed=seed, storage=storage,
+                   recipe=dict(kind="haar_spectrum", rank=min(rank, m, n), decay=1.5, noise=noise))
+
+
+def batched_biometric(count: int = 512, seed: int = 3) -> List[Problem]:
+    """Uneven batch: m~U[256,4096], n~U[1024,16384] (rounded down to s), s in {16..256}, k~U[5,50]."""
+    g = rng(seed, STREAM_SHAPES)
+    out = []
+    for i in range(count):
+        s = int(g.choice([16, 32, 64, 128, 256]))
+        m = int(g.integers(256, 4097)) // s * s
+        n = int(g.integers(1024, 16385)) // s * s
+        k = int(g.integers(5, 51))
+        Gc, Gr = n // s, m // s
+        out.append(Problem(f"bio_{i}", m, n, k=k, p=10, q=2,
+                           col_off=uniform_blocks(n, s), row_off=uniform_blocks(m, s),
+                           g_col=blocks_to_sample(k, s, Gc), g_row=blocks_to_sample(k, s, Gr),
+                           seed=seed * 100003 + i, storage="f32",
+                           recipe=dict(kind="ar1_mixture", rank=k, phi=0.95, noise=0.05)))
+    return out
