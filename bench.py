@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Block CUR benchmark on GB300: decompositions per second (one JSON line).
+
+A *step* is one whole Block CUR decomposition of one synthetic matrix held in
+HBM: randomized range finder + block leverage scores, block sampling, C/R
+gather + U = C^+ A R^+, and the fused residual ||A - CUR||_F.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--sketch-prec P] [--fit-prec P] [--impl native|reference]
+
+Under torchrun (N > 1) every rank decomposes its own matrix (independent
+problems, weak scaling, no collective on the data path); the max over ranks
+of the timed region sets the throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import bcur_inputs as bi  # noqa: E402
+
+METRIC = "Block CUR decomps/sec and p50/p99 latency at rel-Frobenius err <= oracle+1e-3"
+UNIT = "decomp/s"
+
+
+def workload(name: str, rank: int = 0) -> bi.Problem:
+    if name == "fp32_32768":
+        return bi.fp32_32768(seed=1 + 1000 * rank)
+    if name == "precision_32768":
+        return bi.fp32_32768(seed=1 + 1000 * rank, k=100, p=20, q=3)
+    if name == "plain_fp64_512x1024":
+        return bi.plain_fp64_512x1024(seed=rank)
+    if name.startswith("haar_"):   # haar_<n>: the fp32_32768 recipe at n x n
+        n = int(name.split("_")[1])
+        s = max(16, n // 64)
+        return bi.scaled_haar(n, n, s, k=50, p=10, q=2, g_col=16, g_row=16, seed=1 + 1000 * rank,
+                              rank=200, noise=1e-4)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_flops(m, n, c, r, l, q):
+    """FLOP model of the FP64 oracle's dominant steps (used to scale a timed
+    sample to the full size): range finder 2(2q+2) m n l; SVD-based pinv of C
+    and R ~ 4 m c^2 + 8 c^3 and 4 n r^2 + 8 r^3; C^+ A R^+ 2 c m n + 2 c n r;
+    C U R 2 m c r + 2 m r n."""
+    return (2 * (2 * q + 2) * m * n * l + 4 * m * c * c + 8 * c ** 3 + 4 * n * r * r + 8 * r ** 3
+            + 2 * c * m * n + 2 * c * n * r + 2 * m * c * r + 2 * m * r * n)
+
+
+def oracle_sample(full: bi.Problem):
+    """A bounded sample of the workload for the host oracle: the same recipe
+    at 1/8 the size per side, blocks of the same width, c/n and r/m kept."""
+    if full.m <= 4096 and full.n <= 4096:
+        return full, 1.0
+    f = 8
+    m, n = full.m // f, full.n // f
+    s = int(full.col_off[1])
+    gs = max(1, full.g_col // f)
+    p = bi.scaled_haar(m, n, s, k=full.k, p=full.p, q=full.q, g_col=gs, g_row=gs, seed=full.seed,
+                       rank=min(200, m), noise=full.recipe.get("noise", 1e-4))
+    c_full = int(np.sum(np.sort(np.diff(full.col_off))[::-1][:full.g_col]))
+    r_full = int(np.sum(np.sort(np.diff(full.row_off))[::-1][:full.g_row]))
+    scale = oracle_flops(full.m, full.n, c_full, r_full, full.l, full.q) / oracle_flops(
+        m, n, gs * s, gs * s, p.l, p.q)
+    return p, scale
+
+
+def time_oracle(full: bi.Problem, steps: int, warmup: int = 0):
+    import oracle as orc
+
+    p, scale = oracle_sample(full)
+    A = p.matrix()
+    om, uc, ur = p.omega(), p.u_col(), p.u_row()
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, om, uc, ur)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    sample = (f"FP64 NumPy oracle, whole pipeline on a {p.m}x{p.n} matrix of the same recipe "
+              f"({len(p.col_off) - 1}+{len(p.row_off) - 1} blocks of {int(p.col_off[1])}, "
+              f"{p.g_col}+{p.g_row} drawn, k={p.k}, p={p.p}, q={p.q}); mean of {steps} runs "
+              f"{t:.3f} s; decomps/s scaled to {full.m}x{full.n} by the oracle FLOP model "
+              f"(x{scale:.1f})")
+    return 1.0 / (t * scale), sample, t
+
+
+# ---------------------------------------------------------------------------
+# Native arm
+# ---------------------------------------------------------------------------
+def roofline_peak(prec: str, peaks: dict, sm_mhz):
+    """(bound, peak, unit, source) of the dominant kernel for its precision."""
+    if prec == "bf16":
+        return "tensor", peaks.get("bf16_tflops_sustained", 1700.0), "TFLOP/s", "measured bf16 sustained"
+    if prec == "tf32":
+        return ("tensor", peaks.get("bf16_tflops_sustained", 1700.0) / 2.0, "TFLOP/s",
+                "measured bf16 sustained x 1/2 (nominal tf32:bf16 ratio)")
+    # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x SM clock.
+    mhz = peaks.get("sm_max_mhz", 2070.0) if not sm_mhz else sm_mhz
+    if prec == "f32":
+        return "alu", 152 * 128 * 2 * mhz * 1e6 / 1e12, "TFLOP/s", f"FP32 FMA peak at {mhz:.0f} MHz"
+    return "alu", 152 * 2 * 2 * mhz * 1e6 / 1e12, "TFLOP/s", f"FP64 FMA estimate at {mhz:.0f} MHz"
+
+
+def main_native(args):
+    import torch
+
+    import paper_1703_06065_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.load()
+    p = workload(args.workload, rank)
+    sp = args.sketch_prec or ("f64" if p.storage == "f64" else "f32")
+    fp = args.fit_prec or ("f64" if p.storage == "f64" else "f32")
+    tdt = torch.float64 if p.storage == "f64" else torch.float32
+
+    # inputs resident in HBM before the timed region
+    if p.m * p.n > 64 * 1024 * 1024 and p.recipe["kind"] == "haar_spectrum":
+        A = bi.haar_spectrum_device(p.m, p.n, p.recipe["rank"], p.recipe["decay"],
+                                    p.recipe["noise"], p.seed, device=dev, dtype=tdt)
+    else:
+        A = torch.from_numpy(p.matrix()).to(dev, tdt)
+    om = torch.from_numpy(np.ascontiguousarray(p.omega().T)).to(dev, tdt)
+    uc = torch.from_numpy(p.u_col()).to(dev)
+    ur = torch.from_numpy(p.u_row()).to(dev)
+    plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
+                    dtype=p.storage, sketch_prec=sp, fit_prec=fp)
+    Ubuf = torch.empty(plan.c_max, plan.r_max, dtype=tdt, device=dev)
+    ebuf = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def step(Ain):
+        cs, rs = plan.scores(Ain, om)
+        ci, ri, _, _ = plan.sample(cs, rs, uc, ur)
+        plan.fit(Ain, ci, ri, U=Ubuf)
+        plan.error(Ain, out=ebuf)
+        return cs, rs, ci, ri
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(A)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    barrier()
+    torch.cuda.synchronize()
+
+    L = pkg.load()
+    launches0 = L.bcur_launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(s)
+    for _ in range(args.steps):
+        step(A)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = (L.bcur_launch_count() - launches0) // max(args.steps, 1)
+    plan.sync_status()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    e = ebuf.cpu().numpy()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # -- end to end: inputs from pinned host memory, results read back --------
+    e2e = None
+    if not args.no_e2e:
+        A_h = A.cpu().pin_memory()
+        om_h = om.cpu().pin_memory()
+        uc_h, ur_h = uc.cpu().pin_memory(), ur.cpu().pin_memory()
+        A_d = torch.empty_like(A)
+        om_d, uc_d, ur_d = torch.empty_like(om), torch.empty_like(uc), torch.empty_like(ur)
+        U_h = torch.empty(Ubuf.shape, dtype=tdt).pin_memory()
+        e_h = torch.empty(3, dtype=torch.float64).pin_memory()
+        cs_h = torch.empty(p.col_off.size - 1, dtype=torch.float64).pin_memory()
+        rs_h = torch.empty(p.row_off.size - 1, dtype=torch.float64).pin_memory()
+        ci_h = torch.empty(p.g_col, dtype=torch.int32).pin_memory()
+        ri_h = torch.empty(p.g_row, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            A_d.copy_(A_h, non_blocking=True)
+            om_d.copy_(om_h, non_blocking=True)
+            uc_d.copy_(uc_h, non_blocking=True)
+            ur_d.copy_(ur_h, non_blocking=True)
+            cs, rs = plan.scores(A_d, om_d)
+            ci, ri, _, _ = plan.sample(cs, rs, uc_d, ur_d)
+            plan.fit(A_d, ci, ri, U=Ubuf)
+            plan.error(A_d, out=ebuf)
+            U_h.copy_(Ubuf, non_blocking=True)
+            e_h.copy_(ebuf, non_blocking=True)
+            cs_h.copy_(cs, non_blocking=True)
+            rs_h.copy_(rs, non_blocking=True)
+            ci_h.copy_(ci, non_blocking=True)
+            ri_h.copy_(ri, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        k2 = max(1, min(args.steps, 3))
+        ev0.record(s)
+        for _ in range(k2):
+            e2e_step()
+        ev1.record(s)
+        torch.cuda.synchronize()
+        ms2 = ev0.elapsed_time(ev1) / k2
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        h2d = sum(x.numel() * x.element_size() for x in (A_h, om_h, uc_h, ur_h))
+        d2h = sum(x.numel() * x.element_size() for x in (U_h, e_h, cs_h, rs_h, ci_h, ri_h))
+        e2e = {"value": world * 1000.0 / ms2, "unit": UNIT, "ms_per_step": ms2,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        del A_d, A_h
+
+    # -- dominant kernel, timed live: the fused residual GEMM of the fit -----
+    roof = None
+    if rank == 0:
+        r = plan.r_max
+        Pm = torch.randn(p.m, r, device=dev, dtype=tdt) / float(np.sqrt(r))
+        Qm = torch.randn(r, p.n, device=dev, dtype=tdt) / float(np.sqrt(p.n))
+        out = pkg.residual(A, Pm, Qm, fp)
+        torch.cuda.synchronize()
+        nrep = 3
+        ev0.record(s)
+        for _ in range(nrep):
+            pkg.residual(A, Pm, Qm, fp)
+        ev1.record(s)
+        torch.cuda.synchronize()
+        kms = ev0.elapsed_time(ev1) / nrep
+        flops = 2.0 * p.m * p.n * r
+        achieved = flops / (kms * 1e-3) / 1e12
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        bound, peak, unit, src = roofline_peak(fp, peaks, clk.get("sm_mhz"))
+        roof = {"kernel": "fused residual GEMM  sum (A - P Q)^2", "bound": bound,
+                "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": None, "ms": round(kms, 4),
+                "algorithmic": f"2*m*n*r = {flops:.4g} flop per launch (m={p.m}, n={p.n}, r={r})",
+                "peak_source": src}
+        del Pm, Qm, out
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, _ = time_oracle(p, steps=1)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        dtype = sp if sp == fp else f"{sp}/{fp}"
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": p.name, "m": p.m, "n": p.n, "k": p.k, "p": p.p, "q": p.q,
+                       "block": int(p.col_off[1]), "G_col": int(p.col_off.size - 1),
+                       "G_row": int(p.row_off.size - 1), "g_col": p.g_col, "g_row": p.g_row,
+                       "storage": p.storage, "sketch_prec": sp, "fit_prec": fp,
+                       "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "rel_err": float(e[1]), "fro_err": float(e[0]),
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args.workload, 0)
+    steps = args.steps
+    v, sample, t = time_oracle(p, steps=steps, warmup=min(args.warmup, 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": p.name, "m": p.m, "n": p.n, "k": p.k},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="fp32_32768")
+    ap.add_argument("--sketch-prec", default=None)
+    ap.add_argument("--fit-prec", default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * bcur.h -- Block CUR decomposition hot path on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Oswal, Jain, Xu, Eriksson, "Block CUR: Decomposing Matrices using
+ * Groups of Columns" (arXiv 1703.06065).  Given A (m x n) with predefined
+ * contiguous column blocks and row blocks (Sec. 3: G = ceil(n/s) blocks,
+ * sizes may vary), the library computes
+ *
+ *   1. the top-k singular subspaces of A by a randomized range finder with
+ *      q steps of subspace iteration on an n x l test matrix, l = k + p
+ *      (the paper allows sketching in place of its score estimate, Sec. 3.1);
+ *   2. block leverage scores l_g = ||V_{A,k}^T E_g||_F^2 (Def. 2) for column
+ *      blocks, and the same quantity on U_{A,k} for row blocks (Sec. 3 applies
+ *      the column rules to A^T);
+ *   3. g_col column blocks and g_row row blocks drawn by inverse CDF from
+ *      p_j = l_j / sum(l) (Alg. 1 step 2; without replacement by default, as in
+ *      the experiments of Sec. 4.1);
+ *   4. C = A[:, chosen column blocks], R = A[chosen row blocks, :] (Alg. 1);
+ *   5. U = C^+ A R^+ through QR factors of C and R^T;
+ *   6. ||A - CUR||_F and ||A - CUR||_F / ||A||_F (Sec. 4.2) without forming CUR.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense.  "row-major h x w, ld" means element (i, j) at
+ *     base[i * ld + j].  A "panel" of a tall matrix X (h x w) is X^T stored
+ *     row-major (w x h): each column of X is contiguous.
+ *   - Pointers named in the comments as "device" must be CUDA device (or
+ *     managed) memory on the current device; "host" pointers are read before
+ *     the call returns.  The caller owns every buffer it passes; the library
+ *     never frees caller memory.
+ *   - All device work is enqueued on the plan's stream (or the `stream`
+ *     argument, a cudaStream_t; NULL = legacy default stream) and the calls
+ *     return without synchronising, unless stated otherwise.  Inputs must stay
+ *     valid and unmodified until the stream has reached the call.
+ *   - Host-detectable errors return immediately and enqueue nothing.  Errors
+ *     the GPU detects (non-finite data, a wait that ran out) are recorded in a
+ *     status word and returned by bcur_sync_status().
+ *   - A plan is not thread-safe: use one plan per host thread and stream.
+ */
+#ifndef BCUR_H_
+#define BCUR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BCUR_OK = 0,
+  BCUR_EINVAL = 1,      /* invalid argument or descriptor                      */
+  BCUR_ENOMEM = 2,      /* workspace missing or too small                      */
+  BCUR_ECUDA = 3,       /* a CUDA runtime/driver call failed                   */
+  BCUR_ERANK = 4,       /* a factorisation met a zero pivot it could not drop  */
+  BCUR_ENONFINITE = 5,  /* NaN or Inf met in the data                          */
+  BCUR_ETIMEOUT = 6,    /* a bounded device-side wait gave up                  */
+  BCUR_ENOTSUP = 7,     /* combination not supported by this build / device    */
+  BCUR_ESTATE = 8       /* call out of order (e.g. bcur_fit before a workspace) */
+} bcur_status_t;
+
+/* Storage type of A and arithmetic of a stage.
+ *   BCUR_F64  : FP64 storage and FP64 arithmetic everywhere.
+ *   BCUR_F32  : FP32 arithmetic on CUDA cores (FP32 storage).
+ *   BCUR_TF32 : tcgen05 tensor cores, TF32 inputs read from FP32 storage,
+ *               FP32 accumulation in tensor memory.
+ *   BCUR_BF16 : tcgen05 tensor cores on a BF16 copy of A, FP32 accumulation. */
+typedef enum { BCUR_F64 = 0, BCUR_F32 = 1, BCUR_TF32 = 2, BCUR_BF16 = 3 } bcur_prec_t;
+
+typedef struct {
+  int64_t m, n;           /* A is m x n                                        */
+  int64_t lda;            /* leading dimension of A (elements), lda >= n       */
+  int32_t a_dtype;        /* BCUR_F64 or BCUR_F32: storage type of A           */
+  int32_t k;              /* target rank, 1 <= k                               */
+  int32_t p;              /* oversampling; l = k + p <= min(m, n, 128)         */
+  int32_t q;              /* subspace iterations, 0 <= q <= 16                 */
+  int32_t G_col;          /* number of column blocks                           */
+  const int64_t* col_off; /* host, G_col + 1 increasing offsets, 0 ... n       */
+  int32_t G_row;          /* number of row blocks                              */
+  const int64_t* row_off; /* host, G_row + 1 increasing offsets, 0 ... m       */
+  int32_t g_col, g_row;   /* blocks drawn per side (<= G without replacement) */
+  int32_t replacement;    /* 0: without replacement (Sec. 4.1), 1: with (Alg. 1) */
+  int32_t sketch_prec;    /* bcur_prec_t of the range-finder GEMMs             */
+  int32_t fit_prec;       /* bcur_prec_t of the QR / U / residual GEMMs        */
+} bcur_desc_t;
+
+typedef struct bcur_plan_s* bcur_plan_t;
+
+/* ---------------------------------------------------------------------------
+ * Plan: validate a descriptor and size the workspace.  Allocates no device
+ * memory.  `stream` is a cudaStream_t (may be NULL).  On success *out holds a
+ * new plan and *workspace_bytes the device workspace it needs.
+ * Errors: BCUR_EINVAL (any descriptor field out of range, offsets not
+ * increasing, lda < n, l > min(m, n, 128), g > G without replacement, F64
+ * storage with a non-F64 precision), BCUR_ENOTSUP (precision unavailable).
+ */
+bcur_status_t bcur_plan(const bcur_desc_t* desc, void* stream, bcur_plan_t* out,
+                        size_t* workspace_bytes);
+
+/* Attach caller-owned device memory (>= workspace_bytes, 256-byte aligned) as
+ * the plan's workspace.  The plan keeps the pointer until destroyed or given
+ * another one.  Errors: BCUR_EINVAL (NULL plan/pointer, misaligned),
+ * BCUR_ENOMEM (too small). */
+bcur_status_t bcur_set_workspace(bcur_plan_t plan, void* workspace, size_t bytes);
+
+/* Stages 1-2: block leverage scores (Def. 2) for column and row blocks.
+ *   A          device, row-major m x n (lda), storage type desc.a_dtype.
+ *   omega      device, the test matrix Omega (n x l) as a panel: row-major
+ *              l x n (ld n), same storage type as A.  Random input chosen by
+ *              the caller (a Rademacher matrix in the tests).
+ *   col_scores device, G_col doubles;  row_scores device, G_row doubles.
+ * The top-k factors stay in the workspace for inspection (bcur_factors).
+ * Errors: BCUR_ESTATE (no workspace), BCUR_EINVAL (NULL pointer). */
+bcur_status_t bcur_scores(bcur_plan_t plan, const void* A, const void* omega,
+                          double* col_scores, double* row_scores);
+
+/* Copy the top-k factors of the last bcur_scores call, as panels: V_k^T
+ * (k x n, ld n) and U_k^T (k x m, ld m) in the storage type of A, and the k
+ * singular values (double).  Any output may be NULL.  Device pointers. */
+bcur_status_t bcur_factors(bcur_plan_t plan, void* Vt, void* Ut, double* sigma);
+
+/* Stage 3: inverse-CDF block sampling (Alg. 1 step 2).  For draw t with
+ * uniform u[t] in [0,1) the chosen block is the first remaining j whose FP64
+ * running prefix sum of scores (sequential, increasing j, each addition and
+ * the product u[t] * total rounded once, no fused multiply-add) exceeds
+ * u[t] * total, total = the FP64 sum of the remaining scores; if rounding
+ * leaves none, the last remaining block with a positive score; if every
+ * remaining score is zero, the first remaining block.  Without replacement
+ * a drawn block leaves the pool.
+ *   scores  device, G_col (resp. G_row) doubles (e.g. from bcur_scores).
+ *   u_col   device, g_col doubles;  u_row device, g_row doubles.
+ *   col_idx/row_idx  device int32, g_col / g_row block indices in draw order.
+ *   col_prob/row_prob device doubles p_j = l_j / sum(l) per draw (may be NULL).
+ */
+bcur_status_t bcur_sample(bcur_plan_t plan, const double* col_scores, const double* row_scores,
+                          const double* u_col, const double* u_row, int32_t* col_idx,
+                          int32_t* row_idx, double* col_prob, double* row_prob);
+
+/* Stages 4-5: gather C and R for the given blocks and fit U = C^+ A R^+.
+ *   col_idx/row_idx device int32 block indices (g_col / g_row, in order).
+ *   U  device, row-major c x r (ld r), storage type of A; rows follow the
+ *      columns of C, columns follow the rows of R.  c = sum of the chosen
+ *      column-block sizes, r likewise.  May be NULL.
+ *   C  device, optional (NULL): the panel C^T, row-major c x m (ld m).
+ *   R  device, optional (NULL): row-major r x n (ld n).
+ * Directions of C or R^T that are numerically dependent (a pivot of the
+ * Cholesky factor of their Gram matrix below the drop tolerance) are dropped:
+ * U is then a least-squares minimiser restricted to the kept directions and
+ * bcur_rank() reports the kept counts.  Errors: BCUR_ESTATE, BCUR_EINVAL. */
+bcur_status_t bcur_fit(bcur_plan_t plan, const void* A, const int32_t* col_idx,
+                       const int32_t* row_idx, void* U, void* C, void* R);
+
+/* Stage 6: residual of the last fit.  out (device, 3 doubles) receives
+ * ||A - CUR||_F, ||A - CUR||_F / ||A||_F and ||A||_F.  CUR is never stored:
+ * the Frobenius sum is reduced inside the GEMM epilogue in a fixed order, so
+ * repeated calls give bit-identical results. */
+bcur_status_t bcur_error(bcur_plan_t plan, const void* A, double* out);
+
+/* Sizes of the last fit: c, r, and the number of kept directions of C and
+ * R^T.  Host pointers; synchronises the plan's stream. */
+bcur_status_t bcur_rank(bcur_plan_t plan, int64_t* c, int64_t* r, int64_t* rank_c,
+                        int64_t* rank_r);
+
+/* Synchronise the plan's stream and return (then clear) the first error the
+ * device recorded since the last call. */
+bcur_status_t bcur_sync_status(bcur_plan_t plan);
+
+void bcur_destroy(bcur_plan_t plan);
+const char* bcur_status_string(bcur_status_t status);
+
+/* ---------------------------------------------------------------------------
+ * Stage kernels callable without a plan (same arithmetic as the plan calls).
+ */
+
+/* Def. 2 for a factor given as a panel F^T (k x h, row-major, ld ldf):
+ * scores[g] = sum_{j in [off[g], off[g+1])} sum_{t<k} F[j, t]^2, accumulated
+ * in FP64 in a fixed order.  dtype: BCUR_F64 or BCUR_F32.  off: device int64
+ * (G + 1, increasing, off[G] <= h); scores: device double (G). */
+bcur_status_t bcur_block_scores(const void* Ft, int32_t dtype, int32_t k, int64_t h,
+                                int64_t ldf, const int64_t* off, int32_t G, double* scores,
+                                void* stream);
+
+/* Alg. 1 step 2 on one side; the rule is the one stated at bcur_sample.
+ * scores device (G), u device (g), idx device int32 (g), prob device (g) or
+ * NULL.  G <= 32768.  Errors: BCUR_EINVAL (g > G without replacement). */
+bcur_status_t bcur_sample_blocks(const double* scores, int32_t G, const double* u, int32_t g,
+                                 int32_t replacement, int32_t* idx, double* prob, void* stream);
+
+/* ||X - P Q||_F^2 reduced in FP64 without forming P Q, where X is row-major
+ * m x n (ldx), P row-major m x r (ldp) and Q row-major r x n (ldq), all of
+ * storage type dtype (F64 or F32) and precision prec (F64 for F64 data, F32
+ * or TF32 for F32 data).  out: device, 2 doubles {||X - PQ||_F^2, ||X||_F^2}.
+ * workspace: device scratch of at least bcur_residual_workspace(m, n, dtype)
+ * bytes.  P and Q may be NULL when r = 0.  This is the fused kernel behind
+ * bcur_error. */
+size_t bcur_residual_workspace(int64_t m, int64_t n, int32_t dtype);
+bcur_status_t bcur_residual(const void* X, int64_t ldx, const void* P, int64_t ldp,
+                            const void* Q, int64_t ldq, int64_t m, int64_t n, int64_t r,
+                            int32_t dtype, int32_t prec, double* out, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/* Dense GEMM on the library's kernels, exposed for testing the tensor-core
+ * path against the CUDA-core path:  D (M x N, row-major, ldd) = A_op B_op,
+ * A_op(i, kk) = transA ? A[kk * lda + i] : A[i * lda + kk],
+ * B_op(kk, j) = transB ? B[j * ldb + kk] : B[kk * ldb + j].
+ * dtype F64/F32 (storage of A, B, D), prec F64, F32, TF32 or BF16. */
+bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                        int32_t transA, const void* B, int64_t ldb, int32_t transB, void* D,
+                        int64_t ldd, int32_t dtype, int32_t prec, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices).  Used to report launches per timed step. */
+uint64_t bcur_launch_count(void);
+
+/* Library version, "major.minor.patch". */
+const char* bcur_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCUR_H_ */

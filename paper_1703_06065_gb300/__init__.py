@@ -1,0 +1,252 @@
+"""Block CUR (arXiv 1703.06065) hot path on GB300: Python binding.
+
+Thin wrappers with the C ABI's names.  Tensors must live on the current CUDA
+device; the library runs on torch's current stream.  Nothing here computes:
+the arithmetic of every stage is in libbcur.so.
+
+Typical use::
+
+    plan = Plan(m, n, k=50, p=10, q=2, col_off=..., row_off=..., g_col=16, g_row=16,
+                dtype="f32", sketch_prec="tf32", fit_prec="tf32")
+    cs, rs = plan.scores(A, omega)            # Def. 2 block leverage scores
+    ci, ri, cp, rp = plan.sample(cs, rs, u_col, u_row)
+    U = plan.fit(A, ci, ri)                   # U = C^+ A R^+
+    err, rel, norm_a = plan.error(A).tolist()  # ||A - CUR||_F without forming CUR
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_int64, c_size_t, c_void_p
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
+
+__all__ = ["Plan", "block_scores", "sample_blocks", "residual", "gemm", "decompose", "load",
+           "BcurError", "PREC"]
+
+load = _lib.load
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> c_void_p:
+    return c_void_p(0 if t is None else t.data_ptr())
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return BCUR_F64
+    if t.dtype == torch.float32:
+        return BCUR_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensor must be on a CUDA device")
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+
+
+class Plan:
+    """A validated Block CUR problem with its device workspace."""
+
+    def __init__(self, m: int, n: int, k: int, p: int, q: int, col_off: Sequence[int],
+                 row_off: Sequence[int], g_col: int, g_row: int, dtype: str = "f32",
+                 lda: Optional[int] = None, replacement: bool = False,
+                 sketch_prec: Optional[str] = None, fit_prec: Optional[str] = None,
+                 device=None):
+        torch = _torch()
+        L = _lib.load()
+        self._L = L
+        self.dtype = dtype
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        sp = sketch_prec or dtype
+        fp = fit_prec or dtype
+        self._col_off = np.ascontiguousarray(np.asarray(col_off, dtype=np.int64))
+        self._row_off = np.ascontiguousarray(np.asarray(row_off, dtype=np.int64))
+        d = _lib.Desc()
+        d.m, d.n, d.lda = m, n, lda or n
+        d.a_dtype = PREC[dtype]
+        d.k, d.p, d.q = k, p, q
+        d.G_col = len(self._col_off) - 1
+        d.col_off = self._col_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.G_row = len(self._row_off) - 1
+        d.row_off = self._row_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.g_col, d.g_row = g_col, g_row
+        d.replacement = int(bool(replacement))
+        d.sketch_prec, d.fit_prec = PREC[sp], PREC[fp]
+        self.desc = d
+        self.m, self.n, self.k, self.p, self.q = m, n, k, p, q
+        self.G_col, self.G_row, self.g_col, self.g_row = d.G_col, d.G_row, g_col, g_row
+        h = c_void_p()
+        ws = c_size_t()
+        _lib.check(L.bcur_plan(byref(d), _stream(), byref(h), byref(ws)), "bcur_plan")
+        self._h = h
+        self.workspace_bytes = ws.value
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self._ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=dev)
+        _lib.check(L.bcur_set_workspace(h, _ptr(self._ws), c_size_t(self._ws.numel())),
+                   "bcur_set_workspace")
+        self.c_max = self._max_sum(self._col_off, g_col, replacement)
+        self.r_max = self._max_sum(self._row_off, g_row, replacement)
+
+    @staticmethod
+    def _max_sum(off, g, replacement):
+        sz = np.sort(np.diff(off))[::-1]
+        return int(g * sz[0]) if replacement else int(sz[:g].sum())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self._L.bcur_destroy(h)
+            except Exception:  # pragma: no cover
+                pass
+            self._h = None
+
+    # -- stages ------------------------------------------------------------
+    def scores(self, A, omega, out=None):
+        torch = _torch()
+        _need_cuda(A, omega)
+        cs = torch.empty(self.G_col, dtype=torch.float64, device=A.device) if out is None else out[0]
+        rs = torch.empty(self.G_row, dtype=torch.float64, device=A.device) if out is None else out[1]
+        _lib.check(self._L.bcur_scores(self._h, _ptr(A), _ptr(omega), _ptr(cs), _ptr(rs)),
+                   "bcur_scores")
+        return cs, rs
+
+    def factors(self):
+        torch = _torch()
+        Vt = torch.empty(self.k, self.n, dtype=self.tdtype, device=self.device)
+        Ut = torch.empty(self.k, self.m, dtype=self.tdtype, device=self.device)
+        sig = torch.empty(self.k, dtype=torch.float64, device=self.device)
+        _lib.check(self._L.bcur_factors(self._h, _ptr(Vt), _ptr(Ut), _ptr(sig)), "bcur_factors")
+        return Vt, Ut, sig
+
+    def sample(self, cs, rs, u_col, u_row):
+        torch = _torch()
+        _need_cuda(cs, rs, u_col, u_row)
+        dev = cs.device
+        ci = torch.empty(self.g_col, dtype=torch.int32, device=dev)
+        ri = torch.empty(self.g_row, dtype=torch.int32, device=dev)
+        cp = torch.empty(self.g_col, dtype=torch.float64, device=dev)
+        rp = torch.empty(self.g_row, dtype=torch.float64, device=dev)
+        _lib.check(self._L.bcur_sample(self._h, _ptr(cs), _ptr(rs), _ptr(u_col), _ptr(u_row),
+                                       _ptr(ci), _ptr(ri), _ptr(cp), _ptr(rp)), "bcur_sample")
+        return ci, ri, cp, rp
+
+    def fit(self, A, ci, ri, want_c: bool = False, want_r: bool = False, U=None):
+        torch = _torch()
+        _need_cuda(A, ci, ri)
+        if U is None:
+            U = torch.empty(self.c_max, self.r_max, dtype=self.tdtype, device=A.device)
+        C = torch.empty(self.c_max, self.m, dtype=self.tdtype, device=A.device) if want_c else None
+        R = torch.empty(self.r_max, self.n, dtype=self.tdtype, device=A.device) if want_r else None
+        _lib.check(self._L.bcur_fit(self._h, _ptr(A), _ptr(ci), _ptr(ri), _ptr(U), _ptr(C),
+                                    _ptr(R)), "bcur_fit")
+        if want_c or want_r:
+            return U, C, R
+        return U
+
+    def error(self, A, out=None):
+        torch = _torch()
+        _need_cuda(A)
+        out = torch.empty(3, dtype=torch.float64, device=A.device) if out is None else out
+        _lib.check(self._L.bcur_error(self._h, _ptr(A), _ptr(out)), "bcur_error")
+        return out
+
+    def rank(self):
+        v = [c_int64() for _ in range(4)]
+        _lib.check(self._L.bcur_rank(self._h, *[byref(x) for x in v]), "bcur_rank")
+        return tuple(x.value for x in v)
+
+    def sync_status(self):
+        _lib.check(self._L.bcur_sync_status(self._h), "device status")
+
+
+# -- plan-free stage kernels -------------------------------------------------
+
+def block_scores(Ft, off, out=None):
+    """Def. 2 scores of the factor whose panel (k x h) is ``Ft``; ``off`` device int64."""
+    torch = _torch()
+    _need_cuda(Ft, off)
+    G = off.numel() - 1
+    out = torch.empty(G, dtype=torch.float64, device=Ft.device) if out is None else out
+    k, h = Ft.shape
+    _lib.check(_lib.load().bcur_block_scores(_ptr(Ft), _dtype_code(Ft), k, h, h, _ptr(off), G,
+                                             _ptr(out), _stream()), "bcur_block_scores")
+    return out
+
+
+def sample_blocks(scores, u, g: int, replacement: bool = False):
+    torch = _torch()
+    _need_cuda(scores, u)
+    idx = torch.empty(g, dtype=torch.int32, device=scores.device)
+    prob = torch.empty(g, dtype=torch.float64, device=scores.device)
+    _lib.check(_lib.load().bcur_sample_blocks(_ptr(scores), scores.numel(), _ptr(u), g,
+                                              int(bool(replacement)), _ptr(idx), _ptr(prob),
+                                              _stream()), "bcur_sample_blocks")
+    return idx, prob
+
+
+def residual(X, P, Q, prec: str = None):
+    """{||X - P Q||_F^2, ||X||_F^2} (device FP64) from the fused residual kernel."""
+    torch = _torch()
+    _need_cuda(X, P, Q)
+    L = _lib.load()
+    m, n = X.shape
+    r = P.shape[1]
+    code = _dtype_code(X)
+    prec = PREC[prec] if prec else code
+    wsb = L.bcur_residual_workspace(m, n, code)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=X.device)
+    out = torch.empty(2, dtype=torch.float64, device=X.device)
+    _lib.check(L.bcur_residual(_ptr(X), n, _ptr(P), r, _ptr(Q), n, m, n, r, code, prec, _ptr(out),
+                               _ptr(ws), c_size_t(ws.numel()), _stream()), "bcur_residual")
+    return out
+
+
+def gemm(A, B, transA: bool = False, transB: bool = False, prec: str = None, out=None):
+    """D = op(A) op(B) on the library's kernels (row-major tensors)."""
+    torch = _torch()
+    _need_cuda(A, B)
+    M = A.shape[1] if transA else A.shape[0]
+    K = A.shape[0] if transA else A.shape[1]
+    N = B.shape[0] if transB else B.shape[1]
+    code = _dtype_code(A)
+    prec = PREC[prec] if prec else code
+    D = torch.empty(M, N, dtype=A.dtype, device=A.device) if out is None else out
+    _lib.check(_lib.load().bcur_gemm(M, N, K, _ptr(A), A.shape[1], int(transA), _ptr(B),
+                                     B.shape[1], int(transB), _ptr(D), D.shape[1], code, prec,
+                                     _stream()), "bcur_gemm")
+    return D
+
+
+def decompose(plan: Plan, A, omega, u_col, u_row, col_idx=None, row_idx=None):
+    """All stages on one matrix; returns a dict of device tensors."""
+    cs, rs = plan.scores(A, omega)
+    ci, ri, cp, rp = plan.sample(cs, rs, u_col, u_row)
+    if col_idx is not None:
+        ci = col_idx
+    if row_idx is not None:
+        ri = row_idx
+    U = plan.fit(A, ci, ri)
+    e = plan.error(A)
+    return dict(col_scores=cs, row_scores=rs, col_idx=ci, row_idx=ri, col_prob=cp, row_prob=rp,
+                U=U, err=e)

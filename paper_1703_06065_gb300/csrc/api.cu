@@ -1,0 +1,669 @@
+// C ABI of the Block CUR library: plan, workspace layout and the stage
+// orchestration.  Every arithmetic step runs in this library's CUDA kernels;
+// the host only validates, lays out memory and enqueues launches.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "kernels.h"
+
+namespace bcur {
+
+static thread_local char g_last_err[256] = {0};
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file,
+           line);
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+template <typename T> struct EpsOf;
+template <> struct EpsOf<float> { static constexpr double v = 1.1920928955078125e-07; };
+template <> struct EpsOf<double> { static constexpr double v = 2.220446049250313e-16; };
+
+// Bump allocator over the caller's workspace (256-byte aligned slices).
+struct Layout {
+  size_t cur = 0;
+  size_t take(size_t bytes) {
+    const size_t at = cur;
+    cur += (bytes + 255) / 256 * 256;
+    return at;
+  }
+};
+
+}  // namespace bcur
+
+using namespace bcur;
+
+struct bcur_plan_s {
+  bcur_desc_t d;
+  std::vector<int64_t> col_off, row_off;
+  cudaStream_t stream = nullptr;
+  int64_t m = 0, n = 0, lda = 0;
+  int k = 0, l = 0, q = 0;
+  int64_t ldm = 0, ldn = 0;      // padded panel leading dims
+  int64_t c_max = 0, r_max = 0;  // largest possible c, r for the chosen g
+  int64_t c_pad = 0, r_pad = 0;  // padded to the blocked-Cholesky panel size
+  int nb = 64;
+  int ksplit_m = 1, ksplit_n = 1;
+  size_t esz = 8;
+  int sms = 148;
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0, need = 0;
+  struct {
+    size_t Pm0, Pm1, Pn0, Pn1, Pn2, gram_part, G64, L64a, L64b, Lprod64, Linv64, LinvT, Ut, W,
+        sigma, jwork, Vp, Up, col_off, row_off, status, kept, colmap, rowmap, counts, Cp0, Cp1,
+        Rp0, Rp1, GC, L1C, L1Ci, L2C, L2Ci, GR, L1R, L1Ri, L2R, L2Ri, maxdiag, Wb, Mb, U1, U2,
+        partials, result;
+  } o;
+  int64_t n_partials = 0;
+  bool have_scores = false, have_fit = false;
+  template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
+};
+
+namespace {
+
+bool is_tc_prec(int p) { return p == BCUR_TF32 || p == BCUR_BF16; }
+
+// The Cholesky updates must keep the working precision's accuracy: a Gram
+// matrix with condition number kappa^2 loses kappa^2 * u in them.
+template <typename T> constexpr int exact_prec() {
+  return std::is_same<T, double>::value ? BCUR_F64 : BCUR_F32;
+}
+
+int64_t max_sum_of_g(const std::vector<int64_t>& off, int g, bool replacement) {
+  std::vector<int64_t> sz(off.size() - 1);
+  for (size_t i = 0; i + 1 < off.size(); ++i) sz[i] = off[i + 1] - off[i];
+  std::sort(sz.begin(), sz.end(), std::greater<int64_t>());
+  int64_t s = 0;
+  if (replacement) return (int64_t)g * (sz.empty() ? 0 : sz[0]);
+  for (int i = 0; i < g && i < (int)sz.size(); ++i) s += sz[i];
+  return s;
+}
+
+bool valid_offsets(const int64_t* off, int G, int64_t total) {
+  if (!off || G < 1) return false;
+  if (off[0] != 0 || off[G] != total) return false;
+  for (int i = 0; i < G; ++i)
+    if (off[i + 1] <= off[i]) return false;
+  return true;
+}
+
+// GEMM dispatch: tensor-core path for TF32 / BF16 precisions on FP32 data,
+// CUDA-core FMA path otherwise.
+template <typename T>
+bcur_status_t gemm(const GemmDesc& d, int prec, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (is_tc_prec(prec)) {
+      bcur_status_t st = gemm_tc(d, prec, s);
+      if (st != BCUR_ENOTSUP) return st;
+    }
+  }
+  return gemm_simt<T>(d, s);
+}
+
+template <typename T>
+bcur_status_t gemm_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* np) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (is_tc_prec(prec)) {
+      bcur_status_t st = gemm_tc_resid(d, prec, s, np);
+      if (st != BCUR_ENOTSUP) return st;
+    }
+  }
+  return gemm_simt_resid<T>(d, s, np);
+}
+
+GemmDesc mk(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, int tA, const void* B,
+            int64_t ldb, int tB, void* D, int64_t ldd) {
+  GemmDesc g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.transA = tA;
+  g.B = B; g.ldb = ldb; g.transB = tB;
+  g.D = D; g.ldd = ldd;
+  return g;
+}
+
+// --- Skinny Cholesky-QR2 on a panel X (w x h, ld), w <= 128 ----------------
+// X <- Q (rows orthonormal), L64 out = L with X_in = L Q (FP64, w x w).
+template <typename T>
+bcur_status_t orth_panel(bcur_plan_t P, T* X, T* tmp, int w, int64_t h, int64_t ld, int ksplit,
+                         int prec, double* Lout) {
+  cudaStream_t s = P->stream;
+  const double tol = 64.0 * EpsOf<T>::v;
+  T* src = X;
+  T* dst = tmp;
+  double* Ls[2] = {P->at<double>(P->o.L64a), P->at<double>(P->o.L64b)};
+  for (int pass = 0; pass < 2; ++pass) {
+    GemmDesc g = mk(w, w, h, src, ld, 0, src, ld, 1, P->at<T>(P->o.gram_part), w);
+    g.ksplit = ksplit;
+    g.sD = (int64_t)w * w;
+    BCUR_TRY(gemm<T>(g, prec, s));
+    BCUR_TRY(reduce_splits_f64<T>(P->at<T>(P->o.gram_part), ksplit, (int64_t)w * w,
+                                  (int64_t)w * w, P->at<double>(P->o.G64), s));
+    BCUR_TRY(chol_small<T>(P->at<double>(P->o.G64), w, tol, Ls[pass], P->at<double>(P->o.Linv64),
+                           P->at<T>(P->o.LinvT), P->at<int>(P->o.kept), s));
+    GemmDesc a = mk(w, h, w, P->at<T>(P->o.LinvT), w, 0, src, ld, 0, dst, ld);
+    a.triA = 1;
+    BCUR_TRY(gemm<T>(a, prec, s));
+    std::swap(src, dst);
+  }
+  // after two passes the result is back in X
+  if (Lout) BCUR_TRY(trmm_small_f64(Ls[0], Ls[1], w, Lout, s));
+  return BCUR_OK;
+}
+
+// --- Wide Cholesky-QR2 on a panel X (w x h, ld), w a multiple of nb -------
+// X = L1 L2 Q;  writes Q into `Q`, and L1, L1^{-1}, L2, L2^{-1} (w x w).
+template <typename T>
+bcur_status_t chol_inv_blocked(bcur_plan_t P, T* G, T* L, T* Li, int64_t w, int prec, int* kept) {
+  cudaStream_t s = P->stream;
+  const int nb = P->nb;
+  const double tol = 64.0 * EpsOf<T>::v;
+  T* md = P->at<T>(P->o.maxdiag);
+  BCUR_TRY(fill_zero(L, (size_t)w * w * sizeof(T), s));
+  BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(T), s));
+  BCUR_TRY(fill_zero(kept, sizeof(int), s));
+  BCUR_TRY(max_diag<T>(G, w, w, md, s));
+  for (int64_t j0 = 0; j0 < w; j0 += nb) {
+    BCUR_TRY(potrf_diag<T>(G, w, L, w, Li, w, j0, nb, md, tol, kept, s));
+    const int64_t j1 = j0 + nb;
+    if (j1 >= w) break;
+    GemmDesc pn = mk(w - j1, nb, nb, G + j1 * w + j0, w, 0, Li + j0 * w + j0, w, 1,
+                     L + j1 * w + j0, w);
+    pn.triB = 2;
+    BCUR_TRY(gemm<T>(pn, exact_prec<T>(), s));
+    GemmDesc tr = mk(w - j1, w - j1, nb, L + j1 * w + j0, w, 0, L + j1 * w + j0, w, 1,
+                     G + j1 * w + j1, w);
+    tr.alpha = -1.0;
+    tr.beta = 1.0;
+    tr.out_lower = 1;
+    BCUR_TRY(gemm<T>(tr, exact_prec<T>(), s));
+  }
+  // Inverse of the whole lower factor by doubling: with X11, X22 the inverses
+  // of the diagonal halves, X21 = -X22 L21 X11.  G serves as the temporary.
+  for (int64_t h = nb; h < w; h *= 2) {
+    const int64_t npairs_full = w / (2 * h);
+    if (npairs_full > 0) {
+      GemmDesc t1 = mk(h, h, h, L + h * w, w, 0, Li, w, 0, G, h);
+      t1.triB = 1;
+      t1.batch = (int)npairs_full;
+      t1.sA = 2 * h * (w + 1);
+      t1.sB = 2 * h * (w + 1);
+      t1.sD = h * h;
+      BCUR_TRY(gemm<T>(t1, prec, s));
+      GemmDesc t2 = mk(h, h, h, Li + h * w + h, w, 0, G, h, 0, Li + h * w, w);
+      t2.triA = 1;
+      t2.alpha = -1.0;
+      t2.batch = (int)npairs_full;
+      t2.sA = 2 * h * (w + 1);
+      t2.sB = h * h;
+      t2.sD = 2 * h * (w + 1);
+      BCUR_TRY(gemm<T>(t2, prec, s));
+    }
+    const int64_t b1 = npairs_full * 2 * h, b2 = b1 + h;
+    if (b2 < w) {  // ragged last pair
+      const int64_t h2 = w - b2;
+      GemmDesc t1 = mk(h2, h, h, L + b2 * w + b1, w, 0, Li + b1 * w + b1, w, 0, G, h);
+      t1.triB = 1;
+      BCUR_TRY(gemm<T>(t1, prec, s));
+      GemmDesc t2 = mk(h2, h, h2, Li + b2 * w + b2, w, 0, G, h, 0, Li + b2 * w + b1, w);
+      t2.triA = 1;
+      t2.alpha = -1.0;
+      BCUR_TRY(gemm<T>(t2, prec, s));
+    }
+  }
+  return BCUR_OK;
+}
+
+template <typename T>
+bcur_status_t wide_cqr2(bcur_plan_t P, T* X, T* tmp, int64_t w, int64_t h, int64_t ld, T* G,
+                        T* L1, T* L1i, T* L2, T* L2i, int prec, int* kept) {
+  cudaStream_t s = P->stream;
+  T* src = X;
+  T* dst = tmp;
+  T* Ls[2] = {L1, L2};
+  T* Lis[2] = {L1i, L2i};
+  for (int pass = 0; pass < 2; ++pass) {
+    GemmDesc g = mk(w, w, h, src, ld, 0, src, ld, 1, G, w);
+    g.out_lower = 1;
+    BCUR_TRY(gemm<T>(g, prec, s));
+    BCUR_TRY(chol_inv_blocked<T>(P, G, Ls[pass], Lis[pass], w, prec, kept + pass));
+    GemmDesc a = mk(w, h, w, Lis[pass], w, 0, src, ld, 0, dst, ld);
+    a.triA = 1;
+    BCUR_TRY(gemm<T>(a, prec, s));
+    std::swap(src, dst);
+  }
+  return BCUR_OK;  // Q is back in X
+}
+
+// --- Stage 1-2 -------------------------------------------------------------
+template <typename T>
+bcur_status_t run_scores(bcur_plan_t P, const T* A, const T* omega, double* cs, double* rs) {
+  cudaStream_t s = P->stream;
+  const int l = P->l, k = P->k;
+  const int sp = P->d.sketch_prec;
+  const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
+  T* Pm0 = P->at<T>(P->o.Pm0);
+  T* Pm1 = P->at<T>(P->o.Pm1);
+  T* Pn0 = P->at<T>(P->o.Pn0);
+  T* Pn1 = P->at<T>(P->o.Pn1);
+  // Y^T = Omega^T A^T  (Y = A Omega)
+  BCUR_TRY(gemm<T>(mk(l, m, n, omega, n, 0, A, lda, 1, Pm0, ldm), sp, s));
+  BCUR_TRY(orth_panel<T>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, sp, nullptr));
+  for (int it = 0; it < P->q; ++it) {
+    // Z^T = Q^T A  (Z = A^T Q)
+    BCUR_TRY(gemm<T>(mk(l, n, m, Pm0, ldm, 0, A, lda, 0, Pn0, ldn), sp, s));
+    BCUR_TRY(orth_panel<T>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, sp, nullptr));
+    // Y^T = Z^T A^T
+    BCUR_TRY(gemm<T>(mk(l, m, n, Pn0, ldn, 0, A, lda, 1, Pm0, ldm), sp, s));
+    BCUR_TRY(orth_panel<T>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, sp, nullptr));
+  }
+  // B = Q^T A (l x n) = L_B Q_B, then SVD of L_B.
+  BCUR_TRY(gemm<T>(mk(l, n, m, Pm0, ldm, 0, A, lda, 0, Pn0, ldn), sp, s));
+  double* LB = P->at<double>(P->o.Lprod64);
+  BCUR_TRY(orth_panel<T>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, sp, LB));
+  T* Ut = P->at<T>(P->o.Ut);
+  T* W = P->at<T>(P->o.W);
+  BCUR_TRY(jacobi_svd_small<T>(LB, l, Ut, W, P->at<double>(P->o.sigma), P->at<T>(P->o.jwork),
+                               P->at<int>(P->o.status), s));
+  // V_k^T = W_k^T Q_B^T ,  U_k^T = Ut_k^T Q^T
+  T* Vp = P->at<T>(P->o.Vp);
+  T* Up = P->at<T>(P->o.Up);
+  BCUR_TRY(gemm_simt<T>(mk(k, n, l, W, l, 1, Pn0, ldn, 0, Vp, ldn), s));
+  BCUR_TRY(gemm_simt<T>(mk(k, m, l, Ut, l, 1, Pm0, ldm, 0, Up, ldm), s));
+  BCUR_TRY(block_scores<T>(Vp, k, n, ldn, P->at<int64_t>(P->o.col_off), P->d.G_col, cs,
+                           P->at<int>(P->o.status), s));
+  BCUR_TRY(block_scores<T>(Up, k, m, ldm, P->at<int64_t>(P->o.row_off), P->d.G_row, rs,
+                           P->at<int>(P->o.status), s));
+  return BCUR_OK;
+}
+
+// --- Stages 4-5 ------------------------------------------------------------
+template <typename T>
+bcur_status_t run_fit(bcur_plan_t P, const T* A, const int32_t* ci, const int32_t* ri, T* Uout,
+                      T* Cout, T* Rout) {
+  cudaStream_t s = P->stream;
+  const int fp = P->d.fit_prec;
+  const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
+  const int64_t cw = P->c_pad, rw = P->r_pad;
+  int64_t* counts = P->at<int64_t>(P->o.counts);
+  BCUR_TRY(expand_blocks(ci, P->d.g_col, P->at<int64_t>(P->o.col_off), P->d.G_col, cw,
+                         P->at<int64_t>(P->o.colmap), counts, s));
+  BCUR_TRY(expand_blocks(ri, P->d.g_row, P->at<int64_t>(P->o.row_off), P->d.G_row, rw,
+                         P->at<int64_t>(P->o.rowmap), counts + 1, s));
+  T* Cp = P->at<T>(P->o.Cp0);
+  T* Rp = P->at<T>(P->o.Rp0);
+  BCUR_TRY(gather_cols_t<T>(A, lda, m, P->at<int64_t>(P->o.colmap), cw, Cp, ldm, s));
+  BCUR_TRY(gather_rows<T>(A, lda, n, P->at<int64_t>(P->o.rowmap), rw, Rp, ldn, s));
+  if (Cout) BCUR_TRY(copy2d<T>(Cp, ldm, Cout, m, P->c_max, m, s));
+  if (Rout) BCUR_TRY(copy2d<T>(Rp, ldn, Rout, n, P->r_max, n, s));
+  // QR of C (through its panel C^T) and of R^T (through R itself).
+  BCUR_TRY(wide_cqr2<T>(P, Cp, P->at<T>(P->o.Cp1), cw, m, ldm, P->at<T>(P->o.GC),
+                        P->at<T>(P->o.L1C), P->at<T>(P->o.L1Ci), P->at<T>(P->o.L2C),
+                        P->at<T>(P->o.L2Ci), fp, P->at<int>(P->o.kept) + 4));
+  BCUR_TRY(wide_cqr2<T>(P, Rp, P->at<T>(P->o.Rp1), rw, n, ldn, P->at<T>(P->o.GR),
+                        P->at<T>(P->o.L1R), P->at<T>(P->o.L1Ri), P->at<T>(P->o.L2R),
+                        P->at<T>(P->o.L2Ri), fp, P->at<int>(P->o.kept) + 6));
+  // W = A Q_R (m x r),  M = Q_C^T W (c x r)
+  T* Wb = P->at<T>(P->o.Wb);
+  T* Mb = P->at<T>(P->o.Mb);
+  BCUR_TRY(gemm<T>(mk(m, rw, n, A, lda, 0, Rp, ldn, 1, Wb, rw), fp, s));
+  BCUR_TRY(gemm<T>(mk(cw, rw, m, Cp, ldm, 0, Wb, rw, 0, Mb, rw), fp, s));
+  // U = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1}
+  T* U1 = P->at<T>(P->o.U1);
+  T* U2 = P->at<T>(P->o.U2);
+  {
+    GemmDesc g1 = mk(cw, rw, rw, Mb, rw, 0, P->at<T>(P->o.L2Ri), rw, 0, U1, rw);
+    g1.triB = 1;
+    BCUR_TRY(gemm<T>(g1, fp, s));
+    GemmDesc g2 = mk(cw, rw, rw, U1, rw, 0, P->at<T>(P->o.L1Ri), rw, 0, U2, rw);
+    g2.triB = 1;
+    BCUR_TRY(gemm<T>(g2, fp, s));
+    GemmDesc g3 = mk(cw, rw, cw, P->at<T>(P->o.L2Ci), cw, 1, U2, rw, 0, U1, rw);
+    g3.triA = 2;
+    BCUR_TRY(gemm<T>(g3, fp, s));
+    GemmDesc g4 = mk(cw, rw, cw, P->at<T>(P->o.L1Ci), cw, 1, U1, rw, 0, U2, rw);
+    g4.triA = 2;
+    BCUR_TRY(gemm<T>(g4, fp, s));
+  }
+  if (Uout) BCUR_TRY(copy2d<T>(U2, rw, Uout, P->r_max, P->c_max, P->r_max, s));
+  return BCUR_OK;
+}
+
+// --- Stage 6 ---------------------------------------------------------------
+template <typename T>
+bcur_status_t run_error(bcur_plan_t P, const T* A, double* out) {
+  cudaStream_t s = P->stream;
+  const int fp = P->d.fit_prec;
+  const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
+  const int64_t cw = P->c_pad, rw = P->r_pad;
+  T* Wb = P->at<T>(P->o.Wb);
+  // P = Q_C M  (m x r)
+  BCUR_TRY(gemm<T>(mk(m, rw, cw, P->at<T>(P->o.Cp0), ldm, 1, P->at<T>(P->o.Mb), rw, 0, Wb, rw),
+                   fp, s));
+  GemmDesc r = mk(m, n, rw, Wb, rw, 0, P->at<T>(P->o.Rp0), ldn, 0, nullptr, 0);
+  r.X = A;
+  r.ldx = P->lda;
+  r.partials = P->at<double>(P->o.partials);
+  int64_t np = 0;
+  BCUR_TRY(gemm_resid<T>(r, fp, s, &np));
+  BCUR_TRY(finish_residual(P->at<double>(P->o.partials), np, out, 0, s));
+  return BCUR_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* bcur_version(void) { return "0.1.0"; }
+
+uint64_t bcur_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+const char* bcur_status_string(bcur_status_t st) {
+  switch (st) {
+    case BCUR_OK: return "ok";
+    case BCUR_EINVAL: return "invalid argument";
+    case BCUR_ENOMEM: return "workspace missing or too small";
+    case BCUR_ECUDA: return g_last_err[0] ? g_last_err : "CUDA error";
+    case BCUR_ERANK: return "rank breakdown";
+    case BCUR_ENONFINITE: return "non-finite value in the data";
+    case BCUR_ETIMEOUT: return "device wait timed out";
+    case BCUR_ENOTSUP: return "not supported";
+    case BCUR_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
+                        size_t* workspace_bytes) {
+  if (!d || !out) return BCUR_EINVAL;
+  *out = nullptr;
+  if (d->m < 1 || d->n < 1 || d->lda < d->n) return BCUR_EINVAL;
+  if (d->a_dtype != BCUR_F64 && d->a_dtype != BCUR_F32) return BCUR_EINVAL;
+  if (d->k < 1 || d->p < 0 || d->q < 0 || d->q > 16) return BCUR_EINVAL;
+  const int64_t l = (int64_t)d->k + d->p;
+  if (l > 128 || l > d->m || l > d->n) return BCUR_EINVAL;
+  if (d->G_col < 1 || d->G_row < 1 || d->G_col > 32768 || d->G_row > 32768) return BCUR_EINVAL;
+  if (!valid_offsets(d->col_off, d->G_col, d->n) || !valid_offsets(d->row_off, d->G_row, d->m))
+    return BCUR_EINVAL;
+  if (d->g_col < 1 || d->g_row < 1) return BCUR_EINVAL;
+  if (!d->replacement && (d->g_col > d->G_col || d->g_row > d->G_row)) return BCUR_EINVAL;
+  for (int p : {d->sketch_prec, d->fit_prec}) {
+    if (p < BCUR_F64 || p > BCUR_BF16) return BCUR_EINVAL;
+    if (d->a_dtype == BCUR_F64 && p != BCUR_F64) return BCUR_EINVAL;
+    if (d->a_dtype == BCUR_F32 && p == BCUR_F64) return BCUR_EINVAL;
+  }
+  bcur_plan_t P = new (std::nothrow) bcur_plan_s();
+  if (!P) return BCUR_ENOMEM;
+  P->d = *d;
+  P->col_off.assign(d->col_off, d->col_off + d->G_col + 1);
+  P->row_off.assign(d->row_off, d->row_off + d->G_row + 1);
+  P->d.col_off = P->col_off.data();
+  P->d.row_off = P->row_off.data();
+  P->stream = (cudaStream_t)stream;
+  P->m = d->m; P->n = d->n; P->lda = d->lda;
+  P->k = d->k; P->l = (int)l; P->q = d->q;
+  P->esz = d->a_dtype == BCUR_F64 ? 8 : 4;
+  P->nb = d->a_dtype == BCUR_F64 ? 64 : 128;
+  P->ldm = round_up(P->m, 32);
+  P->ldn = round_up(P->n, 32);
+  P->c_max = max_sum_of_g(P->col_off, d->g_col, d->replacement != 0);
+  P->r_max = max_sum_of_g(P->row_off, d->g_row, d->replacement != 0);
+  P->c_pad = round_up(P->c_max, P->nb);
+  P->r_pad = round_up(P->r_max, P->nb);
+  if (P->c_pad > 65535 || P->r_pad > 65535) { delete P; return BCUR_EINVAL; }
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+    P->sms = sms;
+  else
+    cudaGetLastError();
+  P->ksplit_m = (int)std::max<int64_t>(1, std::min<int64_t>(2 * P->sms, P->m / 64));
+  P->ksplit_n = (int)std::max<int64_t>(1, std::min<int64_t>(2 * P->sms, P->n / 64));
+
+  Layout L;
+  const size_t e = P->esz;
+  const int64_t ll = l * l;
+  auto& o = P->o;
+  o.Pm0 = L.take(l * P->ldm * e);
+  o.Pm1 = L.take(l * P->ldm * e);
+  o.Pn0 = L.take(l * P->ldn * e);
+  o.Pn1 = L.take(l * P->ldn * e);
+  o.Pn2 = L.take(l * P->ldn * e);
+  o.gram_part = L.take((size_t)std::max(P->ksplit_m, P->ksplit_n) * ll * e);
+  o.G64 = L.take(ll * 8);
+  o.L64a = L.take(ll * 8);
+  o.L64b = L.take(ll * 8);
+  o.Lprod64 = L.take(ll * 8);
+  o.Linv64 = L.take(ll * 8);
+  o.LinvT = L.take(ll * e);
+  o.Ut = L.take(ll * e);
+  o.W = L.take(ll * e);
+  o.sigma = L.take(l * 8);
+  o.jwork = L.take((l + 1) * (l + 1) * e);
+  o.Vp = L.take((int64_t)P->k * P->ldn * e);
+  o.Up = L.take((int64_t)P->k * P->ldm * e);
+  o.col_off = L.take((P->d.G_col + 1) * 8);
+  o.row_off = L.take((P->d.G_row + 1) * 8);
+  o.status = L.take(16);
+  o.kept = L.take(64);
+  const int64_t cw = P->c_pad, rw = P->r_pad;
+  o.colmap = L.take(cw * 8);
+  o.rowmap = L.take(rw * 8);
+  o.counts = L.take(16);
+  o.Cp0 = L.take(cw * P->ldm * e);
+  o.Cp1 = L.take(cw * P->ldm * e);
+  o.Rp0 = L.take(rw * P->ldn * e);
+  o.Rp1 = L.take(rw * P->ldn * e);
+  o.GC = L.take(cw * cw * e);
+  o.L1C = L.take(cw * cw * e);
+  o.L1Ci = L.take(cw * cw * e);
+  o.L2C = L.take(cw * cw * e);
+  o.L2Ci = L.take(cw * cw * e);
+  o.GR = L.take(rw * rw * e);
+  o.L1R = L.take(rw * rw * e);
+  o.L1Ri = L.take(rw * rw * e);
+  o.L2R = L.take(rw * rw * e);
+  o.L2Ri = L.take(rw * rw * e);
+  o.maxdiag = L.take(16);
+  o.Wb = L.take(P->m * rw * e);
+  o.Mb = L.take(cw * rw * e);
+  o.U1 = L.take(cw * rw * e);
+  o.U2 = L.take(cw * rw * e);
+  P->n_partials = std::max(gemm_simt_resid_ctas<double>(P->m, P->n),
+                           std::max(gemm_simt_resid_ctas<float>(P->m, P->n),
+                                    gemm_tc_resid_ctas(P->m, P->n)));
+  o.partials = L.take(2 * P->n_partials * 8);
+  o.result = L.take(64);
+  P->need = L.cur;
+  if (workspace_bytes) *workspace_bytes = P->need;
+  *out = P;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
+  if (!P || !ws || ((uintptr_t)ws & 255)) return BCUR_EINVAL;
+  if (bytes < P->need) return BCUR_ENOMEM;
+  P->ws = (char*)ws;
+  P->ws_bytes = bytes;
+  cudaStream_t s = P->stream;
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->at<int64_t>(P->o.col_off), P->col_off.data(),
+                                P->col_off.size() * 8, cudaMemcpyHostToDevice, s));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->at<int64_t>(P->o.row_off), P->row_off.data(),
+                                P->row_off.size() * 8, cudaMemcpyHostToDevice, s));
+  BCUR_CUDA_TRY(cudaMemsetAsync(P->at<int>(P->o.status), 0, 16, s));
+  // Panels are read with padded leading dimensions: clear the padding once.
+  BCUR_CUDA_TRY(cudaMemsetAsync(P->ws, 0, P->need, s));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->at<int64_t>(P->o.col_off), P->col_off.data(),
+                                P->col_off.size() * 8, cudaMemcpyHostToDevice, s));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->at<int64_t>(P->o.row_off), P->row_off.data(),
+                                P->row_off.size() * 8, cudaMemcpyHostToDevice, s));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(s));
+  P->have_scores = P->have_fit = false;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, double* cs,
+                          double* rs) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws) return BCUR_ESTATE;
+  if (!A || !omega || !cs || !rs) return BCUR_EINVAL;
+  bcur_status_t st = P->d.a_dtype == BCUR_F64
+                         ? run_scores<double>(P, (const double*)A, (const double*)omega, cs, rs)
+                         : run_scores<float>(P, (const float*)A, (const float*)omega, cs, rs);
+  if (st == BCUR_OK) P->have_scores = true;
+  return st;
+}
+
+bcur_status_t bcur_factors(bcur_plan_t P, void* Vt, void* Ut, double* sigma) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws || !P->have_scores) return BCUR_ESTATE;
+  cudaStream_t s = P->stream;
+  if (P->d.a_dtype == BCUR_F64) {
+    if (Vt) BCUR_TRY(copy2d<double>(P->at<double>(P->o.Vp), P->ldn, (double*)Vt, P->n, P->k, P->n, s));
+    if (Ut) BCUR_TRY(copy2d<double>(P->at<double>(P->o.Up), P->ldm, (double*)Ut, P->m, P->k, P->m, s));
+  } else {
+    if (Vt) BCUR_TRY(copy2d<float>(P->at<float>(P->o.Vp), P->ldn, (float*)Vt, P->n, P->k, P->n, s));
+    if (Ut) BCUR_TRY(copy2d<float>(P->at<float>(P->o.Up), P->ldm, (float*)Ut, P->m, P->k, P->m, s));
+  }
+  if (sigma)
+    BCUR_CUDA_TRY(cudaMemcpyAsync(sigma, P->at<double>(P->o.sigma), P->k * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, s));
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_sample(bcur_plan_t P, const double* cs, const double* rs, const double* uc,
+                          const double* ur, int32_t* ci, int32_t* ri, double* cp, double* rp) {
+  if (!P) return BCUR_EINVAL;
+  if (!cs || !rs || !uc || !ur || !ci || !ri) return BCUR_EINVAL;
+  BCUR_TRY(sample_blocks(cs, P->d.G_col, uc, P->d.g_col, P->d.replacement, ci, cp, P->stream));
+  BCUR_TRY(sample_blocks(rs, P->d.G_row, ur, P->d.g_row, P->d.replacement, ri, rp, P->stream));
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_fit(bcur_plan_t P, const void* A, const int32_t* ci, const int32_t* ri, void* U,
+                       void* C, void* R) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws) return BCUR_ESTATE;
+  if (!A || !ci || !ri) return BCUR_EINVAL;
+  bcur_status_t st =
+      P->d.a_dtype == BCUR_F64
+          ? run_fit<double>(P, (const double*)A, ci, ri, (double*)U, (double*)C, (double*)R)
+          : run_fit<float>(P, (const float*)A, ci, ri, (float*)U, (float*)C, (float*)R);
+  P->have_fit = (st == BCUR_OK);
+  return st;
+}
+
+bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws || !P->have_fit) return BCUR_ESTATE;
+  if (!A || !out) return BCUR_EINVAL;
+  return P->d.a_dtype == BCUR_F64 ? run_error<double>(P, (const double*)A, out)
+                                  : run_error<float>(P, (const float*)A, out);
+}
+
+bcur_status_t bcur_rank(bcur_plan_t P, int64_t* c, int64_t* r, int64_t* rank_c, int64_t* rank_r) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws || !P->have_fit) return BCUR_ESTATE;
+  int64_t counts[2] = {0, 0};
+  int kept[8] = {0};
+  BCUR_CUDA_TRY(cudaMemcpyAsync(counts, P->at<int64_t>(P->o.counts), sizeof(counts),
+                                cudaMemcpyDeviceToHost, P->stream));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(kept, P->at<int>(P->o.kept), sizeof(kept),
+                                cudaMemcpyDeviceToHost, P->stream));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (c) *c = counts[0];
+  if (r) *r = counts[1];
+  if (rank_c) *rank_c = kept[4];
+  if (rank_r) *rank_r = kept[6];
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_sync_status(bcur_plan_t P) {
+  if (!P) return BCUR_EINVAL;
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (!P->ws) return BCUR_OK;
+  int st = 0;
+  BCUR_CUDA_TRY(cudaMemcpy(&st, P->at<int>(P->o.status), sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) BCUR_CUDA_TRY(cudaMemset(P->at<int>(P->o.status), 0, sizeof(int)));
+  return (bcur_status_t)st;
+}
+
+void bcur_destroy(bcur_plan_t P) { delete P; }
+
+bcur_status_t bcur_block_scores(const void* Ft, int32_t dtype, int32_t k, int64_t h, int64_t ldf,
+                                const int64_t* off, int32_t G, double* scores, void* stream) {
+  if (!Ft || !off || !scores || k < 1 || h < 1 || ldf < h || G < 1) return BCUR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == BCUR_F64)
+    return block_scores<double>((const double*)Ft, k, h, ldf, off, G, scores, nullptr, s);
+  if (dtype == BCUR_F32)
+    return block_scores<float>((const float*)Ft, k, h, ldf, off, G, scores, nullptr, s);
+  return BCUR_EINVAL;
+}
+
+bcur_status_t bcur_sample_blocks(const double* scores, int32_t G, const double* u, int32_t g,
+                                 int32_t replacement, int32_t* idx, double* prob, void* stream) {
+  if (!scores || !u || !idx) return BCUR_EINVAL;
+  return sample_blocks(scores, G, u, g, replacement, idx, prob, (cudaStream_t)stream);
+}
+
+size_t bcur_residual_workspace(int64_t m, int64_t n, int32_t dtype) {
+  (void)dtype;
+  const int64_t np = std::max(gemm_simt_resid_ctas<double>(m, n),
+                              std::max(gemm_simt_resid_ctas<float>(m, n), gemm_tc_resid_ctas(m, n)));
+  return (size_t)(2 * np * 8);
+}
+
+bcur_status_t bcur_residual(const void* X, int64_t ldx, const void* Pm, int64_t ldp, const void* Q,
+                            int64_t ldq, int64_t m, int64_t n, int64_t r, int32_t dtype,
+                            int32_t prec, double* out, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  if (!X || !out || !workspace || m < 1 || n < 1 || r < 0) return BCUR_EINVAL;
+  if (r > 0 && (!Pm || !Q)) return BCUR_EINVAL;
+  if (ldx < n || ldp < r || ldq < n) return BCUR_EINVAL;
+  if (ws_bytes < bcur_residual_workspace(m, n, dtype)) return BCUR_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  GemmDesc g = mk(m, n, r, Pm, ldp, 0, Q, ldq, 0, nullptr, 0);
+  g.X = X;
+  g.ldx = ldx;
+  g.partials = (double*)workspace;
+  int64_t np = 0;
+  if (dtype == BCUR_F64) {
+    if (prec != BCUR_F64) return BCUR_EINVAL;
+    BCUR_TRY(gemm_resid<double>(g, prec, s, &np));
+  } else if (dtype == BCUR_F32) {
+    if (prec == BCUR_F64) return BCUR_EINVAL;
+    BCUR_TRY(gemm_resid<float>(g, prec, s, &np));
+  } else {
+    return BCUR_EINVAL;
+  }
+  return finish_residual((const double*)workspace, np, out, 1, s);
+}
+
+bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                        int32_t transA, const void* B, int64_t ldb, int32_t transB, void* D,
+                        int64_t ldd, int32_t dtype, int32_t prec, void* stream) {
+  if (!A || !B || !D || M < 0 || N < 0 || K < 0) return BCUR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  GemmDesc g = mk(M, N, K, A, lda, transA != 0, B, ldb, transB != 0, D, ldd);
+  if (dtype == BCUR_F64) {
+    if (prec != BCUR_F64) return BCUR_EINVAL;
+    return gemm_simt<double>(g, s);
+  }
+  if (dtype != BCUR_F32 || prec == BCUR_F64) return BCUR_EINVAL;
+  if (is_tc_prec(prec)) return gemm_tc(g, prec, s);  // no silent fallback here
+  return gemm_simt<float>(g, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Internal launchers shared between the translation units of the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace bcur {
+
+// ---------------------------------------------------------------------------
+// Dense GEMM on CUDA cores (FP32 / FP64):  D = alpha * A_op B_op + beta * D.
+//   A_op(i, kk) = transA ? A[kk*lda + i] : A[i*lda + kk]     (M x K)
+//   B_op(kk, j) = transB ? B[j*ldb + kk] : B[kk*ldb + j]     (K x N)
+// Triangular operands (stored with explicit zeros) only narrow the K loop:
+//   tri = 1: lower (A_op(i,kk) = 0 for kk > i;  B_op(kk,j) = 0 for kk < j)
+//   tri = 2: upper (A_op(i,kk) = 0 for kk < i;  B_op(kk,j) = 0 for kk > j)
+// batch > 1: independent problems at strides sA, sB, sD.
+// ksplit > 1: K is cut into ksplit chunks; chunk z writes D + z*sD (partials).
+// out_lower: only elements with i >= j are written (symmetric rank-k update).
+// ---------------------------------------------------------------------------
+struct GemmDesc {
+  int64_t M = 0, N = 0, K = 0;
+  const void* A = nullptr; int64_t lda = 0; int transA = 0;
+  const void* B = nullptr; int64_t ldb = 0; int transB = 0;
+  void* D = nullptr; int64_t ldd = 0;
+  double alpha = 1.0, beta = 0.0;
+  int64_t sA = 0, sB = 0, sD = 0;
+  int batch = 1;
+  int ksplit = 1;
+  int triA = 0, triB = 0;
+  int out_lower = 0;
+  // Residual epilogue: accumulate sum (X - alpha*A_op B_op)^2 and sum X^2 per
+  // CTA into partials[2 * cta] (FP64), instead of storing D.
+  const void* X = nullptr; int64_t ldx = 0; double* partials = nullptr;
+};
+
+template <typename T> bcur_status_t gemm_simt(const GemmDesc& d, cudaStream_t s);
+template <typename T> bcur_status_t gemm_simt_resid(const GemmDesc& d, cudaStream_t s,
+                                                    int64_t* n_partials);
+template <typename T> int64_t gemm_simt_resid_ctas(int64_t M, int64_t N);
+
+// tcgen05 tensor-core GEMM (FP32 storage; TF32 or BF16 arithmetic).  Returns
+// BCUR_ENOTSUP for shapes / layouts it does not cover.
+bcur_status_t gemm_tc(const GemmDesc& d, int prec, cudaStream_t s);
+bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* n_partials);
+int64_t gemm_tc_resid_ctas(int64_t M, int64_t N);
+bool gemm_tc_available();
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+// out[e] = sum_{s < nsplit} part[s*stride + e], FP64, fixed order.
+template <typename T>
+bcur_status_t reduce_splits_f64(const T* part, int nsplit, int64_t stride, int64_t count,
+                                double* out, cudaStream_t s);
+
+// Cholesky G = L L^T of a small SPD matrix (w <= 128) in FP64, with the drop
+// rule (pivot <= tol_rel * max diag -> direction dropped), plus L^{-1}.
+// Writes L and Linv (w x w, ld w, zeros above the diagonal) in FP64 and in T;
+// kept[0] = number of kept pivots.
+template <typename T>
+bcur_status_t chol_small(const double* G, int w, double tol_rel, double* L64, double* Linv64,
+                         T* LinvT, int* kept, cudaStream_t s);
+
+// Lc = La * Lb for lower-triangular w x w FP64 matrices (w <= 128).
+bcur_status_t trmm_small_f64(const double* La, const double* Lb, int w, double* Lc,
+                             cudaStream_t s);
+
+// One-sided Jacobi SVD of a w x w matrix X (given in FP64, ld w), computed in
+// T (w <= 128): X = Ut diag(sigma) W^T, sigma descending.  Ut, W: w x w
+// row-major in T; sigma: FP64.  jwork: device scratch, w*w T elements.
+template <typename T>
+bcur_status_t jacobi_svd_small(const double* X, int w, T* Ut, T* W, double* sigma, T* jwork,
+                               int* status, cudaStream_t s);
+
+// Blocked pieces of the wide Cholesky-QR.
+template <typename T>
+bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t s);
+template <typename T>
+bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t ldi, int64_t j0,
+                         int nb, const T* maxdiag, double tol_rel, int* kept, cudaStream_t s);
+
+// Block leverage scores from a panel F^T (k x h).
+template <typename T>
+bcur_status_t block_scores(const T* Ft, int k, int64_t h, int64_t ldf, const int64_t* off,
+                           int G, double* scores, int* status, cudaStream_t s);
+
+bcur_status_t sample_blocks(const double* scores, int G, const double* u, int g, int replacement,
+                            int32_t* idx, double* prob, cudaStream_t s);
+
+// Expand block indices into an index map of length cap (entries past the
+// chosen total are -1); total written to *count.
+bcur_status_t expand_blocks(const int32_t* idx, int g, const int64_t* off, int G, int64_t cap,
+                            int64_t* map, int64_t* count, cudaStream_t s);
+
+// Cp[cc][i] = A[i][map[cc]] (0 where map < 0); Cp is cap x ldc_rows (ld ldp).
+template <typename T>
+bcur_status_t gather_cols_t(const T* A, int64_t lda, int64_t m, const int64_t* map, int64_t cap,
+                            T* Cp, int64_t ldp, cudaStream_t s);
+// R[rr][j] = A[map[rr]][j] (0 where map < 0).
+template <typename T>
+bcur_status_t gather_rows(const T* A, int64_t lda, int64_t n, const int64_t* map, int64_t cap,
+                          T* R, int64_t ldr, cudaStream_t s);
+
+// Fixed-order FP64 reduction of residual partials: out = {sqrt(e2), sqrt(e2)/sqrt(x2), sqrt(x2)}
+// (mode 0) or {e2, x2} (mode 1).
+bcur_status_t finish_residual(const double* partials, int64_t n, double* out, int mode,
+                              cudaStream_t s);
+
+template <typename Tin, typename Tout>
+bcur_status_t convert(const Tin* in, Tout* out, int64_t count, cudaStream_t s);
+
+// Copy a rows x cols sub-matrix (strided) on the device.
+template <typename T>
+bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows, int64_t cols,
+                     cudaStream_t s);
+
+bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+}  // namespace bcur

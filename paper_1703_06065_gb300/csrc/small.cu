@@ -1,0 +1,636 @@
+// Small and memory-bound kernels of the Block CUR hot path (sm_103a):
+// block leverage scores (Def. 2), inverse-CDF block sampling (Alg. 1 step 2),
+// block gathers for C and R (Alg. 1), the FP64 Cholesky of small Gram
+// matrices used by Cholesky-QR, the diagonal-block factorisation of the
+// blocked Cholesky, a one-sided Jacobi SVD for the l x l projected factor,
+// and fixed-order FP64 reductions.
+#include <float.h>
+
+#include "kernels.h"
+
+namespace bcur {
+
+// ---------------------------------------------------------------------------
+// Fixed-order reductions
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void reduce_splits_kernel(const T* part, int nsplit, int64_t stride, int64_t count,
+                                     double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  double s = 0.0;
+  for (int z = 0; z < nsplit; ++z) s += (double)part[(int64_t)z * stride + e];
+  out[e] = s;
+}
+
+template <typename T>
+bcur_status_t reduce_splits_f64(const T* part, int nsplit, int64_t stride, int64_t count,
+                                double* out, cudaStream_t s) {
+  if (count <= 0) return BCUR_OK;
+  reduce_splits_kernel<T><<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(part, nsplit, stride,
+                                                                          count, out);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void finish_residual_kernel(const double* partials, int64_t n, double* out, int mode) {
+  double e2 = 0.0, x2 = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    e2 += partials[2 * i];
+    x2 += partials[2 * i + 1];
+  }
+  e2 = warp_sum(e2);
+  x2 = warp_sum(x2);
+  __shared__ double r[2][32];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { r[0][w] = e2; r[1][w] = x2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double se = 0.0, sx = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { se += r[0][i]; sx += r[1][i]; }
+    if (mode == 0) {
+      const double e = sqrt(se), a = sqrt(sx);
+      out[0] = e;
+      out[1] = a > 0.0 ? e / a : 0.0;
+      out[2] = a;
+    } else {
+      out[0] = se;
+      out[1] = sx;
+    }
+  }
+}
+
+bcur_status_t finish_residual(const double* partials, int64_t n, double* out, int mode,
+                              cudaStream_t s) {
+  finish_residual_kernel<<<1, 1024, 0, s>>>(partials, n, out, mode);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Small FP64 Cholesky with the drop rule, and its inverse
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void chol_small_kernel(const double* G, int w, double tol_rel, double* L64,
+                                  double* Linv64, T* LinvT, int* kept) {
+  extern __shared__ double S[];
+  const int ld = w + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e % w;
+    S[i * ld + j] = (j <= i) ? G[i * w + j] : 0.0;
+  }
+  __shared__ double s_tol, s_piv;
+  __shared__ int s_kept;
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < w; ++i) mx = fmax(mx, S[i * ld + i]);
+    s_tol = tol_rel * mx;
+    s_kept = 0;
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (tid == 0) {
+      const double d = S[j * ld + j];
+      double p = 0.0;
+      if (d > s_tol && d > 0.0) { p = sqrt(d); s_kept++; }
+      S[j * ld + j] = p;
+      s_piv = p;
+    }
+    __syncthreads();
+    const double p = s_piv;
+    for (int i = j + 1 + tid; i < w; i += nt) S[i * ld + j] = (p > 0.0) ? S[i * ld + j] / p : 0.0;
+    __syncthreads();
+    const int rem = w - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int a = e / rem, b = e % rem;
+      if (b <= a) {
+        const int i = j + 1 + a, i2 = j + 1 + b;
+        S[i * ld + i2] -= S[i * ld + j] * S[i2 * ld + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e % w;
+    L64[e] = (j <= i) ? S[i * ld + j] : 0.0;
+  }
+  // L^{-1} by forward substitution, one column per thread; dropped rows -> 0.
+  for (int c = tid; c < w; c += nt) {
+    for (int i = 0; i < w; ++i) {
+      double x = 0.0;
+      if (i >= c) {
+        const double lii = S[i * ld + i];
+        if (lii > 0.0) {
+          double acc = (i == c) ? 1.0 : 0.0;
+          for (int k = c; k < i; ++k) acc -= S[i * ld + k] * Linv64[k * w + c];
+          x = acc / lii;
+        }
+      }
+      Linv64[i * w + c] = x;
+      LinvT[i * w + c] = (T)x;
+    }
+  }
+  if (tid == 0) *kept = s_kept;
+}
+
+template <typename T>
+bcur_status_t chol_small(const double* G, int w, double tol_rel, double* L64, double* Linv64,
+                         T* LinvT, int* kept, cudaStream_t s) {
+  if (w < 1 || w > 128) return BCUR_EINVAL;
+  const size_t smem = (size_t)w * (w + 1) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(chol_small_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    attr_set = true;
+  }
+  chol_small_kernel<T><<<1, 256, smem, s>>>(G, w, tol_rel, L64, Linv64, LinvT, kept);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+__global__ void trmm_small_kernel(const double* La, const double* Lb, int w, double* Lc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= w * w) return;
+  const int i = e / w, j = e % w;
+  double acc = 0.0;
+  if (j <= i)
+    for (int k = j; k <= i; ++k) acc += La[i * w + k] * Lb[k * w + j];
+  Lc[e] = acc;
+}
+
+bcur_status_t trmm_small_f64(const double* La, const double* Lb, int w, double* Lc,
+                             cudaStream_t s) {
+  trmm_small_kernel<<<(unsigned)ceil_div((int64_t)w * w, 256), 256, 0, s>>>(La, Lb, w, Lc);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi SVD of a small square matrix, one CTA.
+// Columns of X are rotated pairwise until mutually orthogonal: X J = U Sigma,
+// so X = U Sigma J^T.  Pairs follow a round-robin tournament so that each
+// round's rotations are disjoint and run in parallel, one warp per pair.
+// ---------------------------------------------------------------------------
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+
+__device__ __forceinline__ int rr_player(int pos, int round, int wp) {
+  return pos == 0 ? 0 : ((pos - 1 + round) % (wp - 1)) + 1;
+}
+
+template <typename T>
+__global__ void jacobi_svd_kernel(const double* X, int w, T* Ut, T* W, double* sigma, T* J,
+                                  int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Xs = reinterpret_cast<T*>(smem_raw);  // column-major: column p at Xs[p * w]
+  const int wp = w + (w & 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int e = tid; e < wp * w; e += blockDim.x) {
+    const int p = e / w, i = e % w;
+    Xs[e] = (p < w) ? (T)X[i * w + p] : T(0);
+  }
+  for (int e = tid; e < wp * wp; e += blockDim.x) J[e] = (e / wp == e % wp) ? T(1) : T(0);
+  __shared__ int s_rot;
+  __shared__ int s_order[128];
+  __shared__ double s_sig[128];
+  __syncthreads();
+  const T tol = (T)(8.0 * Eps<T>::v);
+  const int max_sweeps = 40;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < wp - 1; ++round) {
+      for (int pr = warp; pr < wp / 2; pr += nwarps) {
+        int p = rr_player(pr, round, wp), q = rr_player(wp - 1 - pr, round, wp);
+        if (p > q) { const int t = p; p = q; q = t; }
+        T* xp = Xs + (int64_t)p * w;
+        T* xq = Xs + (int64_t)q * w;
+        T a = 0, b = 0, g = 0;
+        for (int i = lane; i < w; i += 32) {
+          const T u = xp[i], v = xq[i];
+          a += u * u;
+          b += v * v;
+          g += u * v;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (g != T(0) && a > T(0) && b > T(0) && fabs(g) > tol * sqrt(a * b)) {
+          const T zeta = (b - a) / (T(2) * g);
+          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + t * t);
+          const T sn = c * t;
+          for (int i = lane; i < w; i += 32) {
+            const T u = xp[i], v = xq[i];
+            xp[i] = c * u - sn * v;
+            xq[i] = sn * u + c * v;
+          }
+          T* jp = J + (int64_t)p * wp;
+          T* jq = J + (int64_t)q * wp;
+          for (int i = lane; i < wp; i += 32) {
+            const T u = jp[i], v = jq[i];
+            jp[i] = c * u - sn * v;
+            jq[i] = sn * u + c * v;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // singular values and descending order (stable insertion sort)
+  for (int p = warp; p < wp; p += nwarps) {
+    double a = 0.0;
+    for (int i = lane; i < w; i += 32) a += (double)Xs[p * w + i] * (double)Xs[p * w + i];
+    a = warp_sum(a);
+    if (lane == 0) s_sig[p] = sqrt(a);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int p = 0; p < wp; ++p) s_order[p] = p;
+    for (int p = 1; p < wp; ++p) {
+      const int v = s_order[p];
+      int j = p - 1;
+      while (j >= 0 && s_sig[s_order[j]] < s_sig[v]) { s_order[j + 1] = s_order[j]; --j; }
+      s_order[j + 1] = v;
+    }
+    if (sweep == max_sweeps && status) atomicCAS(status, 0, (int)BCUR_ETIMEOUT);
+  }
+  __syncthreads();
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int i = e / w, t = e % w;
+    const int p = s_order[t];
+    const double sg = s_sig[p];
+    Ut[i * w + t] = sg > 0.0 ? (T)((double)Xs[p * w + i] / sg) : T(0);
+    W[i * w + t] = J[(int64_t)p * wp + i];
+  }
+  for (int t = tid; t < w; t += blockDim.x) sigma[t] = s_sig[s_order[t]];
+}
+
+template <typename T>
+bcur_status_t jacobi_svd_small(const double* X, int w, T* Ut, T* W, double* sigma, T* jwork,
+                               int* status, cudaStream_t s) {
+  if (w < 1 || w > 128) return BCUR_EINVAL;
+  const int wp = w + (w & 1);
+  const size_t smem = (size_t)wp * w * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    attr_set = true;
+  }
+  const int warps = wp / 2 < 32 ? (wp / 2 < 1 ? 1 : wp / 2) : 32;
+  jacobi_svd_kernel<T><<<1, warps * 32, smem, s>>>(X, w, Ut, W, sigma, jwork, status);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Cholesky pieces (working precision T)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void max_diag_kernel(const T* G, int64_t w, int64_t ldg, T* out) {
+  T mx = T(0);
+  for (int64_t i = threadIdx.x; i < w; i += blockDim.x) mx = fmax(mx, G[i * ldg + i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ T r[32];
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T m2 = T(0);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m2 = fmax(m2, r[i]);
+    *out = m2;
+  }
+}
+
+template <typename T>
+bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t s) {
+  max_diag_kernel<T><<<1, 1024, 0, s>>>(G, w, ldg, out);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// Factor the diagonal block G[j0:j0+nbb, j0:j0+nbb] (lower part, already
+// updated by the trailing updates) as L L^T with the drop rule, and write L
+// and L^{-1} into the same block position of L and Linv (zeros above the
+// diagonal).  nbb = min(nb, w - j0) is passed through nb by the caller.
+template <typename T>
+__global__ void potrf_diag_kernel(const T* G, int64_t ldg, T* L, int64_t ldl, T* Linv,
+                                  int64_t ldi, int64_t j0, int nb, const T* maxdiag,
+                                  double tol_rel, int* kept) {
+  extern __shared__ unsigned char smem_raw[];
+  const int ld = nb + 1;
+  T* S = reinterpret_cast<T*>(smem_raw);
+  T* X = S + nb * ld;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < nb * nb; e += nt) {
+    const int i = e / nb, j = e % nb;
+    S[i * ld + j] = (j <= i) ? G[(j0 + i) * ldg + j0 + j] : T(0);
+    X[i * ld + j] = (i == j) ? T(1) : T(0);
+  }
+  __shared__ T s_piv;
+  __shared__ int s_kept;
+  if (tid == 0) s_kept = 0;
+  const T tol = (T)(tol_rel * (double)(*maxdiag));
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      const T d = S[j * ld + j];
+      T p = T(0);
+      if (d > tol && d > T(0)) { p = sqrt(d); s_kept++; }
+      S[j * ld + j] = p;
+      s_piv = p;
+    }
+    __syncthreads();
+    const T p = s_piv;
+    for (int i = j + 1 + tid; i < nb; i += nt) S[i * ld + j] = (p > T(0)) ? S[i * ld + j] / p : T(0);
+    __syncthreads();
+    const int rem = nb - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int a = e / rem, b = e % rem;
+      if (b <= a) {
+        const int i = j + 1 + a, i2 = j + 1 + b;
+        S[i * ld + i2] -= S[i * ld + j] * S[i2 * ld + j];
+      }
+    }
+    __syncthreads();
+  }
+  // X <- L^{-1} by right-looking forward substitution on the identity.
+  for (int k = 0; k < nb; ++k) {
+    const T lkk = S[k * ld + k];
+    for (int c = tid; c <= k; c += nt) X[k * ld + c] = (lkk > T(0)) ? X[k * ld + c] / lkk : T(0);
+    __syncthreads();
+    const int rows = nb - k - 1, cols = k + 1;
+    for (int e = tid; e < rows * cols; e += nt) {
+      const int i = k + 1 + e / cols, c = e % cols;
+      X[i * ld + c] -= S[i * ld + k] * X[k * ld + c];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += nt) {
+    const int i = e / nb, j = e % nb;
+    L[(j0 + i) * ldl + j0 + j] = (j <= i) ? S[i * ld + j] : T(0);
+    Linv[(j0 + i) * ldi + j0 + j] = (j <= i) ? X[i * ld + j] : T(0);
+  }
+  if (tid == 0) atomicAdd(kept, s_kept);
+}
+
+template <typename T>
+bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t ldi, int64_t j0,
+                         int nb, const T* maxdiag, double tol_rel, int* kept, cudaStream_t s) {
+  if (nb < 1 || nb > 128) return BCUR_EINVAL;
+  const size_t smem = 2 * (size_t)nb * (nb + 1) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  potrf_diag_kernel<T><<<1, 256, smem, s>>>(G, ldg, L, ldl, Linv, ldi, j0, nb, maxdiag, tol_rel,
+                                            kept);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Block leverage scores (Def. 2): one CTA per block, FP64 accumulation in a
+// fixed order (strided per thread, xor-tree per warp, warps in order).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void block_scores_kernel(const T* Ft, int k, int64_t ldf, const int64_t* off,
+                                    double* scores, int* status) {
+  const int g = blockIdx.x;
+  const int64_t j0 = off[g], size = off[g + 1] - off[g];
+  const int64_t total = size * k;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int64_t t = e / size, j = j0 + e % size;
+    const double v = (double)Ft[t * ldf + j];
+    acc = fma(v, v, acc);
+  }
+  acc = warp_sum(acc);
+  __shared__ double r[32];
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += r[w];
+    scores[g] = sum;
+    if (!isfinite(sum)) dev_set_status(status, (int)BCUR_ENONFINITE);
+  }
+}
+
+template <typename T>
+bcur_status_t block_scores(const T* Ft, int k, int64_t h, int64_t ldf, const int64_t* off, int G,
+                           double* scores, int* status, cudaStream_t s) {
+  (void)h;
+  if (G <= 0) return BCUR_OK;
+  block_scores_kernel<T><<<G, 256, 0, s>>>(Ft, k, ldf, off, scores, status);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Inverse-CDF sampling, one thread: the arithmetic must be the sequential
+// FP64 order of the oracle, so every add / multiply is an explicit
+// round-to-nearest intrinsic (no contraction into FMA).
+// ---------------------------------------------------------------------------
+__global__ void sample_kernel(const double* scores, int G, const double* u, int g,
+                              int replacement, int32_t* idx, double* prob) {
+  extern __shared__ unsigned char remaining[];
+  if (threadIdx.x != 0) return;
+  for (int j = 0; j < G; ++j) remaining[j] = 1;
+  double total0 = 0.0;
+  for (int j = 0; j < G; ++j) total0 = __dadd_rn(total0, scores[j]);
+  for (int t = 0; t < g; ++t) {
+    double T = 0.0;
+    for (int j = 0; j < G; ++j)
+      if (remaining[j]) T = __dadd_rn(T, scores[j]);
+    const double x = __dmul_rn(u[t], T);
+    int pick = -1;
+    double S = 0.0;
+    for (int j = 0; j < G; ++j) {
+      if (!remaining[j]) continue;
+      S = __dadd_rn(S, scores[j]);
+      if (S > x) { pick = j; break; }
+    }
+    if (pick < 0) {
+      for (int j = G - 1; j >= 0; --j)
+        if (remaining[j] && scores[j] > 0.0) { pick = j; break; }
+      if (pick < 0)
+        for (int j = 0; j < G; ++j)
+          if (remaining[j]) { pick = j; break; }
+    }
+    idx[t] = pick;
+    if (prob) prob[t] = total0 > 0.0 ? __ddiv_rn(scores[pick], total0) : 0.0;
+    if (!replacement) remaining[pick] = 0;
+  }
+}
+
+bcur_status_t sample_blocks(const double* scores, int G, const double* u, int g, int replacement,
+                            int32_t* idx, double* prob, cudaStream_t s) {
+  if (G < 1 || G > 32768 || g < 0 || (!replacement && g > G)) return BCUR_EINVAL;
+  if (g == 0) return BCUR_OK;
+  sample_kernel<<<1, 32, G, s>>>(scores, G, u, g, replacement, idx, prob);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Block index expansion and gathers
+// ---------------------------------------------------------------------------
+__global__ void expand_blocks_kernel(const int32_t* idx, int g, const int64_t* off, int G,
+                                     int64_t cap, int64_t* map, int64_t* count) {
+  int64_t base = 0;
+  for (int t = 0; t < g; ++t) {
+    const int b = idx[t];
+    const bool ok = (b >= 0 && b < G);
+    const int64_t start = ok ? off[b] : 0;
+    const int64_t size = ok ? off[b + 1] - off[b] : 0;
+    for (int64_t e = threadIdx.x; e < size; e += blockDim.x)
+      if (base + e < cap) map[base + e] = start + e;
+    base += size;
+  }
+  for (int64_t e = base + threadIdx.x; e < cap; e += blockDim.x) map[e] = -1;
+  if (threadIdx.x == 0) *count = base < cap ? base : cap;
+}
+
+bcur_status_t expand_blocks(const int32_t* idx, int g, const int64_t* off, int G, int64_t cap,
+                            int64_t* map, int64_t* count, cudaStream_t s) {
+  expand_blocks_kernel<<<1, 512, 0, s>>>(idx, g, off, G, cap, map, count);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+template <typename T>
+__global__ void gather_cols_kernel(const T* A, int64_t lda, int64_t m, const int64_t* map,
+                                   int64_t cap, T* Cp, int64_t ldp) {
+  __shared__ T tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int x = threadIdx.x;
+  const int64_t cc = c0 + x;
+  const int64_t col = cc < cap ? map[cc] : -1;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t i = i0 + y;
+    tile[y][x] = (col >= 0 && i < m) ? A[i * lda + col] : T(0);
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t c = c0 + y, i = i0 + x;
+    if (c < cap && i < m) Cp[c * ldp + i] = tile[x][y];
+  }
+}
+
+template <typename T>
+bcur_status_t gather_cols_t(const T* A, int64_t lda, int64_t m, const int64_t* map, int64_t cap,
+                            T* Cp, int64_t ldp, cudaStream_t s) {
+  if (cap <= 0 || m <= 0) return BCUR_OK;
+  if (ceil_div(cap, 32) > 65535) return BCUR_EINVAL;
+  dim3 grid((unsigned)ceil_div(m, 32), (unsigned)ceil_div(cap, 32));
+  gather_cols_kernel<T><<<grid, dim3(32, 8), 0, s>>>(A, lda, m, map, cap, Cp, ldp);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+template <typename T>
+__global__ void gather_rows_kernel(const T* A, int64_t lda, int64_t n, const int64_t* map,
+                                   T* R, int64_t ldr) {
+  const int64_t rr = blockIdx.y;
+  const int64_t row = map[rr];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    R[rr * ldr + j] = row >= 0 ? A[row * lda + j] : T(0);
+}
+
+template <typename T>
+bcur_status_t gather_rows(const T* A, int64_t lda, int64_t n, const int64_t* map, int64_t cap,
+                          T* R, int64_t ldr, cudaStream_t s) {
+  if (cap <= 0 || n <= 0) return BCUR_OK;
+  if (cap > 65535) return BCUR_EINVAL;
+  const int64_t gx = ceil_div(n, 256) < 8 ? ceil_div(n, 256) : 8;
+  gather_rows_kernel<T><<<dim3((unsigned)gx, (unsigned)cap), 256, 0, s>>>(A, lda, n, map, R, ldr);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin* in, Tout* out, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (Tout)in[e];
+}
+
+template <typename Tin, typename Tout>
+bcur_status_t convert(const Tin* in, Tout* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return BCUR_OK;
+  const int64_t blocks = ceil_div(count, 256) < 4096 ? ceil_div(count, 256) : 4096;
+  convert_kernel<Tin, Tout><<<(unsigned)blocks, 256, 0, s>>>(in, out, count);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+template <typename T>
+bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows, int64_t cols,
+                     cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return BCUR_OK;
+  BCUR_CUDA_TRY(cudaMemcpy2DAsync(dst, ldd * sizeof(T), src, lds * sizeof(T), cols * sizeof(T),
+                                  rows, cudaMemcpyDeviceToDevice, s));
+  return BCUR_OK;
+}
+
+bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BCUR_OK;
+  BCUR_CUDA_TRY(cudaMemsetAsync(p, 0, bytes, s));
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Instantiations
+// ---------------------------------------------------------------------------
+#define BCUR_INST(T)                                                                              \
+  template bcur_status_t reduce_splits_f64<T>(const T*, int, int64_t, int64_t, double*,           \
+                                              cudaStream_t);                                      \
+  template bcur_status_t chol_small<T>(const double*, int, double, double*, double*, T*, int*,    \
+                                       cudaStream_t);                                             \
+  template bcur_status_t jacobi_svd_small<T>(const double*, int, T*, T*, double*, T*, int*,       \
+                                             cudaStream_t);                                       \
+  template bcur_status_t max_diag<T>(const T*, int64_t, int64_t, T*, cudaStream_t);               \
+  template bcur_status_t potrf_diag<T>(T*, int64_t, T*, int64_t, T*, int64_t, int64_t, int,       \
+                                       const T*, double, int*, cudaStream_t);                     \
+  template bcur_status_t block_scores<T>(const T*, int, int64_t, int64_t, const int64_t*, int,    \
+                                         double*, int*, cudaStream_t);                            \
+  template bcur_status_t gather_cols_t<T>(const T*, int64_t, int64_t, const int64_t*, int64_t,    \
+                                          T*, int64_t, cudaStream_t);                             \
+  template bcur_status_t gather_rows<T>(const T*, int64_t, int64_t, const int64_t*, int64_t, T*,  \
+                                        int64_t, cudaStream_t);                                   \
+  template bcur_status_t copy2d<T>(const T*, int64_t, T*, int64_t, int64_t, int64_t, cudaStream_t);
+BCUR_INST(float)
+BCUR_INST(double)
+template bcur_status_t convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template bcur_status_t convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template bcur_status_t convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+template bcur_status_t convert<float, float>(const float*, float*, int64_t, cudaStream_t);
+
+}  // namespace bcur

@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry
+point include/bcur.h declares, and validates descriptors without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1703_06065_gb300 import build
+
+    build.build()
+    import paper_1703_06065_gb300 as pkg
+
+    return pkg.load()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "bcur.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bcur_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1703_06065_gb300 import _lib
+
+    names = header_functions()
+    assert "bcur_plan" in names and "bcur_error" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.EXPORTS) == names
+    assert lib.bcur_version().decode().count(".") == 2
+
+
+def _desc(m=256, n=512, lda=None, k=8, p=8, q=1, s=32, g_col=4, g_row=3, dtype=1, sp=1, fp=1,
+          replacement=0, col_off=None, row_off=None):
+    from paper_1703_06065_gb300 import _lib
+
+    co = np.asarray(col_off if col_off is not None else np.arange(0, n + 1, s), dtype=np.int64)
+    ro = np.asarray(row_off if row_off is not None else np.arange(0, m + 1, s), dtype=np.int64)
+    d = _lib.Desc()
+    d.m, d.n, d.lda = m, n, lda or n
+    d.a_dtype, d.k, d.p, d.q = dtype, k, p, q
+    d.G_col, d.col_off = len(co) - 1, co.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.G_row, d.row_off = len(ro) - 1, ro.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.g_col, d.g_row, d.replacement = g_col, g_row, replacement
+    d.sketch_prec, d.fit_prec = sp, fp
+    return d, (co, ro)
+
+
+def _plan(lib, **kw):
+    d, keep = _desc(**kw)
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    st = lib.bcur_plan(ctypes.byref(d), None, ctypes.byref(h), ctypes.byref(ws))
+    if st == 0:
+        lib.bcur_destroy(h)
+    return st, ws.value
+
+
+@pytest.mark.parametrize("kw,want", [
+    (dict(), 0),
+    (dict(dtype=0, sp=0, fp=0), 0),
+    (dict(sp=2, fp=3), 0),
+    (dict(lda=100), 1),                      # lda < n
+    (dict(k=100, p=40), 1),                  # l > 128
+    (dict(k=0), 1),
+    (dict(q=17), 1),
+    (dict(g_col=17), 1),                     # more blocks than exist, no replacement
+    (dict(g_col=17, replacement=1), 0),      # fine with replacement
+    (dict(dtype=0, sp=2, fp=0), 1),          # FP64 data with a TF32 stage
+    (dict(dtype=1, sp=0, fp=1), 1),          # FP32 data with an FP64 stage
+    (dict(col_off=[0, 32, 32, 512]), 1),     # empty block
+    (dict(col_off=[0, 100, 500]), 1),        # does not end at n
+    (dict(col_off=[0, 100, 512], g_col=2), 0),  # unequal blocks are allowed
+    (dict(m=20, n=30, s=5, k=20, p=5, g_col=2, g_row=2), 1),  # l > m
+])
+def test_plan_validation(lib, kw, want):
+    st, ws = _plan(lib, **kw)
+    assert st == want
+    if want == 0:
+        assert ws > 0
+
+
+def test_calls_before_workspace_and_null_plan(lib):
+    d, keep = _desc()
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    assert lib.bcur_plan(ctypes.byref(d), None, ctypes.byref(h), ctypes.byref(ws)) == 0
+    dummy = ctypes.c_void_p(0x1000)
+    assert lib.bcur_scores(h, dummy, dummy, dummy, dummy) == 8      # ESTATE
+    assert lib.bcur_fit(h, dummy, dummy, dummy, None, None, None) == 8
+    assert lib.bcur_error(h, dummy, dummy) == 8
+    assert lib.bcur_set_workspace(h, ctypes.c_void_p(0x1001), ws.value) == 1  # misaligned
+    assert lib.bcur_set_workspace(h, ctypes.c_void_p(0x1000), ws.value - 256) == 2
+    lib.bcur_destroy(h)
+    assert lib.bcur_scores(None, dummy, dummy, dummy, dummy) == 1
+    assert lib.bcur_status_string(5).decode().startswith("non-finite")
+
+
+def test_workspace_grows_with_blocks(lib):
+    _, a = _plan(lib, g_col=2, g_row=2)
+    _, b = _plan(lib, g_col=8, g_row=6)
+    assert b > a

@@ -1,0 +1,158 @@
+"""End-to-end parity of the library against the FP64 oracle on the same
+stored matrices (small sizes the oracle finishes in seconds)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from _gpu_common import device, run_problem, to_dev, torch  # noqa: F401
+import bcur_inputs as bi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_plain_fp64_512x1024():
+    p = bi.plain_fp64_512x1024()
+    ref, gpu, plan = run_problem(p)
+    for side in ("col", "row"):
+        d = np.max(np.abs(gpu[f"{side}_scores"] - ref[f"{side}_scores"]))
+        assert d <= 1e-6 * np.max(ref[f"{side}_scores"]), side
+        assert abs(np.sum(gpu[f"{side}_scores"]) - p.k) < 1e-9
+    assert gpu["col_ok_draws"] == p.g_col and gpu["row_ok_draws"] == p.g_row
+    assert gpu["col_idx"] == ref["col_idx"]
+    assert gpu["row_idx"] == ref["row_idx"]
+    np.testing.assert_array_equal(gpu["C"], ref["C"])
+    np.testing.assert_array_equal(gpu["R"], ref["R"])
+    assert _rel(gpu["U"], ref["U"]) < 1e-7
+    assert abs(gpu["err"][1] - ref["rel"]) <= 1e-3
+    assert abs(gpu["err"][0] - ref["err"]) <= 1e-9 * ref["err"]
+    assert gpu["rank"] == (256, 192, 256, 192)
+
+
+@pytest.mark.parametrize("sp,fp", [("f32", "f32")])
+def test_haar_fp32_small(sp, fp):
+    p = bi.scaled_haar(1536, 2048, 64, k=10, p=10, q=2, g_col=6, g_row=5, seed=7, rank=120,
+                       noise=1e-4)
+    ref, gpu, plan = run_problem(p, sp, fp)
+    for side in ("col", "row"):
+        d = np.max(np.abs(gpu[f"{side}_scores"] - ref[f"{side}_scores"]))
+        assert d <= 1e-4 * np.max(ref[f"{side}_scores"]), (side, d)
+    for side in ("col", "row"):
+        n_ok = gpu[f"{side}_ok_draws"]
+        assert gpu[f"{side}_idx"][:n_ok] == ref[f"{side}_idx"][:n_ok]
+    assert abs(gpu["err"][1] - ref["rel"]) <= 1e-3
+    assert abs(gpu["err"][0] - ref["err"]) <= 1e-4 * ref["err"]
+
+
+@pytest.mark.parametrize("i", [0, 1, 2])
+def test_biometric_batch_members(i):
+    # the smallest members of the 512-matrix uneven batch
+    probs = sorted(bi.batched_biometric(512), key=lambda q: q.m * q.n)[: 3]
+    p = probs[i]
+    ref, gpu, plan = run_problem(p, "f32", "f32")
+    assert abs(gpu["err"][1] - ref["rel"]) <= 1e-3
+    for side in ("col", "row"):
+        n_ok = gpu[f"{side}_ok_draws"]
+        assert gpu[f"{side}_idx"][:n_ok] == ref[f"{side}_idx"][:n_ok]
+
+
+def test_ragged_blocks_fp64():
+    rg = np.random.default_rng(3)
+    m, n = 203, 331
+    A = rg.standard_normal((m, 6)) @ rg.standard_normal((6, n)) + 0.01 * rg.standard_normal((m, n))
+    col_off = np.array([0, 1, 40, 41, 100, 200, 300, 331], dtype=np.int64)
+    row_off = bi.uniform_blocks(m, 25)                     # short last block
+    p = bi.Problem("ragged", m, n, k=5, p=4, q=1, col_off=col_off, row_off=row_off, g_col=3,
+                   g_row=4, seed=2, storage="f64", recipe={})
+    ref, gpu, plan = run_problem(p, A=A)
+    np.testing.assert_allclose(gpu["col_scores"], ref["col_scores"], atol=1e-9)
+    np.testing.assert_allclose(gpu["row_scores"], ref["row_scores"], atol=1e-9)
+    assert gpu["col_idx"][:gpu["col_ok_draws"]] == ref["col_idx"][:gpu["col_ok_draws"]]
+    c, r, kc, kr = gpu["rank"]
+    assert c == ref["C"].shape[1] and r == ref["R"].shape[0]
+    assert abs(gpu["err"][0] - ref["err"]) <= 1e-8 * ref["err"]
+    # C has more columns than A has rows, so U is not unique (the oracle's is
+    # the minimum-norm one); the product CUR is, and it must agree.
+    assert kc <= m and c > m
+    cur_gpu = gpu["C"][:, :c] @ gpu["U"][:c, :r] @ gpu["R"][:r]
+    cur_orc = ref["C"] @ ref["U"] @ ref["R"]
+    assert _rel(cur_gpu, cur_orc) < 1e-8
+
+
+def test_duplicate_blocks_with_replacement():
+    """Drawing the same block twice makes C rank deficient: the library drops
+    the dependent directions and still reaches the least-squares error."""
+    rg = np.random.default_rng(4)
+    A = rg.standard_normal((96, 128))
+    off_c, off_r = bi.uniform_blocks(128, 16), bi.uniform_blocks(96, 16)
+    import paper_1703_06065_gb300 as pkg
+
+    dev = device()
+    plan = pkg.Plan(96, 128, 4, 4, 1, off_c, off_r, 3, 2, dtype="f64", replacement=True)
+    At = to_dev(A)
+    ci = to_dev(np.array([2, 5, 2], dtype=np.int32))
+    ri = to_dev(np.array([1, 1], dtype=np.int32))
+    plan.fit(At, ci, ri)
+    e = plan.error(At).cpu().numpy()
+    C = orc.gather_columns(A, off_c, [2, 5, 2])
+    R = orc.gather_rows(A, off_r, [1, 1])
+    want = orc.residual(A, C, orc.fit_u(A, C, R), R)[0]
+    assert abs(e[0] - want) <= 1e-9 * want
+    c, r, kc, kr = plan.rank()
+    assert (c, r, kc, kr) == (48, 32, 32, 16)
+
+
+def test_brute_force_all_block_pairs():
+    """12 x 16, s = 4: the library's fit and residual on every block choice
+    equal the oracle's least-squares error."""
+    import paper_1703_06065_gb300 as pkg
+
+    dev = device()
+    rg = np.random.default_rng(15)
+    A = rg.standard_normal((12, 16))
+    col_off, row_off = bi.uniform_blocks(16, 4), bi.uniform_blocks(12, 4)
+    plan = pkg.Plan(12, 16, 3, 1, 1, col_off, row_off, 2, 2, dtype="f64")
+    At = to_dev(A)
+    for cj in itertools.combinations(range(4), 2):
+        for ri in itertools.combinations(range(3), 2):
+            plan.fit(At, to_dev(np.array(cj, np.int32)), to_dev(np.array(ri, np.int32)))
+            e = plan.error(At).cpu().numpy()
+            C = orc.gather_columns(A, col_off, cj)
+            R = orc.gather_rows(A, row_off, ri)
+            want = orc.residual(A, C, orc.fit_u(A, C, R), R)[0]
+            assert abs(e[0] - want) <= 1e-10 * np.linalg.norm(A)
+
+
+def test_nonfinite_input_is_reported():
+    import paper_1703_06065_gb300 as pkg
+
+    dev = device()
+    p = bi.plain_fp64_512x1024()
+    A = p.matrix()
+    A[7, 9] = np.nan
+    plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row, dtype="f64")
+    plan.scores(to_dev(A), to_dev(p.omega().T))
+    with pytest.raises(pkg.BcurError) as ei:
+        plan.sync_status()
+    assert ei.value.status == 5
+
+
+def test_error_is_deterministic():
+    p = bi.plain_fp64_512x1024()
+    import paper_1703_06065_gb300 as pkg
+
+    dev = device()
+    A = to_dev(p.matrix())
+    plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row, dtype="f64")
+    ci = to_dev(np.arange(8, dtype=np.int32))
+    ri = to_dev(np.arange(6, dtype=np.int32))
+    plan.fit(A, ci, ri)
+    a = plan.error(A).cpu().numpy()
+    plan.fit(A, ci, ri)
+    b = plan.error(A).cpu().numpy()
+    assert a.tobytes() == b.tobytes()
