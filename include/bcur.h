@@ -198,6 +198,31 @@ bcur_status_t bcur_residual(const void* X, int64_t ldx, const void* P, int64_t l
                             int32_t dtype, int32_t prec, double* out, void* workspace,
                             size_t workspace_bytes, void* stream);
 
+/* bcur_residual for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ * Who needs it: code whose device memory is entirely owned by another
+ * framework's pool (so a fresh cudaMalloc fails or fragments it), request
+ * loops that must never call cudaMalloc/cudaFree (cudaFree synchronises the
+ * whole device), and plug-ins that are handed only input and output pointers.
+ * Same arguments and result as bcur_residual, minus the workspace: the
+ * per-CTA partial sums go to a fixed 1 MiB array inside the library's device
+ * image (65536 partial pairs; every GPU that loads the library holds it until
+ * the process exits).
+ *   - Sizes whose kernel would need more than 65536 partial pairs (FP32:
+ *     more than 65536 tiles of 128 x 128 in X; FP64: tiles of 64 x 64) are
+ *     rejected with BCUR_ENOMEM before anything is enqueued.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture begins.
+ *   - No call allocates or frees device memory.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call writes every slot it later reads, so nothing needs clearing,
+ *     but calls that overlap on the GPU (different streams or threads) race
+ *     on it and must be serialised by the caller. */
+bcur_status_t bcur_residual_noalloc(const void* X, int64_t ldx, const void* P, int64_t ldp,
+                                    const void* Q, int64_t ldq, int64_t m, int64_t n, int64_t r,
+                                    int32_t dtype, int32_t prec, double* out, void* stream);
+
 /* Dense GEMM on the library's kernels, exposed for testing the tensor-core
  * path against the CUDA-core path:  D (M x N, row-major, ldd) = A_op B_op,
  * A_op(i, kk) = transA ? A[kk * lda + i] : A[i * lda + kk],

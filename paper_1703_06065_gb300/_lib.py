@@ -23,7 +23,7 @@ EXPORTS = [
     "bcur_plan", "bcur_set_workspace", "bcur_scores", "bcur_factors", "bcur_sample", "bcur_fit",
     "bcur_error", "bcur_rank", "bcur_sync_status", "bcur_destroy", "bcur_status_string",
     "bcur_block_scores", "bcur_sample_blocks", "bcur_residual_workspace", "bcur_residual",
-    "bcur_gemm", "bcur_launch_count", "bcur_version",
+    "bcur_gemm", "bcur_launch_count", "bcur_version", "bcur_residual_noalloc",
 ]
 
 
@@ -97,6 +97,10 @@ def load():
                                 c_int64, c_int64, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
                                 c_void_p]
     L.bcur_residual.restype = st
+    L.bcur_residual_noalloc.argtypes = [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
+                                        c_int64, c_int64, c_int64, c_int32, c_int32, c_void_p,
+                                        c_void_p]
+    L.bcur_residual_noalloc.restype = st
     L.bcur_gemm.argtypes = [c_int64, c_int64, c_int64, c_void_p, c_int64, c_int32, c_void_p,
                             c_int64, c_int32, c_void_p, c_int64, c_int32, c_int32, c_void_p]
     L.bcur_gemm.restype = st
