@@ -59,12 +59,21 @@ typedef enum {
 } bcur_status_t;
 
 /* Storage type of A and arithmetic of a stage.
- *   BCUR_F64  : FP64 storage and FP64 arithmetic everywhere.
- *   BCUR_F32  : FP32 arithmetic on CUDA cores (FP32 storage).
- *   BCUR_TF32 : tcgen05 tensor cores, TF32 inputs read from FP32 storage,
- *               FP32 accumulation in tensor memory.
- *   BCUR_BF16 : tcgen05 tensor cores on a BF16 copy of A, FP32 accumulation. */
-typedef enum { BCUR_F64 = 0, BCUR_F32 = 1, BCUR_TF32 = 2, BCUR_BF16 = 3 } bcur_prec_t;
+ *   BCUR_F64    : FP64 storage and FP64 arithmetic everywhere.
+ *   BCUR_F32    : FP32 arithmetic on CUDA cores (FP32 storage).
+ *   BCUR_TF32   : tcgen05 tensor cores reading FP32 storage as TF32 (bcur_gemm
+ *                 only, both operands K-major; plans refuse it).
+ *   BCUR_BF16   : tcgen05 tensor cores on BF16 roundings of the FP32 operands,
+ *                 FP32 accumulation in tensor memory (about 8 mantissa bits).
+ *   BCUR_BF16X3 : tcgen05 tensor cores on BF16 hi/lo pairs, x = hi + lo, with
+ *                 A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 bits). */
+typedef enum {
+  BCUR_F64 = 0,
+  BCUR_F32 = 1,
+  BCUR_TF32 = 2,
+  BCUR_BF16 = 3,
+  BCUR_BF16X3 = 4
+} bcur_prec_t;
 
 typedef struct {
   int64_t m, n;           /* A is m x n                                        */
@@ -91,7 +100,8 @@ typedef struct bcur_plan_s* bcur_plan_t;
  * new plan and *workspace_bytes the device workspace it needs.
  * Errors: BCUR_EINVAL (any descriptor field out of range, offsets not
  * increasing, lda < n, l > min(m, n, 128), g > G without replacement, F64
- * storage with a non-F64 precision), BCUR_ENOTSUP (precision unavailable).
+ * storage with a non-F64 precision), BCUR_ENOTSUP (TF32 stages, or a BF16
+ * fit: one BF16 term cannot keep Cholesky-QR of C stable, use BF16X3).
  */
 bcur_status_t bcur_plan(const bcur_desc_t* desc, void* stream, bcur_plan_t* out,
                         size_t* workspace_bytes);
@@ -186,9 +196,11 @@ bcur_status_t bcur_sample_blocks(const double* scores, int32_t G, const double* 
                                  int32_t replacement, int32_t* idx, double* prob, void* stream);
 
 /* ||X - P Q||_F^2 reduced in FP64 without forming P Q, where X is row-major
- * m x n (ldx), P row-major m x r (ldp) and Q row-major r x n (ldq), all of
- * storage type dtype (F64 or F32) and precision prec (F64 for F64 data, F32
- * or TF32 for F32 data).  out: device, 2 doubles {||X - PQ||_F^2, ||X||_F^2}.
+ * m x n (ldx), P row-major m x r (ldp) and Q row-major r x n (ldq).  dtype
+ * F64 or F32: X, P, Q of that type, prec F64 (F64 data) or F32 / TF32 (F32
+ * data; TF32 falls back to F32 on CUDA cores where TMA cannot serve it).
+ * dtype BF16: X FP32, P and Q BF16 (ldp, ldq multiples of 8), prec BF16, on
+ * tensor cores.  out: device, 2 doubles {||X - PQ||_F^2, ||X||_F^2}.
  * workspace: device scratch of at least bcur_residual_workspace(m, n, dtype)
  * bytes.  P and Q may be NULL when r = 0.  This is the fused kernel behind
  * bcur_error. */
@@ -227,7 +239,11 @@ bcur_status_t bcur_residual_noalloc(const void* X, int64_t ldx, const void* P, i
  * path against the CUDA-core path:  D (M x N, row-major, ldd) = A_op B_op,
  * A_op(i, kk) = transA ? A[kk * lda + i] : A[i * lda + kk],
  * B_op(kk, j) = transB ? B[j * ldb + kk] : B[kk * ldb + j].
- * dtype F64/F32 (storage of A, B, D), prec F64, F32, TF32 or BF16. */
+ * dtype F64/F32: storage of A, B and D, with prec F64 (F64 data), F32 or
+ * TF32 (F32 data).  dtype BF16: A and B stored as BF16, D as FP32, prec BF16.
+ * The tensor-core precisions return BCUR_ENOTSUP for operands TMA cannot
+ * describe (base not 16-byte aligned, leading dimension not a multiple of
+ * 16 bytes) instead of falling back. */
 bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                         int32_t transA, const void* B, int64_t ldb, int32_t transB, void* D,
                         int64_t ldd, int32_t dtype, int32_t prec, void* stream);

@@ -210,14 +210,15 @@ def residual(X, P, Q, prec: str = None):
     torch = _torch()
     _need_cuda(X, P, Q)
     L = _lib.load()
-    m, n = X.shape
-    r = P.shape[1]
-    code = _dtype_code(X)
+    m, n = X.shape[0], Q.shape[1]
+    r = P.shape[0] and P.shape[1]
+    code = BCUR_BF16 if P.dtype == torch.bfloat16 else _dtype_code(X)
     prec = PREC[prec] if prec else code
     wsb = L.bcur_residual_workspace(m, n, code)
     ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=X.device)
     out = torch.empty(2, dtype=torch.float64, device=X.device)
-    _lib.check(L.bcur_residual(_ptr(X), n, _ptr(P), r, _ptr(Q), n, m, n, r, code, prec, _ptr(out),
+    _lib.check(L.bcur_residual(_ptr(X), X.shape[1], _ptr(P), P.shape[1], _ptr(Q), Q.shape[1], m,
+                               n, P.shape[1] if code != BCUR_BF16 else r, code, prec, _ptr(out),
                                _ptr(ws), c_size_t(ws.numel()), _stream()), "bcur_residual")
     return out
 

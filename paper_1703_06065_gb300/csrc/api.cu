@@ -61,8 +61,13 @@ struct bcur_plan_s {
     size_t Pm0, Pm1, Pn0, Pn1, Pn2, gram_part, G64, L64a, L64b, Lprod64, Linv64, LinvT, Ut, W,
         sigma, jwork, Vp, Up, col_off, row_off, status, kept, colmap, rowmap, counts, Cp0, Cp1,
         Rp0, Rp1, GC, L1C, L1Ci, L2C, L2Ci, GR, L1R, L1Ri, L2R, L2Ri, maxdiag, Wb, Mb, U1, U2,
-        partials, result;
+        partials, result, tc_scratch;
+    // BF16 tensor-core path
+    size_t A16h, A16l, Om16h, Om16l, Qm16h, Qm16l, Zn16h, Zn16l, XC16[4], XR16[4], Lh, Ll, Lih,
+        Lil, T1h, T1l, Pnh, Pnl, Wh, Wl, Mh, Ml, U1h, U1l, U2h, U2l, Ph;
   } o;
+  bool bf16_path = false;
+  size_t tc_scratch_bytes = 0;
   int64_t n_partials = 0;
   bool have_scores = false, have_fit = false;
   template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
@@ -71,6 +76,7 @@ struct bcur_plan_s {
 namespace {
 
 bool is_tc_prec(int p) { return p == BCUR_TF32 || p == BCUR_BF16; }
+bool is_bf16_prec(int p) { return p == BCUR_BF16 || p == BCUR_BF16X3; }
 
 // The Cholesky updates must keep the working precision's accuracy: a Gram
 // matrix with condition number kappa^2 loses kappa^2 * u in them.
@@ -120,6 +126,12 @@ bcur_status_t gemm_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* n
   return gemm_simt_resid<T>(d, s, np);
 }
 
+// Plan-aware dispatch: attaches the plan's split-K scratch and status word.
+template <typename T>
+bcur_status_t pg(bcur_plan_t P, GemmDesc d, int prec);
+template <typename T>
+bcur_status_t pgr(bcur_plan_t P, GemmDesc d, int prec, int64_t* np);
+
 GemmDesc mk(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, int tA, const void* B,
             int64_t ldb, int tB, void* D, int64_t ldd) {
   GemmDesc g;
@@ -128,6 +140,19 @@ GemmDesc mk(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, int tA,
   g.B = B; g.ldb = ldb; g.transB = tB;
   g.D = D; g.ldd = ldd;
   return g;
+}
+
+template <typename T>
+bcur_status_t pg(bcur_plan_t P, GemmDesc d, int prec) {
+  d.scratch = P->at<void>(P->o.tc_scratch);
+  d.scratch_bytes = P->tc_scratch_bytes;
+  d.status = P->at<int>(P->o.status);
+  return gemm<T>(d, prec, P->stream);
+}
+template <typename T>
+bcur_status_t pgr(bcur_plan_t P, GemmDesc d, int prec, int64_t* np) {
+  d.status = P->at<int>(P->o.status);
+  return gemm_resid<T>(d, prec, P->stream, np);
 }
 
 // --- Skinny Cholesky-QR2 on a panel X (w x h, ld), w <= 128 ----------------
@@ -144,14 +169,14 @@ bcur_status_t orth_panel(bcur_plan_t P, T* X, T* tmp, int w, int64_t h, int64_t 
     GemmDesc g = mk(w, w, h, src, ld, 0, src, ld, 1, P->at<T>(P->o.gram_part), w);
     g.ksplit = ksplit;
     g.sD = (int64_t)w * w;
-    BCUR_TRY(gemm<T>(g, prec, s));
+    BCUR_TRY(pg<T>(P, g, prec));
     BCUR_TRY(reduce_splits_f64<T>(P->at<T>(P->o.gram_part), ksplit, (int64_t)w * w,
                                   (int64_t)w * w, P->at<double>(P->o.G64), s));
     BCUR_TRY(chol_small<T>(P->at<double>(P->o.G64), w, tol, Ls[pass], P->at<double>(P->o.Linv64),
                            P->at<T>(P->o.LinvT), P->at<int>(P->o.kept), s));
     GemmDesc a = mk(w, h, w, P->at<T>(P->o.LinvT), w, 0, src, ld, 0, dst, ld);
     a.triA = 1;
-    BCUR_TRY(gemm<T>(a, prec, s));
+    BCUR_TRY(pg<T>(P, a, prec));
     std::swap(src, dst);
   }
   // after two passes the result is back in X
@@ -161,11 +186,22 @@ bcur_status_t orth_panel(bcur_plan_t P, T* X, T* tmp, int w, int64_t h, int64_t 
 
 // --- Wide Cholesky-QR2 on a panel X (w x h, ld), w a multiple of nb -------
 // X = L1 L2 Q;  writes Q into `Q`, and L1, L1^{-1}, L2, L2^{-1} (w x w).
+// Drop tolerance for the pivots of a Gram matrix X X^T with inner dimension
+// h, relative to its largest diagonal entry.  In FP64 the rounding of the
+// Gram itself reaches h * u * max diag, so pivots below 2 h u are noise.  In
+// FP32 that worst case would also drop real directions of well-conditioned
+// inputs (h = 32768 gives 7.8e-3), so FP32 keeps the fixed 64 u.
 template <typename T>
-bcur_status_t chol_inv_blocked(bcur_plan_t P, T* G, T* L, T* Li, int64_t w, int prec, int* kept) {
+double drop_tol(int64_t h) {
+  return std::is_same<T, double>::value ? EpsOf<T>::v * std::max<double>(64.0, 2.0 * (double)h)
+                                        : 64.0 * EpsOf<T>::v;
+}
+
+template <typename T>
+bcur_status_t chol_inv_blocked(bcur_plan_t P, T* G, T* L, T* Li, int64_t w, int prec, int* kept,
+                               double tol) {
   cudaStream_t s = P->stream;
   const int nb = P->nb;
-  const double tol = 64.0 * EpsOf<T>::v;
   T* md = P->at<T>(P->o.maxdiag);
   BCUR_TRY(fill_zero(L, (size_t)w * w * sizeof(T), s));
   BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(T), s));
@@ -178,13 +214,13 @@ bcur_status_t chol_inv_blocked(bcur_plan_t P, T* G, T* L, T* Li, int64_t w, int 
     GemmDesc pn = mk(w - j1, nb, nb, G + j1 * w + j0, w, 0, Li + j0 * w + j0, w, 1,
                      L + j1 * w + j0, w);
     pn.triB = 2;
-    BCUR_TRY(gemm<T>(pn, exact_prec<T>(), s));
+    BCUR_TRY(pg<T>(P, pn, exact_prec<T>()));
     GemmDesc tr = mk(w - j1, w - j1, nb, L + j1 * w + j0, w, 0, L + j1 * w + j0, w, 1,
                      G + j1 * w + j1, w);
     tr.alpha = -1.0;
     tr.beta = 1.0;
     tr.out_lower = 1;
-    BCUR_TRY(gemm<T>(tr, exact_prec<T>(), s));
+    BCUR_TRY(pg<T>(P, tr, exact_prec<T>()));
   }
   // Inverse of the whole lower factor by doubling: with X11, X22 the inverses
   // of the diagonal halves, X21 = -X22 L21 X11.  G serves as the temporary.
@@ -197,7 +233,7 @@ bcur_status_t chol_inv_blocked(bcur_plan_t P, T* G, T* L, T* Li, int64_t w, int 
       t1.sA = 2 * h * (w + 1);
       t1.sB = 2 * h * (w + 1);
       t1.sD = h * h;
-      BCUR_TRY(gemm<T>(t1, prec, s));
+      BCUR_TRY(pg<T>(P, t1, prec));
       GemmDesc t2 = mk(h, h, h, Li + h * w + h, w, 0, G, h, 0, Li + h * w, w);
       t2.triA = 1;
       t2.alpha = -1.0;
@@ -205,18 +241,18 @@ bcur_status_t chol_inv_blocked(bcur_plan_t P, T* G, T* L, T* Li, int64_t w, int 
       t2.sA = 2 * h * (w + 1);
       t2.sB = h * h;
       t2.sD = 2 * h * (w + 1);
-      BCUR_TRY(gemm<T>(t2, prec, s));
+      BCUR_TRY(pg<T>(P, t2, prec));
     }
     const int64_t b1 = npairs_full * 2 * h, b2 = b1 + h;
     if (b2 < w) {  // ragged last pair
       const int64_t h2 = w - b2;
       GemmDesc t1 = mk(h2, h, h, L + b2 * w + b1, w, 0, Li + b1 * w + b1, w, 0, G, h);
       t1.triB = 1;
-      BCUR_TRY(gemm<T>(t1, prec, s));
+      BCUR_TRY(pg<T>(P, t1, prec));
       GemmDesc t2 = mk(h2, h, h2, Li + b2 * w + b2, w, 0, G, h, 0, Li + b2 * w + b1, w);
       t2.triA = 1;
       t2.alpha = -1.0;
-      BCUR_TRY(gemm<T>(t2, prec, s));
+      BCUR_TRY(pg<T>(P, t2, prec));
     }
   }
   return BCUR_OK;
@@ -233,17 +269,20 @@ bcur_status_t wide_cqr2(bcur_plan_t P, T* X, T* tmp, int64_t w, int64_t h, int64
   for (int pass = 0; pass < 2; ++pass) {
     GemmDesc g = mk(w, w, h, src, ld, 0, src, ld, 1, G, w);
     g.out_lower = 1;
-    BCUR_TRY(gemm<T>(g, prec, s));
-    BCUR_TRY(chol_inv_blocked<T>(P, G, Ls[pass], Lis[pass], w, prec, kept + pass));
+    BCUR_TRY(pg<T>(P, g, prec));
+    BCUR_TRY(chol_inv_blocked<T>(P, G, Ls[pass], Lis[pass], w, prec, kept + pass, drop_tol<T>(h)));
     GemmDesc a = mk(w, h, w, Lis[pass], w, 0, src, ld, 0, dst, ld);
     a.triA = 1;
-    BCUR_TRY(gemm<T>(a, prec, s));
+    BCUR_TRY(pg<T>(P, a, prec));
     std::swap(src, dst);
   }
   return BCUR_OK;  // Q is back in X
 }
 
 // --- Stage 1-2 -------------------------------------------------------------
+template <typename T>
+bcur_status_t scores_tail(bcur_plan_t P, double* cs, double* rs);
+
 template <typename T>
 bcur_status_t run_scores(bcur_plan_t P, const T* A, const T* omega, double* cs, double* rs) {
   cudaStream_t s = P->stream;
@@ -255,20 +294,34 @@ bcur_status_t run_scores(bcur_plan_t P, const T* A, const T* omega, double* cs, 
   T* Pn0 = P->at<T>(P->o.Pn0);
   T* Pn1 = P->at<T>(P->o.Pn1);
   // Y^T = Omega^T A^T  (Y = A Omega)
-  BCUR_TRY(gemm<T>(mk(l, m, n, omega, n, 0, A, lda, 1, Pm0, ldm), sp, s));
+  BCUR_TRY(pg<T>(P, mk(l, m, n, omega, n, 0, A, lda, 1, Pm0, ldm), sp));
   BCUR_TRY(orth_panel<T>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, sp, nullptr));
   for (int it = 0; it < P->q; ++it) {
     // Z^T = Q^T A  (Z = A^T Q)
-    BCUR_TRY(gemm<T>(mk(l, n, m, Pm0, ldm, 0, A, lda, 0, Pn0, ldn), sp, s));
+    BCUR_TRY(pg<T>(P, mk(l, n, m, Pm0, ldm, 0, A, lda, 0, Pn0, ldn), sp));
     BCUR_TRY(orth_panel<T>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, sp, nullptr));
     // Y^T = Z^T A^T
-    BCUR_TRY(gemm<T>(mk(l, m, n, Pn0, ldn, 0, A, lda, 1, Pm0, ldm), sp, s));
+    BCUR_TRY(pg<T>(P, mk(l, m, n, Pn0, ldn, 0, A, lda, 1, Pm0, ldm), sp));
     BCUR_TRY(orth_panel<T>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, sp, nullptr));
   }
   // B = Q^T A (l x n) = L_B Q_B, then SVD of L_B.
-  BCUR_TRY(gemm<T>(mk(l, n, m, Pm0, ldm, 0, A, lda, 0, Pn0, ldn), sp, s));
+  BCUR_TRY(pg<T>(P, mk(l, n, m, Pm0, ldm, 0, A, lda, 0, Pn0, ldn), sp));
+  return scores_tail<T>(P, cs, rs);
+}
+
+// Shared end of stage 1-2: with B^T (l x n panel) in Pn0 and Q^T in Pm0,
+// B = L_B Q_B, the SVD of L_B gives V_k = Q_B W_k and U_k = Q U~_k, then the
+// block scores.
+template <typename T>
+bcur_status_t scores_tail(bcur_plan_t P, double* cs, double* rs) {
+  cudaStream_t s = P->stream;
+  const int l = P->l, k = P->k;
+  const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
+  T* Pm0 = P->at<T>(P->o.Pm0);
+  T* Pn0 = P->at<T>(P->o.Pn0);
+  T* Pn1 = P->at<T>(P->o.Pn1);
   double* LB = P->at<double>(P->o.Lprod64);
-  BCUR_TRY(orth_panel<T>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, sp, LB));
+  BCUR_TRY(orth_panel<T>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, exact_prec<T>(), LB));
   T* Ut = P->at<T>(P->o.Ut);
   T* W = P->at<T>(P->o.W);
   BCUR_TRY(jacobi_svd_small<T>(LB, l, Ut, W, P->at<double>(P->o.sigma), P->at<T>(P->o.jwork),
@@ -314,24 +367,24 @@ bcur_status_t run_fit(bcur_plan_t P, const T* A, const int32_t* ci, const int32_
   // W = A Q_R (m x r),  M = Q_C^T W (c x r)
   T* Wb = P->at<T>(P->o.Wb);
   T* Mb = P->at<T>(P->o.Mb);
-  BCUR_TRY(gemm<T>(mk(m, rw, n, A, lda, 0, Rp, ldn, 1, Wb, rw), fp, s));
-  BCUR_TRY(gemm<T>(mk(cw, rw, m, Cp, ldm, 0, Wb, rw, 0, Mb, rw), fp, s));
+  BCUR_TRY(pg<T>(P, mk(m, rw, n, A, lda, 0, Rp, ldn, 1, Wb, rw), fp));
+  BCUR_TRY(pg<T>(P, mk(cw, rw, m, Cp, ldm, 0, Wb, rw, 0, Mb, rw), fp));
   // U = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1}
   T* U1 = P->at<T>(P->o.U1);
   T* U2 = P->at<T>(P->o.U2);
   {
     GemmDesc g1 = mk(cw, rw, rw, Mb, rw, 0, P->at<T>(P->o.L2Ri), rw, 0, U1, rw);
     g1.triB = 1;
-    BCUR_TRY(gemm<T>(g1, fp, s));
+    BCUR_TRY(pg<T>(P, g1, fp));
     GemmDesc g2 = mk(cw, rw, rw, U1, rw, 0, P->at<T>(P->o.L1Ri), rw, 0, U2, rw);
     g2.triB = 1;
-    BCUR_TRY(gemm<T>(g2, fp, s));
+    BCUR_TRY(pg<T>(P, g2, fp));
     GemmDesc g3 = mk(cw, rw, cw, P->at<T>(P->o.L2Ci), cw, 1, U2, rw, 0, U1, rw);
     g3.triA = 2;
-    BCUR_TRY(gemm<T>(g3, fp, s));
+    BCUR_TRY(pg<T>(P, g3, fp));
     GemmDesc g4 = mk(cw, rw, cw, P->at<T>(P->o.L1Ci), cw, 1, U1, rw, 0, U2, rw);
     g4.triA = 2;
-    BCUR_TRY(gemm<T>(g4, fp, s));
+    BCUR_TRY(pg<T>(P, g4, fp));
   }
   if (Uout) BCUR_TRY(copy2d<T>(U2, rw, Uout, P->r_max, P->c_max, P->r_max, s));
   return BCUR_OK;
@@ -346,16 +399,298 @@ bcur_status_t run_error(bcur_plan_t P, const T* A, double* out) {
   const int64_t cw = P->c_pad, rw = P->r_pad;
   T* Wb = P->at<T>(P->o.Wb);
   // P = Q_C M  (m x r)
-  BCUR_TRY(gemm<T>(mk(m, rw, cw, P->at<T>(P->o.Cp0), ldm, 1, P->at<T>(P->o.Mb), rw, 0, Wb, rw),
-                   fp, s));
+  BCUR_TRY(pg<T>(P, mk(m, rw, cw, P->at<T>(P->o.Cp0), ldm, 1, P->at<T>(P->o.Mb), rw, 0, Wb, rw),
+                  fp));
   GemmDesc r = mk(m, n, rw, Wb, rw, 0, P->at<T>(P->o.Rp0), ldn, 0, nullptr, 0);
   r.X = A;
   r.ldx = P->lda;
   r.partials = P->at<double>(P->o.partials);
   int64_t np = 0;
-  BCUR_TRY(gemm_resid<T>(r, fp, s, &np));
+  BCUR_TRY(pgr<T>(P, r, fp, &np));
   BCUR_TRY(finish_residual(P->at<double>(P->o.partials), np, out, 0, s));
   return BCUR_OK;
+}
+
+
+// ===========================================================================
+// BF16 tensor-core pipeline (FP32 storage).  Operands of every large GEMM are
+// BF16 roundings (BCUR_BF16) or BF16 hi/lo pairs (BCUR_BF16X3) produced by
+// split kernels or written directly by the producing GEMM's epilogue; the
+// skinny l x l algebra, the Cholesky diagonal blocks and panels stay FP32 /
+// FP64 on CUDA cores.
+// ===========================================================================
+using bf16 = __nv_bfloat16;
+struct S16 {
+  bf16* h;
+  bf16* l;
+  S16 off(int64_t e) const { return {h + e, l ? l + e : nullptr}; }
+};
+
+int parts_of(int prec) { return prec == BCUR_BF16X3 ? 3 : 1; }
+
+S16 s16(bcur_plan_t P, size_t oh, size_t ol, bool with_lo) {
+  return {P->at<bf16>(oh), with_lo ? P->at<bf16>(ol) : nullptr};
+}
+
+bcur_status_t split(bcur_plan_t P, const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                    S16 out, int64_t ldo) {
+  return split_bf16(X, ldx, rows, cols, out.h, out.l, ldo, P->stream);
+}
+
+GemmDesc mk16(int64_t M, int64_t N, int64_t K, S16 A, int64_t lda, int tA, S16 B, int64_t ldb,
+              int tB, int64_t ldd) {
+  GemmDesc g = mk(M, N, K, A.h, lda, tA, B.h, ldb, tB, nullptr, ldd);
+  g.A_lo = A.l;
+  g.B_lo = B.l;
+  g.ab_bf16 = 1;
+  return g;
+}
+
+// Tensor-core GEMM on BF16 operands; never falls back (ENOTSUP is an error).
+bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) {
+  d.parts = parts;
+  if (parts != 3) { d.A_lo = nullptr; d.B_lo = nullptr; }
+  d.scratch = P->at<void>(P->o.tc_scratch);
+  d.scratch_bytes = P->tc_scratch_bytes;
+  d.status = P->at<int>(P->o.status);
+  return gemm_tc(d, BCUR_BF16, P->stream);
+}
+
+// Blocked Cholesky G = L L^T (w x w, FP32, lower part) and L^{-1}: FP32
+// diagonal blocks and panels on CUDA cores, trailing updates and the
+// inverse-by-doubling products on tensor cores with `parts` BF16 terms.
+bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, int64_t w, int parts,
+                                 int* kept, double tol) {
+  cudaStream_t s = P->stream;
+  const int nb = P->nb;
+  const bool lo = parts == 3;
+  float* md = P->at<float>(P->o.maxdiag);
+  S16 Pn = s16(P, P->o.Pnh, P->o.Pnl, lo);
+  S16 L16 = s16(P, P->o.Lh, P->o.Ll, lo);
+  S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
+  S16 T1 = s16(P, P->o.T1h, P->o.T1l, lo);
+  BCUR_TRY(fill_zero(L, (size_t)w * w * sizeof(float), s));
+  BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(float), s));
+  BCUR_TRY(fill_zero(kept, sizeof(int), s));
+  BCUR_TRY(max_diag<float>(G, w, w, md, s));
+  for (int64_t j0 = 0; j0 < w; j0 += nb) {
+    BCUR_TRY(potrf_diag<float>(G, w, L, w, Li, w, j0, nb, md, tol, kept, s));
+    const int64_t j1 = j0 + nb;
+    if (j1 >= w) break;
+    GemmDesc pn = mk(w - j1, nb, nb, G + j1 * w + j0, w, 0, Li + j0 * w + j0, w, 1,
+                     L + j1 * w + j0, w);
+    pn.triB = 2;
+    BCUR_TRY(gemm_simt<float>(pn, s));
+    BCUR_TRY(split(P, L + j1 * w + j0, w, w - j1, nb, Pn, nb));
+    GemmDesc tr = mk16(w - j1, w - j1, nb, Pn, nb, 0, Pn, nb, 1, w);
+    tr.D = G + j1 * w + j1;
+    tr.alpha = -1.0;
+    tr.beta = 1.0;
+    tr.out_lower = 1;
+    BCUR_TRY(g16(P, tr, parts));
+  }
+  BCUR_TRY(split(P, L, w, w, w, L16, w));
+  for (int64_t h = nb; h < w; h *= 2) {
+    BCUR_TRY(split(P, Li, w, w, w, Li16, w));
+    const int64_t npairs_full = w / (2 * h);
+    if (npairs_full > 0) {
+      GemmDesc t1 = mk16(h, h, h, L16.off(h * w), w, 0, Li16, w, 0, h);
+      t1.Dh = T1.h;
+      t1.Dl = T1.l;
+      t1.triB = 1;
+      t1.batch = (int)npairs_full;
+      t1.sA = 2 * h * (w + 1);
+      t1.sB = 2 * h * (w + 1);
+      t1.sD = h * h;
+      BCUR_TRY(g16(P, t1, parts));
+      GemmDesc t2 = mk16(h, h, h, Li16.off(h * w + h), w, 0, T1, h, 0, w);
+      t2.D = Li + h * w;
+      t2.triA = 1;
+      t2.alpha = -1.0;
+      t2.batch = (int)npairs_full;
+      t2.sA = 2 * h * (w + 1);
+      t2.sB = h * h;
+      t2.sD = 2 * h * (w + 1);
+      BCUR_TRY(g16(P, t2, parts));
+    }
+    const int64_t b1 = npairs_full * 2 * h, b2 = b1 + h;
+    if (b2 < w) {
+      const int64_t h2 = w - b2;
+      GemmDesc t1 = mk16(h2, h, h, L16.off(b2 * w + b1), w, 0, Li16.off(b1 * w + b1), w, 0, h);
+      t1.Dh = T1.h;
+      t1.Dl = T1.l;
+      t1.triB = 1;
+      BCUR_TRY(g16(P, t1, parts));
+      GemmDesc t2 = mk16(h2, h, h2, Li16.off(b2 * w + b2), w, 0, T1, h, 0, w);
+      t2.D = Li + b2 * w + b1;
+      t2.triA = 1;
+      t2.alpha = -1.0;
+      BCUR_TRY(g16(P, t2, parts));
+    }
+  }
+  return BCUR_OK;
+}
+
+// Wide Cholesky-QR2 of a BF16-pair panel X (w x h): X = L1 L2 Q.  The pairs
+// pr[0] (input, then result) and pr[1] (intermediate) ping-pong.
+bcur_status_t wide_cqr2_16(bcur_plan_t P, S16 pr[2], int64_t w, int64_t h, int64_t ld, float* G,
+                           float* L1, float* L1i, float* L2, float* L2i, int parts, int* kept) {
+  const bool lo = parts == 3;
+  S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
+  float* Ls[2] = {L1, L2};
+  float* Lis[2] = {L1i, L2i};
+  for (int pass = 0; pass < 2; ++pass) {
+    S16 src = pr[pass], dst = pr[1 - pass];
+    GemmDesc g = mk16(w, w, h, src, ld, 0, src, ld, 1, w);
+    g.D = G;
+    g.out_lower = 1;
+    BCUR_TRY(g16(P, g, parts));
+    BCUR_TRY(chol_inv_blocked16(P, G, Ls[pass], Lis[pass], w, parts, kept + pass,
+                                drop_tol<float>(h)));
+    BCUR_TRY(split(P, Lis[pass], w, w, w, Li16, w));
+    GemmDesc a = mk16(w, h, w, Li16, w, 0, src, ld, 0, ld);
+    a.Dh = dst.h;
+    a.Dl = dst.l;
+    a.triA = 1;
+    BCUR_TRY(g16(P, a, parts));
+  }
+  return BCUR_OK;
+}
+
+// Stages 1-2 with the products by A on tensor cores.
+bcur_status_t run_scores16(bcur_plan_t P, const float* A, const float* omega, double* cs,
+                           double* rs) {
+  const int l = P->l;
+  const int parts = parts_of(P->d.sketch_prec);
+  const bool lo = parts == 3;
+  const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
+  float* Pm0 = P->at<float>(P->o.Pm0);
+  float* Pm1 = P->at<float>(P->o.Pm1);
+  float* Pn0 = P->at<float>(P->o.Pn0);
+  float* Pn1 = P->at<float>(P->o.Pn1);
+  S16 A16 = s16(P, P->o.A16h, P->o.A16l, lo);
+  S16 Om = s16(P, P->o.Om16h, P->o.Om16l, lo);
+  S16 Q16 = s16(P, P->o.Qm16h, P->o.Qm16l, lo);
+  S16 Z16 = s16(P, P->o.Zn16h, P->o.Zn16l, lo);
+  BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
+  BCUR_TRY(split(P, omega, n, l, n, Om, ldn));
+  auto prodAt = [&](S16 X, float* Y) {  // Y^T (l x m) = X^T A^T, X^T panel l x n
+    GemmDesc g = mk16(l, m, n, X, ldn, 0, A16, ldn, 1, ldm);
+    g.D = Y;
+    return g16(P, g, parts);
+  };
+  auto prodA = [&](S16 X, float* Z) {   // Z^T (l x n) = X^T A, X^T panel l x m
+    GemmDesc g = mk16(l, n, m, X, ldm, 0, A16, ldn, 0, ldn);
+    g.D = Z;
+    return g16(P, g, parts);
+  };
+  const int ep = BCUR_F32;
+  BCUR_TRY(prodAt(Om, Pm0));
+  BCUR_TRY(orth_panel<float>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, ep, nullptr));
+  for (int it = 0; it < P->q; ++it) {
+    BCUR_TRY(split(P, Pm0, ldm, l, m, Q16, ldm));
+    BCUR_TRY(prodA(Q16, Pn0));
+    BCUR_TRY(orth_panel<float>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, ep, nullptr));
+    BCUR_TRY(split(P, Pn0, ldn, l, n, Z16, ldn));
+    BCUR_TRY(prodAt(Z16, Pm0));
+    BCUR_TRY(orth_panel<float>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, ep, nullptr));
+  }
+  BCUR_TRY(split(P, Pm0, ldm, l, m, Q16, ldm));
+  BCUR_TRY(prodA(Q16, Pn0));
+  return scores_tail<float>(P, cs, rs);
+}
+
+// Stages 4-5 on tensor cores.
+bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const int32_t* ri,
+                        float* Uout, float* Cout, float* Rout) {
+  cudaStream_t s = P->stream;
+  const int parts = parts_of(P->d.fit_prec);
+  const bool lo = parts == 3;
+  const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
+  const int64_t cw = P->c_pad, rw = P->r_pad;
+  int64_t* counts = P->at<int64_t>(P->o.counts);
+  BCUR_TRY(expand_blocks(ci, P->d.g_col, P->at<int64_t>(P->o.col_off), P->d.G_col, cw,
+                         P->at<int64_t>(P->o.colmap), counts, s));
+  BCUR_TRY(expand_blocks(ri, P->d.g_row, P->at<int64_t>(P->o.row_off), P->d.G_row, rw,
+                         P->at<int64_t>(P->o.rowmap), counts + 1, s));
+  float* Cp = P->at<float>(P->o.Cp0);
+  float* Rp = P->at<float>(P->o.Rp0);
+  BCUR_TRY(gather_cols_t<float>(A, lda, m, P->at<int64_t>(P->o.colmap), cw, Cp, ldm, s));
+  BCUR_TRY(gather_rows<float>(A, lda, n, P->at<int64_t>(P->o.rowmap), rw, Rp, ldn, s));
+  if (Cout) BCUR_TRY(copy2d<float>(Cp, ldm, Cout, m, P->c_max, m, s));
+  if (Rout) BCUR_TRY(copy2d<float>(Rp, ldn, Rout, n, P->r_max, n, s));
+  S16 XC[2] = {s16(P, P->o.XC16[0], P->o.XC16[1], lo), s16(P, P->o.XC16[2], P->o.XC16[3], lo)};
+  S16 XR[2] = {s16(P, P->o.XR16[0], P->o.XR16[1], lo), s16(P, P->o.XR16[2], P->o.XR16[3], lo)};
+  BCUR_TRY(split(P, Cp, ldm, cw, m, XC[0], ldm));
+  BCUR_TRY(split(P, Rp, ldn, rw, n, XR[0], ldn));
+  int* kept = P->at<int>(P->o.kept);
+  BCUR_TRY(wide_cqr2_16(P, XC, cw, m, ldm, P->at<float>(P->o.GC), P->at<float>(P->o.L1C),
+                        P->at<float>(P->o.L1Ci), P->at<float>(P->o.L2C), P->at<float>(P->o.L2Ci),
+                        parts, kept + 4));
+  BCUR_TRY(wide_cqr2_16(P, XR, rw, n, ldn, P->at<float>(P->o.GR), P->at<float>(P->o.L1R),
+                        P->at<float>(P->o.L1Ri), P->at<float>(P->o.L2R), P->at<float>(P->o.L2Ri),
+                        parts, kept + 6));
+  // W = A Q_R (m x r);  M = Q_C^T W (c x r)
+  S16 A16 = s16(P, P->o.A16h, P->o.A16l, lo);
+  S16 W16 = s16(P, P->o.Wh, P->o.Wl, lo);
+  S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
+  BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
+  {
+    GemmDesc g = mk16(m, rw, n, A16, ldn, 0, XR[0], ldn, 1, rw);
+    g.Dh = W16.h;
+    g.Dl = W16.l;
+    BCUR_TRY(g16(P, g, parts));
+    GemmDesc g2 = mk16(cw, rw, m, XC[0], ldm, 0, W16, rw, 0, rw);
+    g2.D = P->at<float>(P->o.Mb);
+    g2.Dh = M16.h;
+    g2.Dl = M16.l;
+    BCUR_TRY(g16(P, g2, parts));
+  }
+  // U = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1}
+  S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
+  S16 U1 = s16(P, P->o.U1h, P->o.U1l, lo);
+  S16 U2 = s16(P, P->o.U2h, P->o.U2l, lo);
+  float* Uf = P->at<float>(P->o.U2);
+  BCUR_TRY(split(P, P->at<float>(P->o.L2Ri), rw, rw, rw, Li16, rw));
+  GemmDesc g1 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 0, rw);
+  g1.Dh = U1.h; g1.Dl = U1.l; g1.triB = 1;
+  BCUR_TRY(g16(P, g1, parts));
+  BCUR_TRY(split(P, P->at<float>(P->o.L1Ri), rw, rw, rw, Li16, rw));
+  GemmDesc g2 = mk16(cw, rw, rw, U1, rw, 0, Li16, rw, 0, rw);
+  g2.Dh = U2.h; g2.Dl = U2.l; g2.triB = 1;
+  BCUR_TRY(g16(P, g2, parts));
+  BCUR_TRY(split(P, P->at<float>(P->o.L2Ci), cw, cw, cw, Li16, cw));
+  GemmDesc g3 = mk16(cw, rw, cw, Li16, cw, 1, U2, rw, 0, rw);
+  g3.Dh = U1.h; g3.Dl = U1.l; g3.triA = 2;
+  BCUR_TRY(g16(P, g3, parts));
+  BCUR_TRY(split(P, P->at<float>(P->o.L1Ci), cw, cw, cw, Li16, cw));
+  GemmDesc g4 = mk16(cw, rw, cw, Li16, cw, 1, U1, rw, 0, rw);
+  g4.D = Uf; g4.triA = 2;
+  BCUR_TRY(g16(P, g4, parts));
+  if (Uout) BCUR_TRY(copy2d<float>(Uf, rw, Uout, P->r_max, P->c_max, P->r_max, s));
+  return BCUR_OK;
+}
+
+// Stage 6 on tensor cores: P = Q_C M (BF16), then sum (A - P Q_R^T)^2.
+bcur_status_t run_error16(bcur_plan_t P, const float* A, double* out) {
+  const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
+  const int64_t cw = P->c_pad, rw = P->r_pad;
+  S16 QC = {P->at<bf16>(P->o.XC16[0]), nullptr};
+  S16 QR = {P->at<bf16>(P->o.XR16[0]), nullptr};
+  S16 M16 = {P->at<bf16>(P->o.Mh), nullptr};
+  S16 Ph = {P->at<bf16>(P->o.Ph), nullptr};
+  GemmDesc g = mk16(m, rw, cw, QC, ldm, 1, M16, rw, 0, rw);
+  g.Dh = Ph.h;
+  BCUR_TRY(g16(P, g, 1));
+  GemmDesc r = mk16(m, n, rw, Ph, rw, 0, QR, ldn, 0, 0);
+  r.X = A;
+  r.ldx = P->lda;
+  r.partials = P->at<double>(P->o.partials);
+  r.parts = 1;
+  r.status = P->at<int>(P->o.status);
+  int64_t np = 0;
+  BCUR_TRY(gemm_tc_resid(r, BCUR_BF16, P->stream, &np));
+  return finish_residual(P->at<double>(P->o.partials), np, out, 0, P->stream);
 }
 
 }  // namespace
@@ -399,10 +734,14 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
   if (d->g_col < 1 || d->g_row < 1) return BCUR_EINVAL;
   if (!d->replacement && (d->g_col > d->G_col || d->g_row > d->G_row)) return BCUR_EINVAL;
   for (int p : {d->sketch_prec, d->fit_prec}) {
-    if (p < BCUR_F64 || p > BCUR_BF16) return BCUR_EINVAL;
+    if (p < BCUR_F64 || p > BCUR_BF16X3) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F64 && p != BCUR_F64) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F32 && p == BCUR_F64) return BCUR_EINVAL;
+    if (p == BCUR_TF32) return BCUR_ENOTSUP;
   }
+  // A single BF16 term cannot keep Cholesky-QR of C and R^T stable (kappa^2
+  // times 2^-9 exceeds 1 for kappa ~ 50): the fit needs F32 or split BF16.
+  if (d->fit_prec == BCUR_BF16) return BCUR_ENOTSUP;
   bcur_plan_t P = new (std::nothrow) bcur_plan_s();
   if (!P) return BCUR_ENOMEM;
   P->d = *d;
@@ -485,6 +824,44 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
                                     gemm_tc_resid_ctas(P->m, P->n)));
   o.partials = L.take(2 * P->n_partials * 8);
   o.result = L.take(64);
+  P->bf16_path = is_bf16_prec(d->sketch_prec) || is_bf16_prec(d->fit_prec);
+  P->tc_scratch_bytes = P->bf16_path ? (64u << 20) : 0;
+  o.tc_scratch = L.take(P->tc_scratch_bytes);
+  if (P->bf16_path) {
+    const size_t h2 = 2;  // bytes per BF16
+    const int64_t wm = std::max(cw, rw);
+    const bool s3 = d->sketch_prec == BCUR_BF16X3, f3 = d->fit_prec == BCUR_BF16X3;
+    const bool any3 = s3 || f3;
+    o.A16h = L.take(P->m * P->ldn * h2);
+    o.A16l = L.take(any3 ? P->m * P->ldn * h2 : 0);
+    o.Om16h = L.take(l * P->ldn * h2);
+    o.Om16l = L.take(l * P->ldn * h2);
+    o.Qm16h = L.take(l * P->ldm * h2);
+    o.Qm16l = L.take(l * P->ldm * h2);
+    o.Zn16h = L.take(l * P->ldn * h2);
+    o.Zn16l = L.take(l * P->ldn * h2);
+    if (is_bf16_prec(d->fit_prec)) {
+      for (int i = 0; i < 4; ++i) o.XC16[i] = L.take(cw * P->ldm * h2);
+      for (int i = 0; i < 4; ++i) o.XR16[i] = L.take(rw * P->ldn * h2);
+      o.Lh = L.take(wm * wm * h2);
+      o.Ll = L.take(wm * wm * h2);
+      o.Lih = L.take(wm * wm * h2);
+      o.Lil = L.take(wm * wm * h2);
+      o.T1h = L.take(wm * wm * h2);
+      o.T1l = L.take(wm * wm * h2);
+      o.Pnh = L.take(wm * P->nb * h2);
+      o.Pnl = L.take(wm * P->nb * h2);
+      o.Wh = L.take(P->m * rw * h2);
+      o.Wl = L.take(P->m * rw * h2);
+      o.Mh = L.take(cw * rw * h2);
+      o.Ml = L.take(cw * rw * h2);
+      o.U1h = L.take(cw * rw * h2);
+      o.U1l = L.take(cw * rw * h2);
+      o.U2h = L.take(cw * rw * h2);
+      o.U2l = L.take(cw * rw * h2);
+      o.Ph = L.take(P->m * rw * h2);
+    }
+  }
   P->need = L.cur;
   if (workspace_bytes) *workspace_bytes = P->need;
   *out = P;
@@ -518,9 +895,13 @@ bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, doubl
   if (!P) return BCUR_EINVAL;
   if (!P->ws) return BCUR_ESTATE;
   if (!A || !omega || !cs || !rs) return BCUR_EINVAL;
-  bcur_status_t st = P->d.a_dtype == BCUR_F64
-                         ? run_scores<double>(P, (const double*)A, (const double*)omega, cs, rs)
-                         : run_scores<float>(P, (const float*)A, (const float*)omega, cs, rs);
+  bcur_status_t st;
+  if (P->d.a_dtype == BCUR_F64)
+    st = run_scores<double>(P, (const double*)A, (const double*)omega, cs, rs);
+  else if (is_bf16_prec(P->d.sketch_prec))
+    st = run_scores16(P, (const float*)A, (const float*)omega, cs, rs);
+  else
+    st = run_scores<float>(P, (const float*)A, (const float*)omega, cs, rs);
   if (st == BCUR_OK) P->have_scores = true;
   return st;
 }
@@ -556,10 +937,13 @@ bcur_status_t bcur_fit(bcur_plan_t P, const void* A, const int32_t* ci, const in
   if (!P) return BCUR_EINVAL;
   if (!P->ws) return BCUR_ESTATE;
   if (!A || !ci || !ri) return BCUR_EINVAL;
-  bcur_status_t st =
-      P->d.a_dtype == BCUR_F64
-          ? run_fit<double>(P, (const double*)A, ci, ri, (double*)U, (double*)C, (double*)R)
-          : run_fit<float>(P, (const float*)A, ci, ri, (float*)U, (float*)C, (float*)R);
+  bcur_status_t st;
+  if (P->d.a_dtype == BCUR_F64)
+    st = run_fit<double>(P, (const double*)A, ci, ri, (double*)U, (double*)C, (double*)R);
+  else if (is_bf16_prec(P->d.fit_prec))
+    st = run_fit16(P, (const float*)A, ci, ri, (float*)U, (float*)C, (float*)R);
+  else
+    st = run_fit<float>(P, (const float*)A, ci, ri, (float*)U, (float*)C, (float*)R);
   P->have_fit = (st == BCUR_OK);
   return st;
 }
@@ -568,8 +952,9 @@ bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {
   if (!P) return BCUR_EINVAL;
   if (!P->ws || !P->have_fit) return BCUR_ESTATE;
   if (!A || !out) return BCUR_EINVAL;
-  return P->d.a_dtype == BCUR_F64 ? run_error<double>(P, (const double*)A, out)
-                                  : run_error<float>(P, (const float*)A, out);
+  if (P->d.a_dtype == BCUR_F64) return run_error<double>(P, (const double*)A, out);
+  if (is_bf16_prec(P->d.fit_prec)) return run_error16(P, (const float*)A, out);
+  return run_error<float>(P, (const float*)A, out);
 }
 
 bcur_status_t bcur_rank(bcur_plan_t P, int64_t* c, int64_t* r, int64_t* rank_c, int64_t* rank_r) {
@@ -639,7 +1024,11 @@ bcur_status_t bcur_residual(const void* X, int64_t ldx, const void* Pm, int64_t 
   g.ldx = ldx;
   g.partials = (double*)workspace;
   int64_t np = 0;
-  if (dtype == BCUR_F64) {
+  if (dtype == BCUR_BF16) {  // X FP32, P and Q BF16: tensor cores only
+    if (prec != BCUR_BF16) return BCUR_EINVAL;
+    g.ab_bf16 = 1;
+    BCUR_TRY(gemm_tc_resid(g, prec, s, &np));
+  } else if (dtype == BCUR_F64) {
     if (prec != BCUR_F64) return BCUR_EINVAL;
     BCUR_TRY(gemm_resid<double>(g, prec, s, &np));
   } else if (dtype == BCUR_F32) {
@@ -661,7 +1050,12 @@ bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t 
     if (prec != BCUR_F64) return BCUR_EINVAL;
     return gemm_simt<double>(g, s);
   }
-  if (dtype != BCUR_F32 || prec == BCUR_F64) return BCUR_EINVAL;
+  if (dtype == BCUR_BF16) {  // BF16 A and B, FP32 D: tensor cores only
+    if (prec != BCUR_BF16) return BCUR_EINVAL;
+    g.ab_bf16 = 1;
+    return gemm_tc(g, prec, s);
+  }
+  if (dtype != BCUR_F32 || prec == BCUR_F64 || prec == BCUR_BF16) return BCUR_EINVAL;
   if (is_tc_prec(prec)) return gemm_tc(g, prec, s);  // no silent fallback here
   return gemm_simt<float>(g, s);
 }

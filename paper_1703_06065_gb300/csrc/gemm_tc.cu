@@ -1,9 +1,752 @@
-// tcgen05 tensor-core GEMM (placeholder until the kernel lands).
+// Dense GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   D (Mm x Nm, FP32) = alpha * A (Mm x K) . B (Nm x K)^T        ("MMA space")
+//
+// Operands are BF16 (kind::f16), or FP32 read as TF32 (kind::tf32).  A BF16
+// operand is either K-major (rows contiguous along K) or MN-major (contiguous
+// along M / N); TF32 operands must be K-major (the MMA reads zeros for an
+// MN-major TF32 operand on sm_103a, so such calls are refused).  TMA brings
+// 128-byte-wide boxes into shared memory with the 128-byte swizzle, and the
+// shared-memory matrix descriptors describe the same canonical layout to the
+// MMA.  Accumulators live in tensor memory (TMEM), double-buffered so that
+// the epilogue of one tile overlaps the main loop of the next.
+//
+// Split precision ("parts" = 3): an FP32 value x is carried as a BF16 pair
+// hi = bf16(x), lo = bf16(x - hi), and A B is accumulated as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi, which keeps about 16 mantissa bits.  The
+// three products are consecutive K-slices of one accumulation: iteration i
+// of a tile's K loop handles K-block klo + i/3 with the operand pair i%3.
+//
+// CTA = 6 warps, persistent over a static tile schedule:
+//   warp 0      TMA producer (one elected thread)
+//   warp 1      TMEM allocator + MMA issuer (one elected thread)
+//   warps 2..5  epilogue: tcgen05.ld from TMEM (each warp owns the 32 TMEM
+//               lanes of its rank within the warpgroup), then store, split-K
+//               partial store, or fused residual reduction.
+// Every mbarrier wait is bounded (2 s on %globaltimer); a wait that runs out
+// records BCUR_ETIMEOUT, the kernel drains what it issued and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace bcur {
-bool gemm_tc_available() { return false; }
-int64_t gemm_tc_resid_ctas(int64_t, int64_t) { return 0; }
-bcur_status_t gemm_tc(const GemmDesc&, int, cudaStream_t) { return BCUR_ENOTSUP; }
-bcur_status_t gemm_tc_resid(const GemmDesc&, int, cudaStream_t, int64_t*) { return BCUR_ENOTSUP; }
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int kThreads = 192;
+constexpr int kStageABytes = BM * 128;  // 128 rows (or MN elements) x 128 bytes of K
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+enum Epi { EPI_STORE = 0, EPI_PARTIAL = 1, EPI_RESID = 2 };
+
+struct Params {
+  int Mm, Nm, K;
+  int parts;             // 1, or 3 for the split-precision product
+  int a_mn, b_mn;        // 1: operand is MN-major
+  int tiles_m, tiles_n, ksplit, kblocks;
+  int triA, triB;        // 1 lower / 2 upper (A: A(i,k)=0 for k>i / k<i; B: B(k,j)=0 for k<j / k>j)
+  int tri_out;           // 1: keep row >= col, 2: keep row <= col (MMA space)
+  float alpha, beta;
+  float* D;              // FP32 output (may be null)
+  __nv_bfloat16* Dh;     // BF16 hi part of the output (may be null)
+  __nv_bfloat16* Dl;     // BF16 lo part of the output (may be null)
+  int64_t ldd;
+  int transD;            // D stored as D^T (element (i,j) at D[j*ldd + i])
+  float* part;           // split-K partial slices (Mm x Nm, row-major each)
+  const float* X;        // residual reference matrix (Mm x Nm, ldx)
+  int64_t ldx;
+  double* partials;      // per-CTA {sum (X - acc)^2, sum X^2}
+  int* status;
+};
+
+template <int KIND> struct KindCfg;
+template <> struct KindCfg<0> {  // TF32 from FP32 storage
+  static constexpr int esize = 4, bk = 32, kstep_rows = 8, box_mn = 32;
+};
+template <> struct KindCfg<1> {  // BF16
+  static constexpr int esize = 2, bk = 64, kstep_rows = 16, box_mn = 64;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the status word set) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
+                                          volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (now_ns() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      if (status) atomicCAS(status, 0, (int)BCUR_ETIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  if constexpr (KIND == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+// 32 lanes x 32 consecutive 32-bit columns: thread t of the warp receives
+// lane (quarter*32 + t), columns [col, col+32).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle, sm_100 format.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version
+  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format, majors, N, M.
+__host__ __device__ inline uint32_t idesc(int kind, int a_mn, int b_mn, int M, int N) {
+  uint32_t d = 0;
+  d |= 1u << 4;                          // D format F32
+  const uint32_t fmt = kind == 0 ? 2u : 1u;  // TF32 : BF16
+  d |= fmt << 7;
+  d |= fmt << 10;
+  d |= (uint32_t)(a_mn & 1) << 15;
+  d |= (uint32_t)(b_mn & 1) << 16;
+  d |= (uint32_t)(N >> 3) << 17;
+  d |= (uint32_t)(M >> 4) << 24;
+  return d;
+}
+
+// Tensor maps of the operands: [0] = hi (or the only part), [1] = lo.
+struct Maps {
+  CUtensorMap a[2];
+  CUtensorMap b[2];
+};
+
+struct Unit {
+  int m0, n0, z, klo, khi, skip;
+};
+
+template <int BN, int KIND>
+__device__ __forceinline__ Unit decode(const Params& p, int u) {
+  constexpr int BK = KindCfg<KIND>::bk;
+  Unit w;
+  const int tile = u / p.ksplit;
+  w.z = u % p.ksplit;
+  // grouped raster: 16 M-tiles per group for L2 reuse of the B panel
+  const int GM = 16;
+  const int per_group = GM * p.tiles_n;
+  const int g = tile / per_group;
+  const int first = g * GM;
+  const int gm = min(GM, p.tiles_m - first);
+  const int r = tile % per_group;
+  const int tm = first + r % gm;
+  const int tn = r / gm;
+  w.m0 = tm * BM;
+  w.n0 = tn * BN;
+  const int chunk = (p.kblocks + p.ksplit - 1) / p.ksplit;
+  w.klo = w.z * chunk;
+  w.khi = min(p.kblocks, w.klo + chunk);
+  if (p.triA == 1) w.khi = min(w.khi, (w.m0 + BM + BK - 1) / BK);
+  if (p.triA == 2) w.klo = max(w.klo, w.m0 / BK);
+  if (p.triB == 1) w.klo = max(w.klo, w.n0 / BK);
+  if (p.triB == 2) w.khi = min(w.khi, (w.n0 + BN + BK - 1) / BK);
+  w.skip = 0;
+  if (p.tri_out == 1 && w.m0 + BM - 1 < w.n0) w.skip = 1;
+  if (p.tri_out == 2 && w.n0 + BN - 1 < w.m0) w.skip = 1;
+  return w;
+}
+
+template <int BN> struct StageCfg {
+  static constexpr int kStageBBytes = BN * 128;
+  static constexpr int kStageBytes = kStageABytes + kStageBBytes;
+  static constexpr int kStages = 196608 / kStageBytes;  // 192 KB of stages
+  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+};
+
+template <int BN, int KIND, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ Maps maps, const Params p) {
+  using SC = StageCfg<BN>;
+  using KC = KindCfg<KIND>;
+  constexpr int S = SC::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * SC::kStageBytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* red = reinterpret_cast<double*>(tmem_slot + 4);  // 8 doubles
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[i])) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[i])) : "memory");
+    }
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)SC::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int total = p.tiles_m * p.tiles_n * p.ksplit;
+  constexpr int BKR = KC::bk;  // K rows per stage for an MN-major operand
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+        const Unit w = decode<BN, KIND>(p, u);
+        if (w.skip || w.klo >= w.khi) continue;
+        const int n_it = (w.khi - w.klo) * p.parts;
+        for (int i = 0; i < n_it; ++i, ++it) {
+          const int kb = w.klo + i / p.parts, part = i % p.parts;
+          const CUtensorMap* ma = &maps.a[part == 2 ? 1 : 0];
+          const CUtensorMap* mb = &maps.b[part == 1 ? 1 : 0];
+          const uint32_t stage = it % S, round = it / S;
+          if (!mbar_wait(&empty[stage], (round & 1) ^ 1, p.status, abort_flag)) { ok = false; break; }
+          uint8_t* sa = smem + stage * SC::kStageBytes;
+          uint8_t* sb = sa + kStageABytes;
+          mbar_expect_tx(&full[stage], SC::kStageBytes);
+          if (!p.a_mn) {
+            tma_load_2d(sa, ma, &full[stage], kb * KC::bk, w.m0);
+          } else {
+#pragma unroll
+            for (int b = 0; b < BM / KC::box_mn; ++b)
+              tma_load_2d(sa + b * (BKR * 128), ma, &full[stage], w.m0 + b * KC::box_mn, kb * BKR);
+          }
+          if (!p.b_mn) {
+            tma_load_2d(sb, mb, &full[stage], kb * KC::bk, w.n0);
+          } else {
+#pragma unroll
+            for (int b = 0; b < BN / KC::box_mn; ++b)
+              tma_load_2d(sb + b * (BKR * 128), mb, &full[stage], w.n0 + b * KC::box_mn, kb * BKR);
+          }
+        }
+      }
+      // Drain: the last load issued on each stage must have landed before exit.
+      const uint32_t n_last = it < (uint32_t)S ? it : (uint32_t)S;
+      for (uint32_t j = 0; j < n_last; ++j) {
+        const uint32_t i2 = it - 1 - j;
+        const uint32_t stage = i2 % S, round = i2 / S;
+        const uint64_t t0 = now_ns();
+        while (!mbar_try_wait(&full[stage], round & 1) && now_ns() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t id = idesc(KIND, p.a_mn, p.b_mn, BM, BN);
+      uint32_t it = 0, tu = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+        const Unit w = decode<BN, KIND>(p, u);
+        if (w.skip || w.klo >= w.khi) continue;
+        const uint32_t acc = tu & 1, use = tu >> 1;
+        if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, p.status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * BN;
+        const int n_it = (w.khi - w.klo) * p.parts;
+        for (int i = 0; i < n_it; ++i, ++it) {
+          const uint32_t stage = it % S, round = it / S;
+          if (!mbar_wait(&full[stage], round & 1, p.status, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * SC::kStageBytes);
+          const uint32_t sb = sa + kStageABytes;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t ad = p.a_mn ? sdesc(sa + j * KC::kstep_rows * 128, BKR * 128, 1024)
+                                       : sdesc(sa + j * 32, 16, 1024);
+            const uint64_t bd = p.b_mn ? sdesc(sb + j * KC::kstep_rows * 128, BKR * 128, 1024)
+                                       : sdesc(sb + j * 32, 16, 1024);
+            tc_mma<KIND>(d_tmem, ad, bd, id, (i > 0 || j > 0) ? 1u : 0u);
+          }
+          tc_commit(&empty[stage]);
+        }
+        if (!ok) break;
+        tc_commit(&tfull[acc]);
+        ++tu;
+      }
+      // All MMAs this thread issued complete before TMEM is released.
+      tc_commit(done);
+      const uint64_t t0 = now_ns();
+      while (!mbar_try_wait(done, 0) && now_ns() - t0 < kWaitNs) {
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;  // TMEM lanes [32*quarter, 32*quarter + 32)
+    double e2 = 0.0, x2 = 0.0;
+    uint32_t tu = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      const Unit w = decode<BN, KIND>(p, u);
+      if (w.skip) continue;
+      const bool has_acc = w.klo < w.khi;
+      const uint32_t acc = tu & 1, use = tu >> 1;
+      if (has_acc) {
+        if (!mbar_wait(&tfull[acc], use & 1, p.status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+      }
+      const int row = w.m0 + quarter * 32 + lane;
+      const bool row_ok = row < p.Mm;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        __syncwarp();  // tcgen05.ld is warp-aligned: reconverge before it
+        if (has_acc) {
+          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN + c0, v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        }
+        const int col0 = w.n0 + c0;
+        if (col0 >= p.Nm) continue;
+        if constexpr (EPI == EPI_STORE) {
+          if (!row_ok) continue;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = col0 + i;
+            if (col >= p.Nm) break;
+            if (p.tri_out == 1 && row < col) continue;
+            if (p.tri_out == 2 && row > col) continue;
+            const int64_t off = p.transD ? (int64_t)col * p.ldd + row : (int64_t)row * p.ldd + col;
+            float o = p.alpha * v[i];
+            if (p.beta != 0.f) o = fmaf(p.beta, p.D[off], o);
+            if (p.D) p.D[off] = o;
+            if (p.Dh) {
+              const __nv_bfloat16 h = __float2bfloat16_rn(o);
+              p.Dh[off] = h;
+              if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+            }
+          }
+        } else if constexpr (EPI == EPI_PARTIAL) {
+          if (!row_ok) continue;
+          float* prow = p.part + (int64_t)w.z * p.Mm * p.Nm + (int64_t)row * p.Nm;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = col0 + i;
+            if (col >= p.Nm) break;
+            prow[col] = v[i];
+          }
+        } else {  // EPI_RESID
+          if (!row_ok) continue;
+          const float* xr = p.X + (int64_t)row * p.ldx;
+          float se = 0.f, sx = 0.f;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = col0 + i;
+            if (col >= p.Nm) break;
+            const float x = xr[col];
+            const float d = x - p.alpha * v[i];
+            se = fmaf(d, d, se);
+            sx = fmaf(x, x, sx);
+          }
+          e2 += (double)se;
+          x2 += (double)sx;
+        }
+      }
+      if (has_acc) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        ++tu;
+      }
+    }
+    if constexpr (EPI == EPI_RESID) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+      }
+      if (lane == 0) {
+        red[2 * (warp - 2)] = e2;
+        red[2 * (warp - 2) + 1] = x2;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if constexpr (EPI == EPI_RESID) {
+    if (threadIdx.x == 0) {
+      double se = 0.0, sx = 0.0;
+      for (int i = 0; i < 4; ++i) { se += red[2 * i]; sx += red[2 * i + 1]; }
+      p.partials[2 * blockIdx.x] = se;
+      p.partials[2 * blockIdx.x + 1] = sx;
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"((uint32_t)SC::kTmemCols)
+                 : "memory");
+  }
+}
+
+// Sum the split-K slices in a fixed order and apply alpha / beta / layout.
+__global__ void splitk_reduce_kernel(Params p) {
+  const int64_t total = (int64_t)p.Mm * p.Nm;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / p.Nm), col = (int)(e % p.Nm);
+    if (p.tri_out == 1 && row < col) continue;
+    if (p.tri_out == 2 && row > col) continue;
+    float s = 0.f;
+    for (int z = 0; z < p.ksplit; ++z) s += p.part[(int64_t)z * total + e];
+    const int64_t off = p.transD ? (int64_t)col * p.ldd + row : (int64_t)row * p.ldd + col;
+    float o = p.alpha * s;
+    if (p.beta != 0.f) o = fmaf(p.beta, p.D[off], o);
+    if (p.D) p.D[off] = o;
+    if (p.Dh) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(o);
+      p.Dh[off] = h;
+      if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 148;
+    }
+  }
+  return n;
+}
+
+bool tc_device_ok() {
+  static int ok = -1;
+  if (ok < 0) {
+    int dev = 0, major = 0, minor = 0;
+    ok = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+      ok = (major == 10 && minor == 3) ? 1 : 0;
+    else
+      cudaGetLastError();
+  }
+  return ok == 1 && encode_fn() != nullptr;
+}
+
+// Operand in MMA space: rows = MN index when K-major (inner dim K), or
+// rows = K index when MN-major (inner dim MN).
+struct Operand {
+  const void* ptr;
+  int64_t ld;      // elements between consecutive outer-dimension entries
+  int mn_major;
+  int64_t mn, k;   // extents
+};
+
+bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn) {
+  const int esize = kind == 0 ? 4 : 2;
+  const int box_inner = 128 / esize;  // 128 bytes
+  const uintptr_t a = reinterpret_cast<uintptr_t>(op.ptr);
+  if (a % 16 != 0 || (op.ld * esize) % 16 != 0) return false;
+  cuuint64_t dims[2];
+  cuuint64_t strides[1] = {(cuuint64_t)(op.ld * esize)};
+  cuuint32_t box[2];
+  cuuint32_t estr[2] = {1, 1};
+  if (!op.mn_major) {
+    dims[0] = (cuuint64_t)op.k;
+    dims[1] = (cuuint64_t)op.mn;
+    box[0] = (cuuint32_t)box_inner;
+    box[1] = (cuuint32_t)box_rows_mn;  // MN rows of the tile
+  } else {
+    dims[0] = (cuuint64_t)op.mn;
+    dims[1] = (cuuint64_t)op.k;
+    box[0] = (cuuint32_t)box_inner;   // MN elements per box
+    box[1] = (cuuint32_t)(kind == 0 ? KindCfg<0>::bk : KindCfg<1>::bk);  // K rows per stage
+  }
+  if (op.ld < (int64_t)dims[0]) return false;
+  auto fn = encode_fn();
+  if (!fn) return false;
+  CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                  2, const_cast<void*>(op.ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int KIND, int EPI>
+bcur_status_t launch_inst(const Maps& maps, const Params& p, int grid, cudaStream_t s) {
+  using SC = StageCfg<BN>;
+  static bool attr = false;
+  if (!attr) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, KIND, EPI>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SC::kSmemBytes));
+    attr = true;
+  }
+  tc_gemm_kernel<BN, KIND, EPI><<<grid, kThreads, SC::kSmemBytes, s>>>(maps, p);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+template <int KIND, int EPI>
+bcur_status_t launch_bn(int BN, const Maps& maps, const Params& p, int grid, cudaStream_t s) {
+  switch (BN) {
+    case 64: return launch_inst<64, KIND, EPI>(maps, p, grid, s);
+    case 128: return launch_inst<128, KIND, EPI>(maps, p, grid, s);
+    case 256: return launch_inst<256, KIND, EPI>(maps, p, grid, s);
+  }
+  return BCUR_EINVAL;
+}
+
+// Map one GEMM (GemmDesc convention, D row-major M x N) onto MMA space and
+// launch.  `epi` selects store or residual.  Returns ENOTSUP if the operands
+// cannot be described by TMA (alignment) or the device is not sm_103.
+bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t* n_partials) {
+  // TF32 reads FP32 storage; BF16 needs BF16 storage of both operands.
+  if (!((prec == BCUR_TF32 && !d.ab_bf16) || (prec == BCUR_BF16 && d.ab_bf16)))
+    return BCUR_ENOTSUP;
+  if (!tc_device_ok()) return BCUR_ENOTSUP;
+  if (d.M <= 0 || d.N <= 0) {
+    if (n_partials) *n_partials = 0;
+    return BCUR_OK;
+  }
+  if (d.K <= 0 || d.M > INT32_MAX || d.N > INT32_MAX || d.K > INT32_MAX) return BCUR_ENOTSUP;
+  if (d.ksplit > 1) return BCUR_ENOTSUP;
+  const int kind = d.ab_bf16 ? 1 : 0;
+  const int parts = d.parts == 3 ? 3 : 1;
+  if (parts == 3 && (!kind || !d.A_lo || !d.B_lo)) return BCUR_EINVAL;
+  // Small M with a long N: compute D^T = B_op^T A_op^T so the long dimension
+  // runs along the 128-row MMA tile and D is stored transposed.
+  const bool swap = (epi == EPI_STORE) && d.M < 128 && d.N >= 2 * d.M;
+  Operand A, B, Al, Bl;  // MMA-space A (Mm x K) and B (Nm x K), hi and lo
+  int64_t Mm, Nm;
+  int triA, triB, tri_out = d.out_lower ? 1 : 0;
+  if (!swap) {
+    Mm = d.M; Nm = d.N;
+    A = {d.A, d.lda, d.transA ? 1 : 0, d.M, d.K};
+    B = {d.B, d.ldb, d.transB ? 0 : 1, d.N, d.K};
+    Al = {d.A_lo ? d.A_lo : d.A, d.lda, d.transA ? 1 : 0, d.M, d.K};
+    Bl = {d.B_lo ? d.B_lo : d.B, d.ldb, d.transB ? 0 : 1, d.N, d.K};
+    triA = d.triA;
+    triB = d.triB;
+  } else {
+    Mm = d.N; Nm = d.M;
+    A = {d.B, d.ldb, d.transB ? 0 : 1, d.N, d.K};
+    B = {d.A, d.lda, d.transA ? 1 : 0, d.M, d.K};
+    Al = {d.B_lo ? d.B_lo : d.B, d.ldb, d.transB ? 0 : 1, d.N, d.K};
+    Bl = {d.A_lo ? d.A_lo : d.A, d.lda, d.transA ? 1 : 0, d.M, d.K};
+    triA = d.triB == 1 ? 2 : (d.triB == 2 ? 1 : 0);
+    triB = d.triA == 1 ? 2 : (d.triA == 2 ? 1 : 0);
+    if (tri_out) tri_out = 2;
+  }
+  // TF32 operands must be K-major on this tensor core.
+  if (kind == 0 && (A.mn_major || B.mn_major)) return BCUR_ENOTSUP;
+  const int BN = Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256);
+  Maps maps;
+  if (!make_map(&maps.a[0], A, kind, BM) || !make_map(&maps.b[0], B, kind, BN) ||
+      !make_map(&maps.a[1], Al, kind, BM) || !make_map(&maps.b[1], Bl, kind, BN))
+    return BCUR_ENOTSUP;
+  Params p{};
+  p.Mm = (int)Mm; p.Nm = (int)Nm; p.K = (int)d.K;
+  p.parts = parts;
+  p.Dh = (__nv_bfloat16*)d.Dh;
+  p.Dl = (__nv_bfloat16*)d.Dl;
+  p.a_mn = A.mn_major; p.b_mn = B.mn_major;
+  p.tiles_m = (int)ceil_div(Mm, BM);
+  p.tiles_n = (int)ceil_div(Nm, BN);
+  p.kblocks = (int)ceil_div(d.K, kind == 0 ? KindCfg<0>::bk : KindCfg<1>::bk);
+  p.triA = triA; p.triB = triB; p.tri_out = tri_out;
+  p.alpha = (float)d.alpha; p.beta = (float)d.beta;
+  p.D = (float*)d.D; p.ldd = d.ldd; p.transD = swap ? 1 : 0;
+  p.X = (const float*)d.X; p.ldx = d.ldx; p.partials = d.partials;
+  p.status = d.status;
+  p.ksplit = 1;
+  const int sms = sm_count();
+  const int tiles = p.tiles_m * p.tiles_n;
+  // Split K when there are too few tiles to fill the GPU and a scratch
+  // buffer for the partial slices is available.
+  if (epi == EPI_STORE && d.scratch && tiles < sms && p.kblocks >= 8) {
+    int ks = std::min<int64_t>(std::max<int64_t>(1, (4 * sms) / tiles), p.kblocks / 4);
+    const int64_t slice = Mm * Nm * 4;
+    ks = (int)std::min<int64_t>(ks, (int64_t)d.scratch_bytes / slice);
+    if (ks > 1) {
+      p.ksplit = ks;
+      p.part = (float*)d.scratch;
+    }
+  }
+  const int units = tiles * p.ksplit;
+  const int grid = std::max(1, std::min(units, sms));
+  if (epi == EPI_RESID) {
+    if (n_partials) *n_partials = grid;
+    return kind == 0 ? launch_bn<0, EPI_RESID>(BN, maps, p, grid, s)
+                     : launch_bn<1, EPI_RESID>(BN, maps, p, grid, s);
+  }
+  if (p.ksplit > 1) {
+    BCUR_TRY((kind == 0 ? launch_bn<0, EPI_PARTIAL>(BN, maps, p, grid, s)
+                        : launch_bn<1, EPI_PARTIAL>(BN, maps, p, grid, s)));
+    const int64_t total = Mm * Nm;
+    const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4 * sms);
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(p);
+    BCUR_LAUNCH_CHECK();
+    return BCUR_OK;
+  }
+  return kind == 0 ? launch_bn<0, EPI_STORE>(BN, maps, p, grid, s)
+                   : launch_bn<1, EPI_STORE>(BN, maps, p, grid, s);
+}
+
+}  // namespace tc
+
+bool gemm_tc_available() { return tc::tc_device_ok(); }
+
+int64_t gemm_tc_resid_ctas(int64_t, int64_t) { return 1024; }
+
+bcur_status_t gemm_tc(const GemmDesc& d, int prec, cudaStream_t s) {
+  if (d.batch <= 1) return tc::run(d, prec, s, tc::EPI_STORE, nullptr);
+  // independent problems: one launch each (tensor maps are per pointer)
+  for (int b = 0; b < d.batch; ++b) {
+    GemmDesc e = d;
+    e.batch = 1;
+    const size_t es = d.ab_bf16 ? 2 : 4;
+    e.A = (const char*)d.A + b * d.sA * es;
+    e.B = (const char*)d.B + b * d.sB * es;
+    if (d.A_lo) e.A_lo = (const char*)d.A_lo + b * d.sA * es;
+    if (d.B_lo) e.B_lo = (const char*)d.B_lo + b * d.sB * es;
+    if (d.D) e.D = (float*)d.D + b * d.sD;
+    if (d.Dh) e.Dh = (__nv_bfloat16*)d.Dh + b * d.sD;
+    if (d.Dl) e.Dl = (__nv_bfloat16*)d.Dl + b * d.sD;
+    bcur_status_t st = tc::run(e, prec, s, tc::EPI_STORE, nullptr);
+    if (st != BCUR_OK) return st;
+  }
+  return BCUR_OK;
+}
+
+bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* n_partials) {
+  if (d.batch != 1) return BCUR_ENOTSUP;
+  return tc::run(d, prec, s, tc::EPI_RESID, n_partials);
+}
+
 }  // namespace bcur

@@ -1,6 +1,8 @@
 // Internal launchers shared between the translation units of the library.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace bcur {
@@ -30,6 +32,20 @@ struct GemmDesc {
   // Residual epilogue: accumulate sum (X - alpha*A_op B_op)^2 and sum X^2 per
   // CTA into partials[2 * cta] (FP64), instead of storing D.
   const void* X = nullptr; int64_t ldx = 0; double* partials = nullptr;
+  // Optional device scratch the tensor-core path may use for split-K
+  // partial slices, and a status word for device-detected errors.
+  void* scratch = nullptr; size_t scratch_bytes = 0;
+  int* status = nullptr;
+  // A and B are stored as BF16 (tensor-core BF16 path only).  With parts = 3
+  // the operands are BF16 pairs (A = hi, A_lo = lo; same for B) and the
+  // product is A_hi B_hi + A_hi B_lo + A_lo B_hi.  D (FP32) and/or the BF16
+  // pair Dh, Dl (same layout and ldd as D) receive the result.
+  int ab_bf16 = 0;
+  int parts = 1;
+  const void* A_lo = nullptr;
+  const void* B_lo = nullptr;
+  void* Dh = nullptr;
+  void* Dl = nullptr;
 };
 
 template <typename T> bcur_status_t gemm_simt(const GemmDesc& d, cudaStream_t s);
@@ -114,5 +130,11 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
                      cudaStream_t s);
 
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+// Split an FP32 matrix (rows x cols, ldx) into BF16 pairs: hi = bf16(x),
+// lo = bf16(x - hi) (round to nearest even both times); outputs have
+// leading dimension ldo; lo may be null (hi only).
+bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                         __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s);
 
 }  // namespace bcur

@@ -6,6 +6,8 @@
 // and fixed-order FP64 reductions.
 #include <float.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace bcur {
@@ -603,6 +605,58 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s) {
   if (bytes == 0) return BCUR_OK;
   BCUR_CUDA_TRY(cudaMemsetAsync(p, 0, bytes, s));
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 -> BF16 hi/lo pairs
+// ---------------------------------------------------------------------------
+__global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                                  __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, int vec4) {
+  for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = X + r * ldx;
+    __nv_bfloat16* hr = hi + r * ldo;
+    __nv_bfloat16* lr = lo ? lo + r * ldo : nullptr;
+    if (vec4) {
+      const int64_t n4 = cols / 4;
+      for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n4;
+           c += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = reinterpret_cast<const float4*>(xr)[c];
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y);
+        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v.z, v.w);
+        reinterpret_cast<__nv_bfloat162*>(hr)[2 * c] = h01;
+        reinterpret_cast<__nv_bfloat162*>(hr)[2 * c + 1] = h23;
+        if (lr) {
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          reinterpret_cast<__nv_bfloat162*>(lr)[2 * c] = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+          reinterpret_cast<__nv_bfloat162*>(lr)[2 * c + 1] =
+              __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+        }
+      }
+    } else {
+      for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cols;
+           c += (int64_t)gridDim.x * blockDim.x) {
+        const float v = xr[c];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hr[c] = h;
+        if (lr) lr[c] = __float2bfloat16_rn(v - __bfloat162float(h));
+      }
+    }
+  }
+}
+
+bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                         __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return BCUR_OK;
+  const int vec4 = (cols % 4 == 0) && (ldx % 4 == 0) && (ldo % 4 == 0) &&
+                   ((uintptr_t)X % 16 == 0) && ((uintptr_t)hi % 8 == 0) &&
+                   (!lo || (uintptr_t)lo % 8 == 0);
+  const int64_t per_row = vec4 ? cols / 4 : cols;
+  const int64_t gx = std::min<int64_t>(ceil_div(per_row, 256), 64);
+  const int64_t gy = std::min<int64_t>(rows, 65535 / std::max<int64_t>(1, 1));
+  split_bf16_kernel<<<dim3((unsigned)gx, (unsigned)std::min<int64_t>(gy, 8192)), 256, 0, s>>>(
+      X, ldx, rows, cols, hi, lo, ldo, vec4);
+  BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 

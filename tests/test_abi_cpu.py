@@ -66,7 +66,11 @@ def _plan(lib, **kw):
 @pytest.mark.parametrize("kw,want", [
     (dict(), 0),
     (dict(dtype=0, sp=0, fp=0), 0),
-    (dict(sp=2, fp=3), 0),
+    (dict(sp=2, fp=2), 7),                   # TF32 stages are not offered by plans
+    (dict(sp=3, fp=4), 0),                   # BF16 sketch, split-BF16 fit
+    (dict(sp=4, fp=3), 7),                   # a one-term BF16 fit is refused
+    (dict(sp=4, fp=4), 0),
+    (dict(sp=5, fp=1), 1),
     (dict(lda=100), 1),                      # lda < n
     (dict(k=100, p=40), 1),                  # l > 128
     (dict(k=0), 1),

@@ -156,3 +156,26 @@ def test_error_is_deterministic():
     plan.fit(A, ci, ri)
     b = plan.error(A).cpu().numpy()
     assert a.tobytes() == b.tobytes()
+
+
+@pytest.mark.parametrize("sp,fp,score_tol", [
+    ("bf16", "f32", 2e-2), ("f32", "bf16x3", 1e-4), ("bf16x3", "bf16x3", 1e-4),
+    ("bf16", "bf16x3", 2e-2)])
+def test_haar_tensor_core_paths(sp, fp, score_tol):
+    """Tensor-core sketch and/or fit.  The relative error stays within 1e-3 of
+    the FP64 oracle's (the benchmark's accuracy gate) and the returned factors
+    reproduce the oracle's approximation CUR.  BF16 sketches move the scores
+    by about the BF16 unit round-off over the spectral gap; split BF16 keeps
+    about 16 bits."""
+    p = bi.scaled_haar(1536, 2048, 64, k=10, p=10, q=2, g_col=6, g_row=5, seed=7, rank=120,
+                       noise=1e-4)
+    ref, gpu, plan = run_problem(p, sp, fp)
+    assert abs(gpu["err"][1] - ref["rel"]) <= 1e-3
+    for side in ("col", "row"):
+        d = np.max(np.abs(gpu[f"{side}_scores"] - ref[f"{side}_scores"]))
+        assert d <= score_tol * np.max(ref[f"{side}_scores"]), (side, d)
+    c, r = gpu["rank"][0], gpu["rank"][1]
+    cur_gpu = gpu["C"][:, :c] @ gpu["U"][:c, :r] @ gpu["R"][:r]
+    cur_orc = ref["C"] @ ref["U"] @ ref["R"]
+    A = p.matrix().astype(np.float64)
+    assert np.linalg.norm(cur_gpu - cur_orc) <= 1e-3 * np.linalg.norm(A)
