@@ -95,18 +95,13 @@ def haar_spectrum_device(m: int, n: int, rank: int, decay: float, noise: float, 
     import torch
 
     dtype = dtype or torch.float32
+    # The thin Haar factors are drawn and orthonormalised on the host (NumPy),
+    # only the m x n product and the noise are formed on the device.
+    g = rng(seed, STREAM_MATRIX)
+    u = torch.from_numpy(haar_orthonormal(g, m, rank)).to(device)
+    v = torch.from_numpy(haar_orthonormal(g, n, rank)).to(device)
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed) * 1000003 + STREAM_MATRIX)
-
-    def haar(rows: int) -> "torch.Tensor":
-        z = torch.randn(rows, rank, generator=gen, device=device, dtype=torch.float64)
-        q, rr = torch.linalg.qr(z)
-        d = torch.sign(torch.diagonal(rr))
-        d[d == 0] = 1.0
-        return q * d
-
-    u = haar(m)
-    v = haar(n)
     sig = torch.arange(1, rank + 1, device=device, dtype=torch.float64) ** (-decay)
     us = (u * sig)
     a = torch.empty(m, n, device=device, dtype=dtype)

@@ -456,9 +456,15 @@ bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) {
   return gemm_tc(d, BCUR_BF16, P->stream);
 }
 
-// Blocked Cholesky G = L L^T (w x w, FP32, lower part) and L^{-1}: FP32
-// diagonal blocks and panels on CUDA cores, trailing updates and the
-// inverse-by-doubling products on tensor cores with `parts` BF16 terms.
+// Blocked Cholesky G = L L^T (w x w, FP32, lower part) and L^{-1}.  Two
+// levels: outer panels of kOuter columns whose trailing update is one large
+// tensor-core GEMM (K = kOuter), and inside each outer panel leaves of nb
+// columns (FP32 diagonal factorisation and panel solve on CUDA cores, the
+// update of the rest of the outer panel on tensor cores).  The inverse is
+// assembled by doubling (X21 = -X22 L21 X11) on tensor cores.  Tensor-core
+// products use `parts` BF16 terms.
+constexpr int64_t kOuter = 1024;
+
 bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, int64_t w, int parts,
                                  int* kept, double tol) {
   cudaStream_t s = P->stream;
@@ -473,21 +479,37 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, i
   BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(float), s));
   BCUR_TRY(fill_zero(kept, sizeof(int), s));
   BCUR_TRY(max_diag<float>(G, w, w, md, s));
-  for (int64_t j0 = 0; j0 < w; j0 += nb) {
-    BCUR_TRY(potrf_diag<float>(G, w, L, w, Li, w, j0, nb, md, tol, kept, s));
-    const int64_t j1 = j0 + nb;
-    if (j1 >= w) break;
-    GemmDesc pn = mk(w - j1, nb, nb, G + j1 * w + j0, w, 0, Li + j0 * w + j0, w, 1,
-                     L + j1 * w + j0, w);
-    pn.triB = 2;
-    BCUR_TRY(gemm_simt<float>(pn, s));
-    BCUR_TRY(split(P, L + j1 * w + j0, w, w - j1, nb, Pn, nb));
-    GemmDesc tr = mk16(w - j1, w - j1, nb, Pn, nb, 0, Pn, nb, 1, w);
-    tr.D = G + j1 * w + j1;
-    tr.alpha = -1.0;
-    tr.beta = 1.0;
-    tr.out_lower = 1;
-    BCUR_TRY(g16(P, tr, parts));
+  for (int64_t J0 = 0; J0 < w; J0 += kOuter) {
+    const int64_t J1 = std::min(w, J0 + kOuter);
+    for (int64_t j0 = J0; j0 < J1; j0 += nb) {
+      BCUR_TRY(potrf_diag<float>(G, w, L, w, Li, w, j0, nb, md, tol, kept, s));
+      const int64_t j1 = j0 + nb;
+      if (j1 >= w) break;
+      // panel below the leaf, full height: L[j1:, j0:j1] = G[j1:, j0:j1] L_jj^{-T}
+      GemmDesc pn = mk(w - j1, nb, nb, G + j1 * w + j0, w, 0, Li + j0 * w + j0, w, 1,
+                       L + j1 * w + j0, w);
+      pn.triB = 2;
+      BCUR_TRY(gemm_simt<float>(pn, s));
+      if (j1 < J1) {  // update the rest of this outer panel, all rows below
+        BCUR_TRY(split(P, L + j1 * w + j0, w, w - j1, nb, Pn, nb));
+        GemmDesc tr = mk16(w - j1, J1 - j1, nb, Pn, nb, 0, Pn, nb, 1, w);
+        tr.D = G + j1 * w + j1;
+        tr.alpha = -1.0;
+        tr.beta = 1.0;
+        tr.out_lower = 1;
+        BCUR_TRY(g16(P, tr, parts));
+      }
+    }
+    if (J1 < w) {  // outer trailing update with K = the outer panel width
+      const int64_t kw = J1 - J0;
+      BCUR_TRY(split(P, L + J1 * w + J0, w, w - J1, kw, Pn, kw));
+      GemmDesc tr = mk16(w - J1, w - J1, kw, Pn, kw, 0, Pn, kw, 1, w);
+      tr.D = G + J1 * w + J1;
+      tr.alpha = -1.0;
+      tr.beta = 1.0;
+      tr.out_lower = 1;
+      BCUR_TRY(g16(P, tr, parts));
+    }
   }
   BCUR_TRY(split(P, L, w, w, w, L16, w));
   for (int64_t h = nb; h < w; h *= 2) {
@@ -753,7 +775,7 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
   P->m = d->m; P->n = d->n; P->lda = d->lda;
   P->k = d->k; P->l = (int)l; P->q = d->q;
   P->esz = d->a_dtype == BCUR_F64 ? 8 : 4;
-  P->nb = d->a_dtype == BCUR_F64 ? 64 : 128;
+  P->nb = 64;
   P->ldm = round_up(P->m, 32);
   P->ldn = round_up(P->n, 32);
   P->c_max = max_sum_of_g(P->col_off, d->g_col, d->replacement != 0);
@@ -849,8 +871,8 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
       o.Lil = L.take(wm * wm * h2);
       o.T1h = L.take(wm * wm * h2);
       o.T1l = L.take(wm * wm * h2);
-      o.Pnh = L.take(wm * P->nb * h2);
-      o.Pnl = L.take(wm * P->nb * h2);
+      o.Pnh = L.take(wm * std::min<int64_t>(wm, 1024) * h2);
+      o.Pnl = L.take(wm * std::min<int64_t>(wm, 1024) * h2);
       o.Wh = L.take(P->m * rw * h2);
       o.Wl = L.take(P->m * rw * h2);
       o.Mh = L.take(cw * rw * h2);

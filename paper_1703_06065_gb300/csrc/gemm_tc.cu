@@ -51,6 +51,7 @@ struct Params {
   int tiles_m, tiles_n, ksplit, kblocks;
   int triA, triB;        // 1 lower / 2 upper (A: A(i,k)=0 for k>i / k<i; B: B(k,j)=0 for k<j / k>j)
   int tri_out;           // 1: keep row >= col, 2: keep row <= col (MMA space)
+  int rev_m, rev_n;      // visit M / N tiles in reverse order (heaviest first)
   float alpha, beta;
   float* D;              // FP32 output (may be null)
   __nv_bfloat16* Dh;     // BF16 hi part of the output (may be null)
@@ -210,8 +211,15 @@ template <int BN, int KIND>
 __device__ __forceinline__ Unit decode(const Params& p, int u) {
   constexpr int BK = KindCfg<KIND>::bk;
   Unit w;
-  const int tile = u / p.ksplit;
-  w.z = u % p.ksplit;
+  // CTA c takes units c, c + G, c + 2G, ...  Odd full rounds are walked in
+  // reverse ("snake"), so with tiles ordered heaviest first every CTA gets a
+  // similar amount of work.
+  const int G = gridDim.x;
+  const int round = u / G, c = u % G;
+  const int full_rounds = (p.tiles_m * p.tiles_n * p.ksplit) / G;
+  const int uu = (round < full_rounds && (round & 1)) ? round * G + (G - 1 - c) : u;
+  const int tile = uu / p.ksplit;
+  w.z = uu % p.ksplit;
   // grouped raster: 16 M-tiles per group for L2 reuse of the B panel
   const int GM = 16;
   const int per_group = GM * p.tiles_n;
@@ -219,8 +227,10 @@ __device__ __forceinline__ Unit decode(const Params& p, int u) {
   const int first = g * GM;
   const int gm = min(GM, p.tiles_m - first);
   const int r = tile % per_group;
-  const int tm = first + r % gm;
-  const int tn = r / gm;
+  int tm = first + r % gm;
+  int tn = r / gm;
+  if (p.rev_m) tm = p.tiles_m - 1 - tm;  // heavier tiles (longer K range) first
+  if (p.rev_n) tn = p.tiles_n - 1 - tn;
   w.m0 = tm * BM;
   w.n0 = tn * BN;
   const int chunk = (p.kblocks + p.ksplit - 1) / p.ksplit;
@@ -241,7 +251,8 @@ template <int BN> struct StageCfg {
   static constexpr int kStageBytes = kStageABytes + kStageBBytes;
   static constexpr int kStages = 196608 / kStageBytes;  // 192 KB of stages
   static constexpr int kTmemCols = 2 * BN;
-  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+  static constexpr int kStageOut = 4 * 32 * 33 * 4;  // per-warp 32 x 33 FP32 transpose tiles
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kStageOut;
 };
 
 template <int BN, int KIND, int EPI>
@@ -261,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(tmem_slot + 4);  // 8 doubles
+  float* stage_out = reinterpret_cast<float*>(smem + S * SC::kStageBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -409,22 +421,62 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int col0 = w.n0 + c0;
         if (col0 >= p.Nm) continue;
         if constexpr (EPI == EPI_STORE) {
-          if (!row_ok) continue;
+          if (p.transD) {
+            // D^T: lane = row, consecutive lanes write consecutive addresses.
+            if (!row_ok) continue;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int col = col0 + i;
-            if (col >= p.Nm) break;
-            if (p.tri_out == 1 && row < col) continue;
-            if (p.tri_out == 2 && row > col) continue;
-            const int64_t off = p.transD ? (int64_t)col * p.ldd + row : (int64_t)row * p.ldd + col;
-            float o = p.alpha * v[i];
-            if (p.beta != 0.f) o = fmaf(p.beta, p.D[off], o);
-            if (p.D) p.D[off] = o;
-            if (p.Dh) {
-              const __nv_bfloat16 h = __float2bfloat16_rn(o);
-              p.Dh[off] = h;
-              if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+            for (int i = 0; i < 32; ++i) {
+              const int col = col0 + i;
+              if (col >= p.Nm) break;
+              if (p.tri_out == 1 && row < col) continue;
+              if (p.tri_out == 2 && row > col) continue;
+              const int64_t off = (int64_t)col * p.ldd + row;
+              float o = p.alpha * v[i];
+              if (p.beta != 0.f) o = fmaf(p.beta, p.D[off], o);
+              if (p.D) p.D[off] = o;
+              if (p.Dh) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(o);
+                p.Dh[off] = h;
+                if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+              }
             }
+          } else {
+            // Row-major D: transpose the 32 x 32 chunk through shared memory
+            // so that each store instruction writes one contiguous row piece.
+            float* t = stage_out + (warp - 2) * (32 * 33);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
+            __syncwarp();
+            const int col = col0 + lane;
+            const int rbase = w.m0 + quarter * 32;
+            const bool col_ok = col < p.Nm;
+            float old[32];
+            if (p.beta != 0.f) {  // all loads issued before any use
+#pragma unroll
+              for (int r = 0; r < 32; ++r) {
+                const int grow = rbase + r;
+                old[r] = (col_ok && grow < p.Mm) ? p.D[(int64_t)grow * p.ldd + col] : 0.f;
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+              const int grow = rbase + r;
+              bool ok = col_ok && grow < p.Mm;
+              if (p.tri_out == 1 && grow < col) ok = false;
+              if (p.tri_out == 2 && grow > col) ok = false;
+              if (ok) {
+                const int64_t off = (int64_t)grow * p.ldd + col;
+                float o = p.alpha * t[r * 33 + lane];
+                if (p.beta != 0.f) o = fmaf(p.beta, old[r], o);
+                if (p.D) p.D[off] = o;
+                if (p.Dh) {
+                  const __nv_bfloat16 h = __float2bfloat16_rn(o);
+                  p.Dh[off] = h;
+                  if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+                }
+              }
+            }
+            __syncwarp();
           }
         } else if constexpr (EPI == EPI_PARTIAL) {
           if (!row_ok) continue;
@@ -435,18 +487,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (col >= p.Nm) break;
             prow[col] = v[i];
           }
-        } else {  // EPI_RESID
+        } else {  // EPI_RESID: each lane reads its own row piece of X
           if (!row_ok) continue;
-          const float* xr = p.X + (int64_t)row * p.ldx;
+          const float* xr = p.X + (int64_t)row * p.ldx + col0;
+          float xv[32];
+          if (col0 + 32 <= p.Nm && ((reinterpret_cast<uintptr_t>(xr) & 15) == 0)) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float4 q = reinterpret_cast<const float4*>(xr)[i];
+              xv[4 * i] = q.x; xv[4 * i + 1] = q.y; xv[4 * i + 2] = q.z; xv[4 * i + 3] = q.w;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) xv[i] = (col0 + i < p.Nm) ? xr[i] : 0.f;
+          }
           float se = 0.f, sx = 0.f;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const int col = col0 + i;
-            if (col >= p.Nm) break;
-            const float x = xr[col];
-            const float d = x - p.alpha * v[i];
+            const float d = xv[i] - ((col0 + i < p.Nm) ? p.alpha * v[i] : 0.f);
             se = fmaf(d, d, se);
-            sx = fmaf(x, x, sx);
+            sx = fmaf(xv[i], xv[i], sx);
           }
           e2 += (double)se;
           x2 += (double)sx;
@@ -680,6 +740,8 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   p.tiles_n = (int)ceil_div(Nm, BN);
   p.kblocks = (int)ceil_div(d.K, kind == 0 ? KindCfg<0>::bk : KindCfg<1>::bk);
   p.triA = triA; p.triB = triB; p.tri_out = tri_out;
+  p.rev_m = (triA == 1 || tri_out == 1) ? 1 : 0;
+  p.rev_n = (triB == 2 || tri_out == 2) ? 1 : 0;
   p.alpha = (float)d.alpha; p.beta = (float)d.beta;
   p.D = (float*)d.D; p.ldd = d.ldd; p.transD = swap ? 1 : 0;
   p.X = (const float*)d.X; p.ldx = d.ldx; p.partials = d.partials;

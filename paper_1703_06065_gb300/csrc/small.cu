@@ -331,86 +331,115 @@ bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t 
   return BCUR_OK;
 }
 
-// Factor the diagonal block G[j0:j0+nbb, j0:j0+nbb] (lower part, already
+// Factor the diagonal block G[j0:j0+NB, j0:j0+NB] (lower part, already
 // updated by the trailing updates) as L L^T with the drop rule, and write L
 // and L^{-1} into the same block position of L and Linv (zeros above the
-// diagonal).  nbb = min(nb, w - j0) is passed through nb by the caller.
-template <typename T>
-__global__ void potrf_diag_kernel(const T* G, int64_t ldg, T* L, int64_t ldl, T* Linv,
-                                  int64_t ldi, int64_t j0, int nb, const T* maxdiag,
-                                  double tol_rel, int* kept) {
+// diagonal).  Left-looking and column-parallel: for column j every row
+// i >= j forms its dot product with row j of the finished columns (split
+// over 256/NB threads and combined with shuffles), then the pivot owner
+// scales the column.  The inverse is built row by row the same way.  All
+// 256 threads work at every step; one reciprocal per pivot.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) potrf_diag_kernel(const T* G, int64_t ldg, T* L, int64_t ldl,
+                                                         T* Linv, int64_t ldi, int64_t j0,
+                                                         const T* maxdiag, double tol_rel,
+                                                         int* kept) {
+  constexpr int TPR = 256 / NB;  // threads per row (2 or 4), consecutive lanes
+  constexpr int LD = NB + TPR;   // LD = TPR (mod 32): the row-split loads are conflict-free
+  constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ unsigned char smem_raw[];
-  const int ld = nb + 1;
-  T* S = reinterpret_cast<T*>(smem_raw);
-  T* X = S + nb * ld;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < nb * nb; e += nt) {
-    const int i = e / nb, j = e % nb;
-    S[i * ld + j] = (j <= i) ? G[(j0 + i) * ldg + j0 + j] : T(0);
-    X[i * ld + j] = (i == j) ? T(1) : T(0);
+  T* S = reinterpret_cast<T*>(smem_raw);  // NB x LD: G, then L
+  T* X = S + NB * LD;                      // NB x LD: L^{-1}
+  const int tid = threadIdx.x;
+  const int i = tid / TPR, h = tid % TPR;
+  for (int c = h; c < NB; c += TPR) {
+    S[i * LD + c] = (c <= i) ? G[(j0 + i) * ldg + j0 + c] : T(0);
+    X[i * LD + c] = T(0);
   }
-  __shared__ T s_piv;
+  __shared__ T s_inv;
   __shared__ int s_kept;
   if (tid == 0) s_kept = 0;
   const T tol = (T)(tol_rel * (double)(*maxdiag));
   __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      const T d = S[j * ld + j];
-      T p = T(0);
-      if (d > tol && d > T(0)) { p = sqrt(d); s_kept++; }
-      S[j * ld + j] = p;
-      s_piv = p;
+  for (int j = 0; j < NB; ++j) {
+    // four independent partial sums keep the shared-memory loads in flight
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int k = h;
+    for (; k + 3 * TPR < j; k += 4 * TPR) {
+      a0 += S[i * LD + k] * S[j * LD + k];
+      a1 += S[i * LD + k + TPR] * S[j * LD + k + TPR];
+      a2 += S[i * LD + k + 2 * TPR] * S[j * LD + k + 2 * TPR];
+      a3 += S[i * LD + k + 3 * TPR] * S[j * LD + k + 3 * TPR];
+    }
+    for (; k < j; k += TPR) a0 += S[i * LD + k] * S[j * LD + k];
+    T acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    const T v = S[i * LD + j] - acc;
+    if (i == j && h == 0) {
+      const T p = (v > tol && v > T(0)) ? sqrt(v) : T(0);
+      S[j * LD + j] = p;
+      s_inv = (p > T(0)) ? T(1) / p : T(0);
+      if (p > T(0)) s_kept++;
     }
     __syncthreads();
-    const T p = s_piv;
-    for (int i = j + 1 + tid; i < nb; i += nt) S[i * ld + j] = (p > T(0)) ? S[i * ld + j] / p : T(0);
+    if (i > j && h == 0) S[i * LD + j] = v * s_inv;
     __syncthreads();
-    const int rem = nb - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int a = e / rem, b = e % rem;
-      if (b <= a) {
-        const int i = j + 1 + a, i2 = j + 1 + b;
-        S[i * ld + i2] -= S[i * ld + j] * S[i2 * ld + j];
+  }
+  // X = L^{-1}, row r from the rows above it:
+  //   X[r][c] = (delta_rc - sum_{c <= k < r} L[r][k] X[k][c]) / L[r][r]
+  for (int r = 0; r < NB; ++r) {
+    const int c = i;  // column handled by this thread group
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    if (c <= r) {
+      int k = c + h;
+      for (; k + 3 * TPR < r; k += 4 * TPR) {
+        a0 += S[r * LD + k] * X[k * LD + c];
+        a1 += S[r * LD + k + TPR] * X[(k + TPR) * LD + c];
+        a2 += S[r * LD + k + 2 * TPR] * X[(k + 2 * TPR) * LD + c];
+        a3 += S[r * LD + k + 3 * TPR] * X[(k + 3 * TPR) * LD + c];
       }
+      for (; k < r; k += TPR) a0 += S[r * LD + k] * X[k * LD + c];
+    }
+    T acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (c <= r && h == 0) {
+      const T lrr = S[r * LD + r];
+      X[r * LD + c] = (lrr > T(0)) ? (((c == r) ? T(1) : T(0)) - acc) / lrr : T(0);
     }
     __syncthreads();
   }
-  // X <- L^{-1} by right-looking forward substitution on the identity.
-  for (int k = 0; k < nb; ++k) {
-    const T lkk = S[k * ld + k];
-    for (int c = tid; c <= k; c += nt) X[k * ld + c] = (lkk > T(0)) ? X[k * ld + c] / lkk : T(0);
-    __syncthreads();
-    const int rows = nb - k - 1, cols = k + 1;
-    for (int e = tid; e < rows * cols; e += nt) {
-      const int i = k + 1 + e / cols, c = e % cols;
-      X[i * ld + c] -= S[i * ld + k] * X[k * ld + c];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < nb * nb; e += nt) {
-    const int i = e / nb, j = e % nb;
-    L[(j0 + i) * ldl + j0 + j] = (j <= i) ? S[i * ld + j] : T(0);
-    Linv[(j0 + i) * ldi + j0 + j] = (j <= i) ? X[i * ld + j] : T(0);
+  for (int c = h; c < NB; c += TPR) {
+    L[(j0 + i) * ldl + j0 + c] = (c <= i) ? S[i * LD + c] : T(0);
+    Linv[(j0 + i) * ldi + j0 + c] = (c <= i) ? X[i * LD + c] : T(0);
   }
   if (tid == 0) atomicAdd(kept, s_kept);
+}
+
+template <typename T, int NB>
+bcur_status_t potrf_diag_nb(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t ldi,
+                            int64_t j0, const T* maxdiag, double tol_rel, int* kept,
+                            cudaStream_t s) {
+  const size_t smem = 2 * (size_t)NB * (NB + 256 / NB) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel<T, NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  potrf_diag_kernel<T, NB><<<1, 256, smem, s>>>(G, ldg, L, ldl, Linv, ldi, j0, maxdiag, tol_rel,
+                                                kept);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
 }
 
 template <typename T>
 bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t ldi, int64_t j0,
                          int nb, const T* maxdiag, double tol_rel, int* kept, cudaStream_t s) {
-  if (nb < 1 || nb > 128) return BCUR_EINVAL;
-  const size_t smem = 2 * (size_t)nb * (nb + 1) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    BCUR_CUDA_TRY(cudaFuncSetAttribute(potrf_diag_kernel<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
-  potrf_diag_kernel<T><<<1, 256, smem, s>>>(G, ldg, L, ldl, Linv, ldi, j0, nb, maxdiag, tol_rel,
-                                            kept);
-  BCUR_LAUNCH_CHECK();
-  return BCUR_OK;
+  if (nb == 128) return potrf_diag_nb<T, 128>(G, ldg, L, ldl, Linv, ldi, j0, maxdiag, tol_rel, kept, s);
+  if (nb == 64) return potrf_diag_nb<T, 64>(G, ldg, L, ldl, Linv, ldi, j0, maxdiag, tol_rel, kept, s);
+  return BCUR_EINVAL;
 }
 
 // ---------------------------------------------------------------------------
