@@ -248,6 +248,17 @@ bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t 
                         int32_t transA, const void* B, int64_t ldb, int32_t transB, void* D,
                         int64_t ldd, int32_t dtype, int32_t prec, void* stream);
 
+/* D (M x N, FP32, row-major, ldd) = A B with both operands as BF16 hi/lo
+ * pairs (x = hi + lo): A_hi B_hi + A_hi B_lo + A_lo B_hi on the tcgen05
+ * tensor cores with FP32 accumulation -- the product the split-BF16 fit uses.
+ * Layout conventions as bcur_gemm; A_lo / B_lo share the leading dimension
+ * of their hi parts.  All pointers 16-byte aligned, lda, ldb multiples of 8.
+ * Errors: BCUR_EINVAL (NULL pointer, negative size), BCUR_ENOTSUP (alignment,
+ * or not an sm_103 device). */
+bcur_status_t bcur_gemm_split(int64_t M, int64_t N, int64_t K, const void* A_hi, const void* A_lo,
+                              int64_t lda, int32_t transA, const void* B_hi, const void* B_lo,
+                              int64_t ldb, int32_t transB, float* D, int64_t ldd, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices).  Used to report launches per timed step. */
 uint64_t bcur_launch_count(void);

@@ -24,8 +24,8 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "block_scores", "sample_blocks", "residual", "gemm", "decompose", "load",
-           "BcurError", "PREC"]
+__all__ = ["Plan", "block_scores", "sample_blocks", "residual", "gemm", "gemm_split",
+           "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
 
@@ -236,6 +236,21 @@ def gemm(A, B, transA: bool = False, transB: bool = False, prec: str = None, out
     _lib.check(_lib.load().bcur_gemm(M, N, K, _ptr(A), A.shape[1], int(transA), _ptr(B),
                                      B.shape[1], int(transB), _ptr(D), D.shape[1], code, prec,
                                      _stream()), "bcur_gemm")
+    return D
+
+
+def gemm_split(A_hi, A_lo, B_hi, B_lo, transA: bool = False, transB: bool = False, out=None):
+    """D = A B from BF16 hi/lo pairs (3-term split product, FP32 result)."""
+    torch = _torch()
+    _need_cuda(A_hi, A_lo, B_hi, B_lo)
+    M = A_hi.shape[1] if transA else A_hi.shape[0]
+    K = A_hi.shape[0] if transA else A_hi.shape[1]
+    N = B_hi.shape[0] if transB else B_hi.shape[1]
+    D = torch.empty(M, N, dtype=torch.float32, device=A_hi.device) if out is None else out
+    _lib.check(_lib.load().bcur_gemm_split(M, N, K, _ptr(A_hi), _ptr(A_lo), A_hi.shape[1],
+                                           int(transA), _ptr(B_hi), _ptr(B_lo), B_hi.shape[1],
+                                           int(transB), _ptr(D), D.shape[1], _stream()),
+               "bcur_gemm_split")
     return D
 
 

@@ -25,6 +25,7 @@ EXPORTS = [
     "bcur_error", "bcur_rank", "bcur_sync_status", "bcur_destroy", "bcur_status_string",
     "bcur_block_scores", "bcur_sample_blocks", "bcur_residual_workspace", "bcur_residual",
     "bcur_gemm", "bcur_launch_count", "bcur_version", "bcur_residual_noalloc",
+    "bcur_gemm_split",
 ]
 
 
@@ -105,6 +106,10 @@ def load():
     L.bcur_gemm.argtypes = [c_int64, c_int64, c_int64, c_void_p, c_int64, c_int32, c_void_p,
                             c_int64, c_int32, c_void_p, c_int64, c_int32, c_int32, c_void_p]
     L.bcur_gemm.restype = st
+    L.bcur_gemm_split.argtypes = [c_int64, c_int64, c_int64, c_void_p, c_void_p, c_int64, c_int32,
+                                  c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_int64,
+                                  c_void_p]
+    L.bcur_gemm_split.restype = st
     L.bcur_launch_count.argtypes = []
     L.bcur_launch_count.restype = ctypes.c_uint64
     L.bcur_version.argtypes = []

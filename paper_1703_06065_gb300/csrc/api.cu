@@ -726,6 +726,18 @@ const char* bcur_version(void) { return "0.1.0"; }
 
 uint64_t bcur_launch_count(void) { return (uint64_t)g_launches.load(); }
 
+bcur_status_t bcur_gemm_split(int64_t M, int64_t N, int64_t K, const void* A_hi, const void* A_lo,
+                              int64_t lda, int32_t transA, const void* B_hi, const void* B_lo,
+                              int64_t ldb, int32_t transB, float* D, int64_t ldd, void* stream) {
+  if (!A_hi || !A_lo || !B_hi || !B_lo || !D || M < 0 || N < 0 || K < 0) return BCUR_EINVAL;
+  GemmDesc g = mk(M, N, K, A_hi, lda, transA != 0, B_hi, ldb, transB != 0, D, ldd);
+  g.ab_bf16 = 1;
+  g.parts = 3;
+  g.A_lo = A_lo;
+  g.B_lo = B_lo;
+  return gemm_tc(g, BCUR_BF16, (cudaStream_t)stream);
+}
+
 const char* bcur_status_string(bcur_status_t st) {
   switch (st) {
     case BCUR_OK: return "ok";

@@ -52,6 +52,8 @@ struct Params {
   int triA, triB;        // 1 lower / 2 upper (A: A(i,k)=0 for k>i / k<i; B: B(k,j)=0 for k<j / k>j)
   int tri_out;           // 1: keep row >= col, 2: keep row <= col (MMA space)
   int rev_m, rev_n;      // visit M / N tiles in reverse order (heaviest first)
+  int batch;             // independent problems (third tensor-map coordinate)
+  int64_t sD;            // element stride between the batch's outputs
   float alpha, beta;
   float* D;              // FP32 output (may be null)
   __nv_bfloat16* Dh;     // BF16 hi part of the output (may be null)
@@ -118,12 +120,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
     }
   }
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
+// 3-D tile load: (x inner, y outer, z batch).  x is always a multiple of
+// 128 bytes here, so every copy starts 16-byte aligned.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -204,7 +208,7 @@ struct Maps {
 };
 
 struct Unit {
-  int m0, n0, z, klo, khi, skip;
+  int m0, n0, z, b, klo, khi, skip;
 };
 
 template <int BN, int KIND>
@@ -216,10 +220,12 @@ __device__ __forceinline__ Unit decode(const Params& p, int u) {
   // similar amount of work.
   const int G = gridDim.x;
   const int round = u / G, c = u % G;
-  const int full_rounds = (p.tiles_m * p.tiles_n * p.ksplit) / G;
+  const int full_rounds = (p.tiles_m * p.tiles_n * p.ksplit * p.batch) / G;
   const int uu = (round < full_rounds && (round & 1)) ? round * G + (G - 1 - c) : u;
-  const int tile = uu / p.ksplit;
+  const int bt = uu / p.ksplit;
   w.z = uu % p.ksplit;
+  w.b = bt / (p.tiles_m * p.tiles_n);
+  const int tile = bt % (p.tiles_m * p.tiles_n);
   // grouped raster: 16 M-tiles per group for L2 reuse of the B panel
   const int GM = 16;
   const int per_group = GM * p.tiles_n;
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int total = p.tiles_m * p.tiles_n * p.ksplit;
+  const int total = p.tiles_m * p.tiles_n * p.ksplit * p.batch;
   constexpr int BKR = KC::bk;  // K rows per stage for an MN-major operand
 
   if (warp == 0) {
@@ -326,18 +332,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* sb = sa + kStageABytes;
           mbar_expect_tx(&full[stage], SC::kStageBytes);
           if (!p.a_mn) {
-            tma_load_2d(sa, ma, &full[stage], kb * KC::bk, w.m0);
+            tma_load_3d(sa, ma, &full[stage], kb * KC::bk, w.m0, w.b);
           } else {
 #pragma unroll
             for (int b = 0; b < BM / KC::box_mn; ++b)
-              tma_load_2d(sa + b * (BKR * 128), ma, &full[stage], w.m0 + b * KC::box_mn, kb * BKR);
+              tma_load_3d(sa + b * (BKR * 128), ma, &full[stage], w.m0 + b * KC::box_mn, kb * BKR, w.b);
           }
           if (!p.b_mn) {
-            tma_load_2d(sb, mb, &full[stage], kb * KC::bk, w.n0);
+            tma_load_3d(sb, mb, &full[stage], kb * KC::bk, w.n0, w.b);
           } else {
 #pragma unroll
             for (int b = 0; b < BN / KC::box_mn; ++b)
-              tma_load_2d(sb + b * (BKR * 128), mb, &full[stage], w.n0 + b * KC::box_mn, kb * BKR);
+              tma_load_3d(sb + b * (BKR * 128), mb, &full[stage], w.n0 + b * KC::box_mn, kb * BKR, w.b);
           }
         }
       }
@@ -408,6 +414,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int row = w.m0 + quarter * 32 + lane;
       const bool row_ok = row < p.Mm;
+      float* const Dp = p.D ? p.D + (int64_t)w.b * p.sD : nullptr;
+      __nv_bfloat16* const Dhp = p.Dh ? p.Dh + (int64_t)w.b * p.sD : nullptr;
+      __nv_bfloat16* const Dlp = p.Dl ? p.Dl + (int64_t)w.b * p.sD : nullptr;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
@@ -432,12 +441,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (p.tri_out == 2 && row > col) continue;
               const int64_t off = (int64_t)col * p.ldd + row;
               float o = p.alpha * v[i];
-              if (p.beta != 0.f) o = fmaf(p.beta, p.D[off], o);
-              if (p.D) p.D[off] = o;
-              if (p.Dh) {
+              if (p.beta != 0.f) o = fmaf(p.beta, Dp[off], o);
+              if (p.D) Dp[off] = o;
+              if (Dhp) {
                 const __nv_bfloat16 h = __float2bfloat16_rn(o);
-                p.Dh[off] = h;
-                if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+                Dhp[off] = h;
+                if (Dlp) Dlp[off] = __float2bfloat16_rn(o - __bfloat162float(h));
               }
             }
           } else {
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int r = 0; r < 32; ++r) {
                 const int grow = rbase + r;
-                old[r] = (col_ok && grow < p.Mm) ? p.D[(int64_t)grow * p.ldd + col] : 0.f;
+                old[r] = (col_ok && grow < p.Mm) ? Dp[(int64_t)grow * p.ldd + col] : 0.f;
               }
             }
 #pragma unroll
@@ -468,11 +477,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t off = (int64_t)grow * p.ldd + col;
                 float o = p.alpha * t[r * 33 + lane];
                 if (p.beta != 0.f) o = fmaf(p.beta, old[r], o);
-                if (p.D) p.D[off] = o;
-                if (p.Dh) {
+                if (p.D) Dp[off] = o;
+                if (Dhp) {
                   const __nv_bfloat16 h = __float2bfloat16_rn(o);
-                  p.Dh[off] = h;
-                  if (p.Dl) p.Dl[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+                  Dhp[off] = h;
+                  if (Dlp) Dlp[off] = __float2bfloat16_rn(o - __bfloat162float(h));
                 }
               }
             }
@@ -627,15 +636,21 @@ struct Operand {
   int64_t mn, k;   // extents
 };
 
-bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn) {
+bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn, int batch,
+              int64_t sbatch) {
   const int esize = kind == 0 ? 4 : 2;
   const int box_inner = 128 / esize;  // 128 bytes
   const uintptr_t a = reinterpret_cast<uintptr_t>(op.ptr);
   if (a % 16 != 0 || (op.ld * esize) % 16 != 0) return false;
-  cuuint64_t dims[2];
-  cuuint64_t strides[1] = {(cuuint64_t)(op.ld * esize)};
-  cuuint32_t box[2];
-  cuuint32_t estr[2] = {1, 1};
+  cuuint64_t dims[3];
+  const int64_t outer = op.mn_major ? op.k : op.mn;
+  const int64_t bstride = batch > 1 ? sbatch : op.ld * outer;
+  if ((bstride * esize) % 16 != 0) return false;
+  cuuint64_t strides[2] = {(cuuint64_t)(op.ld * esize), (cuuint64_t)(bstride * esize)};
+  cuuint32_t box[3];
+  cuuint32_t estr[3] = {1, 1, 1};
+  dims[2] = (cuuint64_t)batch;
+  box[2] = 1;
   if (!op.mn_major) {
     dims[0] = (cuuint64_t)op.k;
     dims[1] = (cuuint64_t)op.mn;
@@ -651,7 +666,7 @@ bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn) {
   auto fn = encode_fn();
   if (!fn) return false;
   CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                  2, const_cast<void*>(op.ptr), dims, strides, box, estr,
+                  3, const_cast<void*>(op.ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -726,13 +741,17 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   // TF32 operands must be K-major on this tensor core.
   if (kind == 0 && (A.mn_major || B.mn_major)) return BCUR_ENOTSUP;
   const int BN = Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256);
+  const int batch = d.batch > 1 ? d.batch : 1;
+  const int64_t sAm = swap ? d.sB : d.sA, sBm = swap ? d.sA : d.sB;
   Maps maps;
-  if (!make_map(&maps.a[0], A, kind, BM) || !make_map(&maps.b[0], B, kind, BN) ||
-      !make_map(&maps.a[1], Al, kind, BM) || !make_map(&maps.b[1], Bl, kind, BN))
+  if (!make_map(&maps.a[0], A, kind, BM, batch, sAm) || !make_map(&maps.b[0], B, kind, BN, batch, sBm) ||
+      !make_map(&maps.a[1], Al, kind, BM, batch, sAm) || !make_map(&maps.b[1], Bl, kind, BN, batch, sBm))
     return BCUR_ENOTSUP;
   Params p{};
   p.Mm = (int)Mm; p.Nm = (int)Nm; p.K = (int)d.K;
   p.parts = parts;
+  p.batch = batch;
+  p.sD = d.sD;
   p.Dh = (__nv_bfloat16*)d.Dh;
   p.Dl = (__nv_bfloat16*)d.Dl;
   p.a_mn = A.mn_major; p.b_mn = B.mn_major;
@@ -751,7 +770,7 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   const int tiles = p.tiles_m * p.tiles_n;
   // Split K when there are too few tiles to fill the GPU and a scratch
   // buffer for the partial slices is available.
-  if (epi == EPI_STORE && d.scratch && tiles < sms && p.kblocks >= 8) {
+  if (epi == EPI_STORE && d.scratch && batch == 1 && tiles < sms && p.kblocks >= 8) {
     int ks = std::min<int64_t>(std::max<int64_t>(1, (4 * sms) / tiles), p.kblocks / 4);
     const int64_t slice = Mm * Nm * 4;
     ks = (int)std::min<int64_t>(ks, (int64_t)d.scratch_bytes / slice);
@@ -760,7 +779,7 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
       p.part = (float*)d.scratch;
     }
   }
-  const int units = tiles * p.ksplit;
+  const int units = tiles * p.ksplit * batch;
   const int grid = std::max(1, std::min(units, sms));
   if (epi == EPI_RESID) {
     if (n_partials) *n_partials = grid;
@@ -787,23 +806,7 @@ bool gemm_tc_available() { return tc::tc_device_ok(); }
 int64_t gemm_tc_resid_ctas(int64_t, int64_t) { return 1024; }
 
 bcur_status_t gemm_tc(const GemmDesc& d, int prec, cudaStream_t s) {
-  if (d.batch <= 1) return tc::run(d, prec, s, tc::EPI_STORE, nullptr);
-  // independent problems: one launch each (tensor maps are per pointer)
-  for (int b = 0; b < d.batch; ++b) {
-    GemmDesc e = d;
-    e.batch = 1;
-    const size_t es = d.ab_bf16 ? 2 : 4;
-    e.A = (const char*)d.A + b * d.sA * es;
-    e.B = (const char*)d.B + b * d.sB * es;
-    if (d.A_lo) e.A_lo = (const char*)d.A_lo + b * d.sA * es;
-    if (d.B_lo) e.B_lo = (const char*)d.B_lo + b * d.sB * es;
-    if (d.D) e.D = (float*)d.D + b * d.sD;
-    if (d.Dh) e.Dh = (__nv_bfloat16*)d.Dh + b * d.sD;
-    if (d.Dl) e.Dl = (__nv_bfloat16*)d.Dl + b * d.sD;
-    bcur_status_t st = tc::run(e, prec, s, tc::EPI_STORE, nullptr);
-    if (st != BCUR_OK) return st;
-  }
-  return BCUR_OK;
+  return tc::run(d, prec, s, tc::EPI_STORE, nullptr);
 }
 
 bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* n_partials) {

@@ -390,3 +390,17 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(orc, "fit_u", bad)
     with pytest.raises(AssertionError):
         test_pythagoras_normal_equations_and_lower_bounds()
+
+
+def test_paper_u_is_moore_penrose_inverse_of_scaled_intersection():
+    """U = W^+ with W = R S (Alg. 1 step 3) satisfies the four Penrose conditions."""
+    rg = _rng(17)
+    R = rg.standard_normal((5, 24))
+    off = bi.uniform_blocks(24, 4)
+    S = orc.sampling_matrix([1, 4, 2], [0.2, 0.1, 0.3], off)
+    W = R @ S
+    U = orc.fit_w_pinv(R, S)
+    np.testing.assert_allclose(W @ U @ W, W, atol=1e-10)
+    np.testing.assert_allclose(U @ W @ U, U, atol=1e-10)
+    np.testing.assert_allclose((W @ U).T, W @ U, atol=1e-10)
+    np.testing.assert_allclose((U @ W).T, U @ W, atol=1e-10)
