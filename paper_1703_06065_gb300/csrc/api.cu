@@ -45,6 +45,8 @@ struct bcur_plan_s {
   bcur_desc_t d;
   std::vector<int64_t> col_off, row_off;
   cudaStream_t stream = nullptr;
+  cudaStream_t stream2 = nullptr;      // second lane: the R-side QR runs beside the C side
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t m = 0, n = 0, lda = 0;
   int k = 0, l = 0, q = 0;
   int64_t ldm = 0, ldn = 0;      // padded panel leading dims
@@ -65,6 +67,8 @@ struct bcur_plan_s {
     // BF16 tensor-core path
     size_t A16h, A16l, Om16h, Om16l, Qm16h, Qm16l, Zn16h, Zn16l, XC16[4], XR16[4], Lh, Ll, Lih,
         Lil, T1h, T1l, Pnh, Pnl, Wh, Wl, Mh, Ml, U1h, U1l, U2h, U2l, Ph;
+    // per-lane temporaries of the second lane
+    size_t Lh2, Ll2, Lih2, Lil2, T1h2, T1l2, Pnh2, Pnl2, maxdiag2, tc_scratch2;
   } o;
   bool bf16_path = false;
   size_t tc_scratch_bytes = 0;
@@ -446,15 +450,37 @@ GemmDesc mk16(int64_t M, int64_t N, int64_t K, S16 A, int64_t lda, int tA, S16 B
   return g;
 }
 
+// An execution lane: a stream plus the temporaries that must not be shared
+// between concurrently running factorisations.
+struct Lane {
+  cudaStream_t s;
+  size_t Pnh, Pnl, Lh, Ll, Lih, Lil, T1h, T1l, maxdiag, scratch;
+};
+
+Lane lane_of(bcur_plan_t P, int i) {
+  const auto& o = P->o;
+  if (i == 0)
+    return {P->stream, o.Pnh, o.Pnl, o.Lh, o.Ll, o.Lih, o.Lil, o.T1h, o.T1l, o.maxdiag, o.tc_scratch};
+  return {P->stream2, o.Pnh2, o.Pnl2, o.Lh2, o.Ll2, o.Lih2, o.Lil2, o.T1h2, o.T1l2, o.maxdiag2,
+          o.tc_scratch2};
+}
+
+bcur_status_t split_on(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                       S16 out, int64_t ldo) {
+  return split_bf16(X, ldx, rows, cols, out.h, out.l, ldo, st);
+}
+
 // Tensor-core GEMM on BF16 operands; never falls back (ENOTSUP is an error).
-bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) {
+bcur_status_t g16_on(bcur_plan_t P, const Lane& ln, GemmDesc d, int parts) {
   d.parts = parts;
   if (parts != 3) { d.A_lo = nullptr; d.B_lo = nullptr; }
-  d.scratch = P->at<void>(P->o.tc_scratch);
+  d.scratch = P->at<void>(ln.scratch);
   d.scratch_bytes = P->tc_scratch_bytes;
   d.status = P->at<int>(P->o.status);
-  return gemm_tc(d, BCUR_BF16, P->stream);
+  return gemm_tc(d, BCUR_BF16, ln.s);
 }
+
+bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) { return g16_on(P, lane_of(P, 0), d, parts); }
 
 // Blocked Cholesky G = L L^T (w x w, FP32, lower part) and L^{-1}.  Two
 // levels: outer panels of kOuter columns whose trailing update is one large
@@ -465,16 +491,19 @@ bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) {
 // products use `parts` BF16 terms.
 constexpr int64_t kOuter = 1024;
 
-bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, int64_t w, int parts,
-                                 int* kept, double tol) {
-  cudaStream_t s = P->stream;
+bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float* L, float* Li,
+                                 int64_t w, int parts, int* kept, double tol) {
+  cudaStream_t s = ln.s;
   const int nb = P->nb;
   const bool lo = parts == 3;
-  float* md = P->at<float>(P->o.maxdiag);
-  S16 Pn = s16(P, P->o.Pnh, P->o.Pnl, lo);
-  S16 L16 = s16(P, P->o.Lh, P->o.Ll, lo);
-  S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
-  S16 T1 = s16(P, P->o.T1h, P->o.T1l, lo);
+  float* md = P->at<float>(ln.maxdiag);
+  S16 Pn = s16(P, ln.Pnh, ln.Pnl, lo);
+  S16 L16 = s16(P, ln.Lh, ln.Ll, lo);
+  S16 Li16 = s16(P, ln.Lih, ln.Lil, lo);
+  S16 T1 = s16(P, ln.T1h, ln.T1l, lo);
+  auto split = [&](bcur_plan_t, const float* X, int64_t ldx, int64_t rows, int64_t cols, S16 out,
+                   int64_t ldo) { return split_on(s, X, ldx, rows, cols, out, ldo); };
+  auto g16 = [&](bcur_plan_t, GemmDesc d, int pr) { return g16_on(P, ln, d, pr); };
   BCUR_TRY(fill_zero(L, (size_t)w * w * sizeof(float), s));
   BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(float), s));
   BCUR_TRY(fill_zero(kept, sizeof(int), s));
@@ -512,8 +541,8 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, i
     }
   }
   BCUR_TRY(split(P, L, w, w, w, L16, w));
+  BCUR_TRY(split(P, Li, w, w, w, Li16, w));  // diagonal blocks; the doubling keeps it current
   for (int64_t h = nb; h < w; h *= 2) {
-    BCUR_TRY(split(P, Li, w, w, w, Li16, w));
     const int64_t npairs_full = w / (2 * h);
     if (npairs_full > 0) {
       GemmDesc t1 = mk16(h, h, h, L16.off(h * w), w, 0, Li16, w, 0, h);
@@ -527,6 +556,8 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, i
       BCUR_TRY(g16(P, t1, parts));
       GemmDesc t2 = mk16(h, h, h, Li16.off(h * w + h), w, 0, T1, h, 0, w);
       t2.D = Li + h * w;
+      t2.Dh = Li16.h + h * w;
+      t2.Dl = Li16.l ? Li16.l + h * w : nullptr;
       t2.triA = 1;
       t2.alpha = -1.0;
       t2.batch = (int)npairs_full;
@@ -545,6 +576,8 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, i
       BCUR_TRY(g16(P, t1, parts));
       GemmDesc t2 = mk16(h2, h, h2, Li16.off(b2 * w + b2), w, 0, T1, h, 0, w);
       t2.D = Li + b2 * w + b1;
+      t2.Dh = Li16.h + b2 * w + b1;
+      t2.Dl = Li16.l ? Li16.l + b2 * w + b1 : nullptr;
       t2.triA = 1;
       t2.alpha = -1.0;
       BCUR_TRY(g16(P, t2, parts));
@@ -555,10 +588,12 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, float* G, float* L, float* Li, i
 
 // Wide Cholesky-QR2 of a BF16-pair panel X (w x h): X = L1 L2 Q.  The pairs
 // pr[0] (input, then result) and pr[1] (intermediate) ping-pong.
-bcur_status_t wide_cqr2_16(bcur_plan_t P, S16 pr[2], int64_t w, int64_t h, int64_t ld, float* G,
-                           float* L1, float* L1i, float* L2, float* L2i, int parts, int* kept) {
+bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, int64_t h,
+                           int64_t ld, float* G, float* L1, float* L1i, float* L2, float* L2i,
+                           int parts, int* kept) {
   const bool lo = parts == 3;
-  S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
+  S16 Li16 = s16(P, ln.Lih, ln.Lil, lo);
+  auto g16 = [&](bcur_plan_t, GemmDesc d, int pr2) { return g16_on(P, ln, d, pr2); };
   float* Ls[2] = {L1, L2};
   float* Lis[2] = {L1i, L2i};
   for (int pass = 0; pass < 2; ++pass) {
@@ -567,10 +602,9 @@ bcur_status_t wide_cqr2_16(bcur_plan_t P, S16 pr[2], int64_t w, int64_t h, int64
     g.D = G;
     g.out_lower = 1;
     BCUR_TRY(g16(P, g, parts));
-    BCUR_TRY(chol_inv_blocked16(P, G, Ls[pass], Lis[pass], w, parts, kept + pass,
+    BCUR_TRY(chol_inv_blocked16(P, ln, G, Ls[pass], Lis[pass], w, parts, kept + pass,
                                 drop_tol<float>(h)));
-    BCUR_TRY(split(P, Lis[pass], w, w, w, Li16, w));
-    GemmDesc a = mk16(w, h, w, Li16, w, 0, src, ld, 0, ld);
+    GemmDesc a = mk16(w, h, w, Li16, w, 0, src, ld, 0, ld);  // Li16 holds L^{-1} already
     a.Dh = dst.h;
     a.Dl = dst.l;
     a.triA = 1;
@@ -646,12 +680,19 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   BCUR_TRY(split(P, Cp, ldm, cw, m, XC[0], ldm));
   BCUR_TRY(split(P, Rp, ldn, rw, n, XR[0], ldn));
   int* kept = P->at<int>(P->o.kept);
-  BCUR_TRY(wide_cqr2_16(P, XC, cw, m, ldm, P->at<float>(P->o.GC), P->at<float>(P->o.L1C),
+  // The QR factors of C and R^T are independent: the R side runs on the
+  // second lane (fork / join through events, so this also works in a graph).
+  const Lane l0 = lane_of(P, 0), l1 = lane_of(P, 1);
+  BCUR_CUDA_TRY(cudaEventRecord(P->ev_fork, s));
+  BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_fork, 0));
+  BCUR_TRY(wide_cqr2_16(P, l0, XC, cw, m, ldm, P->at<float>(P->o.GC), P->at<float>(P->o.L1C),
                         P->at<float>(P->o.L1Ci), P->at<float>(P->o.L2C), P->at<float>(P->o.L2Ci),
                         parts, kept + 4));
-  BCUR_TRY(wide_cqr2_16(P, XR, rw, n, ldn, P->at<float>(P->o.GR), P->at<float>(P->o.L1R),
+  BCUR_TRY(wide_cqr2_16(P, l1, XR, rw, n, ldn, P->at<float>(P->o.GR), P->at<float>(P->o.L1R),
                         P->at<float>(P->o.L1Ri), P->at<float>(P->o.L2R), P->at<float>(P->o.L2Ri),
                         parts, kept + 6));
+  BCUR_CUDA_TRY(cudaEventRecord(P->ev_join, P->stream2));
+  BCUR_CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
   // W = A Q_R (m x r);  M = Q_C^T W (c x r)
   S16 A16 = s16(P, P->o.A16h, P->o.A16l, lo);
   S16 W16 = s16(P, P->o.Wh, P->o.Wl, lo);
@@ -894,6 +935,16 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
       o.U2h = L.take(cw * rw * h2);
       o.U2l = L.take(cw * rw * h2);
       o.Ph = L.take(P->m * rw * h2);
+      o.Lh2 = L.take(wm * wm * h2);
+      o.Ll2 = L.take(wm * wm * h2);
+      o.Lih2 = L.take(wm * wm * h2);
+      o.Lil2 = L.take(wm * wm * h2);
+      o.T1h2 = L.take(wm * wm * h2);
+      o.T1l2 = L.take(wm * wm * h2);
+      o.Pnh2 = L.take(wm * std::min<int64_t>(wm, 1024) * h2);
+      o.Pnl2 = L.take(wm * std::min<int64_t>(wm, 1024) * h2);
+      o.maxdiag2 = L.take(16);
+      o.tc_scratch2 = L.take(P->tc_scratch_bytes);
     }
   }
   P->need = L.cur;
@@ -905,6 +956,11 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
 bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
   if (!P || !ws || ((uintptr_t)ws & 255)) return BCUR_EINVAL;
   if (bytes < P->need) return BCUR_ENOMEM;
+  if (!P->stream2) {
+    BCUR_CUDA_TRY(cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking));
+    BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  }
   P->ws = (char*)ws;
   P->ws_bytes = bytes;
   cudaStream_t s = P->stream;
@@ -1018,7 +1074,16 @@ bcur_status_t bcur_sync_status(bcur_plan_t P) {
   return (bcur_status_t)st;
 }
 
-void bcur_destroy(bcur_plan_t P) { delete P; }
+void bcur_destroy(bcur_plan_t P) {
+  if (!P) return;
+  if (P->stream2) {
+    cudaStreamSynchronize(P->stream2);
+    cudaStreamDestroy(P->stream2);
+  }
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  delete P;
+}
 
 bcur_status_t bcur_block_scores(const void* Ft, int32_t dtype, int32_t k, int64_t h, int64_t ldf,
                                 const int64_t* off, int32_t G, double* scores, void* stream) {
