@@ -119,10 +119,10 @@ def oracle_flops(m, n, c, r, l, q):
 
 def oracle_sample(full: bi.Problem):
     """A bounded sample of the workload for the host oracle: the same recipe
-    at 1/8 the size per side, blocks of the same width, c/n and r/m kept."""
-    if full.m <= 4096 and full.n <= 4096:
+    at 1/4 the size per side, blocks of the same width, c/n and r/m kept."""
+    if full.m <= 8192 and full.n <= 8192:
         return full, 1.0
-    f = 8
+    f = 4
     m, n = full.m // f, full.n // f
     s = int(full.col_off[1])
     gs = max(1, full.g_col // f)
