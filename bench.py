@@ -392,6 +392,23 @@ def main_native(args):
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": sample}
 
+    # per-stage times of one extra step (events between the C-ABI calls)
+    stage_ms = None
+    if rank == 0:
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        evs[0].record(s)
+        cs_t, rs_t = plan.scores(A, om)
+        evs[1].record(s)
+        ci_t, ri_t, _, _ = plan.sample(cs_t, rs_t, uc, ur)
+        evs[2].record(s)
+        plan.fit(A, ci_t, ri_t, U=Ubuf)
+        evs[3].record(s)
+        plan.error(A, out=ebuf)
+        evs[4].record(s)
+        torch.cuda.synchronize()
+        stage_ms = {nm: round(evs[i].elapsed_time(evs[i + 1]), 3)
+                    for i, nm in enumerate(["scores", "sample", "fit", "error"])}
+
     # accuracy gate against the stored FP64 oracle result for this workload
     gate = None
     ref_path = os.path.join(ROOT, "tests", "golden", f"{p.name}_oracle.json")
@@ -438,7 +455,7 @@ def main_native(args):
                        "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},
             "rel_err": float(e[1]), "fro_err": float(e[0]),
-            "accuracy_gate": gate, "input_generation_s": round(t_gen, 1),
+            "accuracy_gate": gate, "stage_ms": stage_ms, "input_generation_s": round(t_gen, 1),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu,
         }
