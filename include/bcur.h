@@ -189,6 +189,21 @@ bcur_status_t bcur_block_scores(const void* Ft, int32_t dtype, int32_t k, int64_
                                 int64_t ldf, const int64_t* off, int32_t G, double* scores,
                                 void* stream);
 
+/* Block stable rank terms (Sec. 3.2, definition of alpha): for each block g
+ * of the factor F whose panel F^T (k x h, ld ldf) is given,
+ *   ratio[g] = ||F^T E_g||_F^2 / ||F^T E_g||_2^2   (NaN for an all-zero block),
+ * so alpha = min_g ratio[g] and 1 <= ratio[g] <= block size.  The k x k Gram of
+ * each block is formed in FP64 and its largest eigenvalue found by one-sided
+ * Jacobi.  dtype BCUR_F64 or BCUR_F32, k <= 128; off device int64 (G + 1);
+ * ratio device double (G); workspace: device scratch of at least
+ * bcur_block_stable_rank_workspace(k, G) bytes (BCUR_ENOMEM otherwise).
+ * The incoherence mu = (m/k) max_i ||U_k^T e_i||^2 of the same definition
+ * section is bcur_block_scores with blocks of size 1. */
+size_t bcur_block_stable_rank_workspace(int32_t k, int32_t G);
+bcur_status_t bcur_block_stable_rank(const void* Ft, int32_t dtype, int32_t k, int64_t h,
+                                     int64_t ldf, const int64_t* off, int32_t G, double* ratio,
+                                     void* workspace, size_t workspace_bytes, void* stream);
+
 /* Alg. 1 step 2 on one side; the rule is the one stated at bcur_sample.
  * scores device (G), u device (g), idx device int32 (g), prob device (g) or
  * NULL.  G <= 32768.  Errors: BCUR_EINVAL (g > G without replacement). */

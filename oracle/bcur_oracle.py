@@ -119,21 +119,28 @@ def column_leverage_scores(V_k: np.ndarray) -> np.ndarray:
     return np.sum(V_k * V_k, axis=1)
 
 
-def block_stable_rank(V_k: np.ndarray, off: Sequence[int]) -> float:
-    """alpha = min_g ||V_k^T E_g||_F^2 / ||V_k^T E_g||_2^2 (Sec. 3.2 definition).
-
-    Blocks whose restriction is exactly zero carry no information and are
-    skipped (the ratio is undefined there).
-    """
-    vals = []
+def block_stable_rank_terms(V_k: np.ndarray, off: Sequence[int]) -> np.ndarray:
+    """||V_k^T E_g||_F^2 / ||V_k^T E_g||_2^2 for every block g (NaN for a zero block)."""
+    out = np.full(len(off) - 1, np.nan)
     for g in range(len(off) - 1):
         blk = np.asarray(V_k[off[g]:off[g + 1], :], dtype=np.float64)
         fro2 = float(np.sum(blk * blk))
         if fro2 == 0.0:
             continue
         spec = float(np.linalg.norm(blk, 2))
-        vals.append(fro2 / (spec * spec))
-    return min(vals) if vals else float("nan")
+        out[g] = fro2 / (spec * spec)
+    return out
+
+
+def block_stable_rank(V_k: np.ndarray, off: Sequence[int]) -> float:
+    """alpha = min_g ||V_k^T E_g||_F^2 / ||V_k^T E_g||_2^2 (Sec. 3.2 definition).
+
+    Blocks whose restriction is exactly zero carry no information and are
+    skipped (the ratio is undefined there).
+    """
+    t = block_stable_rank_terms(V_k, off)
+    t = t[~np.isnan(t)]
+    return float(t.min()) if t.size else float("nan")
 
 
 def incoherence(U_k: np.ndarray) -> float:

@@ -24,7 +24,7 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "block_scores", "sample_blocks", "residual", "gemm", "gemm_split",
+__all__ = ["Plan", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
            "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
@@ -192,6 +192,32 @@ def block_scores(Ft, off, out=None):
     _lib.check(_lib.load().bcur_block_scores(_ptr(Ft), _dtype_code(Ft), k, h, h, _ptr(off), G,
                                              _ptr(out), _stream()), "bcur_block_scores")
     return out
+
+
+def block_stable_rank(Ft, off):
+    """Per-block ||F_g||_F^2 / ||F_g||_2^2 of the factor whose panel is ``Ft``;
+    alpha of Sec. 3.2 is the minimum over blocks."""
+    torch = _torch()
+    _need_cuda(Ft, off)
+    L = _lib.load()
+    G = off.numel() - 1
+    k, h = Ft.shape
+    ws = torch.empty(max(L.bcur_block_stable_rank_workspace(k, G), 256), dtype=torch.uint8,
+                     device=Ft.device)
+    out = torch.empty(G, dtype=torch.float64, device=Ft.device)
+    _lib.check(L.bcur_block_stable_rank(_ptr(Ft), _dtype_code(Ft), k, h, h, _ptr(off), G, _ptr(out),
+                                        _ptr(ws), c_size_t(ws.numel()), _stream()),
+               "bcur_block_stable_rank")
+    return out
+
+
+def incoherence(Ut):
+    """mu = (m/k) max_i ||U_k^T e_i||^2 (Sec. 3.2) from the panel U_k^T (k x m)."""
+    torch = _torch()
+    k, m = Ut.shape
+    off = torch.arange(m + 1, dtype=torch.int64, device=Ut.device)
+    lev = block_scores(Ut, off)
+    return (m / k) * lev.max()
 
 
 def sample_blocks(scores, u, g: int, replacement: bool = False):

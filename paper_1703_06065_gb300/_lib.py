@@ -25,7 +25,7 @@ EXPORTS = [
     "bcur_error", "bcur_rank", "bcur_sync_status", "bcur_destroy", "bcur_status_string",
     "bcur_block_scores", "bcur_sample_blocks", "bcur_residual_workspace", "bcur_residual",
     "bcur_gemm", "bcur_launch_count", "bcur_version", "bcur_residual_noalloc",
-    "bcur_gemm_split",
+    "bcur_gemm_split", "bcur_block_stable_rank_workspace", "bcur_block_stable_rank",
 ]
 
 
@@ -110,6 +110,11 @@ def load():
                                   c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_int64,
                                   c_void_p]
     L.bcur_gemm_split.restype = st
+    L.bcur_block_stable_rank_workspace.argtypes = [c_int32, c_int32]
+    L.bcur_block_stable_rank_workspace.restype = c_size_t
+    L.bcur_block_stable_rank.argtypes = [c_void_p, c_int32, c_int32, c_int64, c_int64, c_void_p,
+                                         c_int32, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.bcur_block_stable_rank.restype = st
     L.bcur_launch_count.argtypes = []
     L.bcur_launch_count.restype = ctypes.c_uint64
     L.bcur_version.argtypes = []

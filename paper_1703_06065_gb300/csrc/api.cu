@@ -1096,6 +1096,24 @@ bcur_status_t bcur_block_scores(const void* Ft, int32_t dtype, int32_t k, int64_
   return BCUR_EINVAL;
 }
 
+size_t bcur_block_stable_rank_workspace(int32_t k, int32_t G) {
+  return block_stable_rank_workspace(k, G);
+}
+
+bcur_status_t bcur_block_stable_rank(const void* Ft, int32_t dtype, int32_t k, int64_t h,
+                                     int64_t ldf, const int64_t* off, int32_t G, double* ratio,
+                                     void* workspace, size_t workspace_bytes, void* stream) {
+  if (!Ft || !off || !ratio || k < 1 || k > 128 || h < 1 || ldf < h || G < 1) return BCUR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == BCUR_F64)
+    return block_stable_rank<double>((const double*)Ft, k, ldf, off, G, ratio, workspace,
+                                     workspace_bytes, s);
+  if (dtype == BCUR_F32)
+    return block_stable_rank<float>((const float*)Ft, k, ldf, off, G, ratio, workspace,
+                                    workspace_bytes, s);
+  return BCUR_EINVAL;
+}
+
 bcur_status_t bcur_sample_blocks(const double* scores, int32_t G, const double* u, int32_t g,
                                  int32_t replacement, int32_t* idx, double* prob, void* stream) {
   if (!scores || !u || !idx) return BCUR_EINVAL;

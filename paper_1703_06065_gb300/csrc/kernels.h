@@ -99,6 +99,12 @@ template <typename T>
 bcur_status_t block_scores(const T* Ft, int k, int64_t h, int64_t ldf, const int64_t* off,
                            int G, double* scores, int* status, cudaStream_t s);
 
+// Per-block ||F_g||_F^2 / ||F_g||_2^2 (block stable rank terms, Sec. 3.2).
+template <typename T>
+bcur_status_t block_stable_rank(const T* Ft, int k, int64_t ldf, const int64_t* off, int G,
+                                double* ratio, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t block_stable_rank_workspace(int k, int G);
+
 bcur_status_t sample_blocks(const double* scores, int G, const double* u, int g, int replacement,
                             int32_t* idx, double* prob, cudaStream_t s);
 

@@ -201,6 +201,14 @@ __global__ void jacobi_svd_kernel(const double* X, int w, T* Ut, T* W, double* s
   extern __shared__ unsigned char smem_raw[];
   T* Xs = reinterpret_cast<T*>(smem_raw);  // column-major: column p at Xs[p * w]
   const int wp = w + (w & 1);
+  {  // batch: one matrix per CTA
+    const int64_t b = blockIdx.x;
+    X += b * w * w;
+    if (Ut) Ut += b * w * w;
+    if (W) W += b * w * w;
+    sigma += b * w;
+    J += b * wp * wp;
+  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   for (int e = tid; e < wp * w; e += blockDim.x) {
     const int p = e / w, i = e % w;
@@ -281,8 +289,8 @@ __global__ void jacobi_svd_kernel(const double* X, int w, T* Ut, T* W, double* s
     const int i = e / w, t = e % w;
     const int p = s_order[t];
     const double sg = s_sig[p];
-    Ut[i * w + t] = sg > 0.0 ? (T)((double)Xs[p * w + i] / sg) : T(0);
-    W[i * w + t] = J[(int64_t)p * wp + i];
+    if (Ut) Ut[i * w + t] = sg > 0.0 ? (T)((double)Xs[p * w + i] / sg) : T(0);
+    if (W) W[i * w + t] = J[(int64_t)p * wp + i];
   }
   for (int t = tid; t < w; t += blockDim.x) sigma[t] = s_sig[s_order[t]];
 }
@@ -638,6 +646,78 @@ bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Block stable rank (Sec. 3.2): per column block g of a factor F (given as its
+// panel F^T, k x h), ratio_g = ||F_g||_F^2 / ||F_g||_2^2 with F_g the rows of F
+// in block g.  The k x k Gram F_g^T F_g is formed in FP64 (one CTA per block);
+// its largest eigenvalue (= ||F_g||_2^2) comes from the batched one-sided Jacobi
+// kernel above, its trace is ||F_g||_F^2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void block_gram_kernel(const T* Ft, int k, int64_t ldf, const int64_t* off,
+                                  double* gram) {
+  const int g = blockIdx.x;
+  const int64_t j0 = off[g], j1 = off[g + 1];
+  double* out = gram + (int64_t)g * k * k;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int a = e / k, b = e % k;
+    double acc = 0.0;
+    if (b <= a)
+      for (int64_t j = j0; j < j1; ++j) acc = fma((double)Ft[a * ldf + j], (double)Ft[b * ldf + j], acc);
+    out[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int a = e / k, b = e % k;
+    if (b > a) out[e] = out[b * k + a];
+  }
+}
+
+__global__ void stable_rank_finish_kernel(const double* gram, const double* sigma, int k, int G,
+                                          double* ratio) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const double* Gg = gram + (int64_t)g * k * k;
+  double tr = 0.0;
+  for (int a = 0; a < k; ++a) tr += Gg[a * k + a];
+  const double lmax = sigma[(int64_t)g * k];  // singular values of an SPD Gram = eigenvalues
+  ratio[g] = (tr > 0.0 && lmax > 0.0) ? tr / lmax : nan("");
+}
+
+template <typename T>
+bcur_status_t block_stable_rank(const T* Ft, int k, int64_t ldf, const int64_t* off, int G,
+                                double* ratio, void* ws, size_t ws_bytes, cudaStream_t s) {
+  const int kp = k + (k & 1);
+  const size_t need = ((size_t)G * k * k + (size_t)G * k) * sizeof(double) +
+                      (size_t)G * kp * kp * sizeof(double);
+  if (!ws || ws_bytes < need) return BCUR_ENOMEM;
+  if (k < 1 || k > 128 || G < 1) return BCUR_EINVAL;
+  double* gram = static_cast<double*>(ws);
+  double* sig = gram + (size_t)G * k * k;
+  double* jw = sig + (size_t)G * k;
+  block_gram_kernel<T><<<G, 256, 0, s>>>(Ft, k, ldf, off, gram);
+  BCUR_LAUNCH_CHECK();
+  const size_t smem = (size_t)kp * k * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    attr_set = true;
+  }
+  const int warps = kp / 2 < 32 ? (kp / 2 < 1 ? 1 : kp / 2) : 32;
+  jacobi_svd_kernel<double><<<G, warps * 32, smem, s>>>(gram, k, nullptr, nullptr, sig, jw,
+                                                        nullptr);
+  BCUR_LAUNCH_CHECK();
+  stable_rank_finish_kernel<<<(G + 127) / 128, 128, 0, s>>>(gram, sig, k, G, ratio);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+size_t block_stable_rank_workspace(int k, int G) {
+  const int kp = k + (k & 1);
+  return ((size_t)G * k * k + (size_t)G * k + (size_t)G * kp * kp) * sizeof(double);
+}
+
+// ---------------------------------------------------------------------------
 // FP32 -> BF16 hi/lo pairs
 // ---------------------------------------------------------------------------
 __global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int64_t cols,
@@ -711,6 +791,10 @@ bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols
   template bcur_status_t copy2d<T>(const T*, int64_t, T*, int64_t, int64_t, int64_t, cudaStream_t);
 BCUR_INST(float)
 BCUR_INST(double)
+template bcur_status_t block_stable_rank<float>(const float*, int, int64_t, const int64_t*, int,
+                                                double*, void*, size_t, cudaStream_t);
+template bcur_status_t block_stable_rank<double>(const double*, int, int64_t, const int64_t*, int,
+                                                 double*, void*, size_t, cudaStream_t);
 template bcur_status_t convert<double, float>(const double*, float*, int64_t, cudaStream_t);
 template bcur_status_t convert<float, double>(const float*, double*, int64_t, cudaStream_t);
 template bcur_status_t convert<double, double>(const double*, double*, int64_t, cudaStream_t);
