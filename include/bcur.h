@@ -204,6 +204,33 @@ bcur_status_t bcur_block_stable_rank(const void* Ft, int32_t dtype, int32_t k, i
                                      int64_t ldf, const int64_t* off, int32_t G, double* ratio,
                                      void* workspace, size_t workspace_bytes, void* stream);
 
+/* The paper's Algorithm 1 as printed (Sec. 3.1), one call:
+ *   1. r rows of A drawn uniformly with replacement (p_i = 1/m, the inverse-CDF
+ *      rule of bcur_sample on equal scores, uniforms u_rows) and
+ *      R = S_R^T A = sqrt(m/r) A[rows, :];
+ *   2. column-block scores l_i(R) = ||V_R^T E_i||_F^2 with V_R an orthonormal
+ *      basis of the numerical row space of R (Cholesky-QR2; pivots below the
+ *      drop tolerance leave it), g blocks drawn with replacement from
+ *      l / sum(l) (uniforms u_cols);
+ *   3. C = A S and W = R S with the scaling I_s / sqrt(g p_j) of Sec. 3.1 and
+ *      U = W^+ = Q_W^T L^{-1} from W = L Q_W (exact pseudo-inverse when W has
+ *      full row rank, i.e. c >= r and the drawn columns are independent);
+ *   4. err[0..2] = ||A - C U R||_F, its ratio to ||A||_F, and ||A||_F.
+ * A device, row-major m x n (lda), dtype BCUR_F64 or BCUR_F32 (arithmetic in
+ * that precision on CUDA cores).  col_off host int64 (G + 1).  u_rows (r),
+ * u_cols (g), row_idx (r), col_idx (g), col_scores (G), col_prob (g), err (3)
+ * device; U device c x r (ld r, c = g * the largest block size) or NULL.
+ * Limits: r <= 128, m <= 32768, G <= 32768.  workspace: device scratch of at
+ * least bcur_alg1_workspace(...) bytes, 256-byte aligned.
+ * Errors: BCUR_EINVAL (argument out of range), BCUR_ENOMEM (workspace). */
+size_t bcur_alg1_workspace(int64_t m, int64_t n, const int64_t* col_off, int32_t G, int32_t r,
+                           int32_t g, int32_t dtype);
+bcur_status_t bcur_alg1(const void* A, int64_t lda, int64_t m, int64_t n, int32_t dtype,
+                        const int64_t* col_off, int32_t G, int32_t r, int32_t g,
+                        const double* u_rows, const double* u_cols, int32_t* row_idx,
+                        int32_t* col_idx, double* col_scores, double* col_prob, void* U,
+                        double* err, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Alg. 1 step 2 on one side; the rule is the one stated at bcur_sample.
  * scores device (G), u device (g), idx device int32 (g), prob device (g) or
  * NULL.  G <= 32768.  Errors: BCUR_EINVAL (g > G without replacement). */

@@ -283,6 +283,45 @@ def tail_norm(A: np.ndarray, k: int) -> float:
     return float(np.sqrt(np.sum(s[k:] ** 2)))
 
 
+def numerical_rank(X: np.ndarray) -> int:
+    """Number of singular values above max(rows, cols) * eps64 * sigma_1."""
+    X = np.asarray(X, dtype=np.float64)
+    if X.size == 0:
+        return 0
+    s = np.linalg.svd(X, compute_uv=False)
+    return int(np.sum(s > max(X.shape) * EPS64 * s[0])) if s[0] > 0 else 0
+
+
+def algorithm1(A: np.ndarray, col_off: Sequence[int], r: int, g: int, u_rows: Sequence[float],
+               u_cols: Sequence[float]) -> Dict:
+    """Alg. 1 (Sec. 3.1) as printed: r rows uniformly (p_i = 1/m, with
+    replacement) with R = S_R^T A scaled by 1/sqrt(r p_i); column-block scores
+    l_i(R) = ||V_R^T E_i||_F^2 from the right singular vectors of R; g blocks
+    drawn with replacement from p_i = l_i / sum(l); C = A S and W = R S with
+    the scaling of Sec. 3.1; U = W^+.
+
+    Reading: when rank(R) = rho < r the top-r right singular vectors include
+    arbitrary null-space directions, so V_R keeps the rho vectors of the
+    numerical row space (sum(l) = rho) -- the scores are then unique.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    rows, _ = sample_blocks(np.ones(m), u_rows, r, replacement=True)
+    R = math.sqrt(m / r) * A[rows, :]
+    _, sR, VtR = np.linalg.svd(R, full_matrices=False)
+    rho = numerical_rank(R)
+    V_R = VtR[:rho].T
+    scores = block_scores(V_R, col_off)
+    cols, prob = sample_blocks(scores, u_cols, g, replacement=True)
+    S = sampling_matrix(cols, prob, col_off)
+    C = A @ S
+    W = R @ S
+    U = pinv(W)
+    err, rel = residual(A, C, U, R)
+    return dict(row_idx=rows, R=R, rank_R=rho, col_scores=scores, col_idx=cols, col_prob=prob,
+                S=S, C=C, W=W, U=U, err=err, rel=rel)
+
+
 # ----------------------------------------------------------------------------
 # Whole pipeline
 # ----------------------------------------------------------------------------

@@ -24,7 +24,7 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
+__all__ = ["Plan", "alg1", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
            "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
@@ -278,6 +278,33 @@ def gemm_split(A_hi, A_lo, B_hi, B_lo, transA: bool = False, transB: bool = Fals
                                            int(transB), _ptr(D), D.shape[1], _stream()),
                "bcur_gemm_split")
     return D
+
+
+def alg1(A, col_off, r: int, g: int, u_rows, u_cols, want_u: bool = True):
+    """The paper's Algorithm 1 as printed (uniform rows, scores of R's row space,
+    blocks with replacement and the scaling of Sec. 3.1, U = W^+)."""
+    torch = _torch()
+    _need_cuda(A, u_rows, u_cols)
+    L = _lib.load()
+    m, n = A.shape
+    off = np.ascontiguousarray(np.asarray(col_off, dtype=np.int64))
+    G = len(off) - 1
+    code = _dtype_code(A)
+    offp = off.ctypes.data_as(ctypes.c_void_p)
+    wsb = L.bcur_alg1_workspace(m, n, offp, G, r, g, code)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=A.device)
+    dev = A.device
+    ri = torch.empty(r, dtype=torch.int32, device=dev)
+    ci = torch.empty(g, dtype=torch.int32, device=dev)
+    cs = torch.empty(G, dtype=torch.float64, device=dev)
+    cp = torch.empty(g, dtype=torch.float64, device=dev)
+    c_max = int(g * np.max(np.diff(off)))
+    U = torch.empty(c_max, r, dtype=A.dtype, device=dev) if want_u else None
+    err = torch.empty(3, dtype=torch.float64, device=dev)
+    _lib.check(L.bcur_alg1(_ptr(A), n, m, n, code, offp, G, r, g, _ptr(u_rows), _ptr(u_cols),
+                           _ptr(ri), _ptr(ci), _ptr(cs), _ptr(cp), _ptr(U), _ptr(err), _ptr(ws),
+                           c_size_t(ws.numel()), _stream()), "bcur_alg1")
+    return dict(row_idx=ri, col_idx=ci, col_scores=cs, col_prob=cp, U=U, err=err)
 
 
 def decompose(plan: Plan, A, omega, u_col, u_row, col_idx=None, row_idx=None):

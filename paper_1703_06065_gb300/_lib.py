@@ -26,6 +26,7 @@ EXPORTS = [
     "bcur_block_scores", "bcur_sample_blocks", "bcur_residual_workspace", "bcur_residual",
     "bcur_gemm", "bcur_launch_count", "bcur_version", "bcur_residual_noalloc",
     "bcur_gemm_split", "bcur_block_stable_rank_workspace", "bcur_block_stable_rank",
+    "bcur_alg1_workspace", "bcur_alg1",
 ]
 
 
@@ -115,6 +116,12 @@ def load():
     L.bcur_block_stable_rank.argtypes = [c_void_p, c_int32, c_int32, c_int64, c_int64, c_void_p,
                                          c_int32, c_void_p, c_void_p, c_size_t, c_void_p]
     L.bcur_block_stable_rank.restype = st
+    L.bcur_alg1_workspace.argtypes = [c_int64, c_int64, c_void_p, c_int32, c_int32, c_int32, c_int32]
+    L.bcur_alg1_workspace.restype = c_size_t
+    L.bcur_alg1.argtypes = [c_void_p, c_int64, c_int64, c_int64, c_int32, c_void_p, c_int32, c_int32,
+                            c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                            c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.bcur_alg1.restype = st
     L.bcur_launch_count.argtypes = []
     L.bcur_launch_count.restype = ctypes.c_uint64
     L.bcur_version.argtypes = []

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbcur.so")
-SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "small.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "small.cu", "noalloc.cu", "alg1.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -404,3 +404,30 @@ def test_paper_u_is_moore_penrose_inverse_of_scaled_intersection():
     np.testing.assert_allclose(U @ W @ U, U, atol=1e-10)
     np.testing.assert_allclose((W @ U).T, W @ U, atol=1e-10)
     np.testing.assert_allclose((U @ W).T, U @ W, atol=1e-10)
+
+
+def test_algorithm1_scores_sum_to_rank_and_exact_for_low_rank():
+    """Alg. 1 as printed: the scores sum to rank(R); for a rank-3 matrix whose
+    sampled rows and blocks span it, rank(W) = rank(A) and A = C W^+ R exactly
+    (the classical CUR exactness property of the pseudo-inverse of the
+    intersection)."""
+    rg = _rng(18)
+    A = rg.standard_normal((40, 3)) @ rg.standard_normal((3, 48))
+    off = bi.uniform_blocks(48, 4)
+    r = orc.algorithm1(A, off, r=8, g=5, u_rows=bi.uniforms(8, 1, 3), u_cols=bi.uniforms(5, 1, 4))
+    assert r["rank_R"] == 3
+    assert abs(sum(r["col_scores"]) - 3) < 1e-10
+    assert np.linalg.matrix_rank(r["W"]) == 3
+    assert r["rel"] < 1e-10
+    # full-rank noise: scores sum to r, error strictly positive
+    A2 = A + 0.1 * rg.standard_normal(A.shape)
+    r2 = orc.algorithm1(A2, off, r=8, g=5, u_rows=bi.uniforms(8, 2, 3), u_cols=bi.uniforms(5, 2, 4))
+    assert r2["rank_R"] == 8 and abs(sum(r2["col_scores"]) - 8) < 1e-10
+    assert r2["rel"] > 1e-3
+
+
+def test_algorithm1_uniform_rows_follow_the_inverse_cdf():
+    """With equal scores the inverse CDF picks floor(u m)."""
+    u = [0.0, 0.49, 0.999, 0.25]
+    idx, p = orc.sample_blocks(np.ones(10), u, 4, True)
+    assert idx == [0, 4, 9, 2] and all(abs(x - 0.1) < 1e-15 for x in p)
