@@ -213,8 +213,10 @@ bcur_status_t bcur_block_stable_rank(const void* Ft, int32_t dtype, int32_t k, i
  *      drop tolerance leave it), g blocks drawn with replacement from
  *      l / sum(l) (uniforms u_cols);
  *   3. C = A S and W = R S with the scaling I_s / sqrt(g p_j) of Sec. 3.1 and
- *      U = W^+ = Q_W^T L^{-1} from W = L Q_W (exact pseudo-inverse when W has
- *      full row rank, i.e. c >= r and the drawn columns are independent);
+ *      U = W^+ = Q_W^T L^+ from W = L Q_W (Cholesky-QR2 of W's rows) and the
+ *      SVD of the small factor L (singular values at or below
+ *      max(r, c) * eps * sigma_1 dropped): the Moore-Penrose inverse, also
+ *      when W is rank deficient (a row drawn twice, a low-rank A);
  *   4. err[0..2] = ||A - C U R||_F, its ratio to ||A||_F, and ||A||_F.
  * A device, row-major m x n (lda), dtype BCUR_F64 or BCUR_F32 (arithmetic in
  * that precision on CUDA cores).  col_off host int64 (G + 1).  u_rows (r),

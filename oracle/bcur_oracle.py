@@ -201,20 +201,22 @@ def sample_blocks(scores: Sequence[float], u: Sequence[float], g: int,
 
 
 def sampling_matrix(idx: Sequence[int], prob: Sequence[float], off: Sequence[int]) -> np.ndarray:
-    """S (n x g s) of Sec. 3.1: block (j_t, t) is I_s / sqrt(g p_{j_t}).
+    """S (n x sum_t s_{j_t}) of Sec. 3.1: block (j_t, t) is I / sqrt(g p_{j_t}).
 
-    Requires equal-sized blocks (the paper's exposition); column block t of
-    S selects block j_t.
+    Column block t of S selects block j_t.  With equal blocks this is the
+    printed n x g s matrix; Sec. 3 notes the method extends to blocks of
+    varying size, which here means block column t is as wide as block j_t.
     """
     g = len(idx)
     sizes = np.diff(np.asarray(off))
-    s = int(sizes[0])
-    if not np.all(sizes == s):
-        raise ValueError("S is defined for equal-sized blocks")
     n = int(off[-1])
-    S = np.zeros((n, g * s))
+    widths = [int(sizes[j]) for j in idx]
+    S = np.zeros((n, int(sum(widths))))
+    c0 = 0
     for t, (j, p) in enumerate(zip(idx, prob)):
-        S[off[j]:off[j + 1], t * s:(t + 1) * s] = np.eye(s) / math.sqrt(g * p)
+        w = widths[t]
+        S[off[j]:off[j + 1], c0:c0 + w] = np.eye(w) / math.sqrt(g * p)
+        c0 += w
     return S
 
 

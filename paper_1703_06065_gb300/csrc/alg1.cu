@@ -74,23 +74,19 @@ __global__ void gather_cols_rm_kernel(const T* R, int64_t ldr, int64_t rows, con
   }
 }
 
-// Inverse of a w x w lower-triangular FP64 matrix (zero diagonal -> zero row).
+// Moore-Penrose inverse of a small square matrix from its SVD X = Ut S W^T
+// (one-sided Jacobi): X^+ = W S^+ Ut^T, singular values at or below tol
+// treated as zero.
 template <typename T>
-__global__ void trinv_small_kernel(const double* Lm, int w, double* Li, T* LiT) {
-  for (int c = threadIdx.x; c < w; c += blockDim.x) {
-    for (int i = 0; i < w; ++i) {
-      double x = 0.0;
-      if (i >= c) {
-        const double lii = Lm[i * w + i];
-        if (lii != 0.0) {
-          double acc = (i == c) ? 1.0 : 0.0;
-          for (int k = c; k < i; ++k) acc -= Lm[i * w + k] * Li[k * w + c];
-          x = acc / lii;
-        }
-      }
-      Li[i * w + c] = x;
-      LiT[i * w + c] = (T)x;
-    }
+__global__ void pinv_from_svd_kernel(const double* Ut, const double* Wm, const double* sig, int w,
+                                     double tol_rel, T* Xp) {
+  const double tol = tol_rel * sig[0];
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < w * w; e += blockDim.x * gridDim.x) {
+    const int i = e / w, j = e % w;
+    double acc = 0.0;
+    for (int t = 0; t < w; ++t)
+      if (sig[t] > tol) acc += Wm[i * w + t] * Ut[j * w + t] / sig[t];
+    Xp[e] = (T)acc;
   }
 }
 
@@ -102,7 +98,7 @@ template <typename T> constexpr double eps_of() {
 
 struct Alg1Layout {
   size_t ones, iota, row_prob, col_off, rowmap, colmap, counts, scale, Rp, Qp, tmp, gram_part, G64,
-      La, Lb, Lprod, Linv64, LinvT, kept, Cp, W, W2, Ub, Pb, partials, total;
+      La, Lb, Lprod, Linv64, LinvT, kept, Cp, W, W2, Ub, Pb, partials, SU, SW, Ssig, Sj, total;
   int64_t ldn, ldm, ldc, c_pad, r_pad;
   int ks_n, ks_c;
 };
@@ -149,6 +145,10 @@ Alg1Layout layout(int64_t m, int64_t n, int G, int64_t c_max, int r, size_t esz)
   L.Pb = take(m * r * esz);
   L.partials = take(2 * std::max(gemm_simt_resid_ctas<double>(m, n),
                                  gemm_simt_resid_ctas<float>(m, n)) * 8);
+  L.SU = take(rr * 8);
+  L.SW = take(rr * 8);
+  L.Ssig = take(r * 8);
+  L.Sj = take((int64_t)(r + 1) * (r + 1) * 8);
   L.total = cur;
   return L;
 }
@@ -243,12 +243,18 @@ bcur_status_t run_alg1(const T* A, int64_t lda, int64_t m, int64_t n, const int6
   BCUR_LAUNCH_CHECK();
   double* Lprod = (double*)(ws + L.Lprod);
   BCUR_TRY(orth_rows<T>(ws, L, s, W, W2, r, L.c_pad, L.ldc, L.ks_c, Lprod));
-  trinv_small_kernel<T><<<1, 128, 0, s>>>(Lprod, r, (double*)(ws + L.Linv64), (T*)(ws + L.LinvT));
+  // W = L Q_W with Q_W's kept rows orthonormal, so W^+ = Q_W^T L^+ exactly,
+  // also when W is rank deficient (rows drawn twice, low-rank A).
+  BCUR_TRY(jacobi_svd_small<double>(Lprod, r, (double*)(ws + L.SU), (double*)(ws + L.SW),
+                                    (double*)(ws + L.Ssig), (double*)(ws + L.Sj), nullptr, s));
+  pinv_from_svd_kernel<T><<<(r * r + 255) / 256, 256, 0, s>>>(
+      (double*)(ws + L.SU), (double*)(ws + L.SW), (double*)(ws + L.Ssig), r,
+      (double)std::max<int64_t>(r, c_max) * eps_of<T>(), (T*)(ws + L.LinvT));
   BCUR_LAUNCH_CHECK();
   GemmDesc gu;
   gu.M = L.c_pad; gu.N = r; gu.K = r;
   gu.A = W; gu.lda = L.ldc; gu.transA = 1;
-  gu.B = ws + L.LinvT; gu.ldb = r; gu.triB = 1;
+  gu.B = ws + L.LinvT; gu.ldb = r;
   gu.D = Ub; gu.ldd = r;
   BCUR_TRY(gemm_simt<T>(gu, s));
   if (Uout) BCUR_TRY(copy2d<T>(Ub, r, Uout, r, c_max, r, s));

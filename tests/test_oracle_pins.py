@@ -431,3 +431,16 @@ def test_algorithm1_uniform_rows_follow_the_inverse_cdf():
     u = [0.0, 0.49, 0.999, 0.25]
     idx, p = orc.sample_blocks(np.ones(10), u, 4, True)
     assert idx == [0, 4, 9, 2] and all(abs(x - 0.1) < 1e-15 for x in p)
+
+
+def test_sampling_matrix_with_unequal_blocks_selects_and_scales():
+    """Blocks of sizes 1, 3, 2: A S takes the drawn blocks in draw order, each
+    scaled by 1/sqrt(g p)."""
+    off = [0, 1, 4, 6]
+    S = orc.sampling_matrix([2, 0, 2], [0.5, 0.25, 0.5], off)
+    assert S.shape == (6, 5)
+    A = np.arange(12.0).reshape(2, 6)
+    got = A @ S
+    want = np.hstack([A[:, 4:6] / math.sqrt(1.5), A[:, 0:1] / math.sqrt(0.75),
+                      A[:, 4:6] / math.sqrt(1.5)])
+    np.testing.assert_allclose(got, want, atol=1e-14)
