@@ -165,6 +165,19 @@ bcur_status_t bcur_fit(bcur_plan_t plan, const void* A, const int32_t* col_idx,
  * repeated calls give bit-identical results. */
 bcur_status_t bcur_error(bcur_plan_t plan, const void* A, double* out);
 
+/* Rank-kt truncation of the last fit's U (Sec. 4.1: U_k, the best rank-k
+ * approximation of U, gives an exactly rank-k CUR).  The top-kt singular
+ * triplets of U (c x r) come from the same randomized range finder as the
+ * scores (q steps of subspace iteration, l = k + p columns, test matrix omega
+ * given as a panel l x r_max, ld r_max, storage type of A); then
+ *   Uk  (device, optional)  U_k, row-major c_max x r_max (ld r_max);
+ *   out (device, 3 doubles) ||A - C U_k R||_F, its ratio to ||A||_F, ||A||_F.
+ * CUDA-core arithmetic in the storage precision.  1 <= kt <= desc.k; needs
+ * l <= min(c, r).  Errors: BCUR_ESTATE (no fit yet), BCUR_EINVAL, BCUR_ENOTSUP
+ * (c or r larger than the padded m or n). */
+bcur_status_t bcur_truncate(bcur_plan_t plan, const void* A, int32_t kt, const void* omega,
+                            void* Uk, double* out);
+
 /* Sizes of the last fit: c, r, and the number of kept directions of C and
  * R^T.  Host pointers; synchronises the plan's stream. */
 bcur_status_t bcur_rank(bcur_plan_t plan, int64_t* c, int64_t* r, int64_t* rank_c,

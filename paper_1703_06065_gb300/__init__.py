@@ -24,7 +24,7 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "alg1", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
+__all__ = ["Plan", "alg1", "boosted", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
            "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
@@ -171,6 +171,17 @@ class Plan:
         _lib.check(self._L.bcur_error(self._h, _ptr(A), _ptr(out)), "bcur_error")
         return out
 
+    def truncate(self, A, kt: int, omega, want_u: bool = True):
+        """Rank-kt U_k of the last fit (Sec. 4.1) and ||A - C U_k R||_F
+        (returns U_k or None, and {err, rel, ||A||})."""
+        torch = _torch()
+        _need_cuda(A, omega)
+        Uk = torch.empty(self.c_max, self.r_max, dtype=self.tdtype, device=A.device) if want_u else None
+        out = torch.empty(3, dtype=torch.float64, device=A.device)
+        _lib.check(self._L.bcur_truncate(self._h, _ptr(A), kt, _ptr(omega), _ptr(Uk), _ptr(out)),
+                   "bcur_truncate")
+        return Uk, out
+
     def rank(self):
         v = [c_int64() for _ in range(4)]
         _lib.check(self._L.bcur_rank(self._h, *[byref(x) for x in v]), "bcur_rank")
@@ -305,6 +316,19 @@ def alg1(A, col_off, r: int, g: int, u_rows, u_cols, want_u: bool = True):
                            _ptr(ri), _ptr(ci), _ptr(cs), _ptr(cp), _ptr(U), _ptr(err), _ptr(ws),
                            c_size_t(ws.numel()), _stream()), "bcur_alg1")
     return dict(row_idx=ri, col_idx=ci, col_scores=cs, col_prob=cp, U=U, err=err)
+
+
+def boosted(plan: Plan, A, omegas, u_cols, u_rows):
+    """Boosting (Sec. 3.3): run the decomposition once per (omega, u_col, u_row)
+    triple and keep the run with the smallest ||A - CUR||_F.  Returns the
+    chosen run's outputs and the index of the run."""
+    best, best_i, best_e = None, -1, float("inf")
+    for i, (om, uc, ur) in enumerate(zip(omegas, u_cols, u_rows)):
+        res = decompose(plan, A, om, uc, ur)
+        e = float(res["err"][0].item())
+        if e < best_e:
+            best, best_i, best_e = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in res.items()}, i, e
+    return best, best_i
 
 
 def decompose(plan: Plan, A, omega, u_col, u_row, col_idx=None, row_idx=None):

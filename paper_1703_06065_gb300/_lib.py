@@ -26,7 +26,7 @@ EXPORTS = [
     "bcur_block_scores", "bcur_sample_blocks", "bcur_residual_workspace", "bcur_residual",
     "bcur_gemm", "bcur_launch_count", "bcur_version", "bcur_residual_noalloc",
     "bcur_gemm_split", "bcur_block_stable_rank_workspace", "bcur_block_stable_rank",
-    "bcur_alg1_workspace", "bcur_alg1",
+    "bcur_alg1_workspace", "bcur_alg1", "bcur_truncate",
 ]
 
 
@@ -122,6 +122,8 @@ def load():
                             c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                             c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
     L.bcur_alg1.restype = st
+    L.bcur_truncate.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]
+    L.bcur_truncate.restype = st
     L.bcur_launch_count.argtypes = []
     L.bcur_launch_count.restype = ctypes.c_uint64
     L.bcur_version.argtypes = []

@@ -756,6 +756,74 @@ bcur_status_t run_error16(bcur_plan_t P, const float* A, double* out) {
   return finish_residual(P->at<double>(P->o.partials), np, out, 0, P->stream);
 }
 
+
+// --- Rank-k truncation of U (Sec. 4.1) -------------------------------------
+// Randomized top-kt SVD of U (c x r, in the workspace) with the plan's
+// skinny temporaries, then U_k = Ut_k^T diag(sigma) V_k and
+// ||A - C U_k R||_F through P_k = C Ut_k^T (m x kt) and Q_k = diag(sigma) V_k R
+// (kt x n) in the fused residual.  CUDA cores, storage precision.
+template <typename T>
+bcur_status_t run_truncate(bcur_plan_t P, const T* A, int kt, const T* omega, T* Ukout,
+                           double* out) {
+  cudaStream_t s = P->stream;
+  const int l = P->l;
+  const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
+  const int64_t cw = P->c_pad, rw = P->r_pad, c = P->c_max, r = P->r_max;
+  const int ex = exact_prec<T>();
+  T* U = P->at<T>(P->o.U2);  // c_pad x r_pad, ld r_pad
+  T* Ym = P->at<T>(P->o.Pm0);
+  T* Ym1 = P->at<T>(P->o.Pm1);
+  T* Zn = P->at<T>(P->o.Pn0);
+  T* Zn1 = P->at<T>(P->o.Pn1);
+  const int ks_c = (int)std::max<int64_t>(1, std::min<int64_t>(2 * P->sms, cw / 64));
+  const int ks_r = (int)std::max<int64_t>(1, std::min<int64_t>(2 * P->sms, rw / 64));
+  // range finder on U: Y^T = Omega^T U^T, q steps of subspace iteration
+  BCUR_TRY(gemm_simt<T>(mk(l, cw, r, omega, r, 0, U, rw, 1, Ym, ldm), s));
+  BCUR_TRY(orth_panel<T>(P, Ym, Ym1, l, cw, ldm, ks_c, ex, nullptr));
+  for (int it = 0; it < P->q; ++it) {
+    BCUR_TRY(gemm_simt<T>(mk(l, rw, cw, Ym, ldm, 0, U, rw, 0, Zn, ldn), s));
+    BCUR_TRY(orth_panel<T>(P, Zn, Zn1, l, rw, ldn, ks_r, ex, nullptr));
+    BCUR_TRY(gemm_simt<T>(mk(l, cw, rw, Zn, ldn, 0, U, rw, 1, Ym, ldm), s));
+    BCUR_TRY(orth_panel<T>(P, Ym, Ym1, l, cw, ldm, ks_c, ex, nullptr));
+  }
+  BCUR_TRY(gemm_simt<T>(mk(l, rw, cw, Ym, ldm, 0, U, rw, 0, Zn, ldn), s));
+  double* LB = P->at<double>(P->o.Lprod64);
+  BCUR_TRY(orth_panel<T>(P, Zn, Zn1, l, rw, ldn, ks_r, ex, LB));
+  T* Ut = P->at<T>(P->o.Ut);
+  T* W = P->at<T>(P->o.W);
+  double* sig = P->at<double>(P->o.sigma) + l;  // second half of the sigma slot
+  BCUR_TRY(jacobi_svd_small<T>(LB, l, Ut, W, sig, P->at<T>(P->o.jwork), P->at<int>(P->o.status),
+                               s));
+  // Left factor X = Ut_k^T Q^T (kt x c) and right factor Y = diag(sigma) W_k^T Q_B^T (kt x r).
+  T* Xp = P->at<T>(P->o.Pm1);
+  T* Yp = P->at<T>(P->o.Pn1);
+  BCUR_TRY(gemm_simt<T>(mk(kt, cw, l, Ut, l, 1, Ym, ldm, 0, Xp, ldm), s));
+  BCUR_TRY(gemm_simt<T>(mk(kt, rw, l, W, l, 1, Zn, ldn, 0, Yp, ldn), s));
+  BCUR_TRY(scale_rows_by(Yp, kt, rw, ldn, sig, s));
+  if (Ukout) {  // U_k = X^T Y
+    T* Ub = P->at<T>(P->o.U1);
+    BCUR_TRY(gemm_simt<T>(mk(cw, rw, kt, Xp, ldm, 1, Yp, ldn, 0, Ub, rw), s));
+    BCUR_TRY(copy2d<T>(Ub, rw, Ukout, r, c, r, s));
+  }
+  // C and R gathered again (the fit may have overwritten them with Q factors)
+  T* Cp = P->at<T>(P->o.Cp1);
+  T* Rp = P->at<T>(P->o.Rp1);
+  BCUR_TRY(gather_cols_t<T>(A, lda, m, P->at<int64_t>(P->o.colmap), cw, Cp, ldm, s));
+  BCUR_TRY(gather_rows<T>(A, lda, n, P->at<int64_t>(P->o.rowmap), rw, Rp, ldn, s));
+  // P_k = C X^T (m x kt) = Cp^T X^T;  Q_k = Y R (kt x n)
+  T* Pk = P->at<T>(P->o.Wb);
+  T* Qk = P->at<T>(P->o.Pn2);
+  BCUR_TRY(gemm_simt<T>(mk(m, kt, cw, Cp, ldm, 1, Xp, ldm, 1, Pk, kt), s));
+  BCUR_TRY(gemm_simt<T>(mk(kt, n, rw, Yp, ldn, 0, Rp, ldn, 0, Qk, ldn), s));
+  GemmDesc rd = mk(m, n, kt, Pk, kt, 0, Qk, ldn, 0, nullptr, 0);
+  rd.X = A;
+  rd.ldx = lda;
+  rd.partials = P->at<double>(P->o.partials);
+  int64_t np = 0;
+  BCUR_TRY(gemm_simt_resid<T>(rd, s, &np));
+  return finish_residual(P->at<double>(P->o.partials), np, out, 0, s);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -863,7 +931,7 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
   o.LinvT = L.take(ll * e);
   o.Ut = L.take(ll * e);
   o.W = L.take(ll * e);
-  o.sigma = L.take(l * 8);
+  o.sigma = L.take(2 * l * 8);
   o.jwork = L.take((l + 1) * (l + 1) * e);
   o.Vp = L.take((int64_t)P->k * P->ldn * e);
   o.Up = L.take((int64_t)P->k * P->ldm * e);
@@ -1045,6 +1113,18 @@ bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {
   if (P->d.a_dtype == BCUR_F64) return run_error<double>(P, (const double*)A, out);
   if (is_bf16_prec(P->d.fit_prec)) return run_error16(P, (const float*)A, out);
   return run_error<float>(P, (const float*)A, out);
+}
+
+bcur_status_t bcur_truncate(bcur_plan_t P, const void* A, int32_t kt, const void* omega,
+                            void* Uk, double* out) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws || !P->have_fit) return BCUR_ESTATE;
+  if (!A || !omega || !out || kt < 1 || kt > P->k) return BCUR_EINVAL;
+  if (P->c_pad > P->ldm || P->r_pad > P->ldn || P->l > std::min(P->c_max, P->r_max))
+    return BCUR_ENOTSUP;
+  if (P->d.a_dtype == BCUR_F64)
+    return run_truncate<double>(P, (const double*)A, kt, (const double*)omega, (double*)Uk, out);
+  return run_truncate<float>(P, (const float*)A, kt, (const float*)omega, (float*)Uk, out);
 }
 
 bcur_status_t bcur_rank(bcur_plan_t P, int64_t* c, int64_t* r, int64_t* rank_c, int64_t* rank_r) {

@@ -137,6 +137,10 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
 
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
 
+template <typename T>
+bcur_status_t scale_rows_by(T* X, int64_t rows, int64_t cols, int64_t ld, const double* sc,
+                            cudaStream_t s);
+
 // Split an FP32 matrix (rows x cols, ldx) into BF16 pairs: hi = bf16(x),
 // lo = bf16(x - hi) (round to nearest even both times); outputs have
 // leading dimension ldo; lo may be null (hi only).

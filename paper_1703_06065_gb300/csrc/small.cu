@@ -718,6 +718,30 @@ size_t block_stable_rank_workspace(int k, int G) {
 }
 
 // ---------------------------------------------------------------------------
+// Row scaling X[i][:] *= s[i] (FP64 scale factors)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void scale_rows_by_kernel(T* X, int64_t rows, int64_t cols, int64_t ld, const double* sc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    X[i * ld + j] = (T)((double)X[i * ld + j] * sc[i]);
+  }
+}
+
+template <typename T>
+bcur_status_t scale_rows_by(T* X, int64_t rows, int64_t cols, int64_t ld, const double* sc,
+                            cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return BCUR_OK;
+  const int64_t blocks = std::min<int64_t>(ceil_div(rows * cols, 256), 4096);
+  scale_rows_by_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, rows, cols, ld, sc);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+template bcur_status_t scale_rows_by<float>(float*, int64_t, int64_t, int64_t, const double*, cudaStream_t);
+template bcur_status_t scale_rows_by<double>(double*, int64_t, int64_t, int64_t, const double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // FP32 -> BF16 hi/lo pairs
 // ---------------------------------------------------------------------------
 __global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int64_t cols,
