@@ -242,15 +242,19 @@ def scaled_haar(m: int, n: int, s: int, k: int, p: int, q: int, g_col: int, g_ro
                    recipe=dict(kind="haar_spectrum", rank=min(rank, m, n), decay=1.5, noise=noise))
 
 
-def batched_biometric(count: int = 512, seed: int = 3) -> List[Problem]:
-    """Uneven batch: m~U[256,4096], n~U[1024,16384] (rounded down to s), s in {16..256}, k~U[5,50]."""
+def batched_biometric(count: int = 512, seed: int = 3, m_range=(256, 4096), n_range=(1024, 16384),
+                      k_range=(5, 50), blocks=(16, 32, 64, 128, 256)) -> List[Problem]:
+    """Uneven batch: m~U[256,4096], n~U[1024,16384] (rounded down to s), s in {16..256}, k~U[5,50].
+
+    The ranges can be narrowed for test-sized batches; the defaults are the
+    512-matrix biometric workload."""
     g = rng(seed, STREAM_SHAPES)
     out = []
     for i in range(count):
-        s = int(g.choice([16, 32, 64, 128, 256]))
-        m = int(g.integers(256, 4097)) // s * s
-        n = int(g.integers(1024, 16385)) // s * s
-        k = int(g.integers(5, 51))
+        s = int(g.choice(list(blocks)))
+        m = int(g.integers(m_range[0], m_range[1] + 1)) // s * s
+        n = int(g.integers(n_range[0], n_range[1] + 1)) // s * s
+        k = int(g.integers(k_range[0], k_range[1] + 1))
         Gc, Gr = n // s, m // s
         out.append(Problem(f"bio_{i}", m, n, k=k, p=10, q=2,
                            col_off=uniform_blocks(n, s), row_off=uniform_blocks(m, s),

@@ -316,6 +316,80 @@ bcur_status_t bcur_gemm_split(int64_t M, int64_t N, int64_t K, const void* A_hi,
                               int64_t lda, int32_t transA, const void* B_hi, const void* B_lo,
                               int64_t ldb, int32_t transB, float* D, int64_t ldd, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched decompositions: many matrices of different m, n, block size and k
+ * in one pass of the method, each stage one launch over the whole batch
+ * (grouped tcgen05 GEMMs walking every matrix's tiles in one persistent
+ * launch, and grouped small kernels).  Same method and precision as a plan
+ * with sketch_prec = BCUR_BF16 and fit_prec = BCUR_BF16X3 on FP32 storage:
+ * scores from the randomized range finder (Sec. 3.1 allows sketching), block
+ * sampling without replacement (Sec. 4.1), U = C^+ A R^+, ||A - CUR||_F.
+ * A decomposition's results do not depend on the other members of the
+ * batch: every per-matrix sum is formed in a fixed order by the same units of
+ * work, whatever else runs beside it.
+ */
+typedef struct {
+  int64_t m, n, lda;   /* A: FP32, row-major m x n, lda >= n, lda % 4 == 0    */
+  int32_t k, p;        /* rank and oversampling, l = k + p <= 64              */
+  int32_t block;       /* s: column blocks [j s, min((j+1) s, n)), row blocks
+                          likewise over m; G_col = ceil(n/s), G_row = ceil(m/s) */
+  int32_t g_col, g_row;/* blocks drawn without replacement; g * s <= 512     */
+} bcur_batch_item_t;
+
+/* Per-decomposition device pointers of one run (all device memory):
+ *   A          FP32 m x n (lda);  omega: the test matrix as a panel l x n
+ *              (ld n, FP32);  u_col (g_col), u_row (g_row): uniforms in [0,1);
+ *   col_scores (G_col), row_scores (G_row) doubles;  col_idx (g_col),
+ *   row_idx (g_row) int32, in draw order;  U: FP32 (g_col s) x (g_row s),
+ *   ld g_row s, rows / columns in gather order, zero past the actual c, r
+ *   (may be NULL);  err: 3 doubles {||A - CUR||_F, its ratio to ||A||_F,
+ *   ||A||_F}. */
+typedef struct {
+  const float* A;
+  const float* omega;
+  const double* u_col;
+  const double* u_row;
+  double* col_scores;
+  double* row_scores;
+  int32_t* col_idx;
+  int32_t* row_idx;
+  float* U;
+  double* err;
+} bcur_batch_io_t;
+
+typedef struct bcur_batch_s* bcur_batch_t;
+
+/* Validate `count` items and size the workspace; q subspace iterations
+ * (0..16) for every item.  Allocates no device memory.  Errors: BCUR_EINVAL
+ * (an item out of range: l > 64, g > G, g * s > 512, lda < n or not a
+ * multiple of 4, count < 1), BCUR_ENOTSUP (no sm_103 tensor cores). */
+bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int32_t q,
+                              void* stream, bcur_batch_t* out, size_t* workspace_bytes);
+
+/* Attach caller-owned device memory (>= workspace_bytes, 256-byte aligned)
+ * and build the launch tables in it (tensor maps of every grouped GEMM,
+ * work lists).  Synchronous.  Errors: BCUR_EINVAL, BCUR_ENOMEM, BCUR_ECUDA. */
+bcur_status_t bcur_batch_set_workspace(bcur_batch_t plan, void* workspace, size_t bytes);
+
+/* Run the whole method for every item; io: host array of `count` entries
+ * (read before the call returns).  Asynchronous on the plan's stream.  With
+ * use_graph != 0 the launch sequence is captured into a CUDA graph on the
+ * first call and replayed afterwards (the io table is copied by the graph
+ * from the plan's pinned staging buffer).  Errors: BCUR_ESTATE (no
+ * workspace), BCUR_EINVAL (NULL pointer in io). */
+bcur_status_t bcur_batch_run(bcur_batch_t plan, const bcur_batch_io_t* io, int32_t use_graph);
+
+/* Padded sizes of item i: cmax = g_col s, rmax = g_row s (the U layout), and
+ * the number of kernel launches one run makes. */
+bcur_status_t bcur_batch_dims(bcur_batch_t plan, int32_t i, int64_t* cmax, int64_t* rmax,
+                              int64_t* launches_per_run);
+
+/* Synchronise the plan's stream and return (then clear) the first error the
+ * device recorded. */
+bcur_status_t bcur_batch_sync_status(bcur_batch_t plan);
+
+void bcur_batch_destroy(bcur_batch_t plan);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices).  Used to report launches per timed step. */
 uint64_t bcur_launch_count(void);

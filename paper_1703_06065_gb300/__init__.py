@@ -24,7 +24,7 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "alg1", "boosted", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
+__all__ = ["Plan", "Batch", "alg1", "boosted", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
            "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
@@ -192,6 +192,118 @@ class Plan:
 
 
 # -- plan-free stage kernels -------------------------------------------------
+
+
+class Batch:
+    """Many decompositions of different sizes in one pass of the method.
+
+    ``items``: sequence of dicts with keys m, n, k, p, block, g_col, g_row (and
+    optionally lda).  Every stage runs as one launch over the whole batch
+    (BF16 sketch, split-BF16 fit, FP32 storage).  The plan and its workspace
+    are built once; :meth:`run` takes per-item device tensors.
+    """
+
+    def __init__(self, items, q: int = 2, device=None):
+        torch = _torch()
+        L = _lib.load()
+        self._L = L
+        self.items = [dict(it) for it in items]
+        B = len(self.items)
+        arr = (_lib.BatchItem * B)()
+        for i, it in enumerate(self.items):
+            a = arr[i]
+            a.m, a.n = it["m"], it["n"]
+            a.lda = it.get("lda", it["n"])
+            a.k, a.p, a.block = it["k"], it["p"], it["block"]
+            a.g_col, a.g_row = it["g_col"], it["g_row"]
+        self._arr = arr
+        self.B, self.q = B, q
+        h = c_void_p()
+        ws = c_size_t()
+        _lib.check(L.bcur_batch_plan(arr, B, q, _stream(), byref(h), byref(ws)), "bcur_batch_plan")
+        self._h = h
+        self.workspace_bytes = ws.value
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self._ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=dev)
+        _lib.check(L.bcur_batch_set_workspace(h, _ptr(self._ws), c_size_t(self._ws.numel())),
+                   "bcur_batch_set_workspace")
+        self.G_col = [-(-it["n"] // it["block"]) for it in self.items]
+        self.G_row = [-(-it["m"] // it["block"]) for it in self.items]
+        self.c_max = [it["g_col"] * it["block"] for it in self.items]
+        self.r_max = [it["g_row"] * it["block"] for it in self.items]
+        self._out = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self._L.bcur_batch_destroy(h)
+            except Exception:  # pragma: no cover
+                pass
+            self._h = None
+
+    def _outputs(self, want_u: bool):
+        """One flat buffer per output kind; per-item views into it."""
+        torch = _torch()
+        if self._out is not None and self._out["want_u"] == want_u:
+            return self._out
+        dev = self.device
+
+        def views(sizes, dtype):
+            flat = torch.zeros(max(1, sum(sizes)), dtype=dtype, device=dev)
+            out, at = [], 0
+            for s in sizes:
+                out.append(flat[at:at + s])
+                at += s
+            return out
+
+        its = self.items
+        o = dict(want_u=want_u,
+                 col_scores=views(self.G_col, torch.float64),
+                 row_scores=views(self.G_row, torch.float64),
+                 col_idx=views([it["g_col"] for it in its], torch.int32),
+                 row_idx=views([it["g_row"] for it in its], torch.int32),
+                 err=views([3] * self.B, torch.float64))
+        if want_u:
+            us = views([c * r for c, r in zip(self.c_max, self.r_max)], torch.float32)
+            o["U"] = [u.view(c, r) for u, c, r in zip(us, self.c_max, self.r_max)]
+        else:
+            o["U"] = [None] * self.B
+        self._out = o
+        return o
+
+    def run(self, As, omegas, u_cols, u_rows, want_u: bool = True, use_graph: bool = False):
+        """Scores, sampling, fit and error for every item (asynchronous on the
+        plan's stream).  ``omegas[i]`` is the test matrix as an l x n panel.
+        Returns dict of per-item device tensors (reused by the next run)."""
+        B = self.B
+        if not (len(As) == len(omegas) == len(u_cols) == len(u_rows) == B):
+            raise ValueError("one A, omega, u_col, u_row per item")
+        _need_cuda(*As, *omegas, *u_cols, *u_rows)
+        o = self._outputs(want_u)
+        io = (_lib.BatchIO * B)()
+        for i in range(B):
+            e = io[i]
+            e.A, e.omega = As[i].data_ptr(), omegas[i].data_ptr()
+            e.u_col, e.u_row = u_cols[i].data_ptr(), u_rows[i].data_ptr()
+            e.col_scores, e.row_scores = o["col_scores"][i].data_ptr(), o["row_scores"][i].data_ptr()
+            e.col_idx, e.row_idx = o["col_idx"][i].data_ptr(), o["row_idx"][i].data_ptr()
+            e.U = o["U"][i].data_ptr() if want_u else None
+            e.err = o["err"][i].data_ptr()
+        self._keep = (As, omegas, u_cols, u_rows)
+        _lib.check(self._L.bcur_batch_run(self._h, io, int(bool(use_graph))), "bcur_batch_run")
+        return o
+
+    @property
+    def launches_per_run(self) -> int:
+        c, r, nl = c_int64(), c_int64(), c_int64()
+        _lib.check(self._L.bcur_batch_dims(self._h, 0, byref(c), byref(r), byref(nl)),
+                   "bcur_batch_dims")
+        return nl.value
+
+    def sync_status(self):
+        _lib.check(self._L.bcur_batch_sync_status(self._h), "bcur_batch_sync_status")
 
 def block_scores(Ft, off, out=None):
     """Def. 2 scores of the factor whose panel (k x h) is ``Ft``; ``off`` device int64."""

@@ -26,7 +26,9 @@ EXPORTS = [
     "bcur_block_scores", "bcur_sample_blocks", "bcur_residual_workspace", "bcur_residual",
     "bcur_gemm", "bcur_launch_count", "bcur_version", "bcur_residual_noalloc",
     "bcur_gemm_split", "bcur_block_stable_rank_workspace", "bcur_block_stable_rank",
-    "bcur_alg1_workspace", "bcur_alg1", "bcur_truncate",
+    "bcur_alg1_workspace", "bcur_alg1", "bcur_truncate", "bcur_batch_plan",
+    "bcur_batch_set_workspace", "bcur_batch_run", "bcur_batch_dims", "bcur_batch_sync_status",
+    "bcur_batch_destroy",
 ]
 
 
@@ -51,6 +53,20 @@ class Desc(ctypes.Structure):
         ("g_col", c_int32), ("g_row", c_int32), ("replacement", c_int32),
         ("sketch_prec", c_int32), ("fit_prec", c_int32),
     ]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("m", c_int64), ("n", c_int64), ("lda", c_int64),
+        ("k", c_int32), ("p", c_int32), ("block", c_int32), ("g_col", c_int32),
+        ("g_row", c_int32),
+    ]
+
+
+class BatchIO(ctypes.Structure):
+    _fields_ = [(name, c_void_p) for name in (
+        "A", "omega", "u_col", "u_row", "col_scores", "row_scores", "col_idx", "row_idx", "U",
+        "err")]
 
 
 _lib = None
@@ -124,6 +140,20 @@ def load():
     L.bcur_alg1.restype = st
     L.bcur_truncate.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]
     L.bcur_truncate.restype = st
+    L.bcur_batch_plan.argtypes = [POINTER(BatchItem), c_int32, c_int32, c_void_p,
+                                  POINTER(c_void_p), POINTER(c_size_t)]
+    L.bcur_batch_plan.restype = st
+    L.bcur_batch_set_workspace.argtypes = [c_void_p, c_void_p, c_size_t]
+    L.bcur_batch_set_workspace.restype = st
+    L.bcur_batch_run.argtypes = [c_void_p, POINTER(BatchIO), c_int32]
+    L.bcur_batch_run.restype = st
+    L.bcur_batch_dims.argtypes = [c_void_p, c_int32, POINTER(c_int64), POINTER(c_int64),
+                                  POINTER(c_int64)]
+    L.bcur_batch_dims.restype = st
+    L.bcur_batch_sync_status.argtypes = [c_void_p]
+    L.bcur_batch_sync_status.restype = st
+    L.bcur_batch_destroy.argtypes = [c_void_p]
+    L.bcur_batch_destroy.restype = None
     L.bcur_launch_count.argtypes = []
     L.bcur_launch_count.restype = ctypes.c_uint64
     L.bcur_version.argtypes = []

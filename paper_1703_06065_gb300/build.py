@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbcur.so")
-SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "small.cu", "noalloc.cu", "alg1.cu"]
+SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "small.cu", "noalloc.cu", "alg1.cu", "batch.cu",
+           "batch_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

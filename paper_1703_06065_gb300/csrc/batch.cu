@@ -1,0 +1,648 @@
+// Grouped small kernels of the batched Block CUR path (sm_103a).  Each
+// launch covers every decomposition of the batch: a CTA finds its
+// decomposition through a prefix-sum work list (or blockIdx.x when the work
+// is one CTA per decomposition) and reads the decomposition's sizes and
+// buffers from the device table of Items.  Every per-decomposition sum is
+// formed by the same CTA in the same order whatever else is in the batch, so
+// a decomposition's results do not depend on its neighbours.
+#include "batch.h"
+#include "leaf.cuh"
+
+namespace bcur {
+namespace batch {
+
+namespace {
+
+__device__ __forceinline__ float* panel(const Item& I, int sel) {
+  switch (sel) {
+    case PM0: return I.Pm0;
+    case PM1: return I.Pm1;
+    case PN0: return I.Pn0;
+    default: return I.Pn1;
+  }
+}
+__device__ __forceinline__ int64_t panel_h(const Item& I, int sel) { return sel < PN0 ? I.m : I.n; }
+__device__ __forceinline__ int64_t panel_ld(const Item& I, int sel) {
+  return sel < PN0 ? I.ldm : I.ldn;
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block sum: strided per thread (caller), xor tree per warp,
+// warps in order.  Result valid in thread 0.
+__device__ double block_sum(double v, double* red) {
+  v = wsum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// A -> BF16 hi/lo pair (8 rows per CTA) and Omega^T -> BF16 panel (zero rows
+// past l), one launch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcur_batch_io_t* io,
+                                                    Work rows8, int total8) {
+  const int x = blockIdx.x;
+  if (x < total8) {
+    const int b = find_item(rows8, x);
+    const Item& I = items[b];
+    const int64_t r0 = (int64_t)(x - rows8.prefix[b]) * 8;
+    const float* A = io[b].A;
+    const bool v4 = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (I.lda % 4 == 0) &&
+                    (I.n % 4 == 0);
+    for (int rr = 0; rr < 8; ++rr) {
+      const int64_t r = r0 + rr;
+      if (r >= I.m) break;
+      const float* xr = A + r * I.lda;
+      bf16* hr = I.Ah + r * I.ldn;
+      bf16* lr = I.Al + r * I.ldn;
+      if (v4) {
+        for (int64_t c = threadIdx.x; c < I.n / 4; c += blockDim.x) {
+          const float4 v = reinterpret_cast<const float4*>(xr)[c];
+          const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y);
+          const __nv_bfloat162 h23 = __floats2bfloat162_rn(v.z, v.w);
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          reinterpret_cast<__nv_bfloat162*>(hr)[2 * c] = h01;
+          reinterpret_cast<__nv_bfloat162*>(hr)[2 * c + 1] = h23;
+          reinterpret_cast<__nv_bfloat162*>(lr)[2 * c] = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+          reinterpret_cast<__nv_bfloat162*>(lr)[2 * c + 1] =
+              __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+        }
+      } else {
+        for (int64_t c = threadIdx.x; c < I.n; c += blockDim.x) {
+          const float v = xr[c];
+          const bf16 h = __float2bfloat16_rn(v);
+          hr[c] = h;
+          lr[c] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+      }
+    }
+  } else {
+    const int y = x - total8;
+    const int b = y / (LP / 8);
+    const Item& I = items[b];
+    const int t0 = (y % (LP / 8)) * 8;
+    for (int tt = 0; tt < 8; ++tt) {
+      const int t = t0 + tt;
+      bf16* o = I.Om + (int64_t)t * I.ldn;
+      const float* om = io[b].omega + (int64_t)t * I.n;
+      for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x)
+        o[j] = __float2bfloat16_rn(t < I.l ? om[j] : 0.f);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Skinny Cholesky-QR of an LP x h panel X (rows l..LP-1 zero):
+//   gram:  per chunk of CH columns, the FP32 partial Gram X_c X_c^T;
+//   chol:  FP64 sum of the partials in chunk order, Cholesky with the drop
+//          rule (64 u of FP32, relative to the largest diagonal entry) and
+//          L^{-1};
+//   apply: X' = L^{-1} X (FP32), optionally also as BF16 for the next
+//          product with A.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chunks, int sel) {
+  const int b = find_item(chunks, blockIdx.x);
+  const Item& I = items[b];
+  const int ch = blockIdx.x - chunks.prefix[b];
+  const float* X = panel(I, sel);
+  const int64_t h = panel_h(I, sel), ld = panel_ld(I, sel);
+  __shared__ float Xs[LP][65];
+  const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  const int64_t c_begin = (int64_t)ch * CH;
+  const int64_t c_end = c_begin + CH < h ? c_begin + CH : h;
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += 64) {
+    for (int e = tid; e < LP * 64; e += 256) {
+      const int r = e / 64, c = e % 64;
+      Xs[r][c] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < 64; ++c) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = Xs[4 * ti + q][c];
+        bb[q] = Xs[4 * tj + q][c];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
+    }
+    __syncthreads();
+  }
+  float* out = I.gpart + (int64_t)ch * LP * LP;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) out[(4 * ti + q) * LP + 4 * tj + p] = acc[q][p];
+}
+
+__global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, int pass,
+                                                    int want_lb) {
+  extern __shared__ double S[];  // LP x (LP + 1)
+  const Item& I = items[blockIdx.x];
+  const int nch = sel < PN0 ? I.chunks_m : I.chunks_n;
+  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
+    double g = 0.0;
+    for (int c = 0; c < nch; ++c) g += (double)I.gpart[(int64_t)c * LP * LP + e];
+    I.G64[e] = g;
+  }
+  __syncthreads();
+  double* L = pass ? I.L64b : I.L64a;
+  chol_small_body<float>(I.G64, LP, 64.0 * 1.1920928955078125e-07, L, I.Linv64, I.LinvT, nullptr,
+                         S);
+  if (want_lb && pass == 1) {
+    __syncthreads();
+    // L_B = L_a L_b: X = L_a Q' and Q' = L_b Q give X = L_a L_b Q
+    for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
+      const int i = e / LP, j = e % LP;
+      double acc = 0.0;
+      if (j <= i)
+        for (int k = j; k <= i; ++k) acc += I.L64a[i * LP + k] * I.L64b[k * LP + j];
+      I.Lb[e] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(AP) sapply_kernel(const Item* items, Work chunks, int src, int dst,
+                                                    int write_bf16) {
+  const int b = find_item(chunks, blockIdx.x);
+  const Item& I = items[b];
+  const int ch = blockIdx.x - chunks.prefix[b];
+  __shared__ float Ls[LP * LP];
+  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Ls[e] = I.LinvT[e];
+  __syncthreads();
+  const int64_t h = panel_h(I, src), ld = panel_ld(I, src);
+  const int64_t j = (int64_t)ch * AP + threadIdx.x;
+  if (j >= h) return;
+  const float* X = panel(I, src);
+  float* Y = panel(I, dst);
+  bf16* Yb = write_bf16 ? (src < PN0 ? I.Qh : I.Zh) : nullptr;
+  float x[LP];
+#pragma unroll
+  for (int t = 0; t < LP; ++t) x[t] = X[t * ld + j];
+  // rows in groups of 16; each output sums t = 0..r in increasing order
+#pragma unroll
+  for (int r0 = 0; r0 < LP; r0 += 16) {
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int t = 0; t < r0 + 16; ++t)
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (t <= r0 + q) acc[q] = fmaf(Ls[(r0 + q) * LP + t], x[t], acc[q]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      Y[(r0 + q) * ld + j] = acc[q];
+      if (Yb) Yb[(r0 + q) * ld + j] = __float2bfloat16_rn(acc[q]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block leverage scores (Def. 2) straight from the factors: with Q_B (the
+// panel in Pn0) and the right factor W of the small SVD, V_k^T = W_k^T Q_B^T,
+// so column j of V_k^T is W_k^T q_j; the score of block g is the FP64 sum of
+// the squares over the block's columns.  Row blocks use U~ and Q (Pm0).  One
+// CTA per block, fixed order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) scores_kernel(const Item* items, const bcur_batch_io_t* io,
+                                                     Work blocks, int* status) {
+  const int b = find_item(blocks, blockIdx.x);
+  const Item& I = items[b];
+  int g = blockIdx.x - blocks.prefix[b];
+  const bool col = g < I.Gc;
+  if (!col) g -= I.Gc;
+  const float* F = col ? I.W : I.Ut;
+  const float* P = col ? I.Pn0 : I.Pm0;
+  const int64_t h = col ? I.n : I.m, ld = col ? I.ldn : I.ldm;
+  const int k = I.k;
+  __shared__ float Fs[LP * LP];
+  __shared__ double red[4];
+  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Fs[e] = F[e];
+  __syncthreads();
+  const int64_t j0 = (int64_t)g * I.s;
+  const int64_t j1 = j0 + I.s < h ? j0 + I.s : h;
+  double acc = 0.0;
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    float p[LP];
+#pragma unroll
+    for (int i = 0; i < LP; ++i) p[i] = P[i * ld + j];
+    for (int t = 0; t < k; ++t) {
+      float v = 0.f;
+#pragma unroll
+      for (int i = 0; i < LP; ++i) v = fmaf(Fs[i * LP + t], p[i], v);
+      acc = fma((double)v, (double)v, acc);
+    }
+  }
+  const double sum = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    (col ? io[b].col_scores : io[b].row_scores)[g] = sum;
+    if (!isfinite(sum)) dev_set_status(status, (int)BCUR_ENONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sampling (Alg. 1 step 2, without replacement) and the gather map: one
+// thread per (decomposition, side).
+// ---------------------------------------------------------------------------
+__global__ void sample_kernel(const Item* items, const bcur_batch_io_t* io) {
+  if (threadIdx.x != 0) return;
+  const int b = blockIdx.x, side = blockIdx.y;
+  const Item& I = items[b];
+  const int G = side ? I.Gr : I.Gc, g = side ? I.gr : I.gc;
+  const double* sc = side ? io[b].row_scores : io[b].col_scores;
+  const double* u = side ? io[b].u_row : io[b].u_col;
+  int32_t* idx = side ? io[b].row_idx : io[b].col_idx;
+  sample_seq(sc, G, u, g, 0, idx, nullptr, I.remaining + (side ? I.Gc : 0));
+  int* map = side ? I.rowmap : I.colmap;
+  const int cap = side ? I.rpad : I.cpad;
+  const int64_t h = side ? I.m : I.n;
+  int base = 0;
+  for (int t = 0; t < g; ++t) {
+    const int64_t start = (int64_t)idx[t] * I.s;
+    const int64_t size = (h - start) < I.s ? (h - start) : I.s;
+    for (int64_t e = 0; e < size && base + e < cap; ++e) map[base + e] = (int)(start + e);
+    base += (int)size;
+  }
+  for (int e = base; e < cap; ++e) map[e] = -1;
+}
+
+// C^T panel (cpad x m) and R (rpad x n) as BF16 pairs, straight from A.
+__global__ void gather_c_kernel(const Item* items, const bcur_batch_io_t* io, Work tiles) {
+  const int b = find_item(tiles, blockIdx.x);
+  const Item& I = items[b];
+  const int t = blockIdx.x - tiles.prefix[b];
+  const int ti = (int)((I.m + 31) / 32);
+  const int64_t i0 = (int64_t)(t % ti) * 32, c0 = (int64_t)(t / ti) * 32;
+  __shared__ float tile[32][33];
+  const int x = threadIdx.x;
+  const int64_t cc = c0 + x;
+  const int col = cc < I.cpad ? I.colmap[cc] : -1;
+  const float* A = io[b].A;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t i = i0 + y;
+    tile[y][x] = (col >= 0 && i < I.m) ? A[i * I.lda + col] : 0.f;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t c = c0 + y, i = i0 + x;
+    if (c < I.cpad && i < I.m) {
+      const float v = tile[x][y];
+      const bf16 h = __float2bfloat16_rn(v);
+      I.XCh[0][c * I.ldm + i] = h;
+      I.XCl[0][c * I.ldm + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) gather_r_kernel(const Item* items,
+                                                       const bcur_batch_io_t* io, Work rows) {
+  const int b = find_item(rows, blockIdx.x);
+  const Item& I = items[b];
+  const int rr = blockIdx.x - rows.prefix[b];
+  const int row = I.rowmap[rr];
+  const float* A = io[b].A;
+  bf16* hr = I.XRh[0] + (int64_t)rr * I.ldn;
+  bf16* lr = I.XRl[0] + (int64_t)rr * I.ldn;
+  for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x) {
+    const float v = row >= 0 ? A[(int64_t)row * I.lda + j] : 0.f;
+    const bf16 h = __float2bfloat16_rn(v);
+    hr[j] = h;
+    lr[j] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wide Cholesky G = L L^T (w x w, w <= WMAX, FP32, lower part of G) with the
+// drop rule and L^{-1}, one CTA per (decomposition, side).  Right-looking by
+// leaves of NB columns: factor the leaf (potrf_leaf), solve the panel below
+// it (L_iJ = G_iJ L_JJ^{-T}, kept in shared memory), update the trailing
+// lower triangle in place.  Then L^{-1} block row by block row:
+// X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.  Writes L, L^{-1} (zeros above the
+// diagonal) and L^{-1} as a BF16 pair.
+// ---------------------------------------------------------------------------
+constexpr int WLD = NB + 4;   // leaf leading dimension (potrf_leaf<float, 64>)
+constexpr int PLD = NB + 1;
+constexpr size_t kWideSmem =
+    (size_t)(2 * NB * WLD + NB * PLD + (WMAX - NB) * PLD) * sizeof(float);
+
+__device__ __forceinline__ void tile_acc(const float* Arow, int lda, const float* Bcol, int ldb,
+                                         int ti, int tj, float (&acc)[4][4]) {
+  // acc[q][p] += sum_t A[4ti+q][t] * B[t][4tj+p], t < NB
+#pragma unroll 4
+  for (int t = 0; t < NB; ++t) {
+    float a[4], bb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = Arow[(4 * ti + q) * lda + t];
+      bb[q] = Bcol[t * ldb + 4 * tj + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
+  }
+}
+
+__global__ void __launch_bounds__(256, 1) wchol_kernel(const Item* items, int pass) {
+  extern __shared__ float sm[];
+  float* S = sm;              // NB x WLD: leaf L
+  float* X = S + NB * WLD;    // NB x WLD: leaf L^{-1}
+  float* XT = X + NB * WLD;   // NB x PLD: XT[t][c] = X[c][t]
+  float* Ps = XT + NB * PLD;  // (WMAX - NB) x PLD panel / inverse tiles
+  const Item& I = items[blockIdx.x];
+  const int side = blockIdx.y;
+  const int w = side ? I.rpad : I.cpad;
+  float* G = side ? I.GR : I.GC;
+  float* L = side ? I.LR[pass] : I.LC[pass];
+  float* Li = side ? I.LRi[pass] : I.LCi[pass];
+  bf16* Lh = side ? I.LRih[pass] : I.LCih[pass];
+  bf16* Ll = side ? I.LRil[pass] : I.LCil[pass];
+  const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
+  __shared__ float s_red[8];
+  __shared__ float s_tol;
+  float mx = 0.f;
+  for (int i = tid; i < w; i += 256) mx = fmaxf(mx, G[(int64_t)i * w + i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float m2 = 0.f;
+    for (int i = 0; i < 8; ++i) m2 = fmaxf(m2, s_red[i]);
+    s_tol = (float)(64.0 * 1.1920928955078125e-07 * (double)m2);
+  }
+  __syncthreads();
+  const float tol = s_tol;
+  const int nbk = w / NB;
+  int kept = 0;
+  for (int J = 0; J < nbk; ++J) {
+    const int j0 = J * NB;
+    kept += potrf_leaf<float, NB>(G + (int64_t)j0 * w + j0, w, S, X, tol);
+    for (int e = tid; e < NB * NB; e += 256) {
+      const int i = e / NB, c = e % NB;
+      L[(int64_t)(j0 + i) * w + j0 + c] = c <= i ? S[i * WLD + c] : 0.f;
+      Li[(int64_t)(j0 + i) * w + j0 + c] = c <= i ? X[i * WLD + c] : 0.f;
+      XT[c * PLD + i] = X[i * WLD + c];
+    }
+    const int R = w - j0 - NB;
+    if (R > 0) {
+      for (int e = tid; e < R * NB; e += 256) {
+        const int i = e / NB, c = e % NB;
+        Ps[i * PLD + c] = G[(int64_t)(j0 + NB + i) * w + j0 + c];
+      }
+      __syncthreads();
+      // panel: L_iJ = G_iJ X_JJ^T, 64 rows at a time, in place
+      for (int r0 = 0; r0 < R; r0 += NB) {
+        float acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+        tile_acc(Ps + r0 * PLD, PLD, XT, PLD, ti, tj, acc);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int i = r0 + 4 * ti + q, c = 4 * tj + p;
+            Ps[i * PLD + c] = acc[q][p];
+            L[(int64_t)(j0 + NB + i) * w + j0 + c] = acc[q][p];
+          }
+        __syncthreads();
+      }
+      // trailing update of the lower triangle, tile (bi, bj), bj <= bi
+      const int nR = R / NB;
+      for (int t = 0; t < nR * (nR + 1) / 2; ++t) {
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bj = t - bi * (bi + 1) / 2;
+        float acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+        // sum_t P[bi*NB + a][t] P[bj*NB + b][t]
+#pragma unroll 4
+        for (int tt = 0; tt < NB; ++tt) {
+          float a[4], bb[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            a[q] = Ps[(bi * NB + 4 * ti + q) * PLD + tt];
+            bb[q] = Ps[(bj * NB + 4 * tj + q) * PLD + tt];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int64_t row = j0 + NB + bi * NB + 4 * ti + q;
+            const int64_t col = j0 + NB + bj * NB + 4 * tj + p;
+            G[row * w + col] -= acc[q][p];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  // L^{-1}: off-diagonal blocks by block rows
+  float* TA = Ps;
+  float* TB = Ps + NB * PLD;
+  float* TT = Ps + 2 * NB * PLD;
+  for (int Ib = 1; Ib < nbk; ++Ib) {
+    for (int Jb = 0; Jb < Ib; ++Jb) {
+      float acc[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+      for (int Kb = Jb; Kb < Ib; ++Kb) {
+        for (int e = tid; e < NB * NB; e += 256) {
+          const int i = e / NB, c = e % NB;
+          TA[i * PLD + c] = L[(int64_t)(Ib * NB + i) * w + Kb * NB + c];
+          TB[i * PLD + c] = Li[(int64_t)(Kb * NB + i) * w + Jb * NB + c];
+        }
+        __syncthreads();
+        tile_acc(TA, PLD, TB, PLD, ti, tj, acc);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) TT[(4 * ti + q) * PLD + 4 * tj + p] = acc[q][p];
+      for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e / NB, c = e % NB;
+        TA[i * PLD + c] = Li[(int64_t)(Ib * NB + i) * w + Ib * NB + c];
+      }
+      __syncthreads();
+      float acc2[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc2[q][p] = 0.f;
+      tile_acc(TA, PLD, TT, PLD, ti, tj, acc2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+          Li[(int64_t)(Ib * NB + 4 * ti + q) * w + Jb * NB + 4 * tj + p] = -acc2[q][p];
+      __syncthreads();
+    }
+  }
+  // zeros above the block diagonal, then the BF16 pair of L^{-1}
+  for (int64_t e = tid; e < (int64_t)w * w; e += 256) {
+    const int i = (int)(e / w), c = (int)(e % w);
+    if (c / NB > i / NB) {
+      L[e] = 0.f;
+      Li[e] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < (int64_t)w * w; e += 256) {
+    const float v = Li[e];
+    const bf16 h = __float2bfloat16_rn(v);
+    Lh[e] = h;
+    Ll[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+  if (tid == 0) I.kept[side * 2 + pass] = kept;
+}
+
+// U (cpad x rpad workspace) -> the caller's cmax x rmax output.
+__global__ void copy_u_kernel(const Item* items, const bcur_batch_io_t* io, Work rows) {
+  const int b = find_item(rows, blockIdx.x);
+  const Item& I = items[b];
+  float* U = io[b].U;
+  if (!U) return;
+  const int r = blockIdx.x - rows.prefix[b];
+  for (int c = threadIdx.x; c < I.rmax; c += blockDim.x)
+    U[(int64_t)r * I.rmax + c] = I.Uf[(int64_t)r * I.rpad + c];
+}
+
+// ||A - CUR||_F from the residual tiles' partial sums, fixed order.
+__global__ void __launch_bounds__(256) finish_kernel(const Item* items, const bcur_batch_io_t* io) {
+  const Item& I = items[blockIdx.x];
+  __shared__ double red[8];
+  const int64_t n = 4 * I.res_units;
+  double e2 = 0.0, x2 = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    e2 += I.partials[2 * i];
+    x2 += I.partials[2 * i + 1];
+  }
+  const double se = block_sum(e2, red);
+  __syncthreads();
+  const double sx = block_sum(x2, red);
+  if (threadIdx.x == 0) {
+    double* err = io[blockIdx.x].err;
+    const double fe = sqrt(se), fx = sqrt(sx);
+    err[0] = fe;
+    err[1] = fx > 0.0 ? fe / fx : 0.0;
+    err[2] = fx;
+  }
+}
+
+}  // namespace
+
+bcur_status_t split_inputs(const Item* items, const bcur_batch_io_t* io, Work rows8, int total8,
+                           int B, int* status, cudaStream_t s) {
+  (void)status;
+  split_kernel<<<total8 + B * (LP / 8), 256, 0, s>>>(items, io, rows8, total8);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t skinny_gram(const Item* items, Work chunks, int total, int sel, cudaStream_t s) {
+  sgram_kernel<<<total, 256, 0, s>>>(items, chunks, sel);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t skinny_chol(const Item* items, int B, int sel, int pass, int want_lb,
+                          cudaStream_t s) {
+  const size_t smem = (size_t)LP * (LP + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(schol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    attr = true;
+  }
+  schol_kernel<<<B, 256, smem, s>>>(items, sel, pass, want_lb);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t skinny_apply(const Item* items, Work chunks, int total, int src, int dst,
+                           int write_bf16, cudaStream_t s) {
+  sapply_kernel<<<total, AP, 0, s>>>(items, chunks, src, dst, write_bf16);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t scores(const Item* items, const bcur_batch_io_t* io, Work blocks, int total,
+                     int* status, cudaStream_t s) {
+  scores_kernel<<<total, 128, 0, s>>>(items, io, blocks, status);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t sample(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s) {
+  sample_kernel<<<dim3(B, 2), 32, 0, s>>>(items, io);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, int ctotal,
+                     Work rrows, int rtotal, cudaStream_t s) {
+  gather_c_kernel<<<ctotal, dim3(32, 8), 0, s>>>(items, io, ctiles);
+  BCUR_LAUNCH_CHECK();
+  gather_r_kernel<<<rtotal, 256, 0, s>>>(items, io, rrows);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t wide_chol(const Item* items, int B, int pass, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(wchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kWideSmem));
+    attr = true;
+  }
+  wchol_kernel<<<dim3(B, 2), 256, kWideSmem, s>>>(items, pass);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t copy_u(const Item* items, const bcur_batch_io_t* io, Work urows, int total,
+                     cudaStream_t s) {
+  copy_u_kernel<<<total, 256, 0, s>>>(items, io, urows);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s) {
+  finish_kernel<<<B, 256, 0, s>>>(items, io);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+}  // namespace batch
+}  // namespace bcur

@@ -1,0 +1,506 @@
+// Batched plan of the C ABI: validation, workspace layout, the launch tables
+// (grouped GEMMs and work lists) and the fixed launch sequence of one run.
+// Every stage of the method is one launch over the whole batch; the host
+// never synchronises inside a run, so the sequence can be captured in a CUDA
+// graph and replayed.
+#include <algorithm>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "batch.h"
+
+using namespace bcur;
+using namespace bcur::batch;
+
+namespace {
+
+struct WorkList {
+  std::vector<int> h;  // count + 1 prefix sums
+  int* d = nullptr;
+  int total = 0;
+  Work w() const { return Work{d, (int)h.size() - 1}; }
+};
+
+}  // namespace
+
+struct bcur_batch_s {
+  int B = 0, q = 0;
+  std::vector<bcur_batch_item_t> d;
+  std::vector<Item> it;
+  cudaStream_t stream = nullptr;
+  size_t need = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool bound = false;
+  // device tables
+  Item* d_items = nullptr;
+  bcur_batch_io_t* d_io = nullptr;
+  int* d_status = nullptr;
+  double* Lb_all = nullptr;
+  float *Ut_all = nullptr, *W_all = nullptr, *jw_all = nullptr;
+  double* sig_all = nullptr;
+  bcur_batch_io_t* h_io = nullptr;  // pinned staging of the io table
+  cudaEvent_t ev_io = nullptr;
+  WorkList rows8, chunks_m, chunks_n, apply_m, apply_n, blocks, ctiles, rrows, urows;
+  // grouped GEMMs
+  TcGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[4], gP, gRes;
+  // graph mode: the sequence is captured on a stream of the plan's own and
+  // joined to the caller's stream through events
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+
+namespace {
+
+// Bump allocator over the workspace; with base == nullptr it only measures.
+struct Bump {
+  char* base;
+  size_t cur = 0;
+  template <typename T> T* take(size_t count) {
+    const size_t at = cur;
+    cur += (count * sizeof(T) + 255) / 256 * 256;
+    return base ? reinterpret_cast<T*>(base + at) : nullptr;
+  }
+};
+
+void derive(Item& I, const bcur_batch_item_t& d) {
+  I = Item{};
+  I.m = d.m; I.n = d.n; I.lda = d.lda;
+  I.k = d.k; I.l = d.k + d.p; I.s = d.block;
+  I.Gc = (int)ceil_div(d.n, d.block);
+  I.Gr = (int)ceil_div(d.m, d.block);
+  I.gc = d.g_col; I.gr = d.g_row;
+  I.ldm = round_up(d.m, 64);
+  I.ldn = round_up(d.n, 64);
+  I.cmax = d.g_col * d.block;
+  I.rmax = d.g_row * d.block;
+  I.cpad = (int)round_up(I.cmax, NB);
+  I.rpad = (int)round_up(I.rmax, NB);
+  I.chunks_m = (int)ceil_div(d.m, CH);
+  I.chunks_n = (int)ceil_div(d.n, CH);
+  I.res_units = ceil_div(d.m, 128) * ceil_div(d.n, 256);
+}
+
+// Lay out everything; pointers are assigned when P->ws is set.
+size_t layout(bcur_batch_t P) {
+  Bump bp{P->ws};
+  const int B = P->B;
+  P->d_items = bp.take<Item>(B);
+  P->d_io = bp.take<bcur_batch_io_t>(B);
+  P->d_status = bp.take<int>(1);
+  P->Lb_all = bp.take<double>((size_t)B * LP * LP);
+  P->Ut_all = bp.take<float>((size_t)B * LP * LP);
+  P->W_all = bp.take<float>((size_t)B * LP * LP);
+  P->jw_all = bp.take<float>((size_t)B * LP * LP);
+  P->sig_all = bp.take<double>((size_t)B * LP);
+  WorkList* wls[] = {&P->rows8, &P->chunks_m, &P->chunks_n, &P->apply_m, &P->apply_n,
+                     &P->blocks, &P->ctiles, &P->rrows, &P->urows};
+  for (WorkList* w : wls) w->d = bp.take<int>(B + 1);
+  auto grp = [&](TcGroup& g, int count) {
+    g.table = bp.take<char>(gemm_tc_group_bytes(count));
+  };
+  grp(P->gY, B); grp(P->gZ, B); grp(P->gY2, B);
+  for (int i = 0; i < 2; ++i) { grp(P->gGram[i], 2 * B); grp(P->gApply[i], 2 * B); }
+  grp(P->gW, B); grp(P->gM, B);
+  for (int i = 0; i < 4; ++i) grp(P->gU[i], B);
+  grp(P->gP, B); grp(P->gRes, B);
+  for (int b = 0; b < B; ++b) {
+    Item& I = P->it[b];
+    const int64_t m = I.m, n = I.n, ldm = I.ldm, ldn = I.ldn;
+    const int64_t cp = I.cpad, rp = I.rpad;
+    I.Ah = bp.take<bf16>(m * ldn);
+    I.Al = bp.take<bf16>(m * ldn);
+    I.Om = bp.take<bf16>(LP * ldn);
+    I.Pm0 = bp.take<float>(LP * ldm);
+    I.Pm1 = bp.take<float>(LP * ldm);
+    I.Pn0 = bp.take<float>(LP * ldn);
+    I.Pn1 = bp.take<float>(LP * ldn);
+    I.Qh = bp.take<bf16>(LP * ldm);
+    I.Zh = bp.take<bf16>(LP * ldn);
+    I.gpart = bp.take<float>((size_t)std::max(I.chunks_m, I.chunks_n) * LP * LP);
+    I.G64 = bp.take<double>(LP * LP);
+    I.L64a = bp.take<double>(LP * LP);
+    I.L64b = bp.take<double>(LP * LP);
+    I.Linv64 = bp.take<double>(LP * LP);
+    I.LinvT = bp.take<float>(LP * LP);
+    I.remaining = bp.take<unsigned char>(I.Gc + I.Gr);
+    I.colmap = bp.take<int>(cp);
+    I.rowmap = bp.take<int>(rp);
+    for (int i = 0; i < 2; ++i) {
+      I.XCh[i] = bp.take<bf16>(cp * ldm);
+      I.XCl[i] = bp.take<bf16>(cp * ldm);
+      I.XRh[i] = bp.take<bf16>(rp * ldn);
+      I.XRl[i] = bp.take<bf16>(rp * ldn);
+    }
+    I.GC = bp.take<float>(cp * cp);
+    I.GR = bp.take<float>(rp * rp);
+    for (int i = 0; i < 2; ++i) {
+      I.LC[i] = bp.take<float>(cp * cp);
+      I.LCi[i] = bp.take<float>(cp * cp);
+      I.LR[i] = bp.take<float>(rp * rp);
+      I.LRi[i] = bp.take<float>(rp * rp);
+      I.LCih[i] = bp.take<bf16>(cp * cp);
+      I.LCil[i] = bp.take<bf16>(cp * cp);
+      I.LRih[i] = bp.take<bf16>(rp * rp);
+      I.LRil[i] = bp.take<bf16>(rp * rp);
+    }
+    I.Wh = bp.take<bf16>(m * rp);
+    I.Wl = bp.take<bf16>(m * rp);
+    I.Mf = bp.take<float>(cp * rp);
+    I.Mh = bp.take<bf16>(cp * rp);
+    I.Ml = bp.take<bf16>(cp * rp);
+    I.U1h = bp.take<bf16>(cp * rp);
+    I.U1l = bp.take<bf16>(cp * rp);
+    I.U2h = bp.take<bf16>(cp * rp);
+    I.U2l = bp.take<bf16>(cp * rp);
+    I.Uf = bp.take<float>(cp * rp);
+    I.Ph = bp.take<bf16>(m * rp);
+    I.Pl = bp.take<bf16>(m * rp);
+    I.partials = bp.take<double>(8 * I.res_units);
+    I.kept = bp.take<int>(4);
+    if (P->ws) {
+      I.Lb = P->Lb_all + (size_t)b * LP * LP;
+      I.Ut = P->Ut_all + (size_t)b * LP * LP;
+      I.W = P->W_all + (size_t)b * LP * LP;
+    }
+  }
+  return bp.cur;
+}
+
+void build_list(WorkList& w, const std::vector<int>& per) {
+  w.h.assign(per.size() + 1, 0);
+  for (size_t i = 0; i < per.size(); ++i) w.h[i + 1] = w.h[i] + per[i];
+  w.total = w.h.back();
+}
+
+GemmDesc g16(int64_t M, int64_t N, int64_t K, const void* A, const void* Alo, int64_t lda, int tA,
+             const void* B, const void* Blo, int64_t ldb, int tB, int64_t ldd, int parts) {
+  GemmDesc g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.transA = tA;
+  g.B = B; g.ldb = ldb; g.transB = tB;
+  g.ldd = ldd;
+  g.ab_bf16 = 1;
+  g.parts = parts;
+  if (parts == 3) { g.A_lo = Alo; g.B_lo = Blo; }
+  return g;
+}
+
+bcur_status_t prep(bcur_batch_t P, TcGroup& g, std::vector<GemmDesc>& ds, int resid, int BN) {
+  for (auto& d : ds) d.status = P->d_status;
+  void* table = g.table;
+  return gemm_tc_group_prepare(ds.data(), (int)ds.size(), resid, BN, table,
+                               gemm_tc_group_bytes((int)ds.size()), P->d_status, &g);
+}
+
+bcur_status_t build_groups(bcur_batch_t P) {
+  const int B = P->B;
+  std::vector<GemmDesc> y, z, y2, w, mm, u[4], pp, res;
+  std::vector<GemmDesc> gram[2], app[2];
+  for (int b = 0; b < B; ++b) {
+    const Item& I = P->it[b];
+    const int64_t m = I.m, n = I.n, ldm = I.ldm, ldn = I.ldn, cp = I.cpad, rp = I.rpad;
+    GemmDesc d = g16(LP, m, n, I.Om, nullptr, ldn, 0, I.Ah, nullptr, ldn, 1, ldm, 1);
+    d.D = I.Pm0;
+    y.push_back(d);
+    d = g16(LP, n, m, I.Qh, nullptr, ldm, 0, I.Ah, nullptr, ldn, 0, ldn, 1);
+    d.D = I.Pn0;
+    z.push_back(d);
+    d = g16(LP, m, n, I.Zh, nullptr, ldn, 0, I.Ah, nullptr, ldn, 1, ldm, 1);
+    d.D = I.Pm0;
+    y2.push_back(d);
+    for (int pass = 0; pass < 2; ++pass) {
+      d = g16(cp, cp, m, I.XCh[pass], I.XCl[pass], ldm, 0, I.XCh[pass], I.XCl[pass], ldm, 1, cp, 3);
+      d.D = I.GC;
+      d.out_lower = 1;
+      gram[pass].push_back(d);
+      d = g16(rp, rp, n, I.XRh[pass], I.XRl[pass], ldn, 0, I.XRh[pass], I.XRl[pass], ldn, 1, rp, 3);
+      d.D = I.GR;
+      d.out_lower = 1;
+      gram[pass].push_back(d);
+      d = g16(cp, m, cp, I.LCih[pass], I.LCil[pass], cp, 0, I.XCh[pass], I.XCl[pass], ldm, 0, ldm, 3);
+      d.Dh = I.XCh[1 - pass];
+      d.Dl = I.XCl[1 - pass];
+      d.triA = 1;
+      app[pass].push_back(d);
+      d = g16(rp, n, rp, I.LRih[pass], I.LRil[pass], rp, 0, I.XRh[pass], I.XRl[pass], ldn, 0, ldn, 3);
+      d.Dh = I.XRh[1 - pass];
+      d.Dl = I.XRl[1 - pass];
+      d.triA = 1;
+      app[pass].push_back(d);
+    }
+    // W = A Q_R^T (m x r);  M = Q_C W (c x r)
+    d = g16(m, rp, n, I.Ah, I.Al, ldn, 0, I.XRh[0], I.XRl[0], ldn, 1, rp, 3);
+    d.Dh = I.Wh;
+    d.Dl = I.Wl;
+    w.push_back(d);
+    d = g16(cp, rp, m, I.XCh[0], I.XCl[0], ldm, 0, I.Wh, I.Wl, rp, 0, rp, 3);
+    d.D = I.Mf;
+    d.Dh = I.Mh;
+    d.Dl = I.Ml;
+    mm.push_back(d);
+    // U = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1}
+    d = g16(cp, rp, rp, I.Mh, I.Ml, rp, 0, I.LRih[1], I.LRil[1], rp, 0, rp, 3);
+    d.Dh = I.U1h; d.Dl = I.U1l; d.triB = 1;
+    u[0].push_back(d);
+    d = g16(cp, rp, rp, I.U1h, I.U1l, rp, 0, I.LRih[0], I.LRil[0], rp, 0, rp, 3);
+    d.Dh = I.U2h; d.Dl = I.U2l; d.triB = 1;
+    u[1].push_back(d);
+    d = g16(cp, rp, cp, I.LCih[1], I.LCil[1], cp, 1, I.U2h, I.U2l, rp, 0, rp, 3);
+    d.Dh = I.U1h; d.Dl = I.U1l; d.triA = 2;
+    u[2].push_back(d);
+    d = g16(cp, rp, cp, I.LCih[0], I.LCil[0], cp, 1, I.U1h, I.U1l, rp, 0, rp, 3);
+    d.D = I.Uf; d.triA = 2;
+    u[3].push_back(d);
+    // P = Q_C^T M (m x r), then sum (A - P Q_R)^2, both with BF16 pairs
+    d = g16(m, rp, cp, I.XCh[0], I.XCl[0], ldm, 1, I.Mh, I.Ml, rp, 0, rp, 3);
+    d.Dh = I.Ph;
+    d.Dl = I.Pl;
+    pp.push_back(d);
+    d = g16(m, n, rp, I.Ph, I.Pl, rp, 0, I.XRh[0], I.XRl[0], ldn, 0, 0, 3);
+    d.X = nullptr;  // set per run from the io table
+    d.ldx = I.lda;
+    d.partials = I.partials;
+    res.push_back(d);
+  }
+  BCUR_TRY(prep(P, P->gY, y, 0, 64));
+  BCUR_TRY(prep(P, P->gZ, z, 0, 64));
+  BCUR_TRY(prep(P, P->gY2, y2, 0, 64));
+  for (int i = 0; i < 2; ++i) {
+    BCUR_TRY(prep(P, P->gGram[i], gram[i], 0, 0));
+    BCUR_TRY(prep(P, P->gApply[i], app[i], 0, 0));
+  }
+  BCUR_TRY(prep(P, P->gW, w, 0, 0));
+  BCUR_TRY(prep(P, P->gM, mm, 0, 0));
+  for (int i = 0; i < 4; ++i) BCUR_TRY(prep(P, P->gU[i], u[i], 0, 0));
+  BCUR_TRY(prep(P, P->gP, pp, 0, 0));
+  BCUR_TRY(prep(P, P->gRes, res, 1, 256));
+  return BCUR_OK;
+}
+
+bcur_status_t orth(bcur_batch_t P, int s0, int s1, bool want_lb, cudaStream_t s) {
+  const bool m_side = s0 < PN0;
+  const WorkList& ch = m_side ? P->chunks_m : P->chunks_n;
+  const WorkList& ap = m_side ? P->apply_m : P->apply_n;
+  BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s0, s));
+  BCUR_TRY(skinny_chol(P->d_items, P->B, s0, 0, 0, s));
+  BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s0, s1, 0, s));
+  BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s1, s));
+  BCUR_TRY(skinny_chol(P->d_items, P->B, s1, 1, want_lb ? 1 : 0, s));
+  BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s1, s0, 1, s));
+  return BCUR_OK;
+}
+
+// The launch sequence of one run (the io table is already being copied).
+bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
+  const int B = P->B;
+  BCUR_TRY(gemm_tc_group_patch_x(P->gRes, P->d_io, sizeof(bcur_batch_io_t),
+                                 offsetof(bcur_batch_io_t, A), s));
+  BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->d_status, s));
+  // scores: randomized range finder with q subspace iterations (Sec. 3.1)
+  BCUR_TRY(gemm_tc_group_run(P->gY, s));
+  BCUR_TRY(orth(P, PM0, PM1, false, s));
+  for (int i = 0; i < P->q; ++i) {
+    BCUR_TRY(gemm_tc_group_run(P->gZ, s));
+    BCUR_TRY(orth(P, PN0, PN1, false, s));
+    BCUR_TRY(gemm_tc_group_run(P->gY2, s));
+    BCUR_TRY(orth(P, PM0, PM1, false, s));
+  }
+  BCUR_TRY(gemm_tc_group_run(P->gZ, s));
+  BCUR_TRY(orth(P, PN0, PN1, true, s));
+  BCUR_TRY(jacobi_svd_batched<float>(P->Lb_all, LP, P->Ut_all, P->W_all, P->sig_all, P->jw_all,
+                                     P->d_status, B, s));
+  BCUR_TRY(scores(P->d_items, P->d_io, P->blocks.w(), P->blocks.total, P->d_status, s));
+  // sampling (Alg. 1 step 2) and the gathers
+  BCUR_TRY(sample(P->d_items, P->d_io, B, s));
+  BCUR_TRY(gather(P->d_items, P->d_io, P->ctiles.w(), P->ctiles.total, P->rrows.w(),
+                  P->rrows.total, s));
+  // Cholesky-QR2 of C^T and R, both sides in each launch
+  for (int pass = 0; pass < 2; ++pass) {
+    BCUR_TRY(gemm_tc_group_run(P->gGram[pass], s));
+    BCUR_TRY(wide_chol(P->d_items, B, pass, s));
+    BCUR_TRY(gemm_tc_group_run(P->gApply[pass], s));
+  }
+  // U = C^+ A R^+
+  BCUR_TRY(gemm_tc_group_run(P->gW, s));
+  BCUR_TRY(gemm_tc_group_run(P->gM, s));
+  for (int i = 0; i < 4; ++i) BCUR_TRY(gemm_tc_group_run(P->gU[i], s));
+  BCUR_TRY(copy_u(P->d_items, P->d_io, P->urows.w(), P->urows.total, s));
+  // ||A - CUR||_F
+  BCUR_TRY(gemm_tc_group_run(P->gP, s));
+  BCUR_TRY(gemm_tc_group_run(P->gRes, s));
+  BCUR_TRY(finish(P->d_items, P->d_io, B, s));
+  return BCUR_OK;
+}
+
+bool item_ok(const bcur_batch_item_t& d) {
+  if (d.m < 1 || d.n < 1 || d.lda < d.n || d.lda % 4 != 0) return false;
+  if (d.m > INT32_MAX / 2 || d.n > INT32_MAX / 2) return false;
+  if (d.k < 1 || d.p < 0 || d.k + d.p > LP || d.k + d.p > d.m || d.k + d.p > d.n) return false;
+  if (d.block < 1) return false;
+  const int64_t Gc = ceil_div(d.n, d.block), Gr = ceil_div(d.m, d.block);
+  if (Gc > 32768 || Gr > 32768) return false;
+  if (d.g_col < 1 || d.g_row < 1 || d.g_col > Gc || d.g_row > Gr) return false;
+  if ((int64_t)d.g_col * d.block > WMAX || (int64_t)d.g_row * d.block > WMAX) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int32_t q,
+                              void* stream, bcur_batch_t* out, size_t* workspace_bytes) {
+  if (!items || !out || !workspace_bytes || count < 1 || q < 0 || q > 16) return BCUR_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!item_ok(items[i])) return BCUR_EINVAL;
+  bcur_batch_t P = new (std::nothrow) bcur_batch_s();
+  if (!P) return BCUR_ENOMEM;
+  P->B = count;
+  P->q = q;
+  P->d.assign(items, items + count);
+  P->it.resize(count);
+  for (int i = 0; i < count; ++i) derive(P->it[i], items[i]);
+  P->stream = static_cast<cudaStream_t>(stream);
+  P->need = layout(P);
+  *out = P;
+  *workspace_bytes = P->need;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
+  if (!P || !ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return BCUR_EINVAL;
+  if (bytes < P->need) return BCUR_ENOMEM;
+  if (!gemm_tc_available()) return BCUR_ENOTSUP;
+  if (P->exec) { cudaGraphExecDestroy(P->exec); P->exec = nullptr; }
+  if (P->graph) { cudaGraphDestroy(P->graph); P->graph = nullptr; }
+  P->ws = static_cast<char*>(ws);
+  P->ws_bytes = bytes;
+  layout(P);
+  const int B = P->B;
+  std::vector<int> r8(B), cm(B), cn(B), am(B), an(B), bl(B), ct(B), rr(B), ur(B);
+  for (int b = 0; b < B; ++b) {
+    const Item& I = P->it[b];
+    r8[b] = (int)ceil_div(I.m, 8);
+    cm[b] = I.chunks_m;
+    cn[b] = I.chunks_n;
+    am[b] = (int)ceil_div(I.m, AP);
+    an[b] = (int)ceil_div(I.n, AP);
+    bl[b] = I.Gc + I.Gr;
+    ct[b] = (int)(ceil_div(I.cpad, 32) * ceil_div(I.m, 32));
+    rr[b] = I.rpad;
+    ur[b] = I.cmax;
+  }
+  build_list(P->rows8, r8); build_list(P->chunks_m, cm); build_list(P->chunks_n, cn);
+  build_list(P->apply_m, am); build_list(P->apply_n, an); build_list(P->blocks, bl);
+  build_list(P->ctiles, ct); build_list(P->rrows, rr); build_list(P->urows, ur);
+  WorkList* wls[] = {&P->rows8, &P->chunks_m, &P->chunks_n, &P->apply_m, &P->apply_n,
+                     &P->blocks, &P->ctiles, &P->rrows, &P->urows};
+  for (WorkList* w : wls)
+    BCUR_CUDA_TRY(cudaMemcpy(w->d, w->h.data(), w->h.size() * sizeof(int), cudaMemcpyHostToDevice));
+  BCUR_CUDA_TRY(cudaMemcpy(P->d_items, P->it.data(), (size_t)B * sizeof(Item),
+                           cudaMemcpyHostToDevice));
+  BCUR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));
+  BCUR_CUDA_TRY(cudaMemset(P->d_io, 0, (size_t)B * sizeof(bcur_batch_io_t)));
+  if (!P->h_io) {
+    BCUR_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&P->h_io),
+                                (size_t)B * sizeof(bcur_batch_io_t), cudaHostAllocDefault));
+    BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_io, cudaEventDisableTiming));
+  }
+  BCUR_TRY(build_groups(P));
+  P->bound = true;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_batch_run(bcur_batch_t P, const bcur_batch_io_t* io, int32_t use_graph) {
+  if (!P || !io) return BCUR_EINVAL;
+  if (!P->bound) return BCUR_ESTATE;
+  for (int b = 0; b < P->B; ++b) {
+    const bcur_batch_io_t& e = io[b];
+    if (!e.A || !e.omega || !e.u_col || !e.u_row || !e.col_scores || !e.row_scores ||
+        !e.col_idx || !e.row_idx || !e.err)
+      return BCUR_EINVAL;
+  }
+  // the previous run's copy of the staging buffer must have finished
+  BCUR_CUDA_TRY(cudaEventSynchronize(P->ev_io));
+  memcpy(P->h_io, io, (size_t)P->B * sizeof(bcur_batch_io_t));
+  cudaStream_t s = P->stream;
+  if (use_graph && P->exec) {
+    BCUR_CUDA_TRY(cudaEventRecord(P->ev_in, s));
+    BCUR_CUDA_TRY(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
+    BCUR_CUDA_TRY(cudaGraphLaunch(P->exec, P->gstream));
+    BCUR_CUDA_TRY(cudaEventRecord(P->ev_out, P->gstream));
+    BCUR_CUDA_TRY(cudaStreamWaitEvent(s, P->ev_out, 0));
+    return BCUR_OK;
+  }
+  const uint64_t l0 = bcur_launch_count();
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->d_io, P->h_io, (size_t)P->B * sizeof(bcur_batch_io_t),
+                                cudaMemcpyHostToDevice, s));
+  BCUR_CUDA_TRY(cudaEventRecord(P->ev_io, s));
+  BCUR_TRY(enqueue(P, s));
+  P->launches = (int64_t)(bcur_launch_count() - l0);
+  if (use_graph && !P->exec) {
+    // Capture the same sequence (on the plan's own stream) for later runs.
+    if (!P->gstream) {
+      BCUR_CUDA_TRY(cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking));
+      BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+      BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+    }
+    cudaStream_t g = P->gstream;
+    BCUR_CUDA_TRY(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
+    bcur_status_t st = BCUR_OK;
+    if (cudaMemcpyAsync(P->d_io, P->h_io, (size_t)P->B * sizeof(bcur_batch_io_t),
+                        cudaMemcpyHostToDevice, g) != cudaSuccess ||
+        cudaEventRecordWithFlags(P->ev_io, g, cudaEventRecordExternal) != cudaSuccess)
+      st = BCUR_ECUDA;
+    if (st == BCUR_OK) st = enqueue(P, g);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g, &graph);
+    if (st != BCUR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    BCUR_CUDA_TRY(e);
+    P->graph = graph;
+    BCUR_CUDA_TRY(cudaGraphInstantiate(&P->exec, graph, 0));
+  }
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_batch_dims(bcur_batch_t P, int32_t i, int64_t* cmax, int64_t* rmax,
+                              int64_t* launches_per_run) {
+  if (!P || i < 0 || i >= P->B) return BCUR_EINVAL;
+  if (cmax) *cmax = P->it[i].cmax;
+  if (rmax) *rmax = P->it[i].rmax;
+  if (launches_per_run) *launches_per_run = P->launches;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_batch_sync_status(bcur_batch_t P) {
+  if (!P) return BCUR_EINVAL;
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (!P->bound) return BCUR_OK;
+  int st = 0;
+  BCUR_CUDA_TRY(cudaMemcpy(&st, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) BCUR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));
+  return (bcur_status_t)st;
+}
+
+void bcur_batch_destroy(bcur_batch_t P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->ev_io) cudaEventDestroy(P->ev_io);
+  if (P->ev_in) cudaEventDestroy(P->ev_in);
+  if (P->ev_out) cudaEventDestroy(P->ev_out);
+  if (P->gstream) cudaStreamDestroy(P->gstream);
+  if (P->h_io) cudaFreeHost(P->h_io);
+  delete P;
+}
+
+}  // extern "C"

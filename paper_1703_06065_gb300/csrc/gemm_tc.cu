@@ -25,12 +25,20 @@
 //               partial store, or fused residual reduction.
 // Every mbarrier wait is bounded (2 s on %globaltimer); a wait that runs out
 // records BCUR_ETIMEOUT, the kernel drains what it issued and returns.
+//
+// Grouped mode: one persistent launch over many independent GEMMs of
+// different shapes (a batch of decompositions).  Each GEMM's tensor maps and
+// parameters sit in a device table; the CTAs walk the concatenation of all
+// GEMMs' tiles (heaviest GEMMs first, snake order across CTAs) and look up
+// the owning GEMM of each tile by binary search over the tile prefix sums.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "kernels.h"
 
@@ -207,21 +215,37 @@ struct Maps {
   CUtensorMap b[2];
 };
 
-struct Unit {
-  int m0, n0, z, b, klo, khi, skip;
+// One GEMM of a grouped launch (128-byte aligned: the tensor maps need 64).
+struct alignas(128) GEntry {
+  Maps maps;
+  Params p;
+};
+struct Group {
+  const GEntry* e;     // device table, `count` entries
+  const int* starts;   // device, count + 1 prefix sums of the entries' units
+  int count, total;
+  int* status;
 };
 
-template <int BN, int KIND>
-__device__ __forceinline__ Unit decode(const Params& p, int u) {
-  constexpr int BK = KindCfg<KIND>::bk;
-  Unit w;
-  // CTA c takes units c, c + G, c + 2G, ...  Odd full rounds are walked in
-  // reverse ("snake"), so with tiles ordered heaviest first every CTA gets a
-  // similar amount of work.
+struct Unit {
+  int m0, n0, z, b, klo, khi, skip, uu;
+};
+
+// CTA c takes units c, c + G, c + 2G, ...  Odd full rounds are walked in
+// reverse ("snake"), so with units ordered heaviest first every CTA gets a
+// similar amount of work.
+__device__ __forceinline__ int snake(int u, int total) {
   const int G = gridDim.x;
   const int round = u / G, c = u % G;
-  const int full_rounds = (p.tiles_m * p.tiles_n * p.ksplit * p.batch) / G;
-  const int uu = (round < full_rounds && (round & 1)) ? round * G + (G - 1 - c) : u;
+  const int full_rounds = total / G;
+  return (round < full_rounds && (round & 1)) ? round * G + (G - 1 - c) : u;
+}
+
+template <int BN, int KIND>
+__device__ __forceinline__ Unit decode_unit(const Params& p, int uu) {
+  constexpr int BK = KindCfg<KIND>::bk;
+  Unit w;
+  w.uu = uu;
   const int bt = uu / p.ksplit;
   w.z = uu % p.ksplit;
   w.b = bt / (p.tiles_m * p.tiles_n);
@@ -252,6 +276,28 @@ __device__ __forceinline__ Unit decode(const Params& p, int u) {
   return w;
 }
 
+// Unit u of this CTA's walk -> the GEMM that owns it (its parameters and
+// tensor maps) and the decoded tile.
+template <int BN, int KIND, bool GROUPED>
+__device__ __forceinline__ Unit locate(const Maps& maps, const Params& p, const Group& grp, int u,
+                                       int total, const Params*& P, const Maps*& M) {
+  const int uu = snake(u, total);
+  if constexpr (!GROUPED) {
+    P = &p;
+    M = &maps;
+    return decode_unit<BN, KIND>(p, uu);
+  } else {
+    int lo = 0, hi = grp.count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (grp.starts[mid] <= uu) lo = mid; else hi = mid - 1;
+    }
+    P = &grp.e[lo].p;
+    M = &grp.e[lo].maps;
+    return decode_unit<BN, KIND>(*P, uu - grp.starts[lo]);
+  }
+}
+
 template <int BN> struct StageCfg {
   static constexpr int kStageBBytes = BN * 128;
   static constexpr int kStageBytes = kStageABytes + kStageBBytes;
@@ -261,9 +307,10 @@ template <int BN> struct StageCfg {
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kStageOut;
 };
 
-template <int BN, int KIND, int EPI>
+template <int BN, int KIND, int EPI, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ Maps maps, const Params p) {
+    tc_gemm_kernel(const __grid_constant__ Maps maps, const __grid_constant__ Params p,
+                   const Group grp) {
   using SC = StageCfg<BN>;
   using KC = KindCfg<KIND>;
   constexpr int S = SC::kStages;
@@ -279,6 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(tmem_slot + 4);  // 8 doubles
   float* stage_out = reinterpret_cast<float*>(smem + S * SC::kStageBytes + 256);
+  int* const status = GROUPED ? grp.status : p.status;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -293,9 +341,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int i = 0; i < 2; ++i) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[i])) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[i])) : "memory");
+    if constexpr (!GROUPED) {
+      for (int i = 0; i < 2; ++i) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[i])) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[i])) : "memory");
+      }
     }
   }
   if (warp == 1) {
@@ -310,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int total = p.tiles_m * p.tiles_n * p.ksplit * p.batch;
+  const int total = GROUPED ? grp.total : p.tiles_m * p.tiles_n * p.ksplit * p.batch;
   constexpr int BKR = KC::bk;  // K rows per stage for an MN-major operand
 
   if (warp == 0) {
@@ -318,27 +368,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
+      const Maps* last = nullptr;
       for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
-        const Unit w = decode<BN, KIND>(p, u);
+        const Params* P;
+        const Maps* M;
+        const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M);
         if (w.skip || w.klo >= w.khi) continue;
-        const int n_it = (w.khi - w.klo) * p.parts;
+        if constexpr (GROUPED) {
+          if (M != last) {  // maps written by the host into global memory
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(
+                               reinterpret_cast<uint64_t>(&M->a[i]))
+                           : "memory");
+              asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(
+                               reinterpret_cast<uint64_t>(&M->b[i]))
+                           : "memory");
+            }
+            last = M;
+          }
+        }
+        const int parts = P->parts, a_mn = P->a_mn, b_mn = P->b_mn;
+        const int n_it = (w.khi - w.klo) * parts;
         for (int i = 0; i < n_it; ++i, ++it) {
-          const int kb = w.klo + i / p.parts, part = i % p.parts;
-          const CUtensorMap* ma = &maps.a[part == 2 ? 1 : 0];
-          const CUtensorMap* mb = &maps.b[part == 1 ? 1 : 0];
+          const int kb = w.klo + i / parts, part = i % parts;
+          const CUtensorMap* ma = &M->a[part == 2 ? 1 : 0];
+          const CUtensorMap* mb = &M->b[part == 1 ? 1 : 0];
           const uint32_t stage = it % S, round = it / S;
-          if (!mbar_wait(&empty[stage], (round & 1) ^ 1, p.status, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&empty[stage], (round & 1) ^ 1, status, abort_flag)) { ok = false; break; }
           uint8_t* sa = smem + stage * SC::kStageBytes;
           uint8_t* sb = sa + kStageABytes;
           mbar_expect_tx(&full[stage], SC::kStageBytes);
-          if (!p.a_mn) {
+          if (!a_mn) {
             tma_load_3d(sa, ma, &full[stage], kb * KC::bk, w.m0, w.b);
           } else {
 #pragma unroll
             for (int b = 0; b < BM / KC::box_mn; ++b)
               tma_load_3d(sa + b * (BKR * 128), ma, &full[stage], w.m0 + b * KC::box_mn, kb * BKR, w.b);
           }
-          if (!p.b_mn) {
+          if (!b_mn) {
             tma_load_3d(sb, mb, &full[stage], kb * KC::bk, w.n0, w.b);
           } else {
 #pragma unroll
@@ -360,29 +428,32 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t id = idesc(KIND, p.a_mn, p.b_mn, BM, BN);
       uint32_t it = 0, tu = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
-        const Unit w = decode<BN, KIND>(p, u);
+        const Params* P;
+        const Maps* M;
+        const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M);
         if (w.skip || w.klo >= w.khi) continue;
+        const int parts = P->parts, a_mn = P->a_mn, b_mn = P->b_mn;
+        const uint32_t id = idesc(KIND, a_mn, b_mn, BM, BN);
         const uint32_t acc = tu & 1, use = tu >> 1;
-        if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, p.status, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, status, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * BN;
-        const int n_it = (w.khi - w.klo) * p.parts;
+        const int n_it = (w.khi - w.klo) * parts;
         for (int i = 0; i < n_it; ++i, ++it) {
           const uint32_t stage = it % S, round = it / S;
-          if (!mbar_wait(&full[stage], round & 1, p.status, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&full[stage], round & 1, status, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * SC::kStageBytes);
           const uint32_t sb = sa + kStageABytes;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const uint64_t ad = p.a_mn ? sdesc(sa + j * KC::kstep_rows * 128, BKR * 128, 1024)
-                                       : sdesc(sa + j * 32, 16, 1024);
-            const uint64_t bd = p.b_mn ? sdesc(sb + j * KC::kstep_rows * 128, BKR * 128, 1024)
-                                       : sdesc(sb + j * 32, 16, 1024);
+            const uint64_t ad = a_mn ? sdesc(sa + j * KC::kstep_rows * 128, BKR * 128, 1024)
+                                     : sdesc(sa + j * 32, 16, 1024);
+            const uint64_t bd = b_mn ? sdesc(sb + j * KC::kstep_rows * 128, BKR * 128, 1024)
+                                     : sdesc(sb + j * 32, 16, 1024);
             tc_mma<KIND>(d_tmem, ad, bd, id, (i > 0 || j > 0) ? 1u : 0u);
           }
           tc_commit(&empty[stage]);
@@ -404,19 +475,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t tu = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
-      const Unit w = decode<BN, KIND>(p, u);
+      const Params* P;
+      const Maps* M;
+      const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M);
       if (w.skip) continue;
       const bool has_acc = w.klo < w.khi;
       const uint32_t acc = tu & 1, use = tu >> 1;
       if (has_acc) {
-        if (!mbar_wait(&tfull[acc], use & 1, p.status, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&tfull[acc], use & 1, status, abort_flag)) { ok = false; break; }
         tc_fence_after();
       }
+      const int Mm = P->Mm, Nm = P->Nm;
       const int row = w.m0 + quarter * 32 + lane;
-      const bool row_ok = row < p.Mm;
-      float* const Dp = p.D ? p.D + (int64_t)w.b * p.sD : nullptr;
-      __nv_bfloat16* const Dhp = p.Dh ? p.Dh + (int64_t)w.b * p.sD : nullptr;
-      __nv_bfloat16* const Dlp = p.Dl ? p.Dl + (int64_t)w.b * p.sD : nullptr;
+      const bool row_ok = row < Mm;
+      const float alpha = P->alpha, beta = P->beta;
+      const int tri_out = P->tri_out;
+      const int64_t ldd = P->ldd;
+      float* const Dp = P->D ? P->D + (int64_t)w.b * P->sD : nullptr;
+      __nv_bfloat16* const Dhp = P->Dh ? P->Dh + (int64_t)w.b * P->sD : nullptr;
+      __nv_bfloat16* const Dlp = P->Dl ? P->Dl + (int64_t)w.b * P->sD : nullptr;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
@@ -428,21 +505,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
         }
         const int col0 = w.n0 + c0;
-        if (col0 >= p.Nm) continue;
+        if (col0 >= Nm) continue;
         if constexpr (EPI == EPI_STORE) {
-          if (p.transD) {
+          if (P->transD) {
             // D^T: lane = row, consecutive lanes write consecutive addresses.
             if (!row_ok) continue;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
               const int col = col0 + i;
-              if (col >= p.Nm) break;
-              if (p.tri_out == 1 && row < col) continue;
-              if (p.tri_out == 2 && row > col) continue;
-              const int64_t off = (int64_t)col * p.ldd + row;
-              float o = p.alpha * v[i];
-              if (p.beta != 0.f) o = fmaf(p.beta, Dp[off], o);
-              if (p.D) Dp[off] = o;
+              if (col >= Nm) break;
+              if (tri_out == 1 && row < col) continue;
+              if (tri_out == 2 && row > col) continue;
+              const int64_t off = (int64_t)col * ldd + row;
+              float o = alpha * v[i];
+              if (beta != 0.f) o = fmaf(beta, Dp[off], o);
+              if (Dp) Dp[off] = o;
               if (Dhp) {
                 const __nv_bfloat16 h = __float2bfloat16_rn(o);
                 Dhp[off] = h;
@@ -458,26 +535,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             const int col = col0 + lane;
             const int rbase = w.m0 + quarter * 32;
-            const bool col_ok = col < p.Nm;
+            const bool col_ok = col < Nm;
             float old[32];
-            if (p.beta != 0.f) {  // all loads issued before any use
+            if (beta != 0.f) {  // all loads issued before any use
 #pragma unroll
               for (int r = 0; r < 32; ++r) {
                 const int grow = rbase + r;
-                old[r] = (col_ok && grow < p.Mm) ? Dp[(int64_t)grow * p.ldd + col] : 0.f;
+                old[r] = (col_ok && grow < Mm) ? Dp[(int64_t)grow * ldd + col] : 0.f;
               }
             }
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
               const int grow = rbase + r;
-              bool ok = col_ok && grow < p.Mm;
-              if (p.tri_out == 1 && grow < col) ok = false;
-              if (p.tri_out == 2 && grow > col) ok = false;
+              bool ok = col_ok && grow < Mm;
+              if (tri_out == 1 && grow < col) ok = false;
+              if (tri_out == 2 && grow > col) ok = false;
               if (ok) {
-                const int64_t off = (int64_t)grow * p.ldd + col;
-                float o = p.alpha * t[r * 33 + lane];
-                if (p.beta != 0.f) o = fmaf(p.beta, old[r], o);
-                if (p.D) Dp[off] = o;
+                const int64_t off = (int64_t)grow * ldd + col;
+                float o = alpha * t[r * 33 + lane];
+                if (beta != 0.f) o = fmaf(beta, old[r], o);
+                if (Dp) Dp[off] = o;
                 if (Dhp) {
                   const __nv_bfloat16 h = __float2bfloat16_rn(o);
                   Dhp[off] = h;
@@ -489,18 +566,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         } else if constexpr (EPI == EPI_PARTIAL) {
           if (!row_ok) continue;
-          float* prow = p.part + (int64_t)w.z * p.Mm * p.Nm + (int64_t)row * p.Nm;
+          float* prow = P->part + (int64_t)w.z * Mm * Nm + (int64_t)row * Nm;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int col = col0 + i;
-            if (col >= p.Nm) break;
+            if (col >= Nm) break;
             prow[col] = v[i];
           }
         } else {  // EPI_RESID: each lane reads its own row piece of X
           if (!row_ok) continue;
-          const float* xr = p.X + (int64_t)row * p.ldx + col0;
+          const float* xr = P->X + (int64_t)row * P->ldx + col0;
           float xv[32];
-          if (col0 + 32 <= p.Nm && ((reinterpret_cast<uintptr_t>(xr) & 15) == 0)) {
+          if (col0 + 32 <= Nm && ((reinterpret_cast<uintptr_t>(xr) & 15) == 0)) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float4 q = reinterpret_cast<const float4*>(xr)[i];
@@ -508,12 +585,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) xv[i] = (col0 + i < p.Nm) ? xr[i] : 0.f;
+            for (int i = 0; i < 32; ++i) xv[i] = (col0 + i < Nm) ? xr[i] : 0.f;
           }
           float se = 0.f, sx = 0.f;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const float d = xv[i] - ((col0 + i < p.Nm) ? p.alpha * v[i] : 0.f);
+            const float d = xv[i] - ((col0 + i < Nm) ? alpha * v[i] : 0.f);
             se = fmaf(d, d, se);
             sx = fmaf(xv[i], xv[i], sx);
           }
@@ -527,8 +604,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&tempty[acc]);
         ++tu;
       }
+      if constexpr (GROUPED && EPI == EPI_RESID) {
+        // One partial pair per (tile, quarter): the owning GEMM's sums do not
+        // depend on which CTA ran the tile or what else was in the launch.
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+          x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+        }
+        if (lane == 0) {
+          P->partials[2 * (4 * (int64_t)w.uu + quarter)] = e2;
+          P->partials[2 * (4 * (int64_t)w.uu + quarter) + 1] = x2;
+        }
+        e2 = 0.0;
+        x2 = 0.0;
+      }
     }
-    if constexpr (EPI == EPI_RESID) {
+    if constexpr (EPI == EPI_RESID && !GROUPED) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         e2 += __shfl_xor_sync(0xffffffffu, e2, o);
@@ -542,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (EPI == EPI_RESID) {
+  if constexpr (EPI == EPI_RESID && !GROUPED) {
     if (threadIdx.x == 0) {
       double se = 0.0, sx = 0.0;
       for (int i = 0; i < 4; ++i) { se += red[2 * i]; sx += red[2 * i + 1]; }
@@ -672,43 +764,49 @@ bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn, in
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int KIND, int EPI>
-bcur_status_t launch_inst(const Maps& maps, const Params& p, int grid, cudaStream_t s) {
+template <int BN, int KIND, int EPI, bool GROUPED>
+bcur_status_t launch_inst(const Maps& maps, const Params& p, const Group& grp, int grid,
+                          cudaStream_t s) {
   using SC = StageCfg<BN>;
   static bool attr = false;
   if (!attr) {
-    BCUR_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, KIND, EPI>,
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, KIND, EPI, GROUPED>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        SC::kSmemBytes));
     attr = true;
   }
-  tc_gemm_kernel<BN, KIND, EPI><<<grid, kThreads, SC::kSmemBytes, s>>>(maps, p);
+  tc_gemm_kernel<BN, KIND, EPI, GROUPED><<<grid, kThreads, SC::kSmemBytes, s>>>(maps, p, grp);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 
-template <int KIND, int EPI>
-bcur_status_t launch_bn(int BN, const Maps& maps, const Params& p, int grid, cudaStream_t s) {
+template <int KIND, int EPI, bool GROUPED = false>
+bcur_status_t launch_bn(int BN, const Maps& maps, const Params& p, int grid, cudaStream_t s,
+                        const Group& grp = Group{}) {
   switch (BN) {
-    case 64: return launch_inst<64, KIND, EPI>(maps, p, grid, s);
-    case 128: return launch_inst<128, KIND, EPI>(maps, p, grid, s);
-    case 256: return launch_inst<256, KIND, EPI>(maps, p, grid, s);
+    case 64: return launch_inst<64, KIND, EPI, GROUPED>(maps, p, grp, grid, s);
+    case 128: return launch_inst<128, KIND, EPI, GROUPED>(maps, p, grp, grid, s);
+    case 256: return launch_inst<256, KIND, EPI, GROUPED>(maps, p, grp, grid, s);
   }
   return BCUR_EINVAL;
 }
 
-// Map one GEMM (GemmDesc convention, D row-major M x N) onto MMA space and
-// launch.  `epi` selects store or residual.  Returns ENOTSUP if the operands
-// cannot be described by TMA (alignment) or the device is not sm_103.
-bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t* n_partials) {
+// Map one GEMM (GemmDesc convention, D row-major M x N) onto MMA space: the
+// operands' tensor maps and the kernel parameters for tile width BN (0:
+// chosen from the output width).  Split-K is not decided here.  Returns
+// ENOTSUP if the operands cannot be described by TMA (alignment) or the
+// device is not sm_103.
+struct Prepared {
+  Maps maps;
+  Params p;
+  int BN, kind;
+};
+
+bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepared* out) {
   // TF32 reads FP32 storage; BF16 needs BF16 storage of both operands.
   if (!((prec == BCUR_TF32 && !d.ab_bf16) || (prec == BCUR_BF16 && d.ab_bf16)))
     return BCUR_ENOTSUP;
   if (!tc_device_ok()) return BCUR_ENOTSUP;
-  if (d.M <= 0 || d.N <= 0) {
-    if (n_partials) *n_partials = 0;
-    return BCUR_OK;
-  }
   if (d.K <= 0 || d.M > INT32_MAX || d.N > INT32_MAX || d.K > INT32_MAX) return BCUR_ENOTSUP;
   if (d.ksplit > 1) return BCUR_ENOTSUP;
   const int kind = d.ab_bf16 ? 1 : 0;
@@ -740,14 +838,15 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   }
   // TF32 operands must be K-major on this tensor core.
   if (kind == 0 && (A.mn_major || B.mn_major)) return BCUR_ENOTSUP;
-  const int BN = Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256);
+  const int BN = BN_force ? BN_force : (Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256));
   const int batch = d.batch > 1 ? d.batch : 1;
   const int64_t sAm = swap ? d.sB : d.sA, sBm = swap ? d.sA : d.sB;
-  Maps maps;
+  Maps& maps = out->maps;
   if (!make_map(&maps.a[0], A, kind, BM, batch, sAm) || !make_map(&maps.b[0], B, kind, BN, batch, sBm) ||
       !make_map(&maps.a[1], Al, kind, BM, batch, sAm) || !make_map(&maps.b[1], Bl, kind, BN, batch, sBm))
     return BCUR_ENOTSUP;
-  Params p{};
+  Params& p = out->p;
+  p = Params{};
   p.Mm = (int)Mm; p.Nm = (int)Nm; p.K = (int)d.K;
   p.parts = parts;
   p.batch = batch;
@@ -766,13 +865,29 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   p.X = (const float*)d.X; p.ldx = d.ldx; p.partials = d.partials;
   p.status = d.status;
   p.ksplit = 1;
+  out->BN = BN;
+  out->kind = kind;
+  return BCUR_OK;
+}
+
+// Launch one GEMM.  `epi` selects store or residual.
+bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t* n_partials) {
+  if (d.M <= 0 || d.N <= 0) {
+    if (n_partials) *n_partials = 0;
+    return BCUR_OK;
+  }
+  Prepared pr;
+  BCUR_TRY(prepare(d, prec, epi, 0, &pr));
+  Params& p = pr.p;
+  const Maps& maps = pr.maps;
+  const int BN = pr.BN, kind = pr.kind, batch = p.batch;
   const int sms = sm_count();
   const int tiles = p.tiles_m * p.tiles_n;
   // Split K when there are too few tiles to fill the GPU and a scratch
   // buffer for the partial slices is available.
   if (epi == EPI_STORE && d.scratch && batch == 1 && tiles < sms && p.kblocks >= 8) {
     int ks = std::min<int64_t>(std::max<int64_t>(1, (4 * sms) / tiles), p.kblocks / 4);
-    const int64_t slice = Mm * Nm * 4;
+    const int64_t slice = (int64_t)p.Mm * p.Nm * 4;
     ks = (int)std::min<int64_t>(ks, (int64_t)d.scratch_bytes / slice);
     if (ks > 1) {
       p.ksplit = ks;
@@ -789,7 +904,7 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   if (p.ksplit > 1) {
     BCUR_TRY((kind == 0 ? launch_bn<0, EPI_PARTIAL>(BN, maps, p, grid, s)
                         : launch_bn<1, EPI_PARTIAL>(BN, maps, p, grid, s)));
-    const int64_t total = Mm * Nm;
+    const int64_t total = (int64_t)p.Mm * p.Nm;
     const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4 * sms);
     splitk_reduce_kernel<<<blocks, 256, 0, s>>>(p);
     BCUR_LAUNCH_CHECK();
@@ -797,6 +912,113 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   }
   return kind == 0 ? launch_bn<0, EPI_STORE>(BN, maps, p, grid, s)
                    : launch_bn<1, EPI_STORE>(BN, maps, p, grid, s);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches
+// ---------------------------------------------------------------------------
+size_t group_bytes(int count) {
+  return (size_t)count * sizeof(GEntry) + (size_t)(2 * count + 1) * sizeof(int) + 256;
+}
+
+// X pointers of a residual group, read per launch from a caller table:
+// entry i takes *(base + owner[i] * stride + offset).
+__global__ void group_patch_x_kernel(GEntry* e, const int* owner, int count, const char* base,
+                                     size_t stride, size_t offset) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  e[i].p.X = *reinterpret_cast<const float* const*>(base + (size_t)owner[i] * stride + offset);
+}
+
+bcur_status_t group_prepare(const GemmDesc* ds, int count, int epi, int BN_force, void* dev,
+                            size_t bytes, int* status, TcGroup* out) {
+  if (count < 1 || !dev || bytes < group_bytes(count)) return BCUR_EINVAL;
+  if (epi != EPI_STORE && epi != EPI_RESID) return BCUR_EINVAL;
+  if (reinterpret_cast<uintptr_t>(dev) % 128 != 0) return BCUR_EINVAL;
+  // Tile width shared by the whole launch: the least padded MMA work, ties
+  // going to the wider tile.
+  int BN = BN_force;
+  if (!BN) {
+    double best = -1.0;
+    for (int cand : {256, 128, 64}) {
+      double work = 0.0;
+      for (int i = 0; i < count; ++i) {
+        Prepared pr;
+        BCUR_TRY(prepare(ds[i], BCUR_BF16, epi, cand, &pr));
+        work += (double)pr.p.tiles_m * pr.p.tiles_n * cand * pr.p.kblocks * pr.p.parts * pr.p.batch;
+      }
+      if (best < 0.0 || work < best) { best = work; BN = cand; }
+    }
+  }
+  std::vector<GEntry> e(count);
+  std::vector<int> order(count);
+  std::vector<double> weight(count);
+  for (int i = 0; i < count; ++i) {
+    Prepared pr;
+    BCUR_TRY(prepare(ds[i], BCUR_BF16, epi, BN, &pr));
+    if (epi == EPI_RESID && (pr.p.tri_out || pr.p.batch != 1 || !ds[i].partials))
+      return BCUR_EINVAL;
+    e[i].maps = pr.maps;
+    e[i].p = pr.p;
+    order[i] = i;
+    weight[i] = (double)pr.p.kblocks * pr.p.parts;
+  }
+  // heaviest units first
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return weight[x] > weight[y]; });
+  std::vector<GEntry> sorted(count);
+  std::vector<int> starts(count + 1, 0);
+  int64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    sorted[i] = e[order[i]];
+    starts[i] = (int)total;
+    total += (int64_t)sorted[i].p.tiles_m * sorted[i].p.tiles_n * sorted[i].p.batch;
+  }
+  if (total > INT32_MAX) return BCUR_ENOTSUP;
+  starts[count] = (int)total;
+  char* base = static_cast<char*>(dev);
+  BCUR_CUDA_TRY(cudaMemcpy(base, sorted.data(), (size_t)count * sizeof(GEntry),
+                           cudaMemcpyHostToDevice));
+  int* d_starts = reinterpret_cast<int*>(base + (size_t)count * sizeof(GEntry));
+  BCUR_CUDA_TRY(cudaMemcpy(d_starts, starts.data(), (size_t)(count + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice));
+  BCUR_CUDA_TRY(cudaMemcpy(d_starts + count + 1, order.data(), (size_t)count * sizeof(int),
+                           cudaMemcpyHostToDevice));
+  out->BN = BN;
+  out->epi = epi;
+  out->count = count;
+  out->total = (int)total;
+  out->grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, sm_count()));
+  out->table = dev;
+  out->starts = d_starts;
+  out->status = status;
+  return BCUR_OK;
+}
+
+bcur_status_t group_patch_x(const TcGroup& g, const void* base, size_t stride, size_t offset,
+                            cudaStream_t s) {
+  if (g.count < 1) return BCUR_OK;
+  group_patch_x_kernel<<<(g.count + 127) / 128, 128, 0, s>>>(
+      static_cast<GEntry*>(g.table), g.starts + g.count + 1, g.count,
+      static_cast<const char*>(base), stride, offset);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t group_run(const TcGroup& g, cudaStream_t s, int grid) {
+  if (g.count < 1 || g.total < 1) return BCUR_OK;
+  Group grp;
+  grp.e = static_cast<const GEntry*>(g.table);
+  grp.starts = g.starts;
+  grp.count = g.count;
+  grp.total = g.total;
+  grp.status = g.status;
+  Maps maps;
+  memset(&maps, 0, sizeof(maps));
+  Params p{};
+  const int gr = grid > 0 ? std::min(grid, g.total) : g.grid;
+  return g.epi == EPI_RESID ? launch_bn<1, EPI_RESID, true>(g.BN, maps, p, gr, s, grp)
+                            : launch_bn<1, EPI_STORE, true>(g.BN, maps, p, gr, s, grp);
 }
 
 }  // namespace tc
@@ -812,6 +1034,30 @@ bcur_status_t gemm_tc(const GemmDesc& d, int prec, cudaStream_t s) {
 bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* n_partials) {
   if (d.batch != 1) return BCUR_ENOTSUP;
   return tc::run(d, prec, s, tc::EPI_RESID, n_partials);
+}
+
+size_t gemm_tc_group_bytes(int count) { return tc::group_bytes(count); }
+
+bcur_status_t gemm_tc_group_prepare(const GemmDesc* ds, int count, int resid, int BN, void* dev,
+                                    size_t bytes, int* status, TcGroup* out) {
+  return tc::group_prepare(ds, count, resid ? tc::EPI_RESID : tc::EPI_STORE, BN, dev, bytes,
+                           status, out);
+}
+
+bcur_status_t gemm_tc_group_run(const TcGroup& g, cudaStream_t s, int grid) {
+  return tc::group_run(g, s, grid);
+}
+
+bcur_status_t gemm_tc_group_patch_x(const TcGroup& g, const void* base, size_t stride,
+                                    size_t offset, cudaStream_t s) {
+  return tc::group_patch_x(g, base, stride, offset, s);
+}
+
+int64_t gemm_tc_units(const GemmDesc& d, int resid, int BN) {
+  tc::Prepared pr;
+  if (tc::prepare(d, BCUR_BF16, resid ? tc::EPI_RESID : tc::EPI_STORE, BN, &pr) != BCUR_OK)
+    return -1;
+  return (int64_t)pr.p.tiles_m * pr.p.tiles_n * pr.p.batch;
 }
 
 }  // namespace bcur

@@ -60,6 +60,31 @@ bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t
 int64_t gemm_tc_resid_ctas(int64_t M, int64_t N);
 bool gemm_tc_available();
 
+// Grouped tensor-core GEMM: many BF16 GEMMs of different shapes in one
+// persistent launch.  The table (tensor maps + parameters per GEMM, tile
+// prefix sums) is encoded on the host and copied to `dev` once
+// (synchronously); running it is one launch.  BN = 0 picks the tile width
+// with the least padded work.  resid = 1: every GEMM reduces
+// sum (X - A_op B_op)^2 and sum X^2 per (tile, 32-row quarter) into
+// d.partials[8 * tile + 2 * quarter + {0, 1}], tiles numbered as
+// gemm_tc_units counts them (the launch order does not change the sums).
+struct TcGroup {
+  int BN = 0, epi = 0, count = 0, total = 0, grid = 0;
+  void* table = nullptr;
+  const int* starts = nullptr;
+  int* status = nullptr;
+};
+size_t gemm_tc_group_bytes(int count);
+bcur_status_t gemm_tc_group_prepare(const GemmDesc* ds, int count, int resid, int BN, void* dev,
+                                    size_t bytes, int* status, TcGroup* out);
+bcur_status_t gemm_tc_group_run(const TcGroup& g, cudaStream_t s, int grid = 0);
+// Set the residual reference X of every GEMM of a prepared group from a
+// device table: GEMM j (in the order given to prepare) reads the pointer at
+// base + j * stride + offset.  One small launch.
+bcur_status_t gemm_tc_group_patch_x(const TcGroup& g, const void* base, size_t stride,
+                                    size_t offset, cudaStream_t s);
+int64_t gemm_tc_units(const GemmDesc& d, int resid, int BN);
+
 // ---------------------------------------------------------------------------
 // Small kernels
 // ---------------------------------------------------------------------------

@@ -1,0 +1,210 @@
+// Device-side building blocks shared by the single-problem kernels and the
+// batched (grouped) kernels: the same arithmetic in the same order, so that
+// a decomposition gives the same numbers whichever launch it runs in.
+#pragma once
+
+#include "common.cuh"
+
+namespace bcur {
+
+// ---------------------------------------------------------------------------
+// Small FP64 Cholesky with the drop rule, and its inverse (w <= 128).
+// S: shared memory of w * (w + 1) doubles.  G (w x w, ld w): only the lower
+// part is read.  A pivot d with d <= tol_rel * max_i G_ii (or d <= 0) drops
+// its direction: the column of L and the row of L^{-1} are zero.  Writes L64
+// and Linv64 (FP64) and LinvT (T), all w x w with zeros above the diagonal;
+// *kept = number of kept pivots.  Every thread of the block must call it.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void chol_small_body(const double* G, int w, double tol_rel, double* L64,
+                                double* Linv64, T* LinvT, int* kept, double* S) {
+  const int ld = w + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e % w;
+    S[i * ld + j] = (j <= i) ? G[i * w + j] : 0.0;
+  }
+  __shared__ double s_tol, s_piv;
+  __shared__ int s_kept;
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < w; ++i) mx = fmax(mx, S[i * ld + i]);
+    s_tol = tol_rel * mx;
+    s_kept = 0;
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (tid == 0) {
+      const double d = S[j * ld + j];
+      double p = 0.0;
+      if (d > s_tol && d > 0.0) { p = sqrt(d); s_kept++; }
+      S[j * ld + j] = p;
+      s_piv = p;
+    }
+    __syncthreads();
+    const double p = s_piv;
+    for (int i = j + 1 + tid; i < w; i += nt) S[i * ld + j] = (p > 0.0) ? S[i * ld + j] / p : 0.0;
+    __syncthreads();
+    const int rem = w - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int a = e / rem, b = e % rem;
+      if (b <= a) {
+        const int i = j + 1 + a, i2 = j + 1 + b;
+        S[i * ld + i2] -= S[i * ld + j] * S[i2 * ld + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e % w;
+    L64[e] = (j <= i) ? S[i * ld + j] : 0.0;
+  }
+  // L^{-1} by forward substitution, one column per thread; dropped rows -> 0.
+  for (int c = tid; c < w; c += nt) {
+    for (int i = 0; i < w; ++i) {
+      double x = 0.0;
+      if (i >= c) {
+        const double lii = S[i * ld + i];
+        if (lii > 0.0) {
+          double acc = (i == c) ? 1.0 : 0.0;
+          for (int k = c; k < i; ++k) acc -= S[i * ld + k] * Linv64[k * w + c];
+          x = acc / lii;
+        }
+      }
+      Linv64[i * w + c] = x;
+      LinvT[i * w + c] = (T)x;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && kept) *kept = s_kept;
+}
+
+// ---------------------------------------------------------------------------
+// Factor one NB x NB diagonal block of a Gram matrix (lower part of G, ld
+// ldg, already updated by the trailing updates) as L L^T with the drop rule
+// (pivot <= tol -> direction dropped) and form L^{-1}.  Results stay in
+// shared memory: S (NB x LD) holds L, X (NB x LD) holds L^{-1}, LD = NB +
+// 256 / NB, zeros above the diagonal.  Left-looking and column-parallel: for
+// column j every row i >= j forms its dot product with row j of the finished
+// columns (split over 256/NB consecutive threads and combined with shuffles),
+// then the pivot owner scales the column; the inverse is built row by row the
+// same way.  Threads 0..255 work; further threads only take part in the
+// barriers.  Returns the number of kept pivots (valid in every thread).
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__device__ int potrf_leaf(const T* G, int64_t ldg, T* S, T* X, T tol) {
+  constexpr int TPR = 256 / NB;  // threads per row (2 or 4), consecutive lanes
+  constexpr int LD = NB + TPR;   // LD = TPR (mod 32): the row-split loads are conflict-free
+  constexpr unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x;
+  const bool act = tid < 256;
+  const int i = tid / TPR, h = tid % TPR;
+  if (act) {
+    for (int c = h; c < NB; c += TPR) {
+      S[i * LD + c] = (c <= i) ? G[(int64_t)i * ldg + c] : T(0);
+      X[i * LD + c] = T(0);
+    }
+  }
+  __shared__ T s_inv;
+  __shared__ int s_kept;
+  if (tid == 0) s_kept = 0;
+  __syncthreads();
+  for (int j = 0; j < NB; ++j) {
+    T v = T(0);
+    if (act) {
+      // four independent partial sums keep the shared-memory loads in flight
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int k = h;
+      for (; k + 3 * TPR < j; k += 4 * TPR) {
+        a0 += S[i * LD + k] * S[j * LD + k];
+        a1 += S[i * LD + k + TPR] * S[j * LD + k + TPR];
+        a2 += S[i * LD + k + 2 * TPR] * S[j * LD + k + 2 * TPR];
+        a3 += S[i * LD + k + 3 * TPR] * S[j * LD + k + 3 * TPR];
+      }
+      for (; k < j; k += TPR) a0 += S[i * LD + k] * S[j * LD + k];
+      T acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      v = S[i * LD + j] - acc;
+      if (i == j && h == 0) {
+        const T p = (v > tol && v > T(0)) ? sqrt(v) : T(0);
+        S[j * LD + j] = p;
+        s_inv = (p > T(0)) ? T(1) / p : T(0);
+        if (p > T(0)) s_kept++;
+      }
+    }
+    __syncthreads();
+    if (act && i > j && h == 0) S[i * LD + j] = v * s_inv;
+    __syncthreads();
+  }
+  // X = L^{-1}, row r from the rows above it:
+  //   X[r][c] = (delta_rc - sum_{c <= k < r} L[r][k] X[k][c]) / L[r][r]
+  for (int r = 0; r < NB; ++r) {
+    if (act) {
+      const int c = i;  // column handled by this thread group
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      if (c <= r) {
+        int k = c + h;
+        for (; k + 3 * TPR < r; k += 4 * TPR) {
+          a0 += S[r * LD + k] * X[k * LD + c];
+          a1 += S[r * LD + k + TPR] * X[(k + TPR) * LD + c];
+          a2 += S[r * LD + k + 2 * TPR] * X[(k + 2 * TPR) * LD + c];
+          a3 += S[r * LD + k + 3 * TPR] * X[(k + 3 * TPR) * LD + c];
+        }
+        for (; k < r; k += TPR) a0 += S[r * LD + k] * X[k * LD + c];
+      }
+      T acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (c <= r && h == 0) {
+        const T lrr = S[r * LD + r];
+        X[r * LD + c] = (lrr > T(0)) ? (((c == r) ? T(1) : T(0)) - acc) / lrr : T(0);
+      }
+    }
+    __syncthreads();
+  }
+  return s_kept;
+}
+
+// ---------------------------------------------------------------------------
+// Inverse-CDF block sampling, one thread.  The arithmetic is the sequential
+// FP64 order of the oracle: every add / multiply is an explicit
+// round-to-nearest intrinsic (no contraction into FMA).  For draw t with
+// uniform u[t]: T = sum of the remaining scores, x = u[t] * T, pick the first
+// remaining j whose running prefix sum exceeds x; if rounding leaves none,
+// the last remaining block with a positive score, else the first remaining
+// block.  remaining: G bytes of scratch.  prob may be null.
+// ---------------------------------------------------------------------------
+__device__ inline void sample_seq(const double* scores, int G, const double* u, int g,
+                                  int replacement, int32_t* idx, double* prob,
+                                  unsigned char* remaining) {
+  for (int j = 0; j < G; ++j) remaining[j] = 1;
+  double total0 = 0.0;
+  for (int j = 0; j < G; ++j) total0 = __dadd_rn(total0, scores[j]);
+  for (int t = 0; t < g; ++t) {
+    double T = 0.0;
+    for (int j = 0; j < G; ++j)
+      if (remaining[j]) T = __dadd_rn(T, scores[j]);
+    const double x = __dmul_rn(u[t], T);
+    int pick = -1;
+    double S = 0.0;
+    for (int j = 0; j < G; ++j) {
+      if (!remaining[j]) continue;
+      S = __dadd_rn(S, scores[j]);
+      if (S > x) { pick = j; break; }
+    }
+    if (pick < 0) {
+      for (int j = G - 1; j >= 0; --j)
+        if (remaining[j] && scores[j] > 0.0) { pick = j; break; }
+      if (pick < 0)
+        for (int j = 0; j < G; ++j)
+          if (remaining[j]) { pick = j; break; }
+    }
+    idx[t] = pick;
+    if (prob) prob[t] = total0 > 0.0 ? __ddiv_rn(scores[pick], total0) : 0.0;
+    if (!replacement) remaining[pick] = 0;
+  }
+}
+
+}  // namespace bcur

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "leaf.cuh"
 
 namespace bcur {
 
@@ -87,65 +88,7 @@ template <typename T>
 __global__ void chol_small_kernel(const double* G, int w, double tol_rel, double* L64,
                                   double* Linv64, T* LinvT, int* kept) {
   extern __shared__ double S[];
-  const int ld = w + 1;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < w * w; e += nt) {
-    const int i = e / w, j = e % w;
-    S[i * ld + j] = (j <= i) ? G[i * w + j] : 0.0;
-  }
-  __shared__ double s_tol, s_piv;
-  __shared__ int s_kept;
-  __syncthreads();
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < w; ++i) mx = fmax(mx, S[i * ld + i]);
-    s_tol = tol_rel * mx;
-    s_kept = 0;
-  }
-  __syncthreads();
-  for (int j = 0; j < w; ++j) {
-    if (tid == 0) {
-      const double d = S[j * ld + j];
-      double p = 0.0;
-      if (d > s_tol && d > 0.0) { p = sqrt(d); s_kept++; }
-      S[j * ld + j] = p;
-      s_piv = p;
-    }
-    __syncthreads();
-    const double p = s_piv;
-    for (int i = j + 1 + tid; i < w; i += nt) S[i * ld + j] = (p > 0.0) ? S[i * ld + j] / p : 0.0;
-    __syncthreads();
-    const int rem = w - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int a = e / rem, b = e % rem;
-      if (b <= a) {
-        const int i = j + 1 + a, i2 = j + 1 + b;
-        S[i * ld + i2] -= S[i * ld + j] * S[i2 * ld + j];
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < w * w; e += nt) {
-    const int i = e / w, j = e % w;
-    L64[e] = (j <= i) ? S[i * ld + j] : 0.0;
-  }
-  // L^{-1} by forward substitution, one column per thread; dropped rows -> 0.
-  for (int c = tid; c < w; c += nt) {
-    for (int i = 0; i < w; ++i) {
-      double x = 0.0;
-      if (i >= c) {
-        const double lii = S[i * ld + i];
-        if (lii > 0.0) {
-          double acc = (i == c) ? 1.0 : 0.0;
-          for (int k = c; k < i; ++k) acc -= S[i * ld + k] * Linv64[k * w + c];
-          x = acc / lii;
-        }
-      }
-      Linv64[i * w + c] = x;
-      LinvT[i * w + c] = (T)x;
-    }
-  }
-  if (tid == 0) *kept = s_kept;
+  chol_small_body<T>(G, w, tol_rel, L64, Linv64, LinvT, kept, S);
 }
 
 template <typename T>
@@ -313,6 +256,25 @@ bcur_status_t jacobi_svd_small(const double* X, int w, T* Ut, T* W, double* sigm
   return BCUR_OK;
 }
 
+template <typename T>
+bcur_status_t jacobi_svd_batched(const double* X, int w, T* Ut, T* W, double* sigma, T* jwork,
+                                 int* status, int batch, cudaStream_t s) {
+  if (w < 2 || w > 128 || (w & 1) || batch < 1) return BCUR_EINVAL;
+  const size_t smem = (size_t)w * w * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    attr_set = true;
+  }
+  const int warps = w / 2 < 32 ? w / 2 : 32;
+  jacobi_svd_kernel<T><<<batch, warps * 32, smem, s>>>(X, w, Ut, W, sigma, jwork, status);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+template bcur_status_t jacobi_svd_batched<float>(const double*, int, float*, float*, double*,
+                                                 float*, int*, int, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 // Blocked Cholesky pieces (working precision T)
 // ---------------------------------------------------------------------------
@@ -342,87 +304,26 @@ bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t 
 // Factor the diagonal block G[j0:j0+NB, j0:j0+NB] (lower part, already
 // updated by the trailing updates) as L L^T with the drop rule, and write L
 // and L^{-1} into the same block position of L and Linv (zeros above the
-// diagonal).  Left-looking and column-parallel: for column j every row
-// i >= j forms its dot product with row j of the finished columns (split
-// over 256/NB threads and combined with shuffles), then the pivot owner
-// scales the column.  The inverse is built row by row the same way.  All
-// 256 threads work at every step; one reciprocal per pivot.
+// diagonal); the arithmetic is potrf_leaf's.
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) potrf_diag_kernel(const T* G, int64_t ldg, T* L, int64_t ldl,
                                                          T* Linv, int64_t ldi, int64_t j0,
                                                          const T* maxdiag, double tol_rel,
                                                          int* kept) {
-  constexpr int TPR = 256 / NB;  // threads per row (2 or 4), consecutive lanes
-  constexpr int LD = NB + TPR;   // LD = TPR (mod 32): the row-split loads are conflict-free
-  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int TPR = 256 / NB;
+  constexpr int LD = NB + TPR;
   extern __shared__ unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);  // NB x LD: G, then L
+  T* S = reinterpret_cast<T*>(smem_raw);  // NB x LD: L
   T* X = S + NB * LD;                      // NB x LD: L^{-1}
+  const T tol = (T)(tol_rel * (double)(*maxdiag));
+  const int nk = potrf_leaf<T, NB>(G + j0 * ldg + j0, ldg, S, X, tol);
   const int tid = threadIdx.x;
   const int i = tid / TPR, h = tid % TPR;
-  for (int c = h; c < NB; c += TPR) {
-    S[i * LD + c] = (c <= i) ? G[(j0 + i) * ldg + j0 + c] : T(0);
-    X[i * LD + c] = T(0);
-  }
-  __shared__ T s_inv;
-  __shared__ int s_kept;
-  if (tid == 0) s_kept = 0;
-  const T tol = (T)(tol_rel * (double)(*maxdiag));
-  __syncthreads();
-  for (int j = 0; j < NB; ++j) {
-    // four independent partial sums keep the shared-memory loads in flight
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    int k = h;
-    for (; k + 3 * TPR < j; k += 4 * TPR) {
-      a0 += S[i * LD + k] * S[j * LD + k];
-      a1 += S[i * LD + k + TPR] * S[j * LD + k + TPR];
-      a2 += S[i * LD + k + 2 * TPR] * S[j * LD + k + 2 * TPR];
-      a3 += S[i * LD + k + 3 * TPR] * S[j * LD + k + 3 * TPR];
-    }
-    for (; k < j; k += TPR) a0 += S[i * LD + k] * S[j * LD + k];
-    T acc = (a0 + a1) + (a2 + a3);
-#pragma unroll
-    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    const T v = S[i * LD + j] - acc;
-    if (i == j && h == 0) {
-      const T p = (v > tol && v > T(0)) ? sqrt(v) : T(0);
-      S[j * LD + j] = p;
-      s_inv = (p > T(0)) ? T(1) / p : T(0);
-      if (p > T(0)) s_kept++;
-    }
-    __syncthreads();
-    if (i > j && h == 0) S[i * LD + j] = v * s_inv;
-    __syncthreads();
-  }
-  // X = L^{-1}, row r from the rows above it:
-  //   X[r][c] = (delta_rc - sum_{c <= k < r} L[r][k] X[k][c]) / L[r][r]
-  for (int r = 0; r < NB; ++r) {
-    const int c = i;  // column handled by this thread group
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    if (c <= r) {
-      int k = c + h;
-      for (; k + 3 * TPR < r; k += 4 * TPR) {
-        a0 += S[r * LD + k] * X[k * LD + c];
-        a1 += S[r * LD + k + TPR] * X[(k + TPR) * LD + c];
-        a2 += S[r * LD + k + 2 * TPR] * X[(k + 2 * TPR) * LD + c];
-        a3 += S[r * LD + k + 3 * TPR] * X[(k + 3 * TPR) * LD + c];
-      }
-      for (; k < r; k += TPR) a0 += S[r * LD + k] * X[k * LD + c];
-    }
-    T acc = (a0 + a1) + (a2 + a3);
-#pragma unroll
-    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    if (c <= r && h == 0) {
-      const T lrr = S[r * LD + r];
-      X[r * LD + c] = (lrr > T(0)) ? (((c == r) ? T(1) : T(0)) - acc) / lrr : T(0);
-    }
-    __syncthreads();
-  }
   for (int c = h; c < NB; c += TPR) {
     L[(j0 + i) * ldl + j0 + c] = (c <= i) ? S[i * LD + c] : T(0);
     Linv[(j0 + i) * ldi + j0 + c] = (c <= i) ? X[i * LD + c] : T(0);
   }
-  if (tid == 0) atomicAdd(kept, s_kept);
+  if (tid == 0) atomicAdd(kept, nk);
 }
 
 template <typename T, int NB>
@@ -497,32 +398,7 @@ __global__ void sample_kernel(const double* scores, int G, const double* u, int 
                               int replacement, int32_t* idx, double* prob) {
   extern __shared__ unsigned char remaining[];
   if (threadIdx.x != 0) return;
-  for (int j = 0; j < G; ++j) remaining[j] = 1;
-  double total0 = 0.0;
-  for (int j = 0; j < G; ++j) total0 = __dadd_rn(total0, scores[j]);
-  for (int t = 0; t < g; ++t) {
-    double T = 0.0;
-    for (int j = 0; j < G; ++j)
-      if (remaining[j]) T = __dadd_rn(T, scores[j]);
-    const double x = __dmul_rn(u[t], T);
-    int pick = -1;
-    double S = 0.0;
-    for (int j = 0; j < G; ++j) {
-      if (!remaining[j]) continue;
-      S = __dadd_rn(S, scores[j]);
-      if (S > x) { pick = j; break; }
-    }
-    if (pick < 0) {
-      for (int j = G - 1; j >= 0; --j)
-        if (remaining[j] && scores[j] > 0.0) { pick = j; break; }
-      if (pick < 0)
-        for (int j = 0; j < G; ++j)
-          if (remaining[j]) { pick = j; break; }
-    }
-    idx[t] = pick;
-    if (prob) prob[t] = total0 > 0.0 ? __ddiv_rn(scores[pick], total0) : 0.0;
-    if (!replacement) remaining[pick] = 0;
-  }
+  sample_seq(scores, G, u, g, replacement, idx, prob, remaining);
 }
 
 bcur_status_t sample_blocks(const double* scores, int G, const double* u, int g, int replacement,

@@ -111,3 +111,50 @@ def test_workspace_grows_with_blocks(lib):
     _, a = _plan(lib, g_col=2, g_row=2)
     _, b = _plan(lib, g_col=8, g_row=6)
     assert b > a
+
+
+def _batch_plan(lib, items, q=2):
+    from paper_1703_06065_gb300 import _lib
+
+    arr = (_lib.BatchItem * max(1, len(items)))()
+    for i, it in enumerate(items):
+        a = arr[i]
+        a.m, a.n, a.lda = it["m"], it["n"], it.get("lda", it["n"])
+        a.k, a.p, a.block = it["k"], it["p"], it["block"]
+        a.g_col, a.g_row = it["g_col"], it["g_row"]
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    st = lib.bcur_batch_plan(arr, len(items), q, None, ctypes.byref(h), ctypes.byref(ws))
+    if st == 0:
+        lib.bcur_batch_destroy(h)
+    return st, ws.value
+
+
+_GOOD = dict(m=512, n=1024, k=10, p=10, block=64, g_col=3, g_row=2)
+
+
+@pytest.mark.parametrize("change,want", [
+    ({}, 0),
+    ({"p": 60}, 1),                       # l = 70 > 64
+    ({"g_col": 17}, 1),                   # more blocks than G = 16
+    ({"block": 256, "g_col": 3}, 1),      # c = 768 > 512
+    ({"lda": 1022}, 1),                   # lda < n
+    ({"lda": 1026}, 1),                   # lda not a multiple of 4
+    ({"k": 0}, 1),
+    ({"n": 1000, "block": 48}, 0),        # short last block
+])
+def test_batch_plan_validation(lib, change, want):
+    it = dict(_GOOD, **change)
+    st, ws = _batch_plan(lib, [_GOOD, it])
+    assert st == want
+    if want == 0:
+        assert ws > 2 * 512 * 1024 * 4       # at least the two BF16 pairs of A
+
+
+def test_batch_plan_rejects_empty_and_bad_q(lib):
+    assert _batch_plan(lib, [])[0] == 1
+    assert _batch_plan(lib, [_GOOD], q=17)[0] == 1
+    # workspace grows with the batch
+    w1 = _batch_plan(lib, [_GOOD])[1]
+    w2 = _batch_plan(lib, [_GOOD, _GOOD])[1]
+    assert w2 > w1

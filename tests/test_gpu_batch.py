@@ -1,0 +1,174 @@
+"""Batched decompositions (one launch per stage over many uneven matrices):
+parity of every item with the FP64 oracle, independence of an item's results
+from the rest of the batch, and CUDA-graph replay."""
+import numpy as np
+import pytest
+
+from _gpu_common import device, to_dev, torch  # noqa: F401
+import bcur_inputs as bi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems():
+    """Test-sized members of the biometric recipe (AR(1) series mixed by a
+    rank-k loading + 0.05 noise), plus shapes with short last blocks and the
+    largest c = r = 512."""
+    probs = bi.batched_biometric(6, seed=5, m_range=(256, 768), n_range=(512, 1536),
+                                 k_range=(5, 20), blocks=(16, 32, 64, 128))
+    extra = [
+        bi.Problem("short_last", 300, 700, k=6, p=10, q=2, col_off=bi.uniform_blocks(700, 48),
+                   row_off=bi.uniform_blocks(300, 48), g_col=4, g_row=3, seed=11, storage="f32",
+                   recipe=dict(kind="ar1_mixture", rank=6, phi=0.95, noise=0.05)),
+        bi.Problem("wide_fit", 1024, 1536, k=20, p=10, q=2, col_off=bi.uniform_blocks(1536, 256),
+                   row_off=bi.uniform_blocks(1024, 256), g_col=2, g_row=2, seed=12, storage="f32",
+                   recipe=dict(kind="ar1_mixture", rank=20, phi=0.95, noise=0.05)),
+    ]
+    return probs + extra
+
+
+def _item(p):
+    return dict(m=p.m, n=p.n, k=p.k, p=p.p, block=int(p.col_off[1] - p.col_off[0]),
+                g_col=p.g_col, g_row=p.g_row)
+
+
+def _inputs(probs):
+    As = [to_dev(p.matrix(), torch.float32) for p in probs]
+    oms = [to_dev(p.omega().T, torch.float32) for p in probs]
+    ucs = [to_dev(p.u_col()) for p in probs]
+    urs = [to_dev(p.u_row()) for p in probs]
+    return As, oms, ucs, urs
+
+
+def _host(o, i):
+    return {k: (o[k][i].cpu().numpy().copy() if o[k][i] is not None else None)
+            for k in ("col_scores", "row_scores", "col_idx", "row_idx", "U", "err")}
+
+
+def _run(probs, use_graph=False):
+    import paper_1703_06065_gb300 as pkg
+
+    device()
+    b = pkg.Batch([_item(p) for p in probs], q=2)
+    ins = _inputs(probs)
+    o = b.run(*ins, use_graph=use_graph)
+    b.sync_status()
+    return b, ins, [_host(o, i) for i in range(len(probs))]
+
+
+def _tie_free_draws(ref_scores, gpu_scores, u, g):
+    """Draws before the first one whose x = u T lies within the CDF
+    perturbation sum |l_gpu - l_orc| (+ rounding) of an oracle boundary."""
+    tol = float(np.sum(np.abs(np.asarray(gpu_scores) - np.asarray(ref_scores)))) + 1e-12
+    l = [float(v) for v in ref_scores]
+    rem = [True] * len(l)
+    for t in range(g):
+        T = sum(v for v, r in zip(l, rem) if r)
+        x = float(u[t]) * T
+        S, pick = 0.0, -1
+        for j, v in enumerate(l):
+            if not rem[j]:
+                continue
+            S += v
+            if abs(S - x) <= tol:
+                return t
+            if pick < 0 and S > x:
+                pick = j
+        if pick < 0:
+            return t
+        rem[pick] = False
+    return g
+
+
+def test_batch_matches_oracle_per_item():
+    probs = _problems()
+    b, ins, res = _run(probs)
+    for p, r in zip(probs, res):
+        A = p.matrix().astype(np.float64)
+        ref = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(),
+                            p.u_col(), p.u_row())
+        # scores: BF16 sketch, re-orthonormalised in FP32/FP64 after every product
+        for side in ("col", "row"):
+            d = np.max(np.abs(r[f"{side}_scores"] - ref[f"{side}_scores"]))
+            assert d <= 2e-2 * np.max(ref[f"{side}_scores"]), (p.name, side, d)
+            assert abs(np.sum(r[f"{side}_scores"]) - p.k) <= 2e-2 * p.k, (p.name, side)
+        # indices: bit-exact up to the first draw the score perturbation could flip
+        for side, u, g in (("col", p.u_col(), p.g_col), ("row", p.u_row(), p.g_row)):
+            n_ok = _tie_free_draws(ref[f"{side}_scores"], r[f"{side}_scores"], u, g)
+            assert list(r[f"{side}_idx"][:n_ok]) == list(ref[f"{side}_idx"][:n_ok]), (p.name, side)
+        # the accuracy gate against the oracle's own decomposition
+        assert abs(r["err"][1] - ref["rel"]) <= 1e-3, (p.name, r["err"][1], ref["rel"])
+        # the fit on the GPU's own blocks against the oracle's fit on them
+        C = orc.gather_columns(A, p.col_off, list(r["col_idx"]))
+        R = orc.gather_rows(A, p.row_off, list(r["row_idx"]))
+        U = orc.fit_u(A, C, R)
+        err, rel = orc.residual(A, C, U, R)
+        assert abs(r["err"][0] - err) <= 1e-4 * err + 1e-6 * np.linalg.norm(A), p.name
+        assert abs(r["err"][2] - np.linalg.norm(A)) <= 1e-6 * np.linalg.norm(A)
+        c, rr = C.shape[1], R.shape[0]
+        Ug = r["U"][:c, :rr].astype(np.float64)
+        cur_g = C @ Ug @ R
+        cur_o = C @ U @ R
+        assert np.linalg.norm(cur_g - cur_o) <= 1e-3 * np.linalg.norm(A), p.name
+        assert np.all(r["U"][c:, :] == 0) and np.all(r["U"][:, rr:] == 0)
+
+
+def test_item_results_do_not_depend_on_the_batch():
+    probs = _problems()
+    _, _, res_all = _run(probs)
+    for i in (0, len(probs) - 1, 3):
+        _, _, res_one = _run([probs[i]])
+        for k, v in res_one[0].items():
+            np.testing.assert_array_equal(v, res_all[i][k], err_msg=f"{probs[i].name} {k}")
+    # a different mix (reversed order, one item left out) gives the same bits
+    sub = list(reversed(probs[1:]))
+    _, _, res_sub = _run(sub)
+    for j, p in enumerate(sub):
+        i = probs.index(p)
+        for k, v in res_sub[j].items():
+            np.testing.assert_array_equal(v, res_all[i][k], err_msg=f"{p.name} {k}")
+
+
+def test_graph_replay_matches_eager_run():
+    import paper_1703_06065_gb300 as pkg
+
+    probs = _problems()[:4]
+    device()
+    b = pkg.Batch([_item(p) for p in probs], q=2)
+    As, oms, ucs, urs = _inputs(probs)
+    eager = b.run(As, oms, ucs, urs)
+    b.sync_status()
+    ref = [_host(eager, i) for i in range(len(probs))]
+    for _ in range(2):
+        o = b.run(As, oms, ucs, urs, use_graph=True)
+        b.sync_status()
+        for i in range(len(probs)):
+            for k, v in _host(o, i).items():
+                np.testing.assert_array_equal(v, ref[i][k], err_msg=k)
+    # new inputs through the same graph: uniforms swapped between the sides
+    o = b.run(As, oms, urs, ucs, use_graph=True) if all(
+        u.numel() == v.numel() for u, v in zip(ucs, urs)) else None
+    if o is not None:
+        b.sync_status()
+        b2 = pkg.Batch([_item(p) for p in probs], q=2)
+        e2 = b2.run(As, oms, urs, ucs)
+        b2.sync_status()
+        for i in range(len(probs)):
+            for k, v in _host(o, i).items():
+                np.testing.assert_array_equal(v, _host(e2, i)[k], err_msg=k)
+    assert b.launches_per_run > 10
+
+
+def test_nonfinite_item_is_reported():
+    import paper_1703_06065_gb300 as pkg
+
+    probs = _problems()[:2]
+    device()
+    b = pkg.Batch([_item(p) for p in probs], q=1)
+    As, oms, ucs, urs = _inputs(probs)
+    As[1][3, 5] = float("nan")
+    b.run(As, oms, ucs, urs)
+    with pytest.raises(pkg.BcurError) as e:
+        b.sync_status()
+    assert e.value.status == 5
