@@ -115,12 +115,7 @@ def haar_spectrum_device(m: int, n: int, rank: int, decay: float, noise: float, 
     return a
 
 
-def ar1_mixture(m: int, n: int, k: int, phi: float, noise: float, seed: int) -> np.ndarray:
-    """Biometric-like matrix: L (m x k, N(0,1)/sqrt(k)) . X (k x n AR(1)) + noise.
-
-    Each row of X follows x_t = phi x_{t-1} + sqrt(1 - phi^2) e_t with
-    x_0 ~ N(0,1), so every series has unit stationary variance.
-    """
+def _ar1_draw(m: int, n: int, k: int, phi: float, seed: int):
     g = rng(seed, STREAM_MATRIX)
     load = g.standard_normal((m, k)) / math.sqrt(k)
     e = g.standard_normal((k, n))
@@ -129,6 +124,43 @@ def ar1_mixture(m: int, n: int, k: int, phi: float, noise: float, seed: int) -> 
     c = math.sqrt(1.0 - phi * phi)
     for t in range(1, n):
         x[:, t] = phi * x[:, t - 1] + c * e[:, t]
+    return load, x, g
+
+
+def ar1_factors(m: int, n: int, k: int, phi: float, seed: int):
+    """The loading L (m x k) and the AR(1) series X (k x n) of :func:`ar1_mixture`
+    (same generator stream, so both recipes share L and X)."""
+    load, x, _ = _ar1_draw(m, n, k, phi, seed)
+    return load, x
+
+
+def ar1_mixture_device(m: int, n: int, k: int, phi: float, noise: float, seed: int,
+                       device="cuda", dtype=None):
+    """The biometric-like recipe drawn on a torch device: L and X as in
+    :func:`ar1_mixture` (host, small), the product and the noise on the device
+    (noise from a seeded torch generator, so it differs from the host recipe's
+    noise draw; the distribution is the same)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    load, x = ar1_factors(m, n, k, phi, seed)
+    L = torch.from_numpy(load).to(device=device, dtype=torch.float32)
+    X = torch.from_numpy(x).to(device=device, dtype=torch.float32)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + STREAM_MATRIX)
+    a = L @ X
+    if noise:
+        a += noise * torch.randn(m, n, generator=gen, device=device, dtype=torch.float32)
+    return a.to(dtype)
+
+
+def ar1_mixture(m: int, n: int, k: int, phi: float, noise: float, seed: int) -> np.ndarray:
+    """Biometric-like matrix: L (m x k, N(0,1)/sqrt(k)) . X (k x n AR(1)) + noise.
+
+    Each row of X follows x_t = phi x_{t-1} + sqrt(1 - phi^2) e_t with
+    x_0 ~ N(0,1), so every series has unit stationary variance.
+    """
+    load, x, g = _ar1_draw(m, n, k, phi, seed)
     a = load @ x
     if noise:
         a = a + noise * g.standard_normal((m, n))
@@ -205,6 +237,18 @@ class Problem:
         else:
             raise ValueError(kind)
         return a.astype(np.float32) if self.storage == "f32" else a
+
+    def matrix_device(self, device="cuda"):
+        """The stored matrix drawn on a device (the large workloads)."""
+        r = self.recipe
+        kind = r["kind"]
+        if kind == "ar1_mixture":
+            return ar1_mixture_device(self.m, self.n, r["rank"], r["phi"], r["noise"], self.seed,
+                                      device=device)
+        if kind == "haar_spectrum":
+            return haar_spectrum_device(self.m, self.n, r["rank"], r["decay"], r["noise"],
+                                        self.seed, device=device)
+        raise ValueError(kind)
 
     def omega(self) -> np.ndarray:
         return rademacher(self.n, self.l, self.seed)

@@ -466,10 +466,42 @@ def main_native(args):
         dist.destroy_process_group()
 
 
+def main_reference_batched(args, world):
+    """The oracle on random members of the batch (bounded sample per step)."""
+    import oracle as orc
+
+    probs = batch_problems(0)
+    idx = batch_oracle_sample(probs, 2 * max(1, args.steps))
+    times = []
+    for j, i in enumerate(idx[: 2 * args.steps]):
+        p = probs[i]
+        A = p.matrix()
+        t0 = time.perf_counter()
+        orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(), p.u_col(),
+                      p.u_row())
+        times.append(time.perf_counter() - t0)
+    v = len(times) / sum(times)
+    sample = (f"FP64 NumPy oracle, whole pipeline on {len(times)} random members {idx} of the "
+              f"512-matrix batch (host-drawn, same recipe); decomps/s = members / time")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "batched_biometric", "matrices": BATCH_COUNT},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "batched_biometric":
+        main_reference_batched(args, world)
         return
     p = workload(args.workload, 0)
     steps = args.steps
@@ -486,6 +518,231 @@ def main_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: 512 uneven biometric-like matrices, every stage one launch
+# over the whole batch, the launch sequence replayed from a CUDA graph
+# ---------------------------------------------------------------------------
+BATCH_COUNT = 512
+
+
+def batch_problems(rank: int):
+    return bi.batched_biometric(BATCH_COUNT, seed=3 + 1000 * rank)
+
+
+def batch_item(p):
+    return dict(m=p.m, n=p.n, k=p.k, p=p.p, block=int(p.col_off[1] - p.col_off[0]),
+                g_col=p.g_col, g_row=p.g_row)
+
+
+def batch_oracle_sample(probs, count: int, seed: int = 7):
+    """Indices of a uniform random sample of the batch (fixed seed)."""
+    g = np.random.default_rng(seed)
+    return sorted(int(i) for i in g.choice(len(probs), size=count, replace=False))
+
+
+def batch_kernel_model(label: str, probs, items, lp: int = 64):
+    """(bound, algorithmic amount per launch, unit) of a batched kernel kind."""
+    mn = sum(p.m * p.n for p in probs)
+    if label == "sketch_gemm":
+        # A_hi read once (2 B), the skinny panel read (2 B) and the FP32 panel
+        # written (4 B), averaged over Y = A Omega and Z = A^T Q launches
+        byt = sum(2 * p.m * p.n + (2 * lp * (p.m + p.n) + 4 * lp * (p.m + p.n)) / 2 for p in probs)
+        return "hbm", byt, "bytes"
+    if label == "split":
+        return "hbm", 8.0 * mn + sum(4 * p.n * p.l + 2 * 64 * p.n for p in probs), "bytes"
+    if label in ("w_gemm", "residual"):
+        fl = sum(3 * 2.0 * p.m * p.n * (-(-it["g_row"] * it["block"] // 64) * 64)
+                 for p, it in zip(probs, items))
+        return "tensor", fl, "flop"
+    return None, None, None
+
+
+def main_batched(args):
+    import torch
+
+    import paper_1703_06065_gb300 as pkg
+    import oracle as orc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.load()
+    probs = batch_problems(rank)
+    items = [batch_item(p) for p in probs]
+    t_gen = time.perf_counter()
+    As = [p.matrix_device(dev) for p in probs]
+    oms = [torch.from_numpy(np.ascontiguousarray(p.omega().T)).to(dev, torch.float32) for p in probs]
+    ucs = [torch.from_numpy(p.u_col()).to(dev) for p in probs]
+    urs = [torch.from_numpy(p.u_row()).to(dev) for p in probs]
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    batch = pkg.Batch(items, q=2)
+    graph = not args.no_graph
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        out = batch.run(As, oms, ucs, urs, want_u=True, use_graph=graph)
+    torch.cuda.synchronize()
+    batch.sync_status()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(s)
+    for _ in range(args.steps):
+        out = batch.run(As, oms, ucs, urs, want_u=True, use_graph=graph)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    batch.sync_status()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    B = len(probs)
+    value = world * B * 1000.0 / ms
+    launches = batch.launches_per_run
+
+    # -- end to end: every matrix from pinned host memory, results read back ---
+    e2e = None
+    if not args.no_e2e:
+        try:
+            A_h = [a.cpu().pin_memory() for a in As]
+            A_d = [torch.empty_like(a) for a in As]
+            res_h = {k: [torch.empty(v.shape, dtype=v.dtype).pin_memory() for v in out[k]]
+                     for k in ("col_scores", "row_scores", "col_idx", "row_idx", "err", "U")}
+
+            def e2e_step():
+                for d, h in zip(A_d, A_h):
+                    d.copy_(h, non_blocking=True)
+                o = batch.run(A_d, oms, ucs, urs, want_u=True, use_graph=False)
+                for k, lst in res_h.items():
+                    for h, d in zip(lst, o[k]):
+                        h.copy_(d, non_blocking=True)
+
+            e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            k2 = max(1, min(args.steps, 2))
+            ev0.record(s)
+            for _ in range(k2):
+                e2e_step()
+            ev1.record(s)
+            torch.cuda.synchronize()
+            ms2 = ev0.elapsed_time(ev1) / k2
+            h2d = sum(x.numel() * x.element_size() for x in A_h)
+            d2h = sum(x.numel() * x.element_size() for lst in res_h.values() for x in lst)
+            e2e = {"value": world * B * 1000.0 / ms2, "unit": UNIT, "ms_per_step": ms2,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "note": "A of all 512 matrices copied from pinned host memory each step; "
+                           "Omega and the uniforms stay resident"}
+            del A_h, A_d, res_h
+        except RuntimeError as exc:  # host memory for the pinned copies
+            e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None,
+                   "d2h_bytes_per_step": None, "skipped": str(exc)[:200]}
+
+    # -- per-kernel times from one profiled eager run, dominant kernel ------
+    roof, stages = None, None
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        batch.profile(True)
+        batch.run(As, oms, ucs, urs, want_u=True, use_graph=False)
+        torch.cuda.synchronize()
+        steps = batch.profile_steps()
+        batch.profile(False)
+        stages, counts = {}, {}
+        for lab, t in steps:
+            stages[lab] = stages.get(lab, 0.0) + t
+            counts[lab] = counts.get(lab, 0) + 1
+        stages = {k: round(v, 3) for k, v in sorted(stages.items(), key=lambda kv: -kv[1])}
+        dom = next(iter(stages))
+        bound, amount, unit = batch_kernel_model(dom, probs, items)
+        if bound is not None:
+            per_launch_ms = stages[dom] / counts[dom]
+            if bound == "hbm":
+                achieved = amount / (per_launch_ms * 1e-3) / 1e9
+                peak = peaks.get("hbm_gbs", 6789.0)
+                roof = {"bound": "hbm", "unit": "GB/s", "peak_source": "MEASURED_PEAKS hbm_gbs"}
+            else:
+                achieved = amount / (per_launch_ms * 1e-3) / 1e12
+                peak = peaks.get("bf16_tflops_sustained", 1721.0)
+                roof = {"bound": "tensor", "unit": "TFLOP/s",
+                        "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (timed inside the step)"}
+            roof.update(kernel=f"{dom} ({counts[dom]} launches per step)",
+                        achieved=round(achieved, 3), peak=round(peak, 3),
+                        frac=round(achieved / peak, 4), traffic=None, ms=round(per_launch_ms, 4),
+                        algorithmic=f"{amount:.4g} {unit} per launch (model in bench.py)")
+
+    # -- sampled accuracy gate: the FP64 oracle on random members ---------
+    gate, cpu = None, None
+    if rank == 0:
+        idx = batch_oracle_sample(probs, 3 if args.no_cpu_baseline else 4)
+        diffs, ok_idx, t_orc = [], True, []
+        for i in idx:
+            p = probs[i]
+            A64 = As[i].double().cpu().numpy()
+            t0 = time.perf_counter()
+            ref = orc.block_cur(A64, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(),
+                                p.u_col(), p.u_row())
+            t_orc.append(time.perf_counter() - t0)
+            e_gpu = float(out["err"][i][1].item())
+            diffs.append(abs(e_gpu - ref["rel"]))
+            ok_idx &= (out["col_idx"][i].cpu().tolist() == list(ref["col_idx"])
+                       and out["row_idx"][i].cpu().tolist() == list(ref["row_idx"]))
+        gate = {"members": idx, "max_abs_diff_rel_err": max(diffs),
+                "within_1e-3": max(diffs) <= 1e-3, "indices_match": bool(ok_idx),
+                "source": "FP64 oracle run on the same device-drawn matrices (host copies)"}
+        if world == 1 and not args.no_cpu_baseline:
+            v = len(t_orc) / sum(t_orc)
+            cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"FP64 NumPy oracle, whole pipeline on {len(idx)} random members "
+                             f"{idx} of the 512-matrix batch; {sum(t_orc):.2f} s in total, "
+                             f"decomps/s = members / time"}
+
+    if rank == 0:
+        mn = sum(p.m * p.n for p in probs)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/bf16x3", "data": "synthetic",
+            "config": {"workload": "batched_biometric", "matrices": B,
+                       "sum_mn": mn, "storage": "f32", "sketch_prec": "bf16", "fit_prec": "bf16x3",
+                       "q": 2, "cuda_graph": graph,
+                       "l2": f"inputs larger than L2 (A total {4 * mn / 1e9:.1f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "ms_per_decomp": ms / B, "accuracy_gate": gate, "stage_ms": stages,
+            "input_generation_s": round(t_gen, 1), "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -497,11 +754,15 @@ def main():
     ap.add_argument("--fit-prec", default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batched workload: launch eagerly instead of replaying a CUDA graph")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":
         main_reference(args)
+    elif args.workload == "batched_biometric":
+        main_batched(args)
     else:
         main_native(args)
 

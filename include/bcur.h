@@ -388,6 +388,21 @@ bcur_status_t bcur_batch_dims(bcur_batch_t plan, int32_t i, int64_t* cmax, int64
  * device recorded. */
 bcur_status_t bcur_batch_sync_status(bcur_batch_t plan);
 
+/* Profiling of eager runs: with enable != 0 the following runs that are not
+ * replayed from a graph record a CUDA event after each launch (or group of
+ * launches) of the sequence.  After such a run has completed,
+ * bcur_batch_profile_count gives the number of timed steps and
+ * bcur_batch_profile_entry the label of step i (a static string naming the
+ * kernel kind: "split", "sketch_gemm", "skinny_gram", "skinny_chol",
+ * "skinny_apply", "jacobi", "scores", "sample", "gather", "qr_gram",
+ * "wide_chol", "qr_apply", "w_gemm", "m_gemm", "u_gemm", "copy_u", "p_gemm",
+ * "residual", "finish") and its duration in milliseconds.  Errors:
+ * BCUR_EINVAL (no such step), BCUR_ECUDA (run not finished). */
+bcur_status_t bcur_batch_profile(bcur_batch_t plan, int32_t enable);
+int32_t bcur_batch_profile_count(bcur_batch_t plan);
+bcur_status_t bcur_batch_profile_entry(bcur_batch_t plan, int32_t i, const char** label,
+                                       double* ms);
+
 void bcur_batch_destroy(bcur_batch_t plan);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -305,6 +305,21 @@ class Batch:
     def sync_status(self):
         _lib.check(self._L.bcur_batch_sync_status(self._h), "bcur_batch_sync_status")
 
+    def profile(self, enable: bool = True):
+        """Record an event after every launch of the following eager runs."""
+        _lib.check(self._L.bcur_batch_profile(self._h, int(bool(enable))), "bcur_batch_profile")
+
+    def profile_steps(self):
+        """[(label, ms)] of the last profiled run (after it has completed)."""
+        out = []
+        for i in range(self._L.bcur_batch_profile_count(self._h)):
+            lab = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            _lib.check(self._L.bcur_batch_profile_entry(self._h, i, byref(lab), byref(ms)),
+                       "bcur_batch_profile_entry")
+            out.append((lab.value.decode(), ms.value))
+        return out
+
 def block_scores(Ft, off, out=None):
     """Def. 2 scores of the factor whose panel (k x h) is ``Ft``; ``off`` device int64."""
     torch = _torch()

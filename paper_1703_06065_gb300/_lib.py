@@ -28,7 +28,8 @@ EXPORTS = [
     "bcur_gemm_split", "bcur_block_stable_rank_workspace", "bcur_block_stable_rank",
     "bcur_alg1_workspace", "bcur_alg1", "bcur_truncate", "bcur_batch_plan",
     "bcur_batch_set_workspace", "bcur_batch_run", "bcur_batch_dims", "bcur_batch_sync_status",
-    "bcur_batch_destroy",
+    "bcur_batch_destroy", "bcur_batch_profile", "bcur_batch_profile_count",
+    "bcur_batch_profile_entry",
 ]
 
 
@@ -152,6 +153,13 @@ def load():
     L.bcur_batch_dims.restype = st
     L.bcur_batch_sync_status.argtypes = [c_void_p]
     L.bcur_batch_sync_status.restype = st
+    L.bcur_batch_profile.argtypes = [c_void_p, c_int32]
+    L.bcur_batch_profile.restype = st
+    L.bcur_batch_profile_count.argtypes = [c_void_p]
+    L.bcur_batch_profile_count.restype = c_int32
+    L.bcur_batch_profile_entry.argtypes = [c_void_p, c_int32, POINTER(ctypes.c_char_p),
+                                           POINTER(c_double)]
+    L.bcur_batch_profile_entry.restype = st
     L.bcur_batch_destroy.argtypes = [c_void_p]
     L.bcur_batch_destroy.restype = None
     L.bcur_launch_count.argtypes = []

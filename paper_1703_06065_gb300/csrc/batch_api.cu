@@ -53,6 +53,11 @@ struct bcur_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
+  // optional events between the launches of an eager run
+  bool profile = false, marking = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<const char*> plabel;
+  int pn = 0;
 };
 
 namespace {
@@ -283,58 +288,102 @@ bcur_status_t build_groups(bcur_batch_t P) {
   return BCUR_OK;
 }
 
+// Profiling marker: an event after the launch(es) just enqueued.
+bcur_status_t mark(bcur_batch_t P, cudaStream_t s, const char* label) {
+  if (!P->marking) return BCUR_OK;
+  if (P->pn >= (int)P->pev.size()) {
+    cudaEvent_t e;
+    BCUR_CUDA_TRY(cudaEventCreate(&e));
+    P->pev.push_back(e);
+    P->plabel.push_back(nullptr);
+  }
+  BCUR_CUDA_TRY(cudaEventRecord(P->pev[P->pn], s));
+  P->plabel[P->pn] = label;
+  ++P->pn;
+  return BCUR_OK;
+}
+
 bcur_status_t orth(bcur_batch_t P, int s0, int s1, bool want_lb, cudaStream_t s) {
   const bool m_side = s0 < PN0;
   const WorkList& ch = m_side ? P->chunks_m : P->chunks_n;
   const WorkList& ap = m_side ? P->apply_m : P->apply_n;
   BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s0, s));
+  BCUR_TRY(mark(P, s, "skinny_gram"));
   BCUR_TRY(skinny_chol(P->d_items, P->B, s0, 0, 0, s));
+  BCUR_TRY(mark(P, s, "skinny_chol"));
   BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s0, s1, 0, s));
+  BCUR_TRY(mark(P, s, "skinny_apply"));
   BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s1, s));
+  BCUR_TRY(mark(P, s, "skinny_gram"));
   BCUR_TRY(skinny_chol(P->d_items, P->B, s1, 1, want_lb ? 1 : 0, s));
+  BCUR_TRY(mark(P, s, "skinny_chol"));
   BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s1, s0, 1, s));
+  BCUR_TRY(mark(P, s, "skinny_apply"));
   return BCUR_OK;
 }
 
 // The launch sequence of one run (the io table is already being copied).
 bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   const int B = P->B;
+  if (P->marking) P->pn = 0;
+  BCUR_TRY(mark(P, s, "start"));
   BCUR_TRY(gemm_tc_group_patch_x(P->gRes, P->d_io, sizeof(bcur_batch_io_t),
                                  offsetof(bcur_batch_io_t, A), s));
   BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->d_status, s));
+  BCUR_TRY(mark(P, s, "split"));
   // scores: randomized range finder with q subspace iterations (Sec. 3.1)
   BCUR_TRY(gemm_tc_group_run(P->gY, s));
+  BCUR_TRY(mark(P, s, "sketch_gemm"));
   BCUR_TRY(orth(P, PM0, PM1, false, s));
   for (int i = 0; i < P->q; ++i) {
     BCUR_TRY(gemm_tc_group_run(P->gZ, s));
+    BCUR_TRY(mark(P, s, "sketch_gemm"));
     BCUR_TRY(orth(P, PN0, PN1, false, s));
     BCUR_TRY(gemm_tc_group_run(P->gY2, s));
+    BCUR_TRY(mark(P, s, "sketch_gemm"));
     BCUR_TRY(orth(P, PM0, PM1, false, s));
   }
   BCUR_TRY(gemm_tc_group_run(P->gZ, s));
+  BCUR_TRY(mark(P, s, "sketch_gemm"));
   BCUR_TRY(orth(P, PN0, PN1, true, s));
   BCUR_TRY(jacobi_svd_batched<float>(P->Lb_all, LP, P->Ut_all, P->W_all, P->sig_all, P->jw_all,
                                      P->d_status, B, s));
+  BCUR_TRY(mark(P, s, "jacobi"));
   BCUR_TRY(scores(P->d_items, P->d_io, P->blocks.w(), P->blocks.total, P->d_status, s));
+  BCUR_TRY(mark(P, s, "scores"));
   // sampling (Alg. 1 step 2) and the gathers
   BCUR_TRY(sample(P->d_items, P->d_io, B, s));
+  BCUR_TRY(mark(P, s, "sample"));
   BCUR_TRY(gather(P->d_items, P->d_io, P->ctiles.w(), P->ctiles.total, P->rrows.w(),
                   P->rrows.total, s));
+  BCUR_TRY(mark(P, s, "gather"));
   // Cholesky-QR2 of C^T and R, both sides in each launch
   for (int pass = 0; pass < 2; ++pass) {
     BCUR_TRY(gemm_tc_group_run(P->gGram[pass], s));
+    BCUR_TRY(mark(P, s, "qr_gram"));
     BCUR_TRY(wide_chol(P->d_items, B, pass, s));
+    BCUR_TRY(mark(P, s, "wide_chol"));
     BCUR_TRY(gemm_tc_group_run(P->gApply[pass], s));
+    BCUR_TRY(mark(P, s, "qr_apply"));
   }
   // U = C^+ A R^+
   BCUR_TRY(gemm_tc_group_run(P->gW, s));
+  BCUR_TRY(mark(P, s, "w_gemm"));
   BCUR_TRY(gemm_tc_group_run(P->gM, s));
-  for (int i = 0; i < 4; ++i) BCUR_TRY(gemm_tc_group_run(P->gU[i], s));
+  BCUR_TRY(mark(P, s, "m_gemm"));
+  for (int i = 0; i < 4; ++i) {
+    BCUR_TRY(gemm_tc_group_run(P->gU[i], s));
+    BCUR_TRY(mark(P, s, "u_gemm"));
+  }
   BCUR_TRY(copy_u(P->d_items, P->d_io, P->urows.w(), P->urows.total, s));
+  BCUR_TRY(mark(P, s, "copy_u"));
   // ||A - CUR||_F
   BCUR_TRY(gemm_tc_group_run(P->gP, s));
+  BCUR_TRY(mark(P, s, "p_gemm"));
   BCUR_TRY(gemm_tc_group_run(P->gRes, s));
+  BCUR_TRY(mark(P, s, "residual"));
   BCUR_TRY(finish(P->d_items, P->d_io, B, s));
+  BCUR_TRY(mark(P, s, "finish"));
   return BCUR_OK;
 }
 
@@ -442,7 +491,10 @@ bcur_status_t bcur_batch_run(bcur_batch_t P, const bcur_batch_io_t* io, int32_t 
   BCUR_CUDA_TRY(cudaMemcpyAsync(P->d_io, P->h_io, (size_t)P->B * sizeof(bcur_batch_io_t),
                                 cudaMemcpyHostToDevice, s));
   BCUR_CUDA_TRY(cudaEventRecord(P->ev_io, s));
-  BCUR_TRY(enqueue(P, s));
+  P->marking = P->profile;
+  const bcur_status_t st0 = enqueue(P, s);
+  P->marking = false;
+  BCUR_TRY(st0);
   P->launches = (int64_t)(bcur_launch_count() - l0);
   if (use_graph && !P->exec) {
     // Capture the same sequence (on the plan's own stream) for later runs.
@@ -491,8 +543,26 @@ bcur_status_t bcur_batch_sync_status(bcur_batch_t P) {
   return (bcur_status_t)st;
 }
 
+bcur_status_t bcur_batch_profile(bcur_batch_t P, int32_t enable) {
+  if (!P) return BCUR_EINVAL;
+  P->profile = enable != 0;
+  return BCUR_OK;
+}
+
+int32_t bcur_batch_profile_count(bcur_batch_t P) { return P ? (P->pn > 0 ? P->pn - 1 : 0) : 0; }
+
+bcur_status_t bcur_batch_profile_entry(bcur_batch_t P, int32_t i, const char** label, double* ms) {
+  if (!P || i < 0 || i + 1 >= P->pn || !label || !ms) return BCUR_EINVAL;
+  float t = 0.f;
+  BCUR_CUDA_TRY(cudaEventElapsedTime(&t, P->pev[i], P->pev[i + 1]));
+  *label = P->plabel[i + 1];
+  *ms = (double)t;
+  return BCUR_OK;
+}
+
 void bcur_batch_destroy(bcur_batch_t P) {
   if (!P) return;
+  for (cudaEvent_t e : P->pev) cudaEventDestroy(e);
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->ev_io) cudaEventDestroy(P->ev_io);
