@@ -525,8 +525,9 @@ def main_reference(args):
 BATCH_COUNT = 512
 
 
-def batch_problems(rank: int):
-    return bi.batched_biometric(BATCH_COUNT, seed=3 + 1000 * rank)
+def batch_problems(rank: int, count: int = BATCH_COUNT):
+    """The first `count` matrices of the 512-matrix batch (all of it by default)."""
+    return bi.batched_biometric(BATCH_COUNT, seed=3 + 1000 * rank)[:count]
 
 
 def batch_item(p):
@@ -573,7 +574,7 @@ def main_batched(args):
 
         dist.init_process_group("nccl", device_id=dev)
     pkg.load()
-    probs = batch_problems(rank)
+    probs = batch_problems(rank, args.count)
     items = [batch_item(p) for p in probs]
     t_gen = time.perf_counter()
     As = [p.matrix_device(dev) for p in probs]
@@ -727,7 +728,8 @@ def main_batched(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16/bf16x3", "data": "synthetic",
-            "config": {"workload": "batched_biometric", "matrices": B,
+            "config": {"workload": "batched_biometric" if B == BATCH_COUNT
+                       else f"batched_biometric[:{B}]", "matrices": B,
                        "sum_mn": mn, "storage": "f32", "sketch_prec": "bf16", "fit_prec": "bf16x3",
                        "q": 2, "cuda_graph": graph,
                        "l2": f"inputs larger than L2 (A total {4 * mn / 1e9:.1f} GB)",
@@ -754,6 +756,8 @@ def main():
     ap.add_argument("--fit-prec", default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=BATCH_COUNT,
+                    help="batched workload: decompose only the first COUNT matrices (profiling)")
     ap.add_argument("--no-graph", action="store_true",
                     help="batched workload: launch eagerly instead of replaying a CUDA graph")
     args = ap.parse_args()

@@ -66,7 +66,7 @@ struct bcur_plan_s {
         partials, result, tc_scratch;
     // BF16 tensor-core path
     size_t A16h, A16l, Om16h, Om16l, Qm16h, Qm16l, Zn16h, Zn16l, XC16[4], XR16[4], Lh, Ll, Lih,
-        Lil, T1h, T1l, Pnh, Pnl, Wh, Wl, Mh, Ml, U1h, U1l, U2h, U2l, Ph, Pl;
+        Lil, T1h, T1l, Pnh, Pnl, Wh, Wl, Mh, Ml, U1h, U1l, U2h, U2l, Ph, Pl, refine;
     // per-lane temporaries of the second lane
     size_t Lh2, Ll2, Lih2, Lil2, T1h2, T1l2, Pnh2, Pnl2, maxdiag2, tc_scratch2;
   } o;
@@ -735,32 +735,41 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
 }
 
 // Stage 6 on tensor cores: P = Q_C^T M, then sum (A - P Q_R)^2 in the GEMM
-// epilogue.  The products use the fit's precision: with BF16 pairs the
-// reconstruction P Q_R keeps about 16 bits, so the error of ||A - CUR||_F^2
-// stays near 2^-16 ||CUR||_F^2 even when the residual is small; a single BF16
-// term would add about 2^-8 ||CUR||_F^2, which swamps small residuals.
+// epilogue.  First with one BF16 term; when the fit runs in BF16 pairs and
+// the one-term result is too coarse for the relative error it reports
+// (residual_needs_refine, decided on the device), P and the residual are
+// recomputed with BF16 pairs.  The second pair of launches is always
+// enqueued (the sequence stays capturable) and does nothing unless the flag
+// is set.
 bcur_status_t run_error16(bcur_plan_t P, const float* A, double* out) {
   const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
   const int64_t cw = P->c_pad, rw = P->r_pad;
   const int parts = parts_of(P->d.fit_prec);
-  const bool lo = parts == 3;
-  S16 QC = s16(P, P->o.XC16[0], P->o.XC16[1], lo);
-  S16 QR = s16(P, P->o.XR16[0], P->o.XR16[1], lo);
-  S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
-  S16 Pp = s16(P, P->o.Ph, P->o.Pl, lo);
-  GemmDesc g = mk16(m, rw, cw, QC, ldm, 1, M16, rw, 0, rw);
-  g.Dh = Pp.h;
-  g.Dl = Pp.l;
-  BCUR_TRY(g16(P, g, parts));
-  GemmDesc r = mk16(m, n, rw, Pp, rw, 0, QR, ldn, 0, 0);
-  r.X = A;
-  r.ldx = P->lda;
-  r.partials = P->at<double>(P->o.partials);
-  r.parts = parts;
-  r.status = P->at<int>(P->o.status);
-  int64_t np = 0;
-  BCUR_TRY(gemm_tc_resid(r, BCUR_BF16, P->stream, &np));
-  return finish_residual(P->at<double>(P->o.partials), np, out, 0, P->stream);
+  int* flag = P->at<int>(P->o.refine);
+  for (int pass = 0; pass < (parts == 3 ? 2 : 1); ++pass) {
+    const bool lo = pass == 1;
+    S16 QC = s16(P, P->o.XC16[0], P->o.XC16[1], lo);
+    S16 QR = s16(P, P->o.XR16[0], P->o.XR16[1], lo);
+    S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
+    S16 Pp = s16(P, P->o.Ph, P->o.Pl, lo);
+    GemmDesc g = mk16(m, rw, cw, QC, ldm, 1, M16, rw, 0, rw);
+    g.Dh = Pp.h;
+    g.Dl = Pp.l;
+    if (pass == 1) g.run_flag = flag;
+    BCUR_TRY(g16(P, g, lo ? 3 : 1));
+    GemmDesc r = mk16(m, n, rw, Pp, rw, 0, QR, ldn, 0, 0);
+    r.X = A;
+    r.ldx = P->lda;
+    r.partials = P->at<double>(P->o.partials);
+    r.parts = lo ? 3 : 1;
+    r.status = P->at<int>(P->o.status);
+    if (pass == 1) r.run_flag = flag;
+    int64_t np = 0;
+    BCUR_TRY(gemm_tc_resid(r, BCUR_BF16, P->stream, &np));
+    const int mode = parts == 3 ? (pass == 0 ? 2 : 3) : 0;
+    BCUR_TRY(finish_residual(P->at<double>(P->o.partials), np, out, mode, P->stream, flag));
+  }
+  return BCUR_OK;
 }
 
 
@@ -1011,6 +1020,7 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
       o.U2l = L.take(cw * rw * h2);
       o.Ph = L.take(P->m * rw * h2);
       o.Pl = L.take(P->m * rw * h2);
+      o.refine = L.take(sizeof(int));
       o.Lh2 = L.take(wm * wm * h2);
       o.Ll2 = L.take(wm * wm * h2);
       o.Lih2 = L.take(wm * wm * h2);

@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
   const int ch = blockIdx.x - chunks.prefix[b];
   const float* X = panel(I, sel);
   const int64_t h = panel_h(I, sel), ld = panel_ld(I, sel);
-  __shared__ float Xs[LP][65];
+  constexpr int TLD = LP + 4;         // XsT[c][r]: column c of the chunk, rows r
+  __shared__ __align__(16) float XsT[64 * TLD];
   const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
   float acc[4][4];
 #pragma unroll
@@ -127,17 +128,15 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
   for (int64_t c0 = c_begin; c0 < c_end; c0 += 64) {
     for (int e = tid; e < LP * 64; e += 256) {
       const int r = e / 64, c = e % 64;
-      Xs[r][c] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
+      XsT[c * TLD + r] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
     for (int c = 0; c < 64; ++c) {
-      float a[4], bb[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = Xs[4 * ti + q][c];
-        bb[q] = Xs[4 * tj + q][c];
-      }
+      const float4 a4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + 4 * ti]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + 4 * tj]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -179,12 +178,12 @@ __global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, 
   }
 }
 
-__global__ void __launch_bounds__(AP) sapply_kernel(const Item* items, Work chunks, int src, int dst,
+__global__ void __launch_bounds__(AP, 2) sapply_kernel(const Item* items, Work chunks, int src, int dst,
                                                     int write_bf16) {
   const int b = find_item(chunks, blockIdx.x);
   const Item& I = items[b];
   const int ch = blockIdx.x - chunks.prefix[b];
-  __shared__ float Ls[LP * LP];
+  __shared__ __align__(16) float Ls[LP * LP];
   for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Ls[e] = I.LinvT[e];
   __syncthreads();
   const int64_t h = panel_h(I, src), ld = panel_ld(I, src);
@@ -196,17 +195,24 @@ __global__ void __launch_bounds__(AP) sapply_kernel(const Item* items, Work chun
   float x[LP];
 #pragma unroll
   for (int t = 0; t < LP; ++t) x[t] = X[t * ld + j];
-  // rows in groups of 16; each output sums t = 0..r in increasing order
+  // rows in groups of 16; each output sums t = 0..r in increasing order,
+  // reading L^{-1} four entries at a time
 #pragma unroll
   for (int r0 = 0; r0 < LP; r0 += 16) {
     float acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.f;
 #pragma unroll
-    for (int t = 0; t < r0 + 16; ++t)
+    for (int t = 0; t < r0 + 16; t += 4)
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (t <= r0 + q) acc[q] = fmaf(Ls[(r0 + q) * LP + t], x[t], acc[q]);
+      for (int q = 0; q < 16; ++q) {
+        if (t > r0 + q) continue;
+        const float4 l4 = *reinterpret_cast<const float4*>(&Ls[(r0 + q) * LP + t]);
+        acc[q] = fmaf(l4.x, x[t], acc[q]);
+        if (t + 1 <= r0 + q) acc[q] = fmaf(l4.y, x[t + 1], acc[q]);
+        if (t + 2 <= r0 + q) acc[q] = fmaf(l4.z, x[t + 2], acc[q]);
+        if (t + 3 <= r0 + q) acc[q] = fmaf(l4.w, x[t + 3], acc[q]);
+      }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       Y[(r0 + q) * ld + j] = acc[q];
@@ -340,8 +346,14 @@ __global__ void __launch_bounds__(256) gather_r_kernel(const Item* items,
 // ---------------------------------------------------------------------------
 constexpr int WLD = NB + 4;   // leaf leading dimension (potrf_leaf<float, 64>)
 constexpr int PLD = NB + 1;
-constexpr size_t kWideSmem =
-    (size_t)(2 * NB * WLD + NB * PLD + (WMAX - NB) * PLD) * sizeof(float);
+// Shared memory: leaf L and L^{-1}, the transposed inverse (later reused for
+// the three tiles of the inverse phase), and the panel below the leaf, whose
+// height depends on the largest w of the launch.
+constexpr int kWideBase = 2 * NB * WLD + NB * PLD;
+static_assert(3 * NB * PLD <= kWideBase, "inverse tiles must fit in the leaf area");
+constexpr size_t wide_smem(int wmax) {
+  return (size_t)(kWideBase + (wmax - NB) * PLD) * sizeof(float);
+}
 
 __device__ __forceinline__ void tile_acc(const float* Arow, int lda, const float* Bcol, int ldb,
                                          int ti, int tj, float (&acc)[4][4]) {
@@ -361,14 +373,16 @@ __device__ __forceinline__ void tile_acc(const float* Arow, int lda, const float
   }
 }
 
-__global__ void __launch_bounds__(256, 1) wchol_kernel(const Item* items, int pass) {
+__global__ void __launch_bounds__(256) wchol_kernel(const Item* items, const int* entries,
+                                                    int pass) {
   extern __shared__ float sm[];
   float* S = sm;              // NB x WLD: leaf L
   float* X = S + NB * WLD;    // NB x WLD: leaf L^{-1}
   float* XT = X + NB * WLD;   // NB x PLD: XT[t][c] = X[c][t]
-  float* Ps = XT + NB * PLD;  // (WMAX - NB) x PLD panel / inverse tiles
-  const Item& I = items[blockIdx.x];
-  const int side = blockIdx.y;
+  float* Ps = XT + NB * PLD;  // (w - NB) x PLD panel
+  const int e0 = entries[blockIdx.x];
+  const Item& I = items[e0 >> 1];
+  const int side = e0 & 1;
   const int w = side ? I.rpad : I.cpad;
   float* G = side ? I.GR : I.GC;
   float* L = side ? I.LR[pass] : I.LC[pass];
@@ -465,10 +479,10 @@ __global__ void __launch_bounds__(256, 1) wchol_kernel(const Item* items, int pa
     }
     __syncthreads();
   }
-  // L^{-1}: off-diagonal blocks by block rows
-  float* TA = Ps;
-  float* TB = Ps + NB * PLD;
-  float* TT = Ps + 2 * NB * PLD;
+  // L^{-1}: off-diagonal blocks by block rows (tiles in the leaf area)
+  float* TA = sm;
+  float* TB = sm + NB * PLD;
+  float* TT = sm + 2 * NB * PLD;
   for (int Ib = 1; Ib < nbk; ++Ib) {
     for (int Jb = 0; Jb < Ib; ++Jb) {
       float acc[4][4];
@@ -538,11 +552,16 @@ __global__ void copy_u_kernel(const Item* items, const bcur_batch_io_t* io, Work
     U[(int64_t)r * I.rmax + c] = I.Uf[(int64_t)r * I.rpad + c];
 }
 
-// ||A - CUR||_F from the residual tiles' partial sums, fixed order.
-__global__ void __launch_bounds__(256) finish_kernel(const Item* items, const bcur_batch_io_t* io) {
+// ||A - CUR||_F from the residual tiles' partial sums, fixed order.  refine =
+// 0: from the one-term residual, and set the item's refinement flag
+// (residual_needs_refine); refine = 1: from the three-term residual, only for
+// items whose flag is set.
+__global__ void __launch_bounds__(256) finish_kernel(const Item* items, const bcur_batch_io_t* io,
+                                                     int refine) {
   const Item& I = items[blockIdx.x];
+  if (refine && *I.refine == 0) return;
   __shared__ double red[8];
-  const int64_t n = 4 * I.res_units;
+  const int64_t n = kResidSlots * I.res_units;
   double e2 = 0.0, x2 = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     e2 += I.partials[2 * i];
@@ -557,6 +576,7 @@ __global__ void __launch_bounds__(256) finish_kernel(const Item* items, const bc
     err[0] = fe;
     err[1] = fx > 0.0 ? fe / fx : 0.0;
     err[2] = fx;
+    if (!refine) *I.refine = residual_needs_refine(err[1]) ? 1 : 0;
   }
 }
 
@@ -619,14 +639,17 @@ bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, 
   return BCUR_OK;
 }
 
-bcur_status_t wide_chol(const Item* items, int B, int pass, cudaStream_t s) {
+bcur_status_t wide_chol(const Item* items, const int* entries, int count, int wmax, int pass,
+                        cudaStream_t s) {
+  if (count < 1) return BCUR_OK;
+  if (wmax < NB || wmax > WMAX) return BCUR_EINVAL;
   static bool attr = false;
   if (!attr) {
     BCUR_CUDA_TRY(cudaFuncSetAttribute(wchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kWideSmem));
+                                       (int)wide_smem(WMAX)));
     attr = true;
   }
-  wchol_kernel<<<dim3(B, 2), 256, kWideSmem, s>>>(items, pass);
+  wchol_kernel<<<count, 256, wide_smem(wmax), s>>>(items, entries, pass);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
@@ -638,8 +661,9 @@ bcur_status_t copy_u(const Item* items, const bcur_batch_io_t* io, Work urows, i
   return BCUR_OK;
 }
 
-bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s) {
-  finish_kernel<<<B, 256, 0, s>>>(items, io);
+bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, int refine,
+                     cudaStream_t s) {
+  finish_kernel<<<B, 256, 0, s>>>(items, io, refine);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }

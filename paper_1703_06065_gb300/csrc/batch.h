@@ -28,7 +28,7 @@ struct Item {
   int cpad, rpad;            // c and r padded to the leaf size
   int cmax, rmax;            // gc * s, gr * s: the U output is cmax x rmax
   int chunks_m, chunks_n;    // skinny-Gram chunks along m and n
-  int64_t res_units;         // residual tiles (8 partial doubles each)
+  int64_t res_units;         // residual tiles (2 kResidSlots partial doubles each)
   // sketch
   bf16 *Ah, *Al;             // A as BF16 pair, m x ldn
   bf16* Om;                  // Omega^T, LP x ldn
@@ -55,6 +55,7 @@ struct Item {
   bf16 *Ph, *Pl;             // P = Q_C^T M as a BF16 pair, m x rpad
   double* partials;          // 8 * res_units
   int* kept;                 // 4: C pass 0/1, R pass 0/1
+  int* refine;               // 1: recompute the residual with BF16 pairs
 };
 
 // Work list: prefix sums of per-item unit counts (count + 1 entries).
@@ -85,10 +86,14 @@ bcur_status_t scores(const Item* items, const bcur_batch_io_t* io, Work blocks, 
 bcur_status_t sample(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s);
 bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, int ctotal,
                      Work rrows, int rtotal, cudaStream_t s);
-bcur_status_t wide_chol(const Item* items, int B, int pass, cudaStream_t s);
+// entries: (item << 1 | side) of the decompositions in this launch, all with
+// w <= wmax (side 0: C^T with w = cpad, side 1: R with w = rpad).
+bcur_status_t wide_chol(const Item* items, const int* entries, int count, int wmax, int pass,
+                        cudaStream_t s);
 bcur_status_t copy_u(const Item* items, const bcur_batch_io_t* io, Work urows, int total,
                      cudaStream_t s);
-bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s);
+bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, int refine,
+                     cudaStream_t s);
 
 }  // namespace batch
 

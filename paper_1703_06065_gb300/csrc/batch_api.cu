@@ -44,8 +44,18 @@ struct bcur_batch_s {
   bcur_batch_io_t* h_io = nullptr;  // pinned staging of the io table
   cudaEvent_t ev_io = nullptr;
   WorkList rows8, chunks_m, chunks_n, apply_m, apply_n, blocks, ctiles, rrows, urows;
-  // grouped GEMMs
-  TcGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[4], gP, gRes;
+  // wide Cholesky launches by size class (w <= 128, 256, 512): the shared
+  // memory of a launch, and so the CTAs per SM, follows its largest w
+  int* wide_entries[3] = {nullptr, nullptr, nullptr};
+  int wide_count[3] = {0, 0, 0};
+  // grouped GEMMs; each stage is split by output width into up to three
+  // launches with 64-, 128- and 256-wide tiles
+  struct MGroup {
+    void* tab[3] = {nullptr, nullptr, nullptr};  // table memory per width slot
+    TcGroup g[3];                                // the prepared launches
+    int n = 0;
+  };
+  MGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[4], gP, gRes, gP3, gRes3;
   // graph mode: the sequence is captured on a stream of the plan's own and
   // joined to the caller's stream through events
   cudaStream_t gstream = nullptr;
@@ -106,14 +116,15 @@ size_t layout(bcur_batch_t P) {
   WorkList* wls[] = {&P->rows8, &P->chunks_m, &P->chunks_n, &P->apply_m, &P->apply_n,
                      &P->blocks, &P->ctiles, &P->rrows, &P->urows};
   for (WorkList* w : wls) w->d = bp.take<int>(B + 1);
-  auto grp = [&](TcGroup& g, int count) {
-    g.table = bp.take<char>(gemm_tc_group_bytes(count));
+  for (int i = 0; i < 3; ++i) P->wide_entries[i] = bp.take<int>(2 * B);
+  auto grp = [&](bcur_batch_s::MGroup& g, int count) {
+    for (int i = 0; i < 3; ++i) g.tab[i] = bp.take<char>(gemm_tc_group_bytes(count));
   };
   grp(P->gY, B); grp(P->gZ, B); grp(P->gY2, B);
   for (int i = 0; i < 2; ++i) { grp(P->gGram[i], 2 * B); grp(P->gApply[i], 2 * B); }
   grp(P->gW, B); grp(P->gM, B);
   for (int i = 0; i < 4; ++i) grp(P->gU[i], B);
-  grp(P->gP, B); grp(P->gRes, B);
+  grp(P->gP, B); grp(P->gRes, B); grp(P->gP3, B); grp(P->gRes3, B);
   for (int b = 0; b < B; ++b) {
     Item& I = P->it[b];
     const int64_t m = I.m, n = I.n, ldm = I.ldm, ldn = I.ldn;
@@ -166,8 +177,9 @@ size_t layout(bcur_batch_t P) {
     I.Uf = bp.take<float>(cp * rp);
     I.Ph = bp.take<bf16>(m * rp);
     I.Pl = bp.take<bf16>(m * rp);
-    I.partials = bp.take<double>(8 * I.res_units);
+    I.partials = bp.take<double>(2 * kResidSlots * I.res_units);
     I.kept = bp.take<int>(4);
+    I.refine = bp.take<int>(1);
     if (P->ws) {
       I.Lb = P->Lb_all + (size_t)b * LP * LP;
       I.Ut = P->Ut_all + (size_t)b * LP * LP;
@@ -196,16 +208,42 @@ GemmDesc g16(int64_t M, int64_t N, int64_t K, const void* A, const void* Alo, in
   return g;
 }
 
-bcur_status_t prep(bcur_batch_t P, TcGroup& g, std::vector<GemmDesc>& ds, int resid, int BN) {
-  for (auto& d : ds) d.status = P->d_status;
-  void* table = g.table;
-  return gemm_tc_group_prepare(ds.data(), (int)ds.size(), resid, BN, table,
-                               gemm_tc_group_bytes((int)ds.size()), P->d_status, &g);
+// Tile width for one GEMM: from its output width in MMA space (the kernel
+// stores D^T when M < 128 and N >= 2M).
+int pick_bn(const GemmDesc& d, int resid) {
+  const bool swap = !resid && d.M < 128 && d.N >= 2 * d.M;
+  const int64_t Nm = swap ? d.M : d.N;
+  return Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256);
+}
+
+bcur_status_t prep(bcur_batch_t P, bcur_batch_s::MGroup& g, std::vector<GemmDesc>& ds, int resid,
+                   int BN) {
+  const int widths[3] = {64, 128, 256};
+  g.n = 0;
+  for (int wi = 0; wi < 3; ++wi) {
+    std::vector<GemmDesc> part;
+    for (size_t i = 0; i < ds.size(); ++i) {
+      const int bn = BN ? BN : pick_bn(ds[i], resid);
+      if (bn != widths[wi]) continue;
+      part.push_back(ds[i]);
+      part.back().status = P->d_status;
+    }
+    if (part.empty()) continue;
+    BCUR_TRY(gemm_tc_group_prepare(part.data(), (int)part.size(), resid, widths[wi], g.tab[wi],
+                                   gemm_tc_group_bytes((int)ds.size()), P->d_status, &g.g[g.n]));
+    ++g.n;
+  }
+  return BCUR_OK;
+}
+
+bcur_status_t run_group(const bcur_batch_s::MGroup& g, cudaStream_t s) {
+  for (int i = 0; i < g.n; ++i) BCUR_TRY(gemm_tc_group_run(g.g[i], s));
+  return BCUR_OK;
 }
 
 bcur_status_t build_groups(bcur_batch_t P) {
   const int B = P->B;
-  std::vector<GemmDesc> y, z, y2, w, mm, u[4], pp, res;
+  std::vector<GemmDesc> y, z, y2, w, mm, u[4], pp, res, pp3, res3;
   std::vector<GemmDesc> gram[2], app[2];
   for (int b = 0; b < B; ++b) {
     const Item& I = P->it[b];
@@ -262,16 +300,27 @@ bcur_status_t build_groups(bcur_batch_t P) {
     d = g16(cp, rp, cp, I.LCih[0], I.LCil[0], cp, 1, I.U1h, I.U1l, rp, 0, rp, 3);
     d.D = I.Uf; d.triA = 2;
     u[3].push_back(d);
-    // P = Q_C^T M (m x r), then sum (A - P Q_R)^2, both with BF16 pairs
-    d = g16(m, rp, cp, I.XCh[0], I.XCl[0], ldm, 1, I.Mh, I.Ml, rp, 0, rp, 3);
+    // P = Q_C^T M (m x r), then sum (A - P Q_R)^2: one BF16 term, and the
+    // BF16-pair version for the items the first result flags
+    d = g16(m, rp, cp, I.XCh[0], nullptr, ldm, 1, I.Mh, nullptr, rp, 0, rp, 1);
     d.Dh = I.Ph;
-    d.Dl = I.Pl;
     pp.push_back(d);
-    d = g16(m, n, rp, I.Ph, I.Pl, rp, 0, I.XRh[0], I.XRl[0], ldn, 0, 0, 3);
+    d = g16(m, n, rp, I.Ph, nullptr, rp, 0, I.XRh[0], nullptr, ldn, 0, 0, 1);
     d.X = nullptr;  // set per run from the io table
     d.ldx = I.lda;
     d.partials = I.partials;
     res.push_back(d);
+    d = g16(m, rp, cp, I.XCh[0], I.XCl[0], ldm, 1, I.Mh, I.Ml, rp, 0, rp, 3);
+    d.Dh = I.Ph;
+    d.Dl = I.Pl;
+    d.run_flag = I.refine;
+    pp3.push_back(d);
+    d = g16(m, n, rp, I.Ph, I.Pl, rp, 0, I.XRh[0], I.XRl[0], ldn, 0, 0, 3);
+    d.X = nullptr;
+    d.ldx = I.lda;
+    d.partials = I.partials;
+    d.run_flag = I.refine;
+    res3.push_back(d);
   }
   BCUR_TRY(prep(P, P->gY, y, 0, 64));
   BCUR_TRY(prep(P, P->gZ, z, 0, 64));
@@ -285,6 +334,8 @@ bcur_status_t build_groups(bcur_batch_t P) {
   for (int i = 0; i < 4; ++i) BCUR_TRY(prep(P, P->gU[i], u[i], 0, 0));
   BCUR_TRY(prep(P, P->gP, pp, 0, 0));
   BCUR_TRY(prep(P, P->gRes, res, 1, 256));
+  BCUR_TRY(prep(P, P->gP3, pp3, 0, 0));
+  BCUR_TRY(prep(P, P->gRes3, res3, 1, 256));
   return BCUR_OK;
 }
 
@@ -327,23 +378,25 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   const int B = P->B;
   if (P->marking) P->pn = 0;
   BCUR_TRY(mark(P, s, "start"));
-  BCUR_TRY(gemm_tc_group_patch_x(P->gRes, P->d_io, sizeof(bcur_batch_io_t),
-                                 offsetof(bcur_batch_io_t, A), s));
+  for (const auto* g : {&P->gRes, &P->gRes3})
+    for (int i = 0; i < g->n; ++i)
+      BCUR_TRY(gemm_tc_group_patch_x(g->g[i], P->d_io, sizeof(bcur_batch_io_t),
+                                     offsetof(bcur_batch_io_t, A), s));
   BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->d_status, s));
   BCUR_TRY(mark(P, s, "split"));
   // scores: randomized range finder with q subspace iterations (Sec. 3.1)
-  BCUR_TRY(gemm_tc_group_run(P->gY, s));
+  BCUR_TRY(run_group(P->gY, s));
   BCUR_TRY(mark(P, s, "sketch_gemm"));
   BCUR_TRY(orth(P, PM0, PM1, false, s));
   for (int i = 0; i < P->q; ++i) {
-    BCUR_TRY(gemm_tc_group_run(P->gZ, s));
+    BCUR_TRY(run_group(P->gZ, s));
     BCUR_TRY(mark(P, s, "sketch_gemm"));
     BCUR_TRY(orth(P, PN0, PN1, false, s));
-    BCUR_TRY(gemm_tc_group_run(P->gY2, s));
+    BCUR_TRY(run_group(P->gY2, s));
     BCUR_TRY(mark(P, s, "sketch_gemm"));
     BCUR_TRY(orth(P, PM0, PM1, false, s));
   }
-  BCUR_TRY(gemm_tc_group_run(P->gZ, s));
+  BCUR_TRY(run_group(P->gZ, s));
   BCUR_TRY(mark(P, s, "sketch_gemm"));
   BCUR_TRY(orth(P, PN0, PN1, true, s));
   BCUR_TRY(jacobi_svd_batched<float>(P->Lb_all, LP, P->Ut_all, P->W_all, P->sig_all, P->jw_all,
@@ -359,30 +412,38 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   BCUR_TRY(mark(P, s, "gather"));
   // Cholesky-QR2 of C^T and R, both sides in each launch
   for (int pass = 0; pass < 2; ++pass) {
-    BCUR_TRY(gemm_tc_group_run(P->gGram[pass], s));
+    BCUR_TRY(run_group(P->gGram[pass], s));
     BCUR_TRY(mark(P, s, "qr_gram"));
-    BCUR_TRY(wide_chol(P->d_items, B, pass, s));
+    const int wmax[3] = {128, 256, 512};
+    for (int c = 0; c < 3; ++c)
+      BCUR_TRY(wide_chol(P->d_items, P->wide_entries[c], P->wide_count[c], wmax[c], pass, s));
     BCUR_TRY(mark(P, s, "wide_chol"));
-    BCUR_TRY(gemm_tc_group_run(P->gApply[pass], s));
+    BCUR_TRY(run_group(P->gApply[pass], s));
     BCUR_TRY(mark(P, s, "qr_apply"));
   }
   // U = C^+ A R^+
-  BCUR_TRY(gemm_tc_group_run(P->gW, s));
+  BCUR_TRY(run_group(P->gW, s));
   BCUR_TRY(mark(P, s, "w_gemm"));
-  BCUR_TRY(gemm_tc_group_run(P->gM, s));
+  BCUR_TRY(run_group(P->gM, s));
   BCUR_TRY(mark(P, s, "m_gemm"));
   for (int i = 0; i < 4; ++i) {
-    BCUR_TRY(gemm_tc_group_run(P->gU[i], s));
+    BCUR_TRY(run_group(P->gU[i], s));
     BCUR_TRY(mark(P, s, "u_gemm"));
   }
   BCUR_TRY(copy_u(P->d_items, P->d_io, P->urows.w(), P->urows.total, s));
   BCUR_TRY(mark(P, s, "copy_u"));
   // ||A - CUR||_F
-  BCUR_TRY(gemm_tc_group_run(P->gP, s));
+  BCUR_TRY(run_group(P->gP, s));
   BCUR_TRY(mark(P, s, "p_gemm"));
-  BCUR_TRY(gemm_tc_group_run(P->gRes, s));
+  BCUR_TRY(run_group(P->gRes, s));
   BCUR_TRY(mark(P, s, "residual"));
-  BCUR_TRY(finish(P->d_items, P->d_io, B, s));
+  BCUR_TRY(finish(P->d_items, P->d_io, B, 0, s));
+  BCUR_TRY(mark(P, s, "finish"));
+  BCUR_TRY(run_group(P->gP3, s));
+  BCUR_TRY(mark(P, s, "p_gemm"));
+  BCUR_TRY(run_group(P->gRes3, s));
+  BCUR_TRY(mark(P, s, "residual"));
+  BCUR_TRY(finish(P->d_items, P->d_io, B, 1, s));
   BCUR_TRY(mark(P, s, "finish"));
   return BCUR_OK;
 }
@@ -452,6 +513,20 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
                      &P->blocks, &P->ctiles, &P->rrows, &P->urows};
   for (WorkList* w : wls)
     BCUR_CUDA_TRY(cudaMemcpy(w->d, w->h.data(), w->h.size() * sizeof(int), cudaMemcpyHostToDevice));
+  {
+    std::vector<int> cls[3];
+    for (int b = 0; b < B; ++b)
+      for (int side = 0; side < 2; ++side) {
+        const int w = side ? P->it[b].rpad : P->it[b].cpad;
+        cls[w <= 128 ? 0 : (w <= 256 ? 1 : 2)].push_back(b << 1 | side);
+      }
+    for (int c = 0; c < 3; ++c) {
+      P->wide_count[c] = (int)cls[c].size();
+      if (!cls[c].empty())
+        BCUR_CUDA_TRY(cudaMemcpy(P->wide_entries[c], cls[c].data(), cls[c].size() * sizeof(int),
+                                 cudaMemcpyHostToDevice));
+    }
+  }
   BCUR_CUDA_TRY(cudaMemcpy(P->d_items, P->it.data(), (size_t)B * sizeof(Item),
                            cudaMemcpyHostToDevice));
   BCUR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));

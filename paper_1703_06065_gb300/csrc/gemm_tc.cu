@@ -46,7 +46,11 @@ namespace bcur {
 namespace tc {
 
 constexpr int BM = 128;
-constexpr int kThreads = 192;
+// Epilogue warps: 4 (one per TMEM lane quarter) for the store variants; 8
+// for the residual, whose epilogue streams X from HBM and needs the extra
+// loads in flight (two warps per lane quarter, each on half the columns).
+template <int EPI> __host__ __device__ constexpr int epi_warps() { return EPI == 2 ? 8 : 4; }
+template <int EPI> __host__ __device__ constexpr int threads_of() { return 64 + 32 * epi_warps<EPI>(); }
 constexpr int kStageABytes = BM * 128;  // 128 rows (or MN elements) x 128 bytes of K
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -73,6 +77,7 @@ struct Params {
   int64_t ldx;
   double* partials;      // per-CTA {sum (X - acc)^2, sum X^2}
   int* status;
+  const int* run_flag;   // when non-null and 0 at launch: nothing to do
 };
 
 template <int KIND> struct KindCfg;
@@ -273,45 +278,61 @@ __device__ __forceinline__ Unit decode_unit(const Params& p, int uu) {
   w.skip = 0;
   if (p.tri_out == 1 && w.m0 + BM - 1 < w.n0) w.skip = 1;
   if (p.tri_out == 2 && w.n0 + BN - 1 < w.m0) w.skip = 1;
+  if (p.run_flag && *p.run_flag == 0) w.skip = 1;
   return w;
 }
+
+// The GEMM a thread looked up last and its unit range: consecutive units of
+// a CTA's walk usually belong to the same GEMM, so the search (a chain of
+// dependent global loads) is only repeated when the walk leaves the range.
+struct LocCache {
+  int entry = -1, begin = 0, end = 0;
+};
 
 // Unit u of this CTA's walk -> the GEMM that owns it (its parameters and
 // tensor maps) and the decoded tile.
 template <int BN, int KIND, bool GROUPED>
 __device__ __forceinline__ Unit locate(const Maps& maps, const Params& p, const Group& grp, int u,
-                                       int total, const Params*& P, const Maps*& M) {
+                                       int total, const Params*& P, const Maps*& M,
+                                       LocCache& lc) {
   const int uu = snake(u, total);
   if constexpr (!GROUPED) {
     P = &p;
     M = &maps;
     return decode_unit<BN, KIND>(p, uu);
   } else {
-    int lo = 0, hi = grp.count - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (grp.starts[mid] <= uu) lo = mid; else hi = mid - 1;
+    if (uu < lc.begin || uu >= lc.end) {
+      int lo = 0, hi = grp.count - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (grp.starts[mid] <= uu) lo = mid; else hi = mid - 1;
+      }
+      lc.entry = lo;
+      lc.begin = grp.starts[lo];
+      lc.end = grp.starts[lo + 1];
     }
-    P = &grp.e[lo].p;
-    M = &grp.e[lo].maps;
-    return decode_unit<BN, KIND>(*P, uu - grp.starts[lo]);
+    P = &grp.e[lc.entry].p;
+    M = &grp.e[lc.entry].maps;
+    return decode_unit<BN, KIND>(*P, uu - lc.begin);
   }
 }
 
-template <int BN> struct StageCfg {
+template <int BN, int EPI> struct StageCfg {
   static constexpr int kStageBBytes = BN * 128;
   static constexpr int kStageBytes = kStageABytes + kStageBBytes;
-  static constexpr int kStages = 196608 / kStageBytes;  // 192 KB of stages
+  // 192 KB of stages; the residual keeps 160 KB and gives the rest to its
+  // eight per-warp 32 x 36 transpose tiles
+  static constexpr int kStages = (EPI == 2 ? 163840 : 196608) / kStageBytes;
   static constexpr int kTmemCols = 2 * BN;
-  static constexpr int kStageOut = 4 * 32 * 33 * 4;  // per-warp 32 x 33 FP32 transpose tiles
-  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kStageOut;
+  static constexpr int kStageOut = EPI == 2 ? 8 * 32 * 36 * 4 : 4 * 32 * 33 * 4;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 512 + kStageOut;
 };
 
 template <int BN, int KIND, int EPI, bool GROUPED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of<EPI>(), 1)
     tc_gemm_kernel(const __grid_constant__ Maps maps, const __grid_constant__ Params p,
                    const Group grp) {
-  using SC = StageCfg<BN>;
+  using SC = StageCfg<BN, EPI>;
   using KC = KindCfg<KIND>;
   constexpr int S = SC::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -324,9 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  double* red = reinterpret_cast<double*>(tmem_slot + 4);  // 8 doubles
-  float* stage_out = reinterpret_cast<float*>(smem + S * SC::kStageBytes + 256);
+  double* red = reinterpret_cast<double*>(tmem_slot + 4);  // 2 per epilogue warp
+  float* stage_out = reinterpret_cast<float*>(smem + S * SC::kStageBytes + 512);
+  constexpr int EW = epi_warps<EPI>();
   int* const status = GROUPED ? grp.status : p.status;
+  if constexpr (!GROUPED) {
+    if (p.run_flag && *p.run_flag == 0) return;  // uniform: the whole CTA leaves
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -336,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], EW);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -369,10 +394,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0;
       bool ok = true;
       const Maps* last = nullptr;
+      LocCache lcache;
       for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
         const Params* P;
         const Maps* M;
-        const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M);
+        const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M, lcache);
         if (w.skip || w.klo >= w.khi) continue;
         if constexpr (GROUPED) {
           if (M != last) {  // maps written by the host into global memory
@@ -430,10 +456,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t it = 0, tu = 0;
       bool ok = true;
+      LocCache lcache;
       for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
         const Params* P;
         const Maps* M;
-        const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M);
+        const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M, lcache);
         if (w.skip || w.klo >= w.khi) continue;
         const int parts = P->parts, a_mn = P->a_mn, b_mn = P->b_mn;
         const uint32_t id = idesc(KIND, a_mn, b_mn, BM, BN);
@@ -468,16 +495,161 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (!mbar_try_wait(done, 0) && now_ns() - t0 < kWaitNs) {
       }
     }
-  } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+  } else if constexpr (EPI == EPI_RESID) {
+    // ---------------- residual epilogue (warps 2..9) ----------------
+    // sum (X - alpha acc)^2 and sum X^2.  X is read coalesced: a lane loads
+    // four consecutive floats, eight lanes one 128-byte row piece, a warp four
+    // rows per instruction.  The accumulator chunk (lane = row in TMEM) is
+    // brought into the same layout through a per-warp 32 x 36 shared tile.
+    // The X loads of two chunks are issued before their accumulators are read.
+    const int ew = warp - 2;
     const int quarter = warp & 3;  // TMEM lanes [32*quarter, 32*quarter + 32)
+    constexpr int CW = BN / (EW / 4);  // columns per warp
+    const int cbeg = (ew / 4) * CW;
+    float* tile = stage_out + ew * (32 * 36);
+    const int lr = lane >> 3, lc = (lane & 7) * 4;  // first row, column of this lane
     double e2 = 0.0, x2 = 0.0;
     uint32_t tu = 0;
     bool ok = true;
+    LocCache lcache;
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
       const Params* P;
       const Maps* M;
-      const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M);
+      const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M, lcache);
+      if (w.skip) continue;
+      const bool has_acc = w.klo < w.khi;
+      const uint32_t acc = tu & 1, use = tu >> 1;
+      if (has_acc) {
+        if (!mbar_wait(&tfull[acc], use & 1, status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+      }
+      const int Mm = P->Mm, Nm = P->Nm;
+      const float alpha = P->alpha;
+      const int64_t ldx = P->ldx;
+      const int rbase = w.m0 + quarter * 32;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(P->X) & 15) == 0) && (ldx % 4 == 0);
+      // rows rbase + lr + 4 i (i < 8), columns col0 + lc .. + 3
+      auto load_x = [&](float4 (&xv)[8], int col0) {
+        const int col = col0 + lc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int row = rbase + lr + 4 * i;
+          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < Mm) {
+            const float* xr = P->X + (int64_t)row * ldx + col;
+            // read once: stream past L1 so the GEMM table and parameters stay cached
+            if (vec_ok && col + 4 <= Nm) {
+              q = __ldcs(reinterpret_cast<const float4*>(xr));
+            } else {
+              if (col < Nm) q.x = __ldcs(xr);
+              if (col + 1 < Nm) q.y = __ldcs(xr + 1);
+              if (col + 2 < Nm) q.z = __ldcs(xr + 2);
+              if (col + 3 < Nm) q.w = __ldcs(xr + 3);
+            }
+          }
+          xv[i] = q;
+        }
+      };
+      // accumulator chunk [c, c+32) of this warp's rows, in the X layout
+      auto read_acc = [&](float4 (&av)[8], int c) {
+        float v[32];
+        __syncwarp();  // tcgen05.ld is warp-aligned: reconverge before it
+        if (has_acc) {
+          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN + c, v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(&tile[lane * 36 + 4 * q]) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          av[i] = *reinterpret_cast<const float4*>(&tile[(lr + 4 * i) * 36 + lc]);
+        __syncwarp();
+      };
+      auto reduce = [&](const float4 (&xv)[8], const float4 (&av)[8], int col0) {
+        const int col = col0 + lc;
+        float se = 0.f, sx = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int row = rbase + lr + 4 * i;
+          const bool rok = row < Mm;
+          const float xs[4] = {xv[i].x, xv[i].y, xv[i].z, xv[i].w};
+          const float as[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float d = xs[j] - ((rok && col + j < Nm) ? alpha * as[j] : 0.f);
+            se = fmaf(d, d, se);
+            sx = fmaf(xs[j], xs[j], sx);
+          }
+        }
+        e2 += (double)se;
+        x2 += (double)sx;
+      };
+#pragma unroll 1
+      for (int c = cbeg; c < cbeg + CW; c += 64) {
+        float4 xa[8], aa[8];
+        if constexpr (CW >= 64) {
+          float4 xb[8];
+          load_x(xa, w.n0 + c);
+          load_x(xb, w.n0 + c + 32);
+          read_acc(aa, c);
+          reduce(xa, aa, w.n0 + c);
+          read_acc(aa, c + 32);
+          reduce(xb, aa, w.n0 + c + 32);
+        } else {
+          load_x(xa, w.n0 + c);
+          read_acc(aa, c);
+          reduce(xa, aa, w.n0 + c);
+        }
+      }
+      if (has_acc) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        ++tu;
+      }
+      if constexpr (GROUPED) {
+        // One partial pair per (tile, epilogue warp): the owning GEMM's sums
+        // do not depend on which CTA ran the tile or what else was in the
+        // launch.
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+          x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+        }
+        if (lane == 0) {
+          P->partials[2 * (kResidSlots * (int64_t)w.uu + ew)] = e2;
+          P->partials[2 * (kResidSlots * (int64_t)w.uu + ew) + 1] = x2;
+        }
+        e2 = 0.0;
+        x2 = 0.0;
+      }
+    }
+    if constexpr (!GROUPED) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+      }
+      if (lane == 0) {
+        red[2 * ew] = e2;
+        red[2 * ew + 1] = x2;
+      }
+    }
+  } else {
+    // ---------------- store epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;  // TMEM lanes [32*quarter, 32*quarter + 32)
+    uint32_t tu = 0;
+    bool ok = true;
+    LocCache lcache;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      const Params* P;
+      const Maps* M;
+      const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M, lcache);
       if (w.skip) continue;
       const bool has_acc = w.klo < w.khi;
       const uint32_t acc = tu & 1, use = tu >> 1;
@@ -573,29 +745,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (col >= Nm) break;
             prow[col] = v[i];
           }
-        } else {  // EPI_RESID: each lane reads its own row piece of X
-          if (!row_ok) continue;
-          const float* xr = P->X + (int64_t)row * P->ldx + col0;
-          float xv[32];
-          if (col0 + 32 <= Nm && ((reinterpret_cast<uintptr_t>(xr) & 15) == 0)) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float4 q = reinterpret_cast<const float4*>(xr)[i];
-              xv[4 * i] = q.x; xv[4 * i + 1] = q.y; xv[4 * i + 2] = q.z; xv[4 * i + 3] = q.w;
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) xv[i] = (col0 + i < Nm) ? xr[i] : 0.f;
-          }
-          float se = 0.f, sx = 0.f;
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float d = xv[i] - ((col0 + i < Nm) ? alpha * v[i] : 0.f);
-            se = fmaf(d, d, se);
-            sx = fmaf(xv[i], xv[i], sx);
-          }
-          e2 += (double)se;
-          x2 += (double)sx;
         }
       }
       if (has_acc) {
@@ -604,32 +753,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&tempty[acc]);
         ++tu;
       }
-      if constexpr (GROUPED && EPI == EPI_RESID) {
-        // One partial pair per (tile, quarter): the owning GEMM's sums do not
-        // depend on which CTA ran the tile or what else was in the launch.
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-          x2 += __shfl_xor_sync(0xffffffffu, x2, o);
-        }
-        if (lane == 0) {
-          P->partials[2 * (4 * (int64_t)w.uu + quarter)] = e2;
-          P->partials[2 * (4 * (int64_t)w.uu + quarter) + 1] = x2;
-        }
-        e2 = 0.0;
-        x2 = 0.0;
-      }
-    }
-    if constexpr (EPI == EPI_RESID && !GROUPED) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-        x2 += __shfl_xor_sync(0xffffffffu, x2, o);
-      }
-      if (lane == 0) {
-        red[2 * (warp - 2)] = e2;
-        red[2 * (warp - 2) + 1] = x2;
-      }
     }
   }
   tc_fence_before();
@@ -637,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (EPI == EPI_RESID && !GROUPED) {
     if (threadIdx.x == 0) {
       double se = 0.0, sx = 0.0;
-      for (int i = 0; i < 4; ++i) { se += red[2 * i]; sx += red[2 * i + 1]; }
+      for (int i = 0; i < EW; ++i) { se += red[2 * i]; sx += red[2 * i + 1]; }
       p.partials[2 * blockIdx.x] = se;
       p.partials[2 * blockIdx.x + 1] = sx;
     }
@@ -652,6 +775,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Sum the split-K slices in a fixed order and apply alpha / beta / layout.
 __global__ void splitk_reduce_kernel(Params p) {
+  if (p.run_flag && *p.run_flag == 0) return;
   const int64_t total = (int64_t)p.Mm * p.Nm;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -767,7 +891,7 @@ bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn, in
 template <int BN, int KIND, int EPI, bool GROUPED>
 bcur_status_t launch_inst(const Maps& maps, const Params& p, const Group& grp, int grid,
                           cudaStream_t s) {
-  using SC = StageCfg<BN>;
+  using SC = StageCfg<BN, EPI>;
   static bool attr = false;
   if (!attr) {
     BCUR_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, KIND, EPI, GROUPED>,
@@ -775,7 +899,8 @@ bcur_status_t launch_inst(const Maps& maps, const Params& p, const Group& grp, i
                                        SC::kSmemBytes));
     attr = true;
   }
-  tc_gemm_kernel<BN, KIND, EPI, GROUPED><<<grid, kThreads, SC::kSmemBytes, s>>>(maps, p, grp);
+  tc_gemm_kernel<BN, KIND, EPI, GROUPED><<<grid, threads_of<EPI>(), SC::kSmemBytes, s>>>(maps, p,
+                                                                                     grp);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
@@ -864,6 +989,7 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
   p.D = (float*)d.D; p.ldd = d.ldd; p.transD = swap ? 1 : 0;
   p.X = (const float*)d.X; p.ldx = d.ldx; p.partials = d.partials;
   p.status = d.status;
+  p.run_flag = d.run_flag;
   p.ksplit = 1;
   out->BN = BN;
   out->kind = kind;

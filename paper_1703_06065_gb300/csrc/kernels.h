@@ -46,6 +46,9 @@ struct GemmDesc {
   const void* B_lo = nullptr;
   void* Dh = nullptr;
   void* Dl = nullptr;
+  // Optional device flag: when it reads 0 at launch the GEMM does nothing
+  // (tensor-core path; in a grouped launch per GEMM).
+  const int* run_flag = nullptr;
 };
 
 template <typename T> bcur_status_t gemm_simt(const GemmDesc& d, cudaStream_t s);
@@ -65,9 +68,11 @@ bool gemm_tc_available();
 // prefix sums) is encoded on the host and copied to `dev` once
 // (synchronously); running it is one launch.  BN = 0 picks the tile width
 // with the least padded work.  resid = 1: every GEMM reduces
-// sum (X - A_op B_op)^2 and sum X^2 per (tile, 32-row quarter) into
-// d.partials[8 * tile + 2 * quarter + {0, 1}], tiles numbered as
+// sum (X - A_op B_op)^2 and sum X^2 per (tile, epilogue warp) into
+// d.partials[2 * (kResidSlots * tile + warp) + {0, 1}], tiles numbered as
 // gemm_tc_units counts them (the launch order does not change the sums).
+// Slots of residual partial pairs per tile (one per epilogue warp).
+constexpr int kResidSlots = 8;
 struct TcGroup {
   int BN = 0, epi = 0, count = 0, total = 0, grid = 0;
   void* table = nullptr;
@@ -148,9 +153,11 @@ bcur_status_t gather_rows(const T* A, int64_t lda, int64_t n, const int64_t* map
                           T* R, int64_t ldr, cudaStream_t s);
 
 // Fixed-order FP64 reduction of residual partials: out = {sqrt(e2), sqrt(e2)/sqrt(x2), sqrt(x2)}
-// (mode 0) or {e2, x2} (mode 1).
+// (mode 0) or {e2, x2} (mode 1).  Mode 2: as mode 0 from a one-term BF16
+// residual, and *flag = whether that residual is too coarse (see
+// residual_needs_refine); mode 3: as mode 0, written only when *flag != 0.
 bcur_status_t finish_residual(const double* partials, int64_t n, double* out, int mode,
-                              cudaStream_t s);
+                              cudaStream_t s, int* flag = nullptr);
 
 template <typename Tin, typename Tout>
 bcur_status_t convert(const Tin* in, Tout* out, int64_t count, cudaStream_t s);

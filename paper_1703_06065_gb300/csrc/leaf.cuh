@@ -8,6 +8,21 @@
 namespace bcur {
 
 // ---------------------------------------------------------------------------
+// Precision of the fused residual.  With P = Q_C^T M and Q_R rounded to BF16
+// (unit round-off u = 2^-8) the reconstruction error dCUR adds about
+// (2/3) u^2 ||CUR||_F^2 to ||A - CUR||_F^2 (the cross term with A - CUR is
+// orthogonal to it up to rounding), so the relative error e moves by about
+// u^2 (1 - e^2) / (3 e).  A one-term residual is kept while the bound
+// u^2 / (2 e) stays below 2.5e-4 (a quarter of the 1e-3 accuracy target);
+// otherwise the residual is recomputed with BF16 pairs (three terms, about
+// 2^-16 relative).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool residual_needs_refine(double rel_err) {
+  const double u = 0.00390625;  // 2^-8
+  return !(rel_err > 0.0) || (u * u / (2.0 * rel_err) > 2.5e-4);
+}
+
+// ---------------------------------------------------------------------------
 // Small FP64 Cholesky with the drop rule, and its inverse (w <= 128).
 // S: shared memory of w * (w + 1) doubles.  G (w x w, ld w): only the lower
 // part is read.  A pivot d with d <= tol_rel * max_i G_ii (or d <= 0) drops
@@ -164,6 +179,147 @@ __device__ int potrf_leaf(const T* G, int64_t ldg, T* S, T* X, T tol) {
     }
     __syncthreads();
   }
+  return s_kept;
+}
+
+// ---------------------------------------------------------------------------
+// One warp: Cholesky with the drop rule and the inverse of a 32 x 32 block
+// (lower part of A, ld lda; may alias Lo).  Lane i holds row i of the block
+// in registers; column j is finished when lane j's updated diagonal is
+// broadcast, and the rank-1 update of the trailing rows takes the column
+// entries l_kj from lane k by shuffle.  The inverse is formed column per
+// lane: X[r][c] = (delta_rc - sum_{c <= k < r} L[r][k] X[k][c]) / L[r][r].
+// Writes L (Lo, ld ldo) and L^{-1} (Xo, ld ldx) with zeros above the
+// diagonal; a dropped pivot zeroes its column of L and its row of L^{-1}.
+// Returns the number of kept pivots (same in every lane).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ int warp_chol32(const T* A, int lda, T* Lo, int ldo, T* Xo, int ldx, T tol) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  T a[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) a[k] = (k <= lane) ? A[lane * lda + k] : T(0);
+  int kept = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const T d = __shfl_sync(FULL, a[j], j);
+    const T p = (d > tol && d > T(0)) ? sqrt(d) : T(0);
+    const T inv = (p > T(0)) ? T(1) / p : T(0);
+    kept += (p > T(0)) ? 1 : 0;
+    if (lane == j) a[j] = p;
+    else if (lane > j) a[j] *= inv;
+#pragma unroll
+    for (int k = j + 1; k < 32; ++k) {
+      const T lkj = __shfl_sync(FULL, a[j], k);
+      if (lane >= k) a[k] = fma(-a[j], lkj, a[k]);
+    }
+  }
+  T x[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    T acc = (r == lane) ? T(1) : T(0);
+#pragma unroll
+    for (int k = 0; k < r; ++k) {
+      const T lrk = __shfl_sync(FULL, a[k], r);
+      acc = fma(-lrk, x[k], acc);  // x[k] = 0 for k < lane
+    }
+    const T lrr = __shfl_sync(FULL, a[r], r);
+    x[r] = (r >= lane && lrr > T(0)) ? acc / lrr : T(0);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 32; ++k) Lo[lane * ldo + k] = (k <= lane) ? a[k] : T(0);
+#pragma unroll
+  for (int r = 0; r < 32; ++r) Xo[r * ldx + lane] = x[r];
+  __syncwarp();
+  return kept;
+}
+
+// The 64 x 64 leaf in FP32 from two warp-level 32 x 32 factorisations:
+//   L11 = chol(G11), X11 = L11^{-1};  L21 = G21 X11^T;
+//   L22 = chol(G22 - L21 L21^T), X22 = L22^{-1};  X21 = -X22 (L21 X11).
+// Same contract as the generic potrf_leaf (S = L, X = L^{-1}, LD = 68,
+// threads 0..255 work).  A dropped pivot of L11 zeroes its column of L21, so
+// the update of G22 is unaffected by it, as in the unblocked order.
+template <>
+__device__ inline int potrf_leaf<float, 64>(const float* G, int64_t ldg, float* S, float* X,
+                                            float tol) {
+  constexpr int NB = 64, LD = 68, H = 32;
+  const int tid = threadIdx.x;
+  const bool act = tid < 256;
+  const int warp = tid >> 5;
+  __shared__ int s_kept;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, c = e % NB;
+    S[i * LD + c] = (c <= i) ? G[(int64_t)i * ldg + c] : 0.f;
+    X[i * LD + c] = 0.f;
+  }
+  __syncthreads();
+  int k1 = 0;
+  if (warp == 0) k1 = warp_chol32<float>(S, LD, S, LD, X, LD, tol);
+  __syncthreads();
+  // L21 = G21 X11^T: 4 outputs per thread (row i, columns c4..c4+3)
+  const int i = (tid >> 3) & 31, c4 = (tid & 7) * 4;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c4 + q;
+      for (int t = 0; t <= c; ++t) acc[q] = fmaf(S[(H + i) * LD + t], X[c * LD + t], acc[q]);
+    }
+  }
+  __syncthreads();
+  if (act)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) S[(H + i) * LD + c4 + q] = acc[q];
+  __syncthreads();
+  // G22 -= L21 L21^T (lower part)
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = c4 + q;
+      if (j > i) continue;
+      float s2 = 0.f;
+      for (int t = 0; t < H; ++t) s2 = fmaf(S[(H + i) * LD + t], S[(H + j) * LD + t], s2);
+      S[(H + i) * LD + H + j] -= s2;
+    }
+  }
+  __syncthreads();
+  int k2 = 0;
+  if (warp == 0) k2 = warp_chol32<float>(S + H * LD + H, LD, S + H * LD + H, LD, X + H * LD + H, LD, tol);
+  if (tid == 0) s_kept = k1 + k2;
+  __syncthreads();
+  // T = L21 X11 (X11 lower: t >= c), kept in X21's place for now
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c4 + q;
+      float t2 = 0.f;
+      for (int t = c; t < H; ++t) t2 = fmaf(S[(H + i) * LD + t], X[t * LD + c], t2);
+      acc[q] = t2;
+    }
+  }
+  __syncthreads();
+  if (act)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[(H + i) * LD + c4 + q] = acc[q];
+  __syncthreads();
+  // X21 = -X22 T (X22 lower: t <= i)
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c4 + q;
+      float t2 = 0.f;
+      for (int t = 0; t <= i; ++t) t2 = fmaf(X[(H + i) * LD + H + t], X[(H + t) * LD + c], t2);
+      acc[q] = -t2;
+    }
+  }
+  __syncthreads();
+  if (act)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[(H + i) * LD + c4 + q] = acc[q];
+  __syncthreads();
   return s_kept;
 }
 

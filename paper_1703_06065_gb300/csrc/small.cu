@@ -47,7 +47,9 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void finish_residual_kernel(const double* partials, int64_t n, double* out, int mode) {
+__global__ void finish_residual_kernel(const double* partials, int64_t n, double* out, int mode,
+                                       int* flag) {
+  if (mode == 3 && *flag == 0) return;
   double e2 = 0.0, x2 = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     e2 += partials[2 * i];
@@ -62,11 +64,12 @@ __global__ void finish_residual_kernel(const double* partials, int64_t n, double
   if (threadIdx.x == 0) {
     double se = 0.0, sx = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { se += r[0][i]; sx += r[1][i]; }
-    if (mode == 0) {
+    if (mode != 1) {
       const double e = sqrt(se), a = sqrt(sx);
       out[0] = e;
       out[1] = a > 0.0 ? e / a : 0.0;
       out[2] = a;
+      if (mode == 2) *flag = residual_needs_refine(out[1]) ? 1 : 0;
     } else {
       out[0] = se;
       out[1] = sx;
@@ -75,8 +78,9 @@ __global__ void finish_residual_kernel(const double* partials, int64_t n, double
 }
 
 bcur_status_t finish_residual(const double* partials, int64_t n, double* out, int mode,
-                              cudaStream_t s) {
-  finish_residual_kernel<<<1, 1024, 0, s>>>(partials, n, out, mode);
+                              cudaStream_t s, int* flag) {
+  if (mode >= 2 && !flag) return BCUR_EINVAL;
+  finish_residual_kernel<<<1, 1024, 0, s>>>(partials, n, out, mode, flag);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }

@@ -179,3 +179,29 @@ def test_haar_tensor_core_paths(sp, fp, score_tol):
     cur_orc = ref["C"] @ ref["U"] @ ref["R"]
     A = p.matrix().astype(np.float64)
     assert np.linalg.norm(cur_gpu - cur_orc) <= 1e-3 * np.linalg.norm(A)
+
+
+def test_residual_refines_when_the_error_is_small():
+    """Exactly rank-8 data: the true relative error is at the FP32 storage
+    level, far below what one BF16 term resolves (about 3e-3 here).  The plan
+    must detect that on the device and recompute the residual with BF16
+    pairs, keeping the error within the 1e-3 target of the oracle's."""
+    p = bi.Problem("rank8_exact", 1024, 1536, k=8, p=8, q=2, col_off=bi.uniform_blocks(1536, 64),
+                   row_off=bi.uniform_blocks(1024, 64), g_col=3, g_row=3, seed=21, storage="f32",
+                   recipe=dict(kind="small_lowrank", rank=8, noise=0.0))
+    ref, gpu, plan = run_problem(p, "bf16", "bf16x3")
+    assert ref["rel"] < 1e-5
+    assert abs(gpu["err"][1] - ref["rel"]) <= 1e-3
+    assert gpu["err"][1] < 5e-4, gpu["err"]  # one BF16 term would give about 3e-3
+
+
+def test_residual_one_term_when_the_error_is_large():
+    """Large relative error: one BF16 term is kept, and its deviation from
+    the oracle follows the rounding model u^2 (1 - e^2) / (3 e), u = 2^-8."""
+    p = bi.scaled_haar(1536, 2048, 64, k=10, p=10, q=2, g_col=6, g_row=5, seed=7, rank=120,
+                       noise=1e-4)
+    ref, gpu, plan = run_problem(p, "bf16", "bf16x3")
+    e = ref["rel"]
+    assert e > 0.1
+    model = 0.00390625 ** 2 * (1 - e * e) / (3 * e)
+    assert abs(gpu["err"][1] - e) <= max(5 * model, 1e-6)
