@@ -134,6 +134,55 @@ def ar1_factors(m: int, n: int, k: int, phi: float, seed: int):
     return load, x
 
 
+def ar1_mixture_stream(m: int, n: int, k: int, phi: float, noise: float, seed: int,
+                       device="cuda", out=None):
+    """The biometric-like recipe drawn entirely on the device (the serving
+    workload, where every request's matrix is drawn at admission): L and the
+    innovations from a seeded torch generator, and the AR(1) series
+    x_t = phi^t e_0 + c sum_{1 <= s <= t} phi^(t-s) e_s, c = sqrt(1 - phi^2),
+    as a causal convolution with the kernel phi^j truncated where phi^j falls
+    below 1e-16 of the first tap.  FP32."""
+    import torch
+    import torch.nn.functional as F
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + STREAM_MATRIX)
+    L = torch.randn(m, k, generator=gen, device=device) / math.sqrt(k)
+    e = torch.randn(k, n, generator=gen, device=device)
+    J = min(n, int(math.ceil(math.log(1e-16) / math.log(phi))) + 1)
+    taps = phi ** torch.arange(J - 1, -1, -1, device=device, dtype=torch.float32)
+    inner = torch.cat([torch.zeros(k, 1, device=device), e[:, 1:]], dim=1)
+    conv = F.conv1d(F.pad(inner.unsqueeze(1), (J - 1, 0)), taps.view(1, 1, J)).squeeze(1)
+    powers = phi ** torch.arange(n, device=device, dtype=torch.float32)
+    x = math.sqrt(1.0 - phi * phi) * conv + e[:, :1] * powers
+    # A = noise * N(0,1) + L x, formed in place (out: a preallocated m x n buffer)
+    a = torch.empty(m, n, device=device) if out is None else out
+    if noise:
+        a.normal_(0.0, noise, generator=gen)
+    else:
+        a.zero_()
+    a.addmm_(L, x)
+    return a
+
+
+def request_inputs_device(p: "Problem", device="cuda", out=None):
+    """Every input of one serving request drawn on the device from its seed:
+    A (the biometric recipe, :func:`ar1_mixture_stream`), the Rademacher test
+    matrix as an l x n panel (FP32) and the column / row uniforms (FP64 in
+    [0, 1))."""
+    import torch
+
+    r = p.recipe
+    A = ar1_mixture_stream(p.m, p.n, r["rank"], r["phi"], r["noise"], p.seed, device=device,
+                           out=out)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(p.seed) * 1000003 + STREAM_OMEGA)
+    om = torch.randint(0, 2, (p.l, p.n), generator=gen, device=device).float().mul_(2.0).sub_(1.0)
+    uc = torch.rand(p.g_col, generator=gen, device=device, dtype=torch.float64)
+    ur = torch.rand(p.g_row, generator=gen, device=device, dtype=torch.float64)
+    return A, om, uc, ur
+
+
 def ar1_mixture_device(m: int, n: int, k: int, phi: float, noise: float, seed: int,
                        device="cuda", dtype=None):
     """The biometric-like recipe drawn on a torch device: L and X as in
@@ -286,6 +335,20 @@ def scaled_haar(m: int, n: int, s: int, k: int, p: int, q: int, g_col: int, g_ro
                    recipe=dict(kind="haar_spectrum", rank=min(rank, m, n), decay=1.5, noise=noise))
 
 
+def _biometric(g: np.random.Generator, name: str, seed: int, m_range=(256, 4096),
+               n_range=(1024, 16384), k_range=(5, 50), blocks=(16, 32, 64, 128, 256)) -> Problem:
+    s = int(g.choice(list(blocks)))
+    m = int(g.integers(m_range[0], m_range[1] + 1)) // s * s
+    n = int(g.integers(n_range[0], n_range[1] + 1)) // s * s
+    k = int(g.integers(k_range[0], k_range[1] + 1))
+    Gc, Gr = n // s, m // s
+    return Problem(name, m, n, k=k, p=10, q=2,
+                   col_off=uniform_blocks(n, s), row_off=uniform_blocks(m, s),
+                   g_col=blocks_to_sample(k, s, Gc), g_row=blocks_to_sample(k, s, Gr),
+                   seed=seed, storage="f32",
+                   recipe=dict(kind="ar1_mixture", rank=k, phi=0.95, noise=0.05))
+
+
 def batched_biometric(count: int = 512, seed: int = 3, m_range=(256, 4096), n_range=(1024, 16384),
                       k_range=(5, 50), blocks=(16, 32, 64, 128, 256)) -> List[Problem]:
     """Uneven batch: m~U[256,4096], n~U[1024,16384] (rounded down to s), s in {16..256}, k~U[5,50].
@@ -293,16 +356,42 @@ def batched_biometric(count: int = 512, seed: int = 3, m_range=(256, 4096), n_ra
     The ranges can be narrowed for test-sized batches; the defaults are the
     512-matrix biometric workload."""
     g = rng(seed, STREAM_SHAPES)
-    out = []
-    for i in range(count):
-        s = int(g.choice(list(blocks)))
-        m = int(g.integers(m_range[0], m_range[1] + 1)) // s * s
-        n = int(g.integers(n_range[0], n_range[1] + 1)) // s * s
-        k = int(g.integers(k_range[0], k_range[1] + 1))
-        Gc, Gr = n // s, m // s
-        out.append(Problem(f"bio_{i}", m, n, k=k, p=10, q=2,
-                           col_off=uniform_blocks(n, s), row_off=uniform_blocks(m, s),
-                           g_col=blocks_to_sample(k, s, Gc), g_row=blocks_to_sample(k, s, Gr),
-                           seed=seed * 100003 + i, storage="f32",
-                           recipe=dict(kind="ar1_mixture", rank=k, phi=0.95, noise=0.05)))
+    return [_biometric(g, f"bio_{i}", seed * 100003 + i, m_range, n_range, k_range, blocks)
+            for i in range(count)]
+
+
+@dataclass
+class Request:
+    """One decomposition request of the serving workload."""
+    rid: int
+    arrival: float          # seconds after the start of the run
+    problem: Problem
+    heavy: bool
+
+
+def serving_requests(rate: float = 2000.0, duration: float = 60.0, seed: int = 4,
+                     heavy_frac: float = 0.1, heavy_n: int = 16384,
+                     **light_ranges) -> List[Request]:
+    """Poisson arrivals at `rate` per second for `duration` seconds: a fraction
+    `heavy_frac` of heavy_n^2 matrices (16384 by default; blocks of 256,
+    k = 64, 2 + 2 blocks drawn), the rest drawn like the members of the
+    biometric batch (`light_ranges` narrows their shapes for tests)."""
+    ga = rng(seed, STREAM_ARRIVALS)
+    gs = rng(seed, STREAM_SHAPES)
+    out, t, i = [], 0.0, 0
+    while True:
+        t += float(ga.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        rseed = seed * 1000003 + i
+        if float(gs.random()) < heavy_frac:
+            n = heavy_n
+            p = Problem(f"heavy_{i}", n, n, k=64, p=10, q=2, col_off=uniform_blocks(n, 256),
+                        row_off=uniform_blocks(n, 256), g_col=2, g_row=2, seed=rseed,
+                        storage="f32", recipe=dict(kind="ar1_mixture", rank=64, phi=0.95,
+                                                   noise=0.05))
+            out.append(Request(i, t, p, True))
+        else:
+            out.append(Request(i, t, _biometric(gs, f"req_{i}", rseed, **light_ranges), False))
+        i += 1
     return out

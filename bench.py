@@ -500,7 +500,7 @@ def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload == "batched_biometric":
+    if args.workload in ("batched_biometric", "serving"):
         main_reference_batched(args, world)
         return
     p = workload(args.workload, 0)
@@ -745,6 +745,84 @@ def main_batched(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Serving workload: Poisson arrivals, continuous batching on several streams
+# ---------------------------------------------------------------------------
+def main_serving(args):
+    import torch
+
+    import paper_1703_06065_gb300 as pkg
+    from paper_1703_06065_gb300 import serve
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.load()
+    reqs = bi.serving_requests(args.rate, args.duration, seed=4 + 1000 * rank)
+    srv = serve.Server(hbm_budget=args.hbm_budget, lanes=3, max_batch=128, heavy_lanes=2,
+                       max_heavy_batch=8)
+    # warm-up: the kernels, the allocator and the plan builders on the first requests
+    warm = bi.serving_requests(args.rate, 0.05, seed=99)
+    srv.run(warm, realtime=False)
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    done = srv.run(reqs, realtime=True, timeout=max(600.0, 20 * args.duration))
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = serve.latency_stats(done)
+    jobs = {}
+    for kind, nreq, a, b in srv.jobs:
+        j = jobs.setdefault(kind, {"groups": 0, "requests": 0, "gpu_s": 0.0})
+        j["groups"] += 1
+        j["requests"] += nreq
+        j["gpu_s"] += b - a
+    for j in jobs.values():
+        j["gpu_s"] = round(j["gpu_s"], 3)
+        j["mean_group"] = round(j["requests"] / max(1, j["groups"]), 1)
+
+    # baseline: the plain one-at-a-time FP32 path (CUDA cores) on a sample of
+    # the same request stream, each request alone on the GPU
+    base = None
+    if not args.no_cpu_baseline:
+        sample = [r for r in reqs if not r.heavy][:40] + [r for r in reqs if r.heavy][:4]
+        times = []
+        for r in sample:
+            p = r.problem
+            A, om, uc, ur = bi.generators.request_inputs_device(p, dev)
+            plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
+                            dtype="f32", sketch_prec="f32", fit_prec="f32")
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            pkg.decompose(plan, A, om, uc, ur)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+            del plan, A
+        nl = sum(1 for r in sample if not r.heavy)
+        tl, th = float(np.mean(times[:nl])), float(np.mean(times[nl:]))
+        frac_h = sum(r.heavy for r in reqs) / len(reqs)
+        cap = 1.0 / ((1 - frac_h) * tl + frac_h * th)
+        base = {"path": "plain FP32 plan, one request at a time (CUDA cores)",
+                "light_ms": round(1e3 * tl, 2), "heavy_ms": round(1e3 * th, 2),
+                "capacity_decomps_per_s": round(cap, 1),
+                "sample": f"{nl} light + {len(sample) - nl} heavy requests of the stream"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": st["decomps_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/bf16x3", "data": "synthetic",
+            "config": {"workload": "serving", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "requests": len(reqs), "heavy": int(sum(r.heavy for r in reqs)),
+                       "lanes": "3 light + 2 heavy streams", "hbm_budget_gb": args.hbm_budget / 1e9},
+            "latency": {k: round(v, 3) for k, v in st.items() if k.endswith("_ms")},
+            "completed": st["requests"], "wall_s": round(wall, 2), "groups": jobs,
+            "clocks": clk, "baseline_one_at_a_time": base,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -758,6 +836,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=BATCH_COUNT,
                     help="batched workload: decompose only the first COUNT matrices (profiling)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=10.0,
+                    help="serving: seconds of arrivals (the full workload is 60)")
+    ap.add_argument("--hbm-budget", type=float, default=160e9, help="serving: admission budget")
     ap.add_argument("--no-graph", action="store_true",
                     help="batched workload: launch eagerly instead of replaying a CUDA graph")
     args = ap.parse_args()
@@ -767,6 +849,8 @@ def main():
         main_reference(args)
     elif args.workload == "batched_biometric":
         main_batched(args)
+    elif args.workload == "serving":
+        main_serving(args)
     else:
         main_native(args)
 

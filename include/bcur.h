@@ -330,7 +330,9 @@ bcur_status_t bcur_gemm_split(int64_t M, int64_t N, int64_t K, const void* A_hi,
  */
 typedef struct {
   int64_t m, n, lda;   /* A: FP32, row-major m x n, lda >= n, lda % 4 == 0    */
-  int32_t k, p;        /* rank and oversampling, l = k + p <= 64              */
+  int32_t k, p;        /* rank and oversampling, l = k + p <= 128; a batch
+                          whose items all have l <= 64 uses 64-row panels,
+                          otherwise 128-row panels for every item            */
   int32_t block;       /* s: column blocks [j s, min((j+1) s, n)), row blocks
                           likewise over m; G_col = ceil(n/s), G_row = ceil(m/s) */
   int32_t g_col, g_row;/* blocks drawn without replacement; g * s <= 512     */
@@ -361,7 +363,7 @@ typedef struct bcur_batch_s* bcur_batch_t;
 
 /* Validate `count` items and size the workspace; q subspace iterations
  * (0..16) for every item.  Allocates no device memory.  Errors: BCUR_EINVAL
- * (an item out of range: l > 64, g > G, g * s > 512, lda < n or not a
+ * (an item out of range: l > 128, g > G, g * s > 512, lda < n or not a
  * multiple of 4, count < 1), BCUR_ENOTSUP (no sm_103 tensor cores). */
 bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int32_t q,
                               void* stream, bcur_batch_t* out, size_t* workspace_bytes);
@@ -378,6 +380,11 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t plan, void* workspace, size_
  * from the plan's pinned staging buffer).  Errors: BCUR_ESTATE (no
  * workspace), BCUR_EINVAL (NULL pointer in io). */
 bcur_status_t bcur_batch_run(bcur_batch_t plan, const bcur_batch_io_t* io, int32_t use_graph);
+
+/* Move the plan to another stream (cudaStream_t; NULL = legacy default) for
+ * the following runs, e.g. a plan built on one host thread and run on the
+ * stream of whichever lane is free.  Errors: BCUR_EINVAL. */
+bcur_status_t bcur_batch_set_stream(bcur_batch_t plan, void* stream);
 
 /* Padded sizes of item i: cmax = g_col s, rmax = g_row s (the U layout), and
  * the number of kernel launches one run makes. */

@@ -203,7 +203,7 @@ class Batch:
     are built once; :meth:`run` takes per-item device tensors.
     """
 
-    def __init__(self, items, q: int = 2, device=None):
+    def __init__(self, items, q: int = 2, device=None, workspace=None):
         torch = _torch()
         L = _lib.load()
         self._L = L
@@ -225,7 +225,12 @@ class Batch:
         self.workspace_bytes = ws.value
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
-        self._ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=dev)
+        if workspace is not None:
+            if workspace.numel() < ws.value:
+                raise ValueError(f"workspace of {workspace.numel()} bytes < {ws.value} needed")
+            self._ws = workspace
+        else:
+            self._ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=dev)
         _lib.check(L.bcur_batch_set_workspace(h, _ptr(self._ws), c_size_t(self._ws.numel())),
                    "bcur_batch_set_workspace")
         self.G_col = [-(-it["n"] // it["block"]) for it in self.items]
@@ -250,8 +255,11 @@ class Batch:
             return self._out
         dev = self.device
 
-        def views(sizes, dtype):
+        flats = {}
+
+        def views(sizes, dtype, kind):
             flat = torch.zeros(max(1, sum(sizes)), dtype=dtype, device=dev)
+            flats[kind] = (flat, list(sizes))
             out, at = [], 0
             for s in sizes:
                 out.append(flat[at:at + s])
@@ -260,16 +268,18 @@ class Batch:
 
         its = self.items
         o = dict(want_u=want_u,
-                 col_scores=views(self.G_col, torch.float64),
-                 row_scores=views(self.G_row, torch.float64),
-                 col_idx=views([it["g_col"] for it in its], torch.int32),
-                 row_idx=views([it["g_row"] for it in its], torch.int32),
-                 err=views([3] * self.B, torch.float64))
+                 col_scores=views(self.G_col, torch.float64, "col_scores"),
+                 row_scores=views(self.G_row, torch.float64, "row_scores"),
+                 col_idx=views([it["g_col"] for it in its], torch.int32, "col_idx"),
+                 row_idx=views([it["g_row"] for it in its], torch.int32, "row_idx"),
+                 err=views([3] * self.B, torch.float64, "err"))
         if want_u:
-            us = views([c * r for c, r in zip(self.c_max, self.r_max)], torch.float32)
+            us = views([c * r for c, r in zip(self.c_max, self.r_max)], torch.float32, "U")
             o["U"] = [u.view(c, r) for u, c, r in zip(us, self.c_max, self.r_max)]
         else:
             o["U"] = [None] * self.B
+        # the flat buffer behind each kind of output and the per-item sizes
+        o["flat"] = flats
         self._out = o
         return o
 
@@ -304,6 +314,11 @@ class Batch:
 
     def sync_status(self):
         _lib.check(self._L.bcur_batch_sync_status(self._h), "bcur_batch_sync_status")
+
+    def set_stream(self, stream):
+        """Run on `stream` (a torch.cuda.Stream) from now on."""
+        _lib.check(self._L.bcur_batch_set_stream(self._h, c_void_p(stream.cuda_stream)),
+                   "bcur_batch_set_stream")
 
     def profile(self, enable: bool = True):
         """Record an event after every launch of the following eager runs."""

@@ -29,7 +29,7 @@ EXPORTS = [
     "bcur_alg1_workspace", "bcur_alg1", "bcur_truncate", "bcur_batch_plan",
     "bcur_batch_set_workspace", "bcur_batch_run", "bcur_batch_dims", "bcur_batch_sync_status",
     "bcur_batch_destroy", "bcur_batch_profile", "bcur_batch_profile_count",
-    "bcur_batch_profile_entry",
+    "bcur_batch_profile_entry", "bcur_batch_set_stream",
 ]
 
 
@@ -160,6 +160,8 @@ def load():
     L.bcur_batch_profile_entry.argtypes = [c_void_p, c_int32, POINTER(ctypes.c_char_p),
                                            POINTER(c_double)]
     L.bcur_batch_profile_entry.restype = st
+    L.bcur_batch_set_stream.argtypes = [c_void_p, c_void_p]
+    L.bcur_batch_set_stream.restype = st
     L.bcur_batch_destroy.argtypes = [c_void_p]
     L.bcur_batch_destroy.restype = None
     L.bcur_launch_count.argtypes = []

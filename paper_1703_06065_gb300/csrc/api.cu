@@ -1167,8 +1167,13 @@ bcur_status_t bcur_sync_status(bcur_plan_t P) {
   BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
   if (!P->ws) return BCUR_OK;
   int st = 0;
-  BCUR_CUDA_TRY(cudaMemcpy(&st, P->at<int>(P->o.status), sizeof(int), cudaMemcpyDeviceToHost));
-  if (st) BCUR_CUDA_TRY(cudaMemset(P->at<int>(P->o.status), 0, sizeof(int)));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(&st, P->at<int>(P->o.status), sizeof(int), cudaMemcpyDeviceToHost,
+                                P->stream));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (st) {
+    BCUR_CUDA_TRY(cudaMemsetAsync(P->at<int>(P->o.status), 0, sizeof(int), P->stream));
+    BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  }
   return (bcur_status_t)st;
 }
 

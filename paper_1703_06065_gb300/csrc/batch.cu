@@ -49,7 +49,7 @@ __device__ double block_sum(double v, double* red) {
 // past l), one launch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcur_batch_io_t* io,
-                                                    Work rows8, int total8) {
+                                                    Work rows8, int total8, int lp) {
   const int x = blockIdx.x;
   if (x < total8) {
     const int b = find_item(rows8, x);
@@ -87,9 +87,9 @@ __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcu
     }
   } else {
     const int y = x - total8;
-    const int b = y / (LP / 8);
+    const int b = y / (lp / 8);
     const Item& I = items[b];
-    const int t0 = (y % (LP / 8)) * 8;
+    const int t0 = (y % (lp / 8)) * 8;
     for (int tt = 0; tt < 8; ++tt) {
       const int t = t0 + tt;
       bf16* o = I.Om + (int64_t)t * I.ldn;
@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcu
 //   apply: X' = L^{-1} X (FP32), optionally also as BF16 for the next
 //          product with A.
 // ---------------------------------------------------------------------------
+template <int LP>
 __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chunks, int sel) {
+  constexpr int R = LP / 16;          // R x R outputs per thread
   const int b = find_item(chunks, blockIdx.x);
   const Item& I = items[b];
   const int ch = blockIdx.x - chunks.prefix[b];
@@ -118,11 +120,11 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
   constexpr int TLD = LP + 4;         // XsT[c][r]: column c of the chunk, rows r
   __shared__ __align__(16) float XsT[64 * TLD];
   const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
-  float acc[4][4];
+  float acc[R][R];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+    for (int c = 0; c < R; ++c) acc[a][c] = 0.f;
   const int64_t c_begin = (int64_t)ch * CH;
   const int64_t c_end = c_begin + CH < h ? c_begin + CH : h;
   for (int64_t c0 = c_begin; c0 < c_end; c0 += 64) {
@@ -131,26 +133,31 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
       XsT[c * TLD + r] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int c = 0; c < 64; ++c) {
-      const float4 a4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + 4 * ti]);
-      const float4 b4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + 4 * tj]);
-      const float a[4] = {a4.x, a4.y, a4.z, a4.w};
-      const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+      float a[R], bb[R];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < R; q += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + R * ti + q]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + R * tj + q]);
+        a[q] = a4.x; a[q + 1] = a4.y; a[q + 2] = a4.z; a[q + 3] = a4.w;
+        bb[q] = b4.x; bb[q + 1] = b4.y; bb[q + 2] = b4.z; bb[q + 3] = b4.w;
+      }
 #pragma unroll
-        for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
+      for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int p = 0; p < R; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
     }
     __syncthreads();
   }
   float* out = I.gpart + (int64_t)ch * LP * LP;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < R; ++q)
 #pragma unroll
-    for (int p = 0; p < 4; ++p) out[(4 * ti + q) * LP + 4 * tj + p] = acc[q][p];
+    for (int p = 0; p < R; ++p) out[(R * ti + q) * LP + R * tj + p] = acc[q][p];
 }
 
+template <int LP>
 __global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, int pass,
                                                     int want_lb) {
   extern __shared__ double S[];  // LP x (LP + 1)
@@ -178,12 +185,14 @@ __global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, 
   }
 }
 
-__global__ void __launch_bounds__(AP, 2) sapply_kernel(const Item* items, Work chunks, int src, int dst,
-                                                    int write_bf16) {
+template <int LP>
+__global__ void __launch_bounds__(AP, LP == 64 ? 2 : 1) sapply_kernel(const Item* items,
+                                                                      Work chunks, int src,
+                                                                      int dst, int write_bf16) {
   const int b = find_item(chunks, blockIdx.x);
   const Item& I = items[b];
   const int ch = blockIdx.x - chunks.prefix[b];
-  __shared__ __align__(16) float Ls[LP * LP];
+  extern __shared__ __align__(16) float Ls[];  // LP x LP
   for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Ls[e] = I.LinvT[e];
   __syncthreads();
   const int64_t h = panel_h(I, src), ld = panel_ld(I, src);
@@ -228,6 +237,7 @@ __global__ void __launch_bounds__(AP, 2) sapply_kernel(const Item* items, Work c
 // the squares over the block's columns.  Row blocks use U~ and Q (Pm0).  One
 // CTA per block, fixed order.
 // ---------------------------------------------------------------------------
+template <int LP>
 __global__ void __launch_bounds__(128) scores_kernel(const Item* items, const bcur_batch_io_t* io,
                                                      Work blocks, int* status) {
   const int b = find_item(blocks, blockIdx.x);
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(128) scores_kernel(const Item* items, const bc
   const float* P = col ? I.Pn0 : I.Pm0;
   const int64_t h = col ? I.n : I.m, ld = col ? I.ldn : I.ldm;
   const int k = I.k;
-  __shared__ float Fs[LP * LP];
+  extern __shared__ float Fs[];  // LP x LP
   __shared__ double red[4];
   for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Fs[e] = F[e];
   __syncthreads();
@@ -583,45 +593,85 @@ __global__ void __launch_bounds__(256) finish_kernel(const Item* items, const bc
 }  // namespace
 
 bcur_status_t split_inputs(const Item* items, const bcur_batch_io_t* io, Work rows8, int total8,
-                           int B, int* status, cudaStream_t s) {
-  (void)status;
-  split_kernel<<<total8 + B * (LP / 8), 256, 0, s>>>(items, io, rows8, total8);
+                           int B, int lp, cudaStream_t s) {
+  split_kernel<<<total8 + B * (lp / 8), 256, 0, s>>>(items, io, rows8, total8, lp);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 
-bcur_status_t skinny_gram(const Item* items, Work chunks, int total, int sel, cudaStream_t s) {
-  sgram_kernel<<<total, 256, 0, s>>>(items, chunks, sel);
+namespace {
+template <typename K>
+bcur_status_t allow_smem(K kernel, size_t bytes, bool& done) {
+  if (!done && bytes > 48 * 1024) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes));
+  }
+  done = true;
+  return BCUR_OK;
+}
+
+template <int LP>
+bcur_status_t gram_lp(const Item* items, Work chunks, int total, int sel, cudaStream_t s) {
+  sgram_kernel<LP><<<total, 256, 0, s>>>(items, chunks, sel);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 
-bcur_status_t skinny_chol(const Item* items, int B, int sel, int pass, int want_lb,
-                          cudaStream_t s) {
+template <int LP>
+bcur_status_t chol_lp(const Item* items, int B, int sel, int pass, int want_lb, cudaStream_t s) {
   const size_t smem = (size_t)LP * (LP + 1) * sizeof(double);
   static bool attr = false;
-  if (!attr) {
-    BCUR_CUDA_TRY(cudaFuncSetAttribute(schol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    attr = true;
-  }
-  schol_kernel<<<B, 256, smem, s>>>(items, sel, pass, want_lb);
+  BCUR_TRY(allow_smem(schol_kernel<LP>, smem, attr));
+  schol_kernel<LP><<<B, 256, smem, s>>>(items, sel, pass, want_lb);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
+}
+
+template <int LP>
+bcur_status_t apply_lp(const Item* items, Work chunks, int total, int src, int dst,
+                       int write_bf16, cudaStream_t s) {
+  const size_t smem = (size_t)LP * LP * sizeof(float);
+  static bool attr = false;
+  BCUR_TRY(allow_smem(sapply_kernel<LP>, smem, attr));
+  sapply_kernel<LP><<<total, AP, smem, s>>>(items, chunks, src, dst, write_bf16);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+template <int LP>
+bcur_status_t scores_lp(const Item* items, const bcur_batch_io_t* io, Work blocks, int total,
+                        int* status, cudaStream_t s) {
+  const size_t smem = (size_t)LP * LP * sizeof(float);
+  static bool attr = false;
+  BCUR_TRY(allow_smem(scores_kernel<LP>, smem, attr));
+  scores_kernel<LP><<<total, 128, smem, s>>>(items, io, blocks, status);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+}  // namespace
+
+bcur_status_t skinny_gram(const Item* items, Work chunks, int total, int sel, int lp,
+                          cudaStream_t s) {
+  return lp == 64 ? gram_lp<64>(items, chunks, total, sel, s)
+                  : gram_lp<128>(items, chunks, total, sel, s);
+}
+
+bcur_status_t skinny_chol(const Item* items, int B, int sel, int pass, int want_lb, int lp,
+                          cudaStream_t s) {
+  return lp == 64 ? chol_lp<64>(items, B, sel, pass, want_lb, s)
+                  : chol_lp<128>(items, B, sel, pass, want_lb, s);
 }
 
 bcur_status_t skinny_apply(const Item* items, Work chunks, int total, int src, int dst,
-                           int write_bf16, cudaStream_t s) {
-  sapply_kernel<<<total, AP, 0, s>>>(items, chunks, src, dst, write_bf16);
-  BCUR_LAUNCH_CHECK();
-  return BCUR_OK;
+                           int write_bf16, int lp, cudaStream_t s) {
+  return lp == 64 ? apply_lp<64>(items, chunks, total, src, dst, write_bf16, s)
+                  : apply_lp<128>(items, chunks, total, src, dst, write_bf16, s);
 }
 
 bcur_status_t scores(const Item* items, const bcur_batch_io_t* io, Work blocks, int total,
-                     int* status, cudaStream_t s) {
-  scores_kernel<<<total, 128, 0, s>>>(items, io, blocks, status);
-  BCUR_LAUNCH_CHECK();
-  return BCUR_OK;
+                     int* status, int lp, cudaStream_t s) {
+  return lp == 64 ? scores_lp<64>(items, io, blocks, total, status, s)
+                  : scores_lp<128>(items, io, blocks, total, status, s);
 }
 
 bcur_status_t sample(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s) {

@@ -9,7 +9,9 @@
 namespace bcur {
 namespace batch {
 
-constexpr int LP = 64;      // panel rows: l = k + p <= 64, rows l..63 stay zero
+// Panel rows of a batch: 64 when every l = k + p <= 64, else 128; rows past
+// an item's l stay zero.
+constexpr int LP_MAX = 128;
 constexpr int CH = 1024;    // columns per skinny-Gram chunk
 constexpr int AP = 256;     // columns per skinny-apply chunk
 constexpr int WMAX = 512;   // largest padded c or r
@@ -23,6 +25,7 @@ enum PanelSel { PM0 = 0, PM1 = 1, PN0 = 2, PN1 = 3 };
 struct Item {
   int64_t m, n, lda;
   int k, l, s;
+  int lp;                    // panel rows of the batch (64 or 128)
   int Gc, Gr, gc, gr;
   int64_t ldm, ldn;          // panel leading dimensions (multiples of 64)
   int cpad, rpad;            // c and r padded to the leaf size
@@ -75,14 +78,15 @@ __device__ __forceinline__ int find_item(const Work& w, int x) {
 
 // Launchers (batch.cu).  `items` / `io` are device tables of B entries.
 bcur_status_t split_inputs(const Item* items, const bcur_batch_io_t* io, Work rows8, int total8,
-                           int B, int* status, cudaStream_t s);
-bcur_status_t skinny_gram(const Item* items, Work chunks, int total, int sel, cudaStream_t s);
-bcur_status_t skinny_chol(const Item* items, int B, int sel, int pass, int want_lb,
+                           int B, int lp, cudaStream_t s);
+bcur_status_t skinny_gram(const Item* items, Work chunks, int total, int sel, int lp,
+                          cudaStream_t s);
+bcur_status_t skinny_chol(const Item* items, int B, int sel, int pass, int want_lb, int lp,
                           cudaStream_t s);
 bcur_status_t skinny_apply(const Item* items, Work chunks, int total, int src, int dst,
-                           int write_bf16, cudaStream_t s);
+                           int write_bf16, int lp, cudaStream_t s);
 bcur_status_t scores(const Item* items, const bcur_batch_io_t* io, Work blocks, int total,
-                     int* status, cudaStream_t s);
+                     int* status, int lp, cudaStream_t s);
 bcur_status_t sample(const Item* items, const bcur_batch_io_t* io, int B, cudaStream_t s);
 bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, int ctotal,
                      Work rrows, int rtotal, cudaStream_t s);

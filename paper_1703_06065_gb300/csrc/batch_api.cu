@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "batch.h"
@@ -27,6 +28,7 @@ struct WorkList {
 
 struct bcur_batch_s {
   int B = 0, q = 0;
+  int lp = 64;  // panel rows: 64, or 128 when some item has l > 64
   std::vector<bcur_batch_item_t> d;
   std::vector<Item> it;
   cudaStream_t stream = nullptr;
@@ -59,6 +61,7 @@ struct bcur_batch_s {
   // graph mode: the sequence is captured on a stream of the plan's own and
   // joined to the caller's stream through events
   cudaStream_t gstream = nullptr;
+  cudaStream_t sstream = nullptr;  // uploads of the launch tables (never waits on other work)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -108,6 +111,7 @@ size_t layout(bcur_batch_t P) {
   P->d_items = bp.take<Item>(B);
   P->d_io = bp.take<bcur_batch_io_t>(B);
   P->d_status = bp.take<int>(1);
+  const int64_t LP = P->lp;
   P->Lb_all = bp.take<double>((size_t)B * LP * LP);
   P->Ut_all = bp.take<float>((size_t)B * LP * LP);
   P->W_all = bp.take<float>((size_t)B * LP * LP);
@@ -127,6 +131,7 @@ size_t layout(bcur_batch_t P) {
   grp(P->gP, B); grp(P->gRes, B); grp(P->gP3, B); grp(P->gRes3, B);
   for (int b = 0; b < B; ++b) {
     Item& I = P->it[b];
+    I.lp = P->lp;
     const int64_t m = I.m, n = I.n, ldm = I.ldm, ldn = I.ldn;
     const int64_t cp = I.cpad, rp = I.rpad;
     I.Ah = bp.take<bf16>(m * ldn);
@@ -230,7 +235,8 @@ bcur_status_t prep(bcur_batch_t P, bcur_batch_s::MGroup& g, std::vector<GemmDesc
     }
     if (part.empty()) continue;
     BCUR_TRY(gemm_tc_group_prepare(part.data(), (int)part.size(), resid, widths[wi], g.tab[wi],
-                                   gemm_tc_group_bytes((int)ds.size()), P->d_status, &g.g[g.n]));
+                                   gemm_tc_group_bytes((int)ds.size()), P->d_status, &g.g[g.n],
+                                   P->sstream));
     ++g.n;
   }
   return BCUR_OK;
@@ -245,6 +251,7 @@ bcur_status_t build_groups(bcur_batch_t P) {
   const int B = P->B;
   std::vector<GemmDesc> y, z, y2, w, mm, u[4], pp, res, pp3, res3;
   std::vector<GemmDesc> gram[2], app[2];
+  const int64_t LP = P->lp;
   for (int b = 0; b < B; ++b) {
     const Item& I = P->it[b];
     const int64_t m = I.m, n = I.n, ldm = I.ldm, ldn = I.ldn, cp = I.cpad, rp = I.rpad;
@@ -322,20 +329,41 @@ bcur_status_t build_groups(bcur_batch_t P) {
     d.run_flag = I.refine;
     res3.push_back(d);
   }
-  BCUR_TRY(prep(P, P->gY, y, 0, 64));
-  BCUR_TRY(prep(P, P->gZ, z, 0, 64));
-  BCUR_TRY(prep(P, P->gY2, y2, 0, 64));
+  // The tables are independent: encode them on parallel host threads (the
+  // tensor-map encoding is pure host work; the uploads share the plan's setup
+  // stream, whose use from several threads is ordered by the runtime).
+  struct Job {
+    bcur_batch_s::MGroup* g;
+    std::vector<GemmDesc>* ds;
+    int resid, BN;
+  };
+  std::vector<Job> jobs = {{&P->gY, &y, 0, 64}, {&P->gZ, &z, 0, 64}, {&P->gY2, &y2, 0, 64},
+                           {&P->gW, &w, 0, 0}, {&P->gM, &mm, 0, 0}, {&P->gP, &pp, 0, 0},
+                           {&P->gRes, &res, 1, 256}, {&P->gP3, &pp3, 0, 0},
+                           {&P->gRes3, &res3, 1, 256}};
   for (int i = 0; i < 2; ++i) {
-    BCUR_TRY(prep(P, P->gGram[i], gram[i], 0, 0));
-    BCUR_TRY(prep(P, P->gApply[i], app[i], 0, 0));
+    jobs.push_back({&P->gGram[i], &gram[i], 0, 0});
+    jobs.push_back({&P->gApply[i], &app[i], 0, 0});
   }
-  BCUR_TRY(prep(P, P->gW, w, 0, 0));
-  BCUR_TRY(prep(P, P->gM, mm, 0, 0));
-  for (int i = 0; i < 4; ++i) BCUR_TRY(prep(P, P->gU[i], u[i], 0, 0));
-  BCUR_TRY(prep(P, P->gP, pp, 0, 0));
-  BCUR_TRY(prep(P, P->gRes, res, 1, 256));
-  BCUR_TRY(prep(P, P->gP3, pp3, 0, 0));
-  BCUR_TRY(prep(P, P->gRes3, res3, 1, 256));
+  for (int i = 0; i < 4; ++i) jobs.push_back({&P->gU[i], &u[i], 0, 0});
+  std::vector<bcur_status_t> st(jobs.size(), BCUR_OK);
+  const unsigned hw = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+  int dev = 0;
+  BCUR_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < hw; ++t)
+    pool.emplace_back([&, t] {
+      // a new host thread has no current context: bind the caller's device
+      // (the tensor-map encoder validates addresses against it)
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        for (size_t j = t; j < jobs.size(); j += hw) st[j] = BCUR_ECUDA;
+        return;
+      }
+      for (size_t j = t; j < jobs.size(); j += hw)
+        st[j] = prep(P, *jobs[j].g, *jobs[j].ds, jobs[j].resid, jobs[j].BN);
+    });
+  for (auto& th : pool) th.join();
+  for (bcur_status_t e : st) BCUR_TRY(e);
   return BCUR_OK;
 }
 
@@ -358,17 +386,18 @@ bcur_status_t orth(bcur_batch_t P, int s0, int s1, bool want_lb, cudaStream_t s)
   const bool m_side = s0 < PN0;
   const WorkList& ch = m_side ? P->chunks_m : P->chunks_n;
   const WorkList& ap = m_side ? P->apply_m : P->apply_n;
-  BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s0, s));
+  const int lp = P->lp;
+  BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s0, lp, s));
   BCUR_TRY(mark(P, s, "skinny_gram"));
-  BCUR_TRY(skinny_chol(P->d_items, P->B, s0, 0, 0, s));
+  BCUR_TRY(skinny_chol(P->d_items, P->B, s0, 0, 0, lp, s));
   BCUR_TRY(mark(P, s, "skinny_chol"));
-  BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s0, s1, 0, s));
+  BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s0, s1, 0, lp, s));
   BCUR_TRY(mark(P, s, "skinny_apply"));
-  BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s1, s));
+  BCUR_TRY(skinny_gram(P->d_items, ch.w(), ch.total, s1, lp, s));
   BCUR_TRY(mark(P, s, "skinny_gram"));
-  BCUR_TRY(skinny_chol(P->d_items, P->B, s1, 1, want_lb ? 1 : 0, s));
+  BCUR_TRY(skinny_chol(P->d_items, P->B, s1, 1, want_lb ? 1 : 0, lp, s));
   BCUR_TRY(mark(P, s, "skinny_chol"));
-  BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s1, s0, 1, s));
+  BCUR_TRY(skinny_apply(P->d_items, ap.w(), ap.total, s1, s0, 1, lp, s));
   BCUR_TRY(mark(P, s, "skinny_apply"));
   return BCUR_OK;
 }
@@ -382,7 +411,7 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
     for (int i = 0; i < g->n; ++i)
       BCUR_TRY(gemm_tc_group_patch_x(g->g[i], P->d_io, sizeof(bcur_batch_io_t),
                                      offsetof(bcur_batch_io_t, A), s));
-  BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->d_status, s));
+  BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->lp, s));
   BCUR_TRY(mark(P, s, "split"));
   // scores: randomized range finder with q subspace iterations (Sec. 3.1)
   BCUR_TRY(run_group(P->gY, s));
@@ -399,10 +428,10 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   BCUR_TRY(run_group(P->gZ, s));
   BCUR_TRY(mark(P, s, "sketch_gemm"));
   BCUR_TRY(orth(P, PN0, PN1, true, s));
-  BCUR_TRY(jacobi_svd_batched<float>(P->Lb_all, LP, P->Ut_all, P->W_all, P->sig_all, P->jw_all,
-                                     P->d_status, B, s));
+  BCUR_TRY(jacobi_svd_batched<float>(P->Lb_all, P->lp, P->Ut_all, P->W_all, P->sig_all,
+                                     P->jw_all, P->d_status, B, s));
   BCUR_TRY(mark(P, s, "jacobi"));
-  BCUR_TRY(scores(P->d_items, P->d_io, P->blocks.w(), P->blocks.total, P->d_status, s));
+  BCUR_TRY(scores(P->d_items, P->d_io, P->blocks.w(), P->blocks.total, P->d_status, P->lp, s));
   BCUR_TRY(mark(P, s, "scores"));
   // sampling (Alg. 1 step 2) and the gathers
   BCUR_TRY(sample(P->d_items, P->d_io, B, s));
@@ -451,7 +480,7 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
 bool item_ok(const bcur_batch_item_t& d) {
   if (d.m < 1 || d.n < 1 || d.lda < d.n || d.lda % 4 != 0) return false;
   if (d.m > INT32_MAX / 2 || d.n > INT32_MAX / 2) return false;
-  if (d.k < 1 || d.p < 0 || d.k + d.p > LP || d.k + d.p > d.m || d.k + d.p > d.n) return false;
+  if (d.k < 1 || d.p < 0 || d.k + d.p > LP_MAX || d.k + d.p > d.m || d.k + d.p > d.n) return false;
   if (d.block < 1) return false;
   const int64_t Gc = ceil_div(d.n, d.block), Gr = ceil_div(d.m, d.block);
   if (Gc > 32768 || Gr > 32768) return false;
@@ -475,7 +504,10 @@ bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int
   P->q = q;
   P->d.assign(items, items + count);
   P->it.resize(count);
-  for (int i = 0; i < count; ++i) derive(P->it[i], items[i]);
+  for (int i = 0; i < count; ++i) {
+    derive(P->it[i], items[i]);
+    if (P->it[i].l > 64) P->lp = 128;
+  }
   P->stream = static_cast<cudaStream_t>(stream);
   P->need = layout(P);
   *out = P;
@@ -489,6 +521,7 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
   if (!gemm_tc_available()) return BCUR_ENOTSUP;
   if (P->exec) { cudaGraphExecDestroy(P->exec); P->exec = nullptr; }
   if (P->graph) { cudaGraphDestroy(P->graph); P->graph = nullptr; }
+  if (!P->sstream) BCUR_CUDA_TRY(cudaStreamCreateWithFlags(&P->sstream, cudaStreamNonBlocking));
   P->ws = static_cast<char*>(ws);
   P->ws_bytes = bytes;
   layout(P);
@@ -512,7 +545,8 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
   WorkList* wls[] = {&P->rows8, &P->chunks_m, &P->chunks_n, &P->apply_m, &P->apply_n,
                      &P->blocks, &P->ctiles, &P->rrows, &P->urows};
   for (WorkList* w : wls)
-    BCUR_CUDA_TRY(cudaMemcpy(w->d, w->h.data(), w->h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    BCUR_CUDA_TRY(cudaMemcpyAsync(w->d, w->h.data(), w->h.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, P->sstream));
   {
     std::vector<int> cls[3];
     for (int b = 0; b < B; ++b)
@@ -523,14 +557,16 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
     for (int c = 0; c < 3; ++c) {
       P->wide_count[c] = (int)cls[c].size();
       if (!cls[c].empty())
-        BCUR_CUDA_TRY(cudaMemcpy(P->wide_entries[c], cls[c].data(), cls[c].size() * sizeof(int),
-                                 cudaMemcpyHostToDevice));
+        BCUR_CUDA_TRY(cudaMemcpyAsync(P->wide_entries[c], cls[c].data(),
+                                      cls[c].size() * sizeof(int), cudaMemcpyHostToDevice,
+                                      P->sstream));
     }
   }
-  BCUR_CUDA_TRY(cudaMemcpy(P->d_items, P->it.data(), (size_t)B * sizeof(Item),
-                           cudaMemcpyHostToDevice));
-  BCUR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));
-  BCUR_CUDA_TRY(cudaMemset(P->d_io, 0, (size_t)B * sizeof(bcur_batch_io_t)));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->d_items, P->it.data(), (size_t)B * sizeof(Item),
+                                cudaMemcpyHostToDevice, P->sstream));
+  BCUR_CUDA_TRY(cudaMemsetAsync(P->d_status, 0, sizeof(int), P->sstream));
+  BCUR_CUDA_TRY(cudaMemsetAsync(P->d_io, 0, (size_t)B * sizeof(bcur_batch_io_t), P->sstream));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->sstream));
   if (!P->h_io) {
     BCUR_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&P->h_io),
                                 (size_t)B * sizeof(bcur_batch_io_t), cudaHostAllocDefault));
@@ -599,6 +635,20 @@ bcur_status_t bcur_batch_run(bcur_batch_t P, const bcur_batch_io_t* io, int32_t 
   return BCUR_OK;
 }
 
+bcur_status_t bcur_batch_set_stream(bcur_batch_t P, void* stream) {
+  if (!P) return BCUR_EINVAL;
+  if (P->exec) {  // a captured graph belongs to the old stream's sequence: recapture
+    cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+  }
+  if (P->graph) {
+    cudaGraphDestroy(P->graph);
+    P->graph = nullptr;
+  }
+  P->stream = static_cast<cudaStream_t>(stream);
+  return BCUR_OK;
+}
+
 bcur_status_t bcur_batch_dims(bcur_batch_t P, int32_t i, int64_t* cmax, int64_t* rmax,
                               int64_t* launches_per_run) {
   if (!P || i < 0 || i >= P->B) return BCUR_EINVAL;
@@ -613,8 +663,12 @@ bcur_status_t bcur_batch_sync_status(bcur_batch_t P) {
   BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
   if (!P->bound) return BCUR_OK;
   int st = 0;
-  BCUR_CUDA_TRY(cudaMemcpy(&st, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st) BCUR_CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int)));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(&st, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (st) {
+    BCUR_CUDA_TRY(cudaMemsetAsync(P->d_status, 0, sizeof(int), P->stream));
+    BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  }
   return (bcur_status_t)st;
 }
 
@@ -644,6 +698,7 @@ void bcur_batch_destroy(bcur_batch_t P) {
   if (P->ev_in) cudaEventDestroy(P->ev_in);
   if (P->ev_out) cudaEventDestroy(P->ev_out);
   if (P->gstream) cudaStreamDestroy(P->gstream);
+  if (P->sstream) cudaStreamDestroy(P->sstream);
   if (P->h_io) cudaFreeHost(P->h_io);
   delete P;
 }

@@ -36,6 +36,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -817,29 +819,31 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int sm_count() {
   static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
-      n = 148;
+      v = 148;
     }
-  }
+    n = v;
+  });
   return n;
 }
 
 bool tc_device_ok() {
-  static int ok = -1;
-  if (ok < 0) {
+  static int ok = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
     int dev = 0, major = 0, minor = 0;
-    ok = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
       ok = (major == 10 && minor == 3) ? 1 : 0;
     else
       cudaGetLastError();
-  }
+  });
   return ok == 1 && encode_fn() != nullptr;
 }
 
@@ -927,12 +931,28 @@ struct Prepared {
   int BN, kind;
 };
 
+// BCUR_DEBUG=1 in the environment: report why a GEMM is refused (stderr).
+bool debug_on() {
+  static const bool on = [] {
+    const char* e = getenv("BCUR_DEBUG");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepared* out) {
   // TF32 reads FP32 storage; BF16 needs BF16 storage of both operands.
   if (!((prec == BCUR_TF32 && !d.ab_bf16) || (prec == BCUR_BF16 && d.ab_bf16)))
     return BCUR_ENOTSUP;
-  if (!tc_device_ok()) return BCUR_ENOTSUP;
-  if (d.K <= 0 || d.M > INT32_MAX || d.N > INT32_MAX || d.K > INT32_MAX) return BCUR_ENOTSUP;
+  if (!tc_device_ok()) {
+    if (debug_on()) fprintf(stderr, "bcur: tensor cores unavailable\n");
+    return BCUR_ENOTSUP;
+  }
+  if (d.K <= 0 || d.M > INT32_MAX || d.N > INT32_MAX || d.K > INT32_MAX) {
+    if (debug_on()) fprintf(stderr, "bcur: GEMM %lld x %lld x %lld out of range\n",
+                            (long long)d.M, (long long)d.N, (long long)d.K);
+    return BCUR_ENOTSUP;
+  }
   if (d.ksplit > 1) return BCUR_ENOTSUP;
   const int kind = d.ab_bf16 ? 1 : 0;
   const int parts = d.parts == 3 ? 3 : 1;
@@ -968,8 +988,13 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
   const int64_t sAm = swap ? d.sB : d.sA, sBm = swap ? d.sA : d.sB;
   Maps& maps = out->maps;
   if (!make_map(&maps.a[0], A, kind, BM, batch, sAm) || !make_map(&maps.b[0], B, kind, BN, batch, sBm) ||
-      !make_map(&maps.a[1], Al, kind, BM, batch, sAm) || !make_map(&maps.b[1], Bl, kind, BN, batch, sBm))
+      !make_map(&maps.a[1], Al, kind, BM, batch, sAm) || !make_map(&maps.b[1], Bl, kind, BN, batch, sBm)) {
+    if (debug_on())
+      fprintf(stderr, "bcur: no tensor map for GEMM %lld x %lld x %lld (A %p ld %lld mn %d, B %p ld %lld mn %d)\n",
+              (long long)d.M, (long long)d.N, (long long)d.K, A.ptr, (long long)A.ld, A.mn_major,
+              B.ptr, (long long)B.ld, B.mn_major);
     return BCUR_ENOTSUP;
+  }
   Params& p = out->p;
   p = Params{};
   p.Mm = (int)Mm; p.Nm = (int)Nm; p.K = (int)d.K;
@@ -1057,7 +1082,7 @@ __global__ void group_patch_x_kernel(GEntry* e, const int* owner, int count, con
 }
 
 bcur_status_t group_prepare(const GemmDesc* ds, int count, int epi, int BN_force, void* dev,
-                            size_t bytes, int* status, TcGroup* out) {
+                            size_t bytes, int* status, TcGroup* out, cudaStream_t setup) {
   if (count < 1 || !dev || bytes < group_bytes(count)) return BCUR_EINVAL;
   if (epi != EPI_STORE && epi != EPI_RESID) return BCUR_EINVAL;
   if (reinterpret_cast<uintptr_t>(dev) % 128 != 0) return BCUR_EINVAL;
@@ -1103,13 +1128,15 @@ bcur_status_t group_prepare(const GemmDesc* ds, int count, int epi, int BN_force
   if (total > INT32_MAX) return BCUR_ENOTSUP;
   starts[count] = (int)total;
   char* base = static_cast<char*>(dev);
-  BCUR_CUDA_TRY(cudaMemcpy(base, sorted.data(), (size_t)count * sizeof(GEntry),
-                           cudaMemcpyHostToDevice));
+  // Pageable sources: each copy has been staged when the call returns.
+  BCUR_CUDA_TRY(cudaMemcpyAsync(base, sorted.data(), (size_t)count * sizeof(GEntry),
+                                cudaMemcpyHostToDevice, setup));
   int* d_starts = reinterpret_cast<int*>(base + (size_t)count * sizeof(GEntry));
-  BCUR_CUDA_TRY(cudaMemcpy(d_starts, starts.data(), (size_t)(count + 1) * sizeof(int),
-                           cudaMemcpyHostToDevice));
-  BCUR_CUDA_TRY(cudaMemcpy(d_starts + count + 1, order.data(), (size_t)count * sizeof(int),
-                           cudaMemcpyHostToDevice));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(d_starts, starts.data(), (size_t)(count + 1) * sizeof(int),
+                                cudaMemcpyHostToDevice, setup));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(d_starts + count + 1, order.data(), (size_t)count * sizeof(int),
+                                cudaMemcpyHostToDevice, setup));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(setup));
   out->BN = BN;
   out->epi = epi;
   out->count = count;
@@ -1165,9 +1192,9 @@ bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t
 size_t gemm_tc_group_bytes(int count) { return tc::group_bytes(count); }
 
 bcur_status_t gemm_tc_group_prepare(const GemmDesc* ds, int count, int resid, int BN, void* dev,
-                                    size_t bytes, int* status, TcGroup* out) {
+                                    size_t bytes, int* status, TcGroup* out, cudaStream_t setup) {
   return tc::group_prepare(ds, count, resid ? tc::EPI_RESID : tc::EPI_STORE, BN, dev, bytes,
-                           status, out);
+                           status, out, setup);
 }
 
 bcur_status_t gemm_tc_group_run(const TcGroup& g, cudaStream_t s, int grid) {

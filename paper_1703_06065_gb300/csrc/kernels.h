@@ -66,7 +66,8 @@ bool gemm_tc_available();
 // Grouped tensor-core GEMM: many BF16 GEMMs of different shapes in one
 // persistent launch.  The table (tensor maps + parameters per GEMM, tile
 // prefix sums) is encoded on the host and copied to `dev` once
-// (synchronously); running it is one launch.  BN = 0 picks the tile width
+// on the `setup` stream, synchronising only that stream; running it is one
+// launch.  BN = 0 picks the tile width
 // with the least padded work.  resid = 1: every GEMM reduces
 // sum (X - A_op B_op)^2 and sum X^2 per (tile, epilogue warp) into
 // d.partials[2 * (kResidSlots * tile + warp) + {0, 1}], tiles numbered as
@@ -81,7 +82,7 @@ struct TcGroup {
 };
 size_t gemm_tc_group_bytes(int count);
 bcur_status_t gemm_tc_group_prepare(const GemmDesc* ds, int count, int resid, int BN, void* dev,
-                                    size_t bytes, int* status, TcGroup* out);
+                                    size_t bytes, int* status, TcGroup* out, cudaStream_t setup);
 bcur_status_t gemm_tc_group_run(const TcGroup& g, cudaStream_t s, int grid = 0);
 // Set the residual reference X of every GEMM of a prepared group from a
 // device table: GEMM j (in the order given to prepare) reads the pointer at

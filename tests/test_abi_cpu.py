@@ -135,7 +135,8 @@ _GOOD = dict(m=512, n=1024, k=10, p=10, block=64, g_col=3, g_row=2)
 
 @pytest.mark.parametrize("change,want", [
     ({}, 0),
-    ({"p": 60}, 1),                       # l = 70 > 64
+    ({"p": 60}, 0),                       # l = 70: 128-row panels
+    ({"p": 120}, 1),                      # l = 130 > 128
     ({"g_col": 17}, 1),                   # more blocks than G = 16
     ({"block": 256, "g_col": 3}, 1),      # c = 768 > 512
     ({"lda": 1022}, 1),                   # lda < n

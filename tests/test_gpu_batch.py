@@ -186,6 +186,31 @@ def test_small_error_items_are_refined():
             assert r["err"][1] < 5e-4, (p.name, r["err"])  # one term: about 3e-3
 
 
+def test_wide_panels_for_large_k():
+    """Items with l = k + p > 64 run with 128-row panels; parity with the
+    oracle and independence from the batch as for the 64-row form."""
+    probs = [
+        bi.Problem("k60", 1024, 2048, k=60, p=10, q=2, col_off=bi.uniform_blocks(2048, 128),
+                   row_off=bi.uniform_blocks(1024, 128), g_col=2, g_row=2, seed=61, storage="f32",
+                   recipe=dict(kind="ar1_mixture", rank=60, phi=0.95, noise=0.05)),
+        bi.Problem("k8", 768, 1280, k=8, p=10, q=2, col_off=bi.uniform_blocks(1280, 64),
+                   row_off=bi.uniform_blocks(768, 64), g_col=2, g_row=2, seed=62, storage="f32",
+                   recipe=dict(kind="ar1_mixture", rank=8, phi=0.95, noise=0.05)),
+    ]
+    _, _, res = _run(probs)
+    for p, r in zip(probs, res):
+        A = p.matrix().astype(np.float64)
+        ref = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(),
+                            p.u_col(), p.u_row())
+        for side in ("col", "row"):
+            d = np.max(np.abs(r[f"{side}_scores"] - ref[f"{side}_scores"]))
+            assert d <= 2e-2 * np.max(ref[f"{side}_scores"]), (p.name, side, d)
+        assert abs(r["err"][1] - ref["rel"]) <= 1e-3, (p.name, r["err"][1], ref["rel"])
+    _, _, alone = _run([probs[0]])
+    for k, v in alone[0].items():
+        np.testing.assert_array_equal(v, res[0][k], err_msg=k)
+
+
 def test_nonfinite_item_is_reported():
     import paper_1703_06065_gb300 as pkg
 
