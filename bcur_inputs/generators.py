@@ -326,6 +326,14 @@ def fp32_32768(seed: int = 1, k: int = 50, p: int = 10, q: int = 2) -> Problem:
                    recipe=dict(kind="haar_spectrum", rank=200, decay=1.5, noise=1e-4))
 
 
+def precision_32768(seed: int = 1) -> Problem:
+    """The 32768^2 matrix of :func:`fp32_32768` with k = 100, p = 20, q = 3 (the
+    precision study: BF16 sketch, error against FP64 reported per stage)."""
+    p = fp32_32768(seed=seed, k=100, p=20, q=3)
+    p.name = "precision_32768"
+    return p
+
+
 def scaled_haar(m: int, n: int, s: int, k: int, p: int, q: int, g_col: int, g_row: int,
                 seed: int, storage: str = "f32", rank: int = 200, noise: float = 1e-4) -> Problem:
     """The Haar-spectrum recipe at an arbitrary (smaller) size, for parity tests."""

@@ -184,54 +184,62 @@ __device__ int potrf_leaf(const T* G, int64_t ldg, T* S, T* X, T tol) {
 
 // ---------------------------------------------------------------------------
 // One warp: Cholesky with the drop rule and the inverse of a 32 x 32 block
-// (lower part of A, ld lda; may alias Lo).  Lane i holds row i of the block
-// in registers; column j is finished when lane j's updated diagonal is
-// broadcast, and the rank-1 update of the trailing rows takes the column
-// entries l_kj from lane k by shuffle.  The inverse is formed column per
-// lane: X[r][c] = (delta_rc - sum_{c <= k < r} L[r][k] X[k][c]) / L[r][r].
-// Writes L (Lo, ld ldo) and L^{-1} (Xo, ld ldx) with zeros above the
-// diagonal; a dropped pivot zeroes its column of L and its row of L^{-1}.
-// Returns the number of kept pivots (same in every lane).
+// held in shared memory (lower part of A, ld lda; factored in place, zeros
+// written above the diagonal).  Lane i owns row i in registers as a window
+// that slides one column per step: at step j, a[t] holds entry (i, j + t), so
+// the register indices stay compile-time constants while the step loop stays
+// rolled (one warp runs this once; unrolling the steps would make it bound on
+// instruction fetch).  Step j: pivot from lane j by shuffle (drop rule: <= tol
+// or <= 0), scale the column, update the row with l_{j+t, j} shuffled from
+// lane j + t.  L^{-1} by forward substitution, one column per lane, with the
+// same sliding window on the right-hand side: x_k = b_k / L_kk, then
+// b_i -= L_ik x_k for i > k.  A dropped pivot zeroes its column of L and its
+// row of L^{-1}.  Returns the number of kept pivots (same in every lane).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int warp_chol32(const T* A, int lda, T* Lo, int ldo, T* Xo, int ldx, T tol) {
+__device__ int warp_chol32(T* A, int lda, T* Xo, int ldx, T tol) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   T a[32];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) a[k] = (k <= lane) ? A[lane * lda + k] : T(0);
+  for (int t = 0; t < 32; ++t) a[t] = (t <= lane) ? A[lane * lda + t] : T(0);
+  __syncwarp();
   int kept = 0;
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 32; ++j) {
-    const T d = __shfl_sync(FULL, a[j], j);
+    const T d = __shfl_sync(FULL, a[0], j);
     const T p = (d > tol && d > T(0)) ? sqrt(d) : T(0);
     const T inv = (p > T(0)) ? T(1) / p : T(0);
     kept += (p > T(0)) ? 1 : 0;
-    if (lane == j) a[j] = p;
-    else if (lane > j) a[j] *= inv;
+    const T l = (lane > j) ? a[0] * inv : ((lane == j) ? p : T(0));
+    A[lane * lda + j] = l;
 #pragma unroll
-    for (int k = j + 1; k < 32; ++k) {
-      const T lkj = __shfl_sync(FULL, a[j], k);
-      if (lane >= k) a[k] = fma(-a[j], lkj, a[k]);
+    for (int t = 1; t < 32; ++t) {
+      const T lkj = __shfl_sync(FULL, l, (j + t) & 31);
+      if (j + t <= lane) a[t] = fma(-l, lkj, a[t]);
     }
-  }
-  T x[32];
 #pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    T acc = (r == lane) ? T(1) : T(0);
-#pragma unroll
-    for (int k = 0; k < r; ++k) {
-      const T lrk = __shfl_sync(FULL, a[k], r);
-      acc = fma(-lrk, x[k], acc);  // x[k] = 0 for k < lane
-    }
-    const T lrr = __shfl_sync(FULL, a[r], r);
-    x[r] = (r >= lane && lrr > T(0)) ? acc / lrr : T(0);
+    for (int t = 0; t < 31; ++t) a[t] = a[t + 1];
+    a[31] = T(0);
   }
   __syncwarp();
+  T b[32];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) Lo[lane * ldo + k] = (k <= lane) ? a[k] : T(0);
+  for (int t = 0; t < 32; ++t) b[t] = (t == lane) ? T(1) : T(0);
+#pragma unroll 1
+  for (int k = 0; k < 32; ++k) {
+    const T lkk = A[k * lda + k];
+    const T xk = (lkk > T(0)) ? b[0] / lkk : T(0);
+    Xo[k * ldx + lane] = xk;
 #pragma unroll
-  for (int r = 0; r < 32; ++r) Xo[r * ldx + lane] = x[r];
+    for (int t = 1; t < 32; ++t) {
+      const T lik = (k + t < 32) ? A[(k + t) * lda + k] : T(0);
+      b[t] = fma(-lik, xk, b[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 31; ++t) b[t] = b[t + 1];
+    b[31] = T(0);
+  }
   __syncwarp();
   return kept;
 }
@@ -257,7 +265,7 @@ __device__ inline int potrf_leaf<float, 64>(const float* G, int64_t ldg, float* 
   }
   __syncthreads();
   int k1 = 0;
-  if (warp == 0) k1 = warp_chol32<float>(S, LD, S, LD, X, LD, tol);
+  if (warp == 0) k1 = warp_chol32<float>(S, LD, X, LD, tol);
   __syncthreads();
   // L21 = G21 X11^T: 4 outputs per thread (row i, columns c4..c4+3)
   const int i = (tid >> 3) & 31, c4 = (tid & 7) * 4;
@@ -287,7 +295,7 @@ __device__ inline int potrf_leaf<float, 64>(const float* G, int64_t ldg, float* 
   }
   __syncthreads();
   int k2 = 0;
-  if (warp == 0) k2 = warp_chol32<float>(S + H * LD + H, LD, S + H * LD + H, LD, X + H * LD + H, LD, tol);
+  if (warp == 0) k2 = warp_chol32<float>(S + H * LD + H, LD, X + H * LD + H, LD, tol);
   if (tid == 0) s_kept = k1 + k2;
   __syncthreads();
   // T = L21 X11 (X11 lower: t >= c), kept in X21's place for now

@@ -1,11 +1,12 @@
-"""Write the FP64 oracle's result for the 32768 x 32768 benchmark workload.
+"""Write the FP64 oracle's result for a 32768 x 32768 workload.
 
 Runs only the oracle (host, NumPy/LAPACK) on the stored FP32 matrix that
-``bcur_inputs.fp32_32768()`` draws, and stores block scores, block indices,
-the top singular values and the residual in ``fp32_32768_oracle.json`` next
-to this file.  Needs about 45 GB of host memory and a few minutes on 16 cores.
+``bcur_inputs.fp32_32768()`` (or ``precision_32768()``, k = 100, p = 20,
+q = 3) draws, and stores block scores, block indices, the top singular values
+and the residual in ``<workload>_oracle.json`` next to this file.  Needs about
+45 GB of host memory and a few minutes on 16 cores.
 
-    python tests/golden/make_fp32_32768_reference.py
+    python tests/golden/make_fp32_32768_reference.py [fp32_32768 | precision_32768]
 """
 import json
 import os
@@ -22,8 +23,9 @@ import oracle as orc  # noqa: E402
 
 
 def main():
+    name = sys.argv[1] if len(sys.argv) > 1 else "fp32_32768"
     t0 = time.time()
-    p = bi.fp32_32768()
+    p = {"fp32_32768": bi.fp32_32768, "precision_32768": bi.precision_32768}[name]()
     A = p.matrix()                      # FP32 storage, as the GPU reads it
     t1 = time.time()
     r = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(), p.u_col(),
@@ -36,7 +38,7 @@ def main():
                sigma=[float(x) for x in r["sigma"]], err=float(r["err"]), rel=float(r["rel"]),
                norm_a=float(np.linalg.norm(A.astype(np.float64))),
                seconds_generate=round(t1 - t0, 1), seconds_oracle=round(t2 - t1, 1))
-    path = os.path.join(HERE, "fp32_32768_oracle.json")
+    path = os.path.join(HERE, f"{p.name}_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps({k: out[k] for k in ("rel", "err", "col_idx", "row_idx",
