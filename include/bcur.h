@@ -66,13 +66,18 @@ typedef enum {
  *   BCUR_BF16   : tcgen05 tensor cores on BF16 roundings of the FP32 operands,
  *                 FP32 accumulation in tensor memory (about 8 mantissa bits).
  *   BCUR_BF16X3 : tcgen05 tensor cores on BF16 hi/lo pairs, x = hi + lo, with
- *                 A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 bits). */
+ *                 A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (about 16 bits).
+ *   BCUR_FP8    : sketch only (FP32 storage): tcgen05 kind::f8f6f4 on e4m3
+ *                 roughly 4-bit operands, A scaled per row and each skinny
+ *                 panel per row (amax / 448), the scales undone exactly in
+ *                 the products' epilogue; FP32 accumulation. */
 typedef enum {
   BCUR_F64 = 0,
   BCUR_F32 = 1,
   BCUR_TF32 = 2,
   BCUR_BF16 = 3,
-  BCUR_BF16X3 = 4
+  BCUR_BF16X3 = 4,
+  BCUR_FP8 = 5
 } bcur_prec_t;
 
 typedef struct {
@@ -298,6 +303,8 @@ bcur_status_t bcur_residual_noalloc(const void* X, int64_t ldx, const void* P, i
  * B_op(kk, j) = transB ? B[j * ldb + kk] : B[kk * ldb + j].
  * dtype F64/F32: storage of A, B and D, with prec F64 (F64 data), F32 or
  * TF32 (F32 data).  dtype BF16: A and B stored as BF16, D as FP32, prec BF16.
+ * dtype FP8: A and B stored as e4m3 bytes, both K-major (transA = 0,
+ * transB = 1; otherwise BCUR_ENOTSUP), D as FP32, prec FP8.
  * The tensor-core precisions return BCUR_ENOTSUP for operands TMA cannot
  * describe (base not 16-byte aligned, leading dimension not a multiple of
  * 16 bytes) instead of falling back. */

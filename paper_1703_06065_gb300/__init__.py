@@ -50,6 +50,10 @@ def _dtype_code(t) -> int:
         return BCUR_F64
     if t.dtype == torch.float32:
         return BCUR_F32
+    if t.dtype == torch.bfloat16:
+        return BCUR_BF16
+    if t.dtype == getattr(torch, "float8_e4m3fn", None):
+        return _lib.BCUR_FP8
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 
@@ -411,7 +415,8 @@ def gemm(A, B, transA: bool = False, transB: bool = False, prec: str = None, out
     N = B.shape[0] if transB else B.shape[1]
     code = _dtype_code(A)
     prec = PREC[prec] if prec else code
-    D = torch.empty(M, N, dtype=A.dtype, device=A.device) if out is None else out
+    ddt = A.dtype if code in (BCUR_F64, BCUR_F32) else torch.float32
+    D = torch.empty(M, N, dtype=ddt, device=A.device) if out is None else out
     _lib.check(_lib.load().bcur_gemm(M, N, K, _ptr(A), A.shape[1], int(transA), _ptr(B),
                                      B.shape[1], int(transB), _ptr(D), D.shape[1], code, prec,
                                      _stream()), "bcur_gemm")

@@ -13,9 +13,9 @@ from ctypes import POINTER, c_double, c_int32, c_int64, c_size_t, c_void_p
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbcur.so")
 
-BCUR_F64, BCUR_F32, BCUR_TF32, BCUR_BF16, BCUR_BF16X3 = 0, 1, 2, 3, 4
+BCUR_F64, BCUR_F32, BCUR_TF32, BCUR_BF16, BCUR_BF16X3, BCUR_FP8 = 0, 1, 2, 3, 4, 5
 PREC = {"f64": BCUR_F64, "f32": BCUR_F32, "tf32": BCUR_TF32, "bf16": BCUR_BF16,
-        "bf16x3": BCUR_BF16X3}
+        "bf16x3": BCUR_BF16X3, "fp8": BCUR_FP8}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ENONFINITE",
           6: "ETIMEOUT", 7: "ENOTSUP", 8: "ESTATE"}
 

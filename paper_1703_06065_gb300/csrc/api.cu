@@ -67,6 +67,8 @@ struct bcur_plan_s {
     // BF16 tensor-core path
     size_t A16h, A16l, Om16h, Om16l, Qm16h, Qm16l, Zn16h, Zn16l, XC16[4], XR16[4], Lh, Ll, Lih,
         Lil, T1h, T1l, Pnh, Pnl, Wh, Wl, Mh, Ml, U1h, U1l, U2h, U2l, Ph, Pl, refine;
+    // FP8 sketch
+    size_t A8, A8T, sA, X8m, X8n, sx;
     // per-lane temporaries of the second lane
     size_t Lh2, Ll2, Lih2, Lil2, T1h2, T1l2, Pnh2, Pnl2, maxdiag2, tc_scratch2;
   } o;
@@ -656,6 +658,65 @@ bcur_status_t run_scores16(bcur_plan_t P, const float* A, const float* omega, do
   return scores_tail<float>(P, cs, rs);
 }
 
+// Stages 1-2 with the products by A on FP8 e4m3 tensor cores.  A is
+// quantised once per row (A = diag(s_A) A8) and kept twice (A8 and its
+// transpose, so both products read K-major operands); each skinny panel is
+// quantised per row before its product, with s_A folded in when the product
+// sums over the rows of A.  All scales come out of the products exactly and
+// are applied in the GEMM epilogue; the panels stay FP32 and are
+// re-orthonormalised after every product as in the BF16 form.
+bcur_status_t run_scores8(bcur_plan_t P, const float* A, const float* omega, double* cs,
+                          double* rs) {
+  cudaStream_t s = P->stream;
+  const int l = P->l;
+  const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
+  const int64_t ldm8 = round_up(m, 16), ldn8 = round_up(n, 16);
+  float* Pm0 = P->at<float>(P->o.Pm0);
+  float* Pm1 = P->at<float>(P->o.Pm1);
+  float* Pn0 = P->at<float>(P->o.Pn0);
+  float* Pn1 = P->at<float>(P->o.Pn1);
+  uint8_t* A8 = P->at<uint8_t>(P->o.A8);
+  uint8_t* A8T = P->at<uint8_t>(P->o.A8T);
+  float* sA = P->at<float>(P->o.sA);
+  uint8_t* X8m = P->at<uint8_t>(P->o.X8m);
+  uint8_t* X8n = P->at<uint8_t>(P->o.X8n);
+  float* sx = P->at<float>(P->o.sx);
+  BCUR_TRY(quant_rows_e4m3(A, lda, m, n, nullptr, A8, ldn8, sA, s));
+  BCUR_TRY(transpose_u8(A8, ldn8, m, n, A8T, ldm8, s));
+  // Y^T (l x m) = X^T A^T from the panel X^T (l x n):  D = X8 A8^T, rows
+  // scaled by sx, columns by sA
+  auto prodAt = [&](const float* X, float* Y) {
+    BCUR_TRY(quant_rows_e4m3(X, ldn, l, n, nullptr, X8n, ldn8, sx, s));
+    GemmDesc g = mk(l, m, n, X8n, ldn8, 0, A8, ldn8, 1, Y, ldm);
+    g.ab_fp8 = 1;
+    g.scale_m = sx;
+    g.scale_n = sA;
+    g.status = P->at<int>(P->o.status);
+    return gemm_tc(g, BCUR_FP8, s);
+  };
+  // Z^T (l x n) = X^T A from the panel X^T (l x m):  X^T diag(s_A) is
+  // quantised, D = X8 A8T^T, rows scaled by sx
+  auto prodA = [&](const float* X, float* Z) {
+    BCUR_TRY(quant_rows_e4m3(X, ldm, l, m, sA, X8m, ldm8, sx, s));
+    GemmDesc g = mk(l, n, m, X8m, ldm8, 0, A8T, ldm8, 1, Z, ldn);
+    g.ab_fp8 = 1;
+    g.scale_m = sx;
+    g.status = P->at<int>(P->o.status);
+    return gemm_tc(g, BCUR_FP8, s);
+  };
+  const int ep = BCUR_F32;
+  BCUR_TRY(prodAt(omega, Pm0));
+  BCUR_TRY(orth_panel<float>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, ep, nullptr));
+  for (int it = 0; it < P->q; ++it) {
+    BCUR_TRY(prodA(Pm0, Pn0));
+    BCUR_TRY(orth_panel<float>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, ep, nullptr));
+    BCUR_TRY(prodAt(Pn0, Pm0));
+    BCUR_TRY(orth_panel<float>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, ep, nullptr));
+  }
+  BCUR_TRY(prodA(Pm0, Pn0));
+  return scores_tail<float>(P, cs, rs);
+}
+
 // Stages 4-5 on tensor cores.
 bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const int32_t* ri,
                         float* Uout, float* Cout, float* Rout) {
@@ -892,7 +953,10 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
     return BCUR_EINVAL;
   if (d->g_col < 1 || d->g_row < 1) return BCUR_EINVAL;
   if (!d->replacement && (d->g_col > d->G_col || d->g_row > d->G_row)) return BCUR_EINVAL;
+  if (d->sketch_prec == BCUR_FP8 && d->a_dtype != BCUR_F32) return BCUR_EINVAL;
+  if (d->fit_prec == BCUR_FP8) return BCUR_EINVAL;  // FP8 is a sketch precision only
   for (int p : {d->sketch_prec, d->fit_prec}) {
+    if (p == BCUR_FP8) continue;
     if (p < BCUR_F64 || p > BCUR_BF16X3) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F64 && p != BCUR_F64) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F32 && p == BCUR_F64) return BCUR_EINVAL;
@@ -1033,6 +1097,15 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
       o.tc_scratch2 = L.take(P->tc_scratch_bytes);
     }
   }
+  if (d->sketch_prec == BCUR_FP8) {
+    const int64_t ldm8 = round_up(P->m, 16), ldn8 = round_up(P->n, 16);
+    o.A8 = L.take(P->m * ldn8);
+    o.A8T = L.take(P->n * ldm8);
+    o.sA = L.take(P->m * 4);
+    o.X8m = L.take(l * ldm8);
+    o.X8n = L.take(l * ldn8);
+    o.sx = L.take(l * 4);
+  }
   P->need = L.cur;
   if (workspace_bytes) *workspace_bytes = P->need;
   *out = P;
@@ -1076,6 +1149,8 @@ bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, doubl
     st = run_scores<double>(P, (const double*)A, (const double*)omega, cs, rs);
   else if (is_bf16_prec(P->d.sketch_prec))
     st = run_scores16(P, (const float*)A, (const float*)omega, cs, rs);
+  else if (P->d.sketch_prec == BCUR_FP8)
+    st = run_scores8(P, (const float*)A, (const float*)omega, cs, rs);
   else
     st = run_scores<float>(P, (const float*)A, (const float*)omega, cs, rs);
   if (st == BCUR_OK) P->have_scores = true;
@@ -1273,6 +1348,11 @@ bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t 
   if (dtype == BCUR_BF16) {  // BF16 A and B, FP32 D: tensor cores only
     if (prec != BCUR_BF16) return BCUR_EINVAL;
     g.ab_bf16 = 1;
+    return gemm_tc(g, prec, s);
+  }
+  if (dtype == BCUR_FP8) {  // e4m3 A and B (K-major), FP32 D: tensor cores only
+    if (prec != BCUR_FP8) return BCUR_EINVAL;
+    g.ab_fp8 = 1;
     return gemm_tc(g, prec, s);
   }
   if (dtype != BCUR_F32 || prec == BCUR_F64 || prec == BCUR_BF16) return BCUR_EINVAL;

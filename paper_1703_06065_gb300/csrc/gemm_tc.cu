@@ -2,7 +2,9 @@
 //
 //   D (Mm x Nm, FP32) = alpha * A (Mm x K) . B (Nm x K)^T        ("MMA space")
 //
-// Operands are BF16 (kind::f16), or FP32 read as TF32 (kind::tf32).  A BF16
+// Operands are BF16 (kind::f16), FP8 e4m3 (kind::f8f6f4, both operands
+// K-major, with optional per-row / per-column output scales that undo a
+// row-wise quantisation exactly), or FP32 read as TF32 (kind::tf32).  A BF16
 // operand is either K-major (rows contiguous along K) or MN-major (contiguous
 // along M / N); TF32 operands must be K-major (the MMA reads zeros for an
 // MN-major TF32 operand on sm_103a, so such calls are refused).  TMA brings
@@ -80,6 +82,8 @@ struct Params {
   double* partials;      // per-CTA {sum (X - acc)^2, sum X^2}
   int* status;
   const int* run_flag;   // when non-null and 0 at launch: nothing to do
+  const float* scale_m;  // optional per-row / per-column factors of the output
+  const float* scale_n;  //   (MMA space), applied after alpha
 };
 
 template <int KIND> struct KindCfg;
@@ -89,6 +93,10 @@ template <> struct KindCfg<0> {  // TF32 from FP32 storage
 template <> struct KindCfg<1> {  // BF16
   static constexpr int esize = 2, bk = 64, kstep_rows = 16, box_mn = 64;
 };
+template <> struct KindCfg<2> {  // FP8 e4m3 (K-major operands only)
+  static constexpr int esize = 1, bk = 128, kstep_rows = 32, box_mn = 128;
+};
+__host__ __device__ constexpr int kind_bk(int kind) { return kind == 0 ? 32 : (kind == 1 ? 64 : 128); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -165,10 +173,16 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
-  } else {
+  } else if constexpr (KIND == 1) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
   }
@@ -206,7 +220,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 __host__ __device__ inline uint32_t idesc(int kind, int a_mn, int b_mn, int M, int N) {
   uint32_t d = 0;
   d |= 1u << 4;                          // D format F32
-  const uint32_t fmt = kind == 0 ? 2u : 1u;  // TF32 : BF16
+  const uint32_t fmt = kind == 0 ? 2u : (kind == 1 ? 1u : 0u);  // TF32 : BF16 : E4M3
   d |= fmt << 7;
   d |= fmt << 10;
   d |= (uint32_t)(a_mn & 1) << 15;
@@ -692,6 +706,8 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
               if (tri_out == 2 && row > col) continue;
               const int64_t off = (int64_t)col * ldd + row;
               float o = alpha * v[i];
+              if (P->scale_m) o *= P->scale_m[row];
+              if (P->scale_n) o *= P->scale_n[col];
               if (beta != 0.f) o = fmaf(beta, Dp[off], o);
               if (Dp) Dp[off] = o;
               if (Dhp) {
@@ -727,6 +743,8 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
               if (ok) {
                 const int64_t off = (int64_t)grow * ldd + col;
                 float o = alpha * t[r * 33 + lane];
+                if (P->scale_m) o *= P->scale_m[grow];
+                if (P->scale_n) o *= P->scale_n[col];
                 if (beta != 0.f) o = fmaf(beta, old[r], o);
                 if (Dp) Dp[off] = o;
                 if (Dhp) {
@@ -858,7 +876,7 @@ struct Operand {
 
 bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn, int batch,
               int64_t sbatch) {
-  const int esize = kind == 0 ? 4 : 2;
+  const int esize = kind == 0 ? 4 : (kind == 1 ? 2 : 1);
   const int box_inner = 128 / esize;  // 128 bytes
   const uintptr_t a = reinterpret_cast<uintptr_t>(op.ptr);
   if (a % 16 != 0 || (op.ld * esize) % 16 != 0) return false;
@@ -880,12 +898,14 @@ bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn, in
     dims[0] = (cuuint64_t)op.mn;
     dims[1] = (cuuint64_t)op.k;
     box[0] = (cuuint32_t)box_inner;   // MN elements per box
-    box[1] = (cuuint32_t)(kind == 0 ? KindCfg<0>::bk : KindCfg<1>::bk);  // K rows per stage
+    box[1] = (cuuint32_t)kind_bk(kind);  // K rows per stage
   }
   if (op.ld < (int64_t)dims[0]) return false;
   auto fn = encode_fn();
   if (!fn) return false;
-  CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                            : (kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                         : CU_TENSOR_MAP_DATA_TYPE_UINT8),
                   3, const_cast<void*>(op.ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -941,8 +961,9 @@ bool debug_on() {
 }
 
 bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepared* out) {
-  // TF32 reads FP32 storage; BF16 needs BF16 storage of both operands.
-  if (!((prec == BCUR_TF32 && !d.ab_bf16) || (prec == BCUR_BF16 && d.ab_bf16)))
+  // TF32 reads FP32 storage; BF16 / FP8 need that storage for both operands.
+  if (!((prec == BCUR_TF32 && !d.ab_bf16 && !d.ab_fp8) ||
+        (prec == BCUR_BF16 && d.ab_bf16 && !d.ab_fp8) || (prec == BCUR_FP8 && d.ab_fp8)))
     return BCUR_ENOTSUP;
   if (!tc_device_ok()) {
     if (debug_on()) fprintf(stderr, "bcur: tensor cores unavailable\n");
@@ -954,9 +975,10 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
     return BCUR_ENOTSUP;
   }
   if (d.ksplit > 1) return BCUR_ENOTSUP;
-  const int kind = d.ab_bf16 ? 1 : 0;
+  const int kind = d.ab_fp8 ? 2 : (d.ab_bf16 ? 1 : 0);
   const int parts = d.parts == 3 ? 3 : 1;
-  if (parts == 3 && (!kind || !d.A_lo || !d.B_lo)) return BCUR_EINVAL;
+  if (parts == 3 && (kind != 1 || !d.A_lo || !d.B_lo)) return BCUR_EINVAL;
+  if (kind == 2 && epi != EPI_STORE) return BCUR_ENOTSUP;
   // Small M with a long N: compute D^T = B_op^T A_op^T so the long dimension
   // runs along the 128-row MMA tile and D is stored transposed.
   const bool swap = (epi == EPI_STORE) && d.M < 128 && d.N >= 2 * d.M;
@@ -981,8 +1003,8 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
     triB = d.triA == 1 ? 2 : (d.triA == 2 ? 1 : 0);
     if (tri_out) tri_out = 2;
   }
-  // TF32 operands must be K-major on this tensor core.
-  if (kind == 0 && (A.mn_major || B.mn_major)) return BCUR_ENOTSUP;
+  // TF32 operands must be K-major on this tensor core; FP8 is used K-major only.
+  if (kind != 1 && (A.mn_major || B.mn_major)) return BCUR_ENOTSUP;
   const int BN = BN_force ? BN_force : (Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256));
   const int batch = d.batch > 1 ? d.batch : 1;
   const int64_t sAm = swap ? d.sB : d.sA, sBm = swap ? d.sA : d.sB;
@@ -1006,7 +1028,7 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
   p.a_mn = A.mn_major; p.b_mn = B.mn_major;
   p.tiles_m = (int)ceil_div(Mm, BM);
   p.tiles_n = (int)ceil_div(Nm, BN);
-  p.kblocks = (int)ceil_div(d.K, kind == 0 ? KindCfg<0>::bk : KindCfg<1>::bk);
+  p.kblocks = (int)ceil_div(d.K, kind_bk(kind));
   p.triA = triA; p.triB = triB; p.tri_out = tri_out;
   p.rev_m = (triA == 1 || tri_out == 1) ? 1 : 0;
   p.rev_n = (triB == 2 || tri_out == 2) ? 1 : 0;
@@ -1015,6 +1037,8 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
   p.X = (const float*)d.X; p.ldx = d.ldx; p.partials = d.partials;
   p.status = d.status;
   p.run_flag = d.run_flag;
+  p.scale_m = swap ? d.scale_n : d.scale_m;
+  p.scale_n = swap ? d.scale_m : d.scale_n;
   p.ksplit = 1;
   out->BN = BN;
   out->kind = kind;
@@ -1036,7 +1060,8 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
   const int tiles = p.tiles_m * p.tiles_n;
   // Split K when there are too few tiles to fill the GPU and a scratch
   // buffer for the partial slices is available.
-  if (epi == EPI_STORE && d.scratch && batch == 1 && tiles < sms && p.kblocks >= 8) {
+  if (epi == EPI_STORE && kind != 2 && d.scratch && batch == 1 && tiles < sms &&
+      p.kblocks >= 8) {
     int ks = std::min<int64_t>(std::max<int64_t>(1, (4 * sms) / tiles), p.kblocks / 4);
     const int64_t slice = (int64_t)p.Mm * p.Nm * 4;
     ks = (int)std::min<int64_t>(ks, (int64_t)d.scratch_bytes / slice);
@@ -1061,6 +1086,7 @@ bcur_status_t run(const GemmDesc& d, int prec, cudaStream_t s, int epi, int64_t*
     BCUR_LAUNCH_CHECK();
     return BCUR_OK;
   }
+  if (kind == 2) return launch_bn<2, EPI_STORE>(BN, maps, p, grid, s);
   return kind == 0 ? launch_bn<0, EPI_STORE>(BN, maps, p, grid, s)
                    : launch_bn<1, EPI_STORE>(BN, maps, p, grid, s);
 }

@@ -49,6 +49,12 @@ struct GemmDesc {
   // Optional device flag: when it reads 0 at launch the GEMM does nothing
   // (tensor-core path; in a grouped launch per GEMM).
   const int* run_flag = nullptr;
+  // FP8 e4m3 operands (prec BCUR_FP8; A and B K-major, one term), and
+  // optional per-row (M) / per-column (N) factors of the result, applied
+  // after alpha (tensor-core store only).
+  int ab_fp8 = 0;
+  const float* scale_m = nullptr;
+  const float* scale_n = nullptr;
 };
 
 template <typename T> bcur_status_t gemm_simt(const GemmDesc& d, cudaStream_t s);
@@ -173,6 +179,17 @@ bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
 template <typename T>
 bcur_status_t scale_rows_by(T* X, int64_t rows, int64_t cols, int64_t ld, const double* sc,
                             cudaStream_t s);
+
+// Row-wise FP8 e4m3 quantisation of an FP32 matrix (rows x cols, ldx): with
+// v_ij = X_ij * (pre ? pre[j] : 1), scale[i] = max_j |v_ij| / 448 (1 for an
+// all-zero row) and Q[i][j] = e4m3(v_ij / scale[i]) (round to nearest,
+// saturating), Q bytes with leading dimension ldq.
+bcur_status_t quant_rows_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                              const float* pre, uint8_t* Q, int64_t ldq, float* scale,
+                              cudaStream_t s);
+// Byte matrix transpose: T[j][i] = Q[i][j] (Q rows x cols, ldq; T ld ldt).
+bcur_status_t transpose_u8(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t cols, uint8_t* T,
+                           int64_t ldt, cudaStream_t s);
 
 // Split an FP32 matrix (rows x cols, ldx) into BF16 pairs: hi = bf16(x),
 // lo = bf16(x - hi) (round to nearest even both times); outputs have

@@ -8,6 +8,8 @@
 
 #include <algorithm>
 
+#include <cuda_fp8.h>
+
 #include "kernels.h"
 #include "leaf.cuh"
 
@@ -620,6 +622,71 @@ bcur_status_t scale_rows_by(T* X, int64_t rows, int64_t cols, int64_t ld, const 
 }
 template bcur_status_t scale_rows_by<float>(float*, int64_t, int64_t, int64_t, const double*, cudaStream_t);
 template bcur_status_t scale_rows_by<double>(double*, int64_t, int64_t, int64_t, const double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP32 -> FP8 e4m3, one scale per row
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) quant_rows_e4m3_kernel(const float* X, int64_t ldx,
+                                                              int64_t rows, int64_t cols,
+                                                              const float* pre, uint8_t* Q,
+                                                              int64_t ldq, float* scale) {
+  __shared__ float red[8];
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float* xr = X + r * ldx;
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < cols; j += blockDim.x)
+      mx = fmaxf(mx, fabsf(xr[j] * (pre ? pre[j] : 1.f)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    float amax = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) amax = fmaxf(amax, red[i]);
+    const float sc = amax > 0.f ? amax / 448.f : 1.f;
+    const float inv = 1.f / sc;
+    if (threadIdx.x == 0) scale[r] = sc;
+    uint8_t* qr = Q + r * ldq;
+    for (int64_t j = threadIdx.x; j < cols; j += blockDim.x)
+      qr[j] = (uint8_t)__nv_cvt_float_to_fp8(xr[j] * (pre ? pre[j] : 1.f) * inv, __NV_SATFINITE,
+                                             __NV_E4M3);
+    __syncthreads();
+  }
+}
+
+bcur_status_t quant_rows_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                              const float* pre, uint8_t* Q, int64_t ldq, float* scale,
+                              cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return BCUR_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>(rows, 1 << 20);
+  quant_rows_e4m3_kernel<<<grid, 256, 0, s>>>(X, ldx, rows, cols, pre, Q, ldq, scale);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+__global__ void transpose_u8_kernel(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t cols,
+                                    uint8_t* T, int64_t ldt) {
+  __shared__ uint8_t tile[64][65];
+  const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int i = e / 64, j = e % 64;
+    tile[i][j] = (r0 + i < rows && c0 + j < cols) ? Q[(r0 + i) * ldq + c0 + j] : (uint8_t)0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int j = e / 64, i = e % 64;
+    if (c0 + j < cols && r0 + i < rows) T[(c0 + j) * ldt + r0 + i] = tile[i][j];
+  }
+}
+
+bcur_status_t transpose_u8(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t cols, uint8_t* T,
+                           int64_t ldt, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return BCUR_OK;
+  if (ceil_div(rows, 64) > 65535) return BCUR_EINVAL;
+  dim3 grid((unsigned)ceil_div(cols, 64), (unsigned)ceil_div(rows, 64));
+  transpose_u8_kernel<<<grid, 256, 0, s>>>(Q, ldq, rows, cols, T, ldt);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
 
 // ---------------------------------------------------------------------------
 // FP32 -> BF16 hi/lo pairs

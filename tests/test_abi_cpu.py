@@ -70,7 +70,10 @@ def _plan(lib, **kw):
     (dict(sp=3, fp=4), 0),                   # BF16 sketch, split-BF16 fit
     (dict(sp=4, fp=3), 7),                   # a one-term BF16 fit is refused
     (dict(sp=4, fp=4), 0),
-    (dict(sp=5, fp=1), 1),
+    (dict(sp=5, fp=4), 0),                   # FP8 sketch, split-BF16 fit
+    (dict(sp=1, fp=5), 1),                   # FP8 is a sketch precision only
+    (dict(dtype=0, sp=5, fp=0), 1),          # FP8 sketch needs FP32 storage
+    (dict(sp=6, fp=1), 1),
     (dict(lda=100), 1),                      # lda < n
     (dict(k=100, p=40), 1),                  # l > 128
     (dict(k=0), 1),

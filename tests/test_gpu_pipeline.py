@@ -160,7 +160,7 @@ def test_error_is_deterministic():
 
 @pytest.mark.parametrize("sp,fp,score_tol", [
     ("bf16", "f32", 2e-2), ("f32", "bf16x3", 1e-4), ("bf16x3", "bf16x3", 1e-4),
-    ("bf16", "bf16x3", 2e-2)])
+    ("bf16", "bf16x3", 2e-2), ("fp8", "bf16x3", 0.25)])
 def test_haar_tensor_core_paths(sp, fp, score_tol):
     """Tensor-core sketch and/or fit.  The relative error stays within 1e-3 of
     the FP64 oracle's (the benchmark's accuracy gate) and the returned factors

@@ -169,3 +169,42 @@ def test_tc_gemm_split_precision(tA, tB):
     # hi/lo carries 16 mantissa bits; the dropped lo*lo term and the FP32
     # accumulation leave a Frobenius-relative error near 2^-17.
     assert _rel(got, ref) < 3e-5
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 512, 256), (300, 520, 200), (60, 4096, 384), (1000, 136, 328)])
+def test_tc_gemm_fp8_exact(M, N, K):
+    """FP8 e4m3 operands (kind::f8f6f4, both K-major): small integers are exact
+    in e4m3 and their products and sums exact in FP32, so the result must equal
+    the FP64 product bit for bit.  Other layouts are refused (ENOTSUP)."""
+    import ctypes
+
+    import paper_1703_06065_gb300 as pkg
+
+    device()
+    f8 = getattr(torch, "float8_e4m3fn", None)
+    if f8 is None:
+        pytest.skip("torch without float8_e4m3fn")
+    rg = np.random.default_rng(M * 3 + N + K)
+    A = rg.integers(-8, 9, size=(M, K)).astype(np.float32)
+    B = rg.integers(-8, 9, size=(N, K)).astype(np.float32)   # B^T stored: K-major
+    def pad16(X):
+        cols = (X.shape[1] + 15) // 16 * 16
+        Y = np.zeros((X.shape[0], cols), dtype=np.float32)
+        Y[:, :X.shape[1]] = X
+        return torch.from_numpy(Y).to(f8).cuda()
+    Ad, Bd = pad16(A), pad16(B)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    D = torch.zeros(M, (N + 3) // 4 * 4, dtype=torch.float32, device="cuda")
+    L = pkg.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = L.bcur_gemm(M, N, K, ctypes.c_void_p(Ad.data_ptr()), Ad.shape[1], 0,
+                     ctypes.c_void_p(Bd.data_ptr()), Bd.shape[1], 1, ctypes.c_void_p(D.data_ptr()),
+                     D.shape[1], 5, 5, stream)
+    assert st == 0, pkg._lib.STATUS.get(st)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(D[:, :N].double().cpu().numpy(), ref)
+    # an MN-major operand is refused rather than read wrongly
+    st = L.bcur_gemm(M, N, K, ctypes.c_void_p(Ad.data_ptr()), Ad.shape[1], 0,
+                     ctypes.c_void_p(Bd.data_ptr()), Bd.shape[1], 0, ctypes.c_void_p(D.data_ptr()),
+                     D.shape[1], 5, 5, stream)
+    assert st == 7
