@@ -553,10 +553,14 @@ def batch_kernel_model(label: str, probs, items, lp: int = 64):
         return "hbm", byt, "bytes"
     if label == "split":
         return "hbm", 8.0 * mn + sum(4 * p.n * p.l + 2 * 64 * p.n for p in probs), "bytes"
-    if label in ("w_gemm", "residual"):
+    if label == "w_gemm":
         fl = sum(3 * 2.0 * p.m * p.n * (-(-it["g_row"] * it["block"] // 64) * 64)
                  for p, it in zip(probs, items))
         return "tensor", fl, "flop"
+    if label == "residual":
+        # one BF16 term (the refinement launch exits at once at these errors):
+        # A read once in FP32 is the bound
+        return "hbm", 4.0 * mn, "bytes"
     return None, None, None
 
 
@@ -699,6 +703,14 @@ def main_batched(args):
                         achieved=round(achieved, 3), peak=round(peak, 3),
                         frac=round(achieved / peak, 4), traffic=None, ms=round(per_launch_ms, 4),
                         algorithmic=f"{amount:.4g} {unit} per launch (model in bench.py)")
+            # DRAM traffic of this kernel kind from its committed ncu capture,
+            # valid while the kernel sources are the ones it was taken on
+            tpath = os.path.join(ROOT, "profiles", f"batched_{dom}_traffic.json")
+            if os.path.exists(tpath) and len(probs) == BATCH_COUNT:
+                tr = json.load(open(tpath))
+                if all(tr.get("sha256", {}).get(f) == _sha(f) for f in tr.get("sha256", {})):
+                    roof["traffic"] = tr["bytes_per_launch"]
+                    roof["traffic_source"] = os.path.relpath(tpath, ROOT)
 
     # -- sampled accuracy gate: the FP64 oracle on random members ---------
     gate, cpu = None, None
@@ -827,6 +839,52 @@ def main_serving(args):
         print(json.dumps(line), flush=True)
 
 
+def _sha(rel: str) -> str:
+    import hashlib
+
+    return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()
+
+
+# ---------------------------------------------------------------------------
+# Kernel-only mode: one tensor-core GEMM of the fit, for profiling
+# ---------------------------------------------------------------------------
+def main_kernel(args):
+    """W = A Q_R as the fit computes it (split BF16, three terms) on random
+    operands of the given shape, timed with CUDA events; prints one JSON line."""
+    import torch
+
+    import paper_1703_06065_gb300 as pkg
+
+    m, n, r = (int(x) for x in args.shape.split(","))
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    A = torch.randn(m, n, device=dev, generator=g)
+    Ah = A.to(torch.bfloat16)
+    Al = (A - Ah.float()).to(torch.bfloat16)
+    del A
+    Q = torch.randn(r, n, device=dev, generator=g) / float(np.sqrt(n))
+    Qh = Q.to(torch.bfloat16)
+    Ql = (Q - Qh.float()).to(torch.bfloat16)
+    del Q
+    W = torch.empty(m, r, device=dev)
+    for _ in range(args.warmup):
+        pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=W)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_timed")
+    e0.record()
+    for _ in range(args.steps):
+        pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=W)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"kernel": "tc_gemm_kernel<256, BF16, store> split BF16 (3 terms)",
+                      "m": m, "n": n, "r": r, "ms": ms,
+                      "bf16_mma_tflops": 3 * 2.0 * m * n * r / (ms * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -844,12 +902,17 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0,
                     help="serving: seconds of arrivals (the full workload is 60)")
     ap.add_argument("--hbm-budget", type=float, default=160e9, help="serving: admission budget")
+    ap.add_argument("--kernel", default=None, choices=["wgemm"],
+                    help="time one kernel instead of the workload (profiling)")
+    ap.add_argument("--shape", default="32768,32768,8192", help="kernel mode: m,n,r")
     ap.add_argument("--no-graph", action="store_true",
                     help="batched workload: launch eagerly instead of replaying a CUDA graph")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.kernel:
+        main_kernel(args)
+    elif args.impl == "reference":
         main_reference(args)
     elif args.workload == "batched_biometric":
         main_batched(args)
