@@ -337,10 +337,10 @@ template <int BN, int EPI> struct StageCfg {
   static constexpr int kStageBBytes = BN * 128;
   static constexpr int kStageBytes = kStageABytes + kStageBBytes;
   // 192 KB of stages; the residual keeps 160 KB and gives the rest to its
-  // eight per-warp 32 x 36 transpose tiles
+  // eight per-warp 32 x 36 transpose tiles (four for the store epilogue)
   static constexpr int kStages = (EPI == 2 ? 163840 : 196608) / kStageBytes;
   static constexpr int kTmemCols = 2 * BN;
-  static constexpr int kStageOut = EPI == 2 ? 8 * 32 * 36 * 4 : 4 * 32 * 33 * 4;
+  static constexpr int kStageOut = (EPI == 2 ? 8 : 4) * 32 * 36 * 4;
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 512 + kStageOut;
 };
 
@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
       const float alpha = P->alpha;
       const int64_t ldx = P->ldx;
       const int rbase = w.m0 + quarter * 32;
-      const bool vec_ok = ((reinterpret_cast<uintptr_t>(P->X) & 15) == 0) && (ldx % 4 == 0);
+      const float* const Xp = P->X;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(Xp) & 15) == 0) && (ldx % 4 == 0);
       // rows rbase + lr + 4 i (i < 8), columns col0 + lc .. + 3
       auto load_x = [&](float4 (&xv)[8], int col0) {
         const int col = col0 + lc;
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
           const int row = rbase + lr + 4 * i;
           float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
           if (row < Mm) {
-            const float* xr = P->X + (int64_t)row * ldx + col;
+            const float* xr = Xp + (int64_t)row * ldx + col;
             // read once: stream past L1 so the GEMM table and parameters stay cached
             if (vec_ok && col + 4 <= Nm) {
               q = __ldcs(reinterpret_cast<const float4*>(xr));
@@ -679,9 +680,21 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
       const float alpha = P->alpha, beta = P->beta;
       const int tri_out = P->tri_out;
       const int64_t ldd = P->ldd;
+      // Every parameter the chunk loop needs is read here, once per tile: P
+      // points into parameter (or table) memory that the compiler cannot tell
+      // apart from D, so a read inside the loop would be repeated after every
+      // store and serialise the row loop on its latency.
+      const int transD = P->transD;
+      const float* const scale_m = P->scale_m;
+      const float* const scale_n = P->scale_n;
       float* const Dp = P->D ? P->D + (int64_t)w.b * P->sD : nullptr;
       __nv_bfloat16* const Dhp = P->Dh ? P->Dh + (int64_t)w.b * P->sD : nullptr;
       __nv_bfloat16* const Dlp = P->Dl ? P->Dl + (int64_t)w.b * P->sD : nullptr;
+      const float sm_lane = (scale_m && row_ok) ? scale_m[row] : 1.f;  // row scale of this lane
+      // four-wide stores need 16-byte rows (8-byte for the BF16 pair)
+      const bool vec_ok = (ldd % 4 == 0) && ((reinterpret_cast<uintptr_t>(Dp) & 15) == 0) &&
+                          ((reinterpret_cast<uintptr_t>(Dhp) & 7) == 0) &&
+                          ((reinterpret_cast<uintptr_t>(Dlp) & 7) == 0);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
@@ -695,8 +708,20 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
         const int col0 = w.n0 + c0;
         if (col0 >= Nm) continue;
         if constexpr (EPI == EPI_STORE) {
-          if (P->transD) {
+          constexpr unsigned FULL = 0xffffffffu;
+          // alpha and the scales are applied while the warp is converged (the
+          // scale of the other index is shuffled), and the old values of D are
+          // loaded before the first store.
+          const float sn_lane = (scale_n && col0 + lane < Nm) ? scale_n[col0 + lane] : 1.f;
+          if (transD) {
             // D^T: lane = row, consecutive lanes write consecutive addresses.
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              float o = alpha * v[i];
+              if (scale_m) o *= sm_lane;
+              if (scale_n) o *= __shfl_sync(FULL, sn_lane, i);
+              v[i] = o;
+            }
             if (!row_ok) continue;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
@@ -705,9 +730,7 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
               if (tri_out == 1 && row < col) continue;
               if (tri_out == 2 && row > col) continue;
               const int64_t off = (int64_t)col * ldd + row;
-              float o = alpha * v[i];
-              if (P->scale_m) o *= P->scale_m[row];
-              if (P->scale_n) o *= P->scale_n[col];
+              float o = v[i];
               if (beta != 0.f) o = fmaf(beta, Dp[off], o);
               if (Dp) Dp[off] = o;
               if (Dhp) {
@@ -717,40 +740,98 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
               }
             }
           } else {
-            // Row-major D: transpose the 32 x 32 chunk through shared memory
-            // so that each store instruction writes one contiguous row piece.
-            float* t = stage_out + (warp - 2) * (32 * 33);
+            // Row-major D: the 32 x 32 chunk goes through a per-warp 32 x 36
+            // shared tile (t[row * 36 + col]).  A chunk that is whole (inside
+            // D, and wholly on the kept side of the diagonal) is written four
+            // columns per lane: lane (lr, lc) takes columns lc..lc+3 of rows
+            // lr + 4 i, so each store instruction writes four 128-byte row
+            // pieces (a quarter of the instructions of one column per lane,
+            // which is what bounds a short-K tile).  Other chunks: one column
+            // per lane with per-element masks.
+            float* t = stage_out + (warp - 2) * (32 * 36);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
+            for (int q = 0; q < 8; ++q)
+              *reinterpret_cast<float4*>(&t[lane * 36 + 4 * q]) =
+                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             __syncwarp();
-            const int col = col0 + lane;
             const int rbase = w.m0 + quarter * 32;
-            const bool col_ok = col < Nm;
-            float old[32];
-            if (beta != 0.f) {  // all loads issued before any use
+            const bool whole = vec_ok && rbase + 32 <= Mm && col0 + 32 <= Nm &&
+                               (tri_out == 0 || (tri_out == 1 && rbase >= col0 + 31) ||
+                                (tri_out == 2 && rbase + 31 <= col0));
+            if (whole) {
+              const int lr = lane >> 3, lc = (lane & 7) * 4;
+              const int col = col0 + lc;
+              float4 a[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                a[i] = *reinterpret_cast<const float4*>(&t[(lr + 4 * i) * 36 + lc]);
+              float sn[4] = {1.f, 1.f, 1.f, 1.f};
+              if (scale_n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sn[j] = scale_n[col + j];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float sm = scale_m ? scale_m[rbase + lr + 4 * i] : 1.f;
+                float* e = &a[i].x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  float o = alpha * e[j];
+                  if (scale_m) o *= sm;
+                  if (scale_n) o *= sn[j];
+                  e[j] = o;
+                }
+              }
+              if (beta != 0.f) {  // all loads issued before any store
+                float4 old[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                  old[i] = *reinterpret_cast<const float4*>(
+                      Dp + (int64_t)(rbase + lr + 4 * i) * ldd + col);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  a[i].x = fmaf(beta, old[i].x, a[i].x);
+                  a[i].y = fmaf(beta, old[i].y, a[i].y);
+                  a[i].z = fmaf(beta, old[i].z, a[i].z);
+                  a[i].w = fmaf(beta, old[i].w, a[i].w);
+                }
+              }
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int64_t off = (int64_t)(rbase + lr + 4 * i) * ldd + col;
+                if (Dp) *reinterpret_cast<float4*>(Dp + off) = a[i];
+                if (Dhp) {
+                  const float* e = &a[i].x;
+                  __nv_bfloat16 h[4], l[4];
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    h[j] = __float2bfloat16_rn(e[j]);
+                    l[j] = __float2bfloat16_rn(e[j] - __bfloat162float(h[j]));
+                  }
+                  *reinterpret_cast<uint2*>(Dhp + off) = *reinterpret_cast<const uint2*>(h);
+                  if (Dlp) *reinterpret_cast<uint2*>(Dlp + off) = *reinterpret_cast<const uint2*>(l);
+                }
+              }
+            } else {
+              const int col = col0 + lane;
+              const bool col_ok = col < Nm;
 #pragma unroll
               for (int r = 0; r < 32; ++r) {
                 const int grow = rbase + r;
-                old[r] = (col_ok && grow < Mm) ? Dp[(int64_t)grow * ldd + col] : 0.f;
-              }
-            }
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-              const int grow = rbase + r;
-              bool ok = col_ok && grow < Mm;
-              if (tri_out == 1 && grow < col) ok = false;
-              if (tri_out == 2 && grow > col) ok = false;
-              if (ok) {
-                const int64_t off = (int64_t)grow * ldd + col;
-                float o = alpha * t[r * 33 + lane];
-                if (P->scale_m) o *= P->scale_m[grow];
-                if (P->scale_n) o *= P->scale_n[col];
-                if (beta != 0.f) o = fmaf(beta, old[r], o);
-                if (Dp) Dp[off] = o;
-                if (Dhp) {
-                  const __nv_bfloat16 h = __float2bfloat16_rn(o);
-                  Dhp[off] = h;
-                  if (Dlp) Dlp[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+                bool ok = col_ok && grow < Mm;
+                if (tri_out == 1 && grow < col) ok = false;
+                if (tri_out == 2 && grow > col) ok = false;
+                float o = alpha * t[r * 36 + lane];  // row rbase + r, column col
+                if (scale_m) o *= __shfl_sync(FULL, sm_lane, r);
+                if (scale_n) o *= sn_lane;
+                if (ok) {
+                  const int64_t off = (int64_t)grow * ldd + col;
+                  if (beta != 0.f) o = fmaf(beta, Dp[off], o);
+                  if (Dp) Dp[off] = o;
+                  if (Dhp) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(o);
+                    Dhp[off] = h;
+                    if (Dlp) Dlp[off] = __float2bfloat16_rn(o - __bfloat162float(h));
+                  }
                 }
               }
             }
