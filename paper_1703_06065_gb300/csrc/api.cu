@@ -485,13 +485,17 @@ bcur_status_t g16_on(bcur_plan_t P, const Lane& ln, GemmDesc d, int parts) {
 bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) { return g16_on(P, lane_of(P, 0), d, parts); }
 
 // Blocked Cholesky G = L L^T (w x w, FP32, lower part) and L^{-1}.  Two
-// levels: outer panels of kOuter columns whose trailing update is one large
-// tensor-core GEMM (K = kOuter), and inside each outer panel leaves of nb
-// columns (FP32 diagonal factorisation and panel solve on CUDA cores, the
+// levels: outer panels whose trailing update is one large tensor-core GEMM
+// (K = the panel width), and inside each outer panel steps of nb = 64
+// columns.  With w a multiple of 64 a step is one launch, left-looking inside
+// the outer panel (chol_step: exact FP32 products, outer panels of
+// kOuterStep columns); otherwise the right-looking order with kOuter-wide
+// panels (FP32 diagonal factorisation and panel solve on CUDA cores, the
 // update of the rest of the outer panel on tensor cores).  The inverse is
 // assembled by doubling (X21 = -X22 L21 X11) on tensor cores.  Tensor-core
 // products use `parts` BF16 terms.
 constexpr int64_t kOuter = 1024;
+constexpr int64_t kOuterStep = 512;
 
 bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float* L, float* Li,
                                  int64_t w, int parts, int* kept, double tol) {
@@ -510,9 +514,13 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float*
   BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(float), s));
   BCUR_TRY(fill_zero(kept, sizeof(int), s));
   BCUR_TRY(max_diag<float>(G, w, w, md, s));
-  for (int64_t J0 = 0; J0 < w; J0 += kOuter) {
-    const int64_t J1 = std::min(w, J0 + kOuter);
-    for (int64_t j0 = J0; j0 < J1; j0 += nb) {
+  const bool step = nb == 64 && w % 64 == 0;
+  const int64_t outer = step ? kOuterStep : kOuter;
+  for (int64_t J0 = 0; J0 < w; J0 += outer) {
+    const int64_t J1 = std::min(w, J0 + outer);
+    for (int64_t j0 = J0; step && j0 < J1; j0 += nb)
+      BCUR_TRY(chol_step(G, w, L, Li, J0, j0, md, tol, kept, s));
+    for (int64_t j0 = J0; !step && j0 < J1; j0 += nb) {
       BCUR_TRY(potrf_diag<float>(G, w, L, w, Li, w, j0, nb, md, tol, kept, s));
       const int64_t j1 = j0 + nb;
       if (j1 >= w) break;

@@ -130,6 +130,10 @@ bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t 
 template <typename T>
 bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t ldi, int64_t j0,
                          int nb, const T* maxdiag, double tol_rel, int* kept, cudaStream_t s);
+// One left-looking 64-column step of the blocked FP32 Cholesky (see small.cu):
+// L[j0:, j0:j0+64] and Linv's diagonal block from G and L[:, J0:j0].
+bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_t J0, int64_t j0,
+                        const float* maxdiag, double tol_rel, int* kept, cudaStream_t s);
 
 // Block leverage scores from a panel F^T (k x h).
 template <typename T>

@@ -247,23 +247,17 @@ __device__ int warp_chol32(T* A, int lda, T* Xo, int ldx, T tol) {
 // The 64 x 64 leaf in FP32 from two warp-level 32 x 32 factorisations:
 //   L11 = chol(G11), X11 = L11^{-1};  L21 = G21 X11^T;
 //   L22 = chol(G22 - L21 L21^T), X22 = L22^{-1};  X21 = -X22 (L21 X11).
-// Same contract as the generic potrf_leaf (S = L, X = L^{-1}, LD = 68,
-// threads 0..255 work).  A dropped pivot of L11 zeroes its column of L21, so
-// the update of G22 is unaffected by it, as in the unblocked order.
-template <>
-__device__ inline int potrf_leaf<float, 64>(const float* G, int64_t ldg, float* S, float* X,
-                                            float tol) {
-  constexpr int NB = 64, LD = 68, H = 32;
+// leaf64_core starts from the block already in shared memory (S: lower part,
+// zeros above the diagonal, LD = 68; X: zeros) after a block barrier; it
+// leaves S = L and X = L^{-1} (threads 0..255 work, all must call it).  A
+// dropped pivot of L11 zeroes its column of L21, so the update of G22 is
+// unaffected by it, as in the unblocked order.
+__device__ inline int leaf64_core(float* S, float* X, float tol) {
+  constexpr int LD = 68, H = 32;
   const int tid = threadIdx.x;
   const bool act = tid < 256;
   const int warp = tid >> 5;
   __shared__ int s_kept;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, c = e % NB;
-    S[i * LD + c] = (c <= i) ? G[(int64_t)i * ldg + c] : 0.f;
-    X[i * LD + c] = 0.f;
-  }
-  __syncthreads();
   int k1 = 0;
   if (warp == 0) k1 = warp_chol32<float>(S, LD, X, LD, tol);
   __syncthreads();
@@ -329,6 +323,31 @@ __device__ inline int potrf_leaf<float, 64>(const float* G, int64_t ldg, float* 
     for (int q = 0; q < 4; ++q) X[(H + i) * LD + c4 + q] = acc[q];
   __syncthreads();
   return s_kept;
+}
+
+// Same contract as the generic potrf_leaf (S = L, X = L^{-1}, LD = 68).  The
+// block is loaded with all of a thread's reads in flight at once.
+template <>
+__device__ inline int potrf_leaf<float, 64>(const float* G, int64_t ldg, float* S, float* X,
+                                            float tol) {
+  constexpr int NB = 64, LD = 68;
+  const int tid = threadIdx.x;
+  if (tid < 256) {
+    float g[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, i = e / NB, c = e % NB;
+      g[q] = (c <= i) ? G[(int64_t)i * ldg + c] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, i = e / NB, c = e % NB;
+      S[i * LD + c] = g[q];
+      X[i * LD + c] = 0.f;
+    }
+  }
+  __syncthreads();
+  return leaf64_core(S, X, tol);
 }
 
 // ---------------------------------------------------------------------------

@@ -358,6 +358,160 @@ bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// One 64-column step of the blocked Cholesky G = L L^T (FP32, w x w, ld w,
+// w a multiple of 64), left-looking inside the outer panel that starts at
+// column J0 (the columns J0.. of G already carry the updates of the earlier
+// outer panels).  With j1 = j0 + 64 and K = j0 - J0:
+//   D  = G[j0:j1, j0:j1] - L[j0:j1, J0:j0] L[j0:j1, J0:j0]^T
+//   L_jj = chol(D) with the drop rule, X = L_jj^{-1}        (leaf64_core)
+//   L[R, j0:j1] = (G[R, j0:j1] - L[R, J0:j0] L[j0:j1, J0:j0]^T) X^T
+// for the 64-row blocks R below j1.  CTA b handles rows j0 + 64 b; every CTA
+// factors D itself (the same arithmetic in each, so every copy of X is the
+// same), CTA 0 writes L_jj and X into L and Linv and adds its kept pivots.
+// One launch per step replaces the leaf, panel solve, split and inner
+// trailing update of the right-looking order; the products are exact FP32.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kStepLD = 68;   // leaf tiles S and X
+constexpr int kStepKC = 32;   // K chunk of the products
+constexpr int kStepALD = 33;  // product tiles (row-major, 32 + 1)
+
+// acc += A B^T for 64 x 64 outputs, A = rows of Ab, B = rows of Bb (row
+// major, ld), K a multiple of 32.  Thread (ty, tx) = (tid / 16, tid % 16)
+// holds rows ty + 16 a and columns tx + 16 b.  The next K chunk is loaded
+// into registers while the current one is multiplied.
+__device__ void step_prod64(const float* Ab, const float* Bb, int64_t ld, int K, float (&acc)[4][4],
+                            float* As, float* Bs) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  if (K <= 0) return;
+  float ra[8], rb[8];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q, r = e >> 5, c = e & 31;
+      ra[q] = Ab[(int64_t)r * ld + k0 + c];
+      rb[q] = Bb[(int64_t)r * ld + k0 + c];
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < K; k0 += kStepKC) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q, r = e >> 5, c = e & 31;
+      As[r * kStepALD + c] = ra[q];
+      Bs[r * kStepALD + c] = rb[q];
+    }
+    __syncthreads();
+    if (k0 + kStepKC < K) fetch(k0 + kStepKC);
+#pragma unroll 8
+    for (int k = 0; k < kStepKC; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[(ty + 16 * i) * kStepALD + k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[(tx + 16 * j) * kStepALD + k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t w, float* L,
+                                                        float* Linv, int64_t J0, int64_t j0,
+                                                        const float* maxdiag, double tol_rel,
+                                                        int* kept) {
+  extern __shared__ float step_smem[];
+  float* S = step_smem;                     // 64 x 68: D, then L_jj
+  float* X = S + 64 * kStepLD;              // 64 x 68: L_jj^{-1}
+  float* As = X + 64 * kStepLD;             // 64 x 33
+  float* Bs = As + 64 * kStepALD;           // 64 x 33
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int K = (int)(j0 - J0);
+  const float tol = (float)(tol_rel * (double)(*maxdiag));
+  const float* Ljj = L + j0 * w + J0;       // rows j0.., columns J0..j0
+  // D, every CTA
+  float acc[4][4] = {};
+  step_prod64(Ljj, Ljj, w, K, acc, As, Bs);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      S[r * kStepLD + c] = (c <= r) ? G[(j0 + r) * w + j0 + c] - acc[i][j] : 0.f;
+      X[r * kStepLD + c] = 0.f;
+    }
+  __syncthreads();
+  const int nk = leaf64_core(S, X, tol);
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < 64 * 64; e += 256) {
+      const int r = e >> 6, c = e & 63;
+      L[(j0 + r) * w + j0 + c] = (c <= r) ? S[r * kStepLD + c] : 0.f;
+      Linv[(j0 + r) * w + j0 + c] = (c <= r) ? X[r * kStepLD + c] : 0.f;
+    }
+    if (tid == 0) atomicAdd(kept, nk);
+    return;
+  }
+  // the panel rows of this CTA
+  const int64_t r0 = j0 + 64 * (int64_t)blockIdx.x;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  step_prod64(L + r0 * w + J0, Ljj, w, K, acc, As, Bs);
+  float* Pt = As;  // 64 x 65 (spans As and Bs), P = G[R, j0:j1] - acc
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      Pt[r * 65 + c] = G[(r0 + r) * w + j0 + c] - acc[i][j];
+    }
+  __syncthreads();
+  // L[R, j0:j1] = P X^T (X lower: X[c][t] = 0 for t > c)
+  float o[4][4] = {};
+  for (int t = 0; t < 64; ++t) {
+    float a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = Pt[(ty + 16 * i) * 65 + t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = X[(tx + 16 * j) * kStepLD + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[i][j] = fmaf(a[i], b[j], o[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) L[(r0 + ty + 16 * i) * w + j0 + tx + 16 * j] = o[i][j];
+}
+
+size_t chol_step_smem() {
+  return (size_t)(2 * 64 * kStepLD + 2 * 64 * kStepALD) * sizeof(float);
+}
+
+bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_t J0, int64_t j0,
+                        const float* maxdiag, double tol_rel, int* kept, cudaStream_t s) {
+  if (w % 64 != 0 || j0 % 64 != 0 || J0 > j0 || (j0 - J0) % 64 != 0 || j0 + 64 > w)
+    return BCUR_EINVAL;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BCUR_CUDA_TRY(cudaFuncSetAttribute(chol_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)chol_step_smem()));
+    attr_set = true;
+  }
+  const unsigned blocks = (unsigned)((w - j0) / 64);
+  chol_step_kernel<<<blocks, 256, chol_step_smem(), s>>>(G, w, L, Linv, J0, j0, maxdiag, tol_rel,
+                                                        kept);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Block leverage scores (Def. 2): one CTA per block, FP64 accumulation in a
 // fixed order (strided per thread, xor-tree per warp, warps in order).
 // ---------------------------------------------------------------------------
