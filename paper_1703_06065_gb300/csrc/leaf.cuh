@@ -183,62 +183,82 @@ __device__ int potrf_leaf(const T* G, int64_t ldg, T* S, T* X, T tol) {
 }
 
 // ---------------------------------------------------------------------------
-// One warp: Cholesky with the drop rule and the inverse of a 32 x 32 block
-// held in shared memory (lower part of A, ld lda; factored in place, zeros
-// written above the diagonal).  Lane i owns row i in registers as a window
-// that slides one column per step: at step j, a[t] holds entry (i, j + t), so
-// the register indices stay compile-time constants while the step loop stays
-// rolled (one warp runs this once; unrolling the steps would make it bound on
-// instruction fetch).  Step j: pivot from lane j by shuffle (drop rule: <= tol
-// or <= 0), scale the column, update the row with l_{j+t, j} shuffled from
-// lane j + t.  L^{-1} by forward substitution, one column per lane, with the
-// same sliding window on the right-hand side: x_k = b_k / L_kk, then
-// b_i -= L_ik x_k for i > k.  A dropped pivot zeroes its column of L and its
-// row of L^{-1}.  Returns the number of kept pivots (same in every lane).
+// One warp: Cholesky with the drop rule and the inverse of a 32 x 32 FP32
+// block held in shared memory (lower part of A, ld lda; factored in place,
+// zeros written above the diagonal).  Lane i owns row i in registers as a
+// window that slides one column per step: at step j, a[t] holds entry
+// (i, j + t), so the register indices stay compile-time constants while the
+// step loop stays rolled (unrolling the steps would make it bound on
+// instruction fetch).  Step j: pivot d from lane j by shuffle; drop rule
+// d <= tol or d <= 0; r = 1/sqrt(d) (rsqrtf), L_jj = d r, l_ij = a_ij r.
+// Column j is also written to cb row j, shifted (cb[j][t] = L[j + t][j], zero
+// past the block), so that the update a[t] -= l_i l_{j+t} reads it with eight
+// broadcast float4 loads.  Entries above the diagonal are updated too (their
+// lanes carry l = 0 from then on, so they never feed back; A gets zeros
+// there).  L^{-1} by forward substitution, one column per lane, with the same
+// sliding window: x_k = b_k r_k, then b_{k+t} -= L[k+t][k] x_k from cb row k.
+// A dropped pivot zeroes its column of L and its row of L^{-1}.  cb: 32 x 36
+// + 32 floats of shared scratch for this warp.  Returns the number of kept
+// pivots (same in every lane).
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ int warp_chol32(T* A, int lda, T* Xo, int ldx, T tol) {
+__device__ inline int warp_chol32(float* A, int lda, float* Xo, int ldx, float tol, float* cb) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int CL = 36;
+  float* rp = cb + 32 * CL;  // 1 / L_jj (0 when dropped)
   const int lane = threadIdx.x & 31;
-  T a[32];
+  float a[32];
 #pragma unroll
-  for (int t = 0; t < 32; ++t) a[t] = (t <= lane) ? A[lane * lda + t] : T(0);
+  for (int t = 0; t < 32; ++t) a[t] = (t <= lane) ? A[lane * lda + t] : 0.f;
   __syncwarp();
   int kept = 0;
 #pragma unroll 1
   for (int j = 0; j < 32; ++j) {
-    const T d = __shfl_sync(FULL, a[0], j);
-    const T p = (d > tol && d > T(0)) ? sqrt(d) : T(0);
-    const T inv = (p > T(0)) ? T(1) / p : T(0);
-    kept += (p > T(0)) ? 1 : 0;
-    const T l = (lane > j) ? a[0] * inv : ((lane == j) ? p : T(0));
+    const float d = __shfl_sync(FULL, a[0], j);
+    const bool keep = d > tol && d > 0.f;
+    const float r = keep ? rsqrtf(d) : 0.f;
+    kept += keep ? 1 : 0;
+    const float l = (lane > j) ? a[0] * r : ((lane == j) ? d * r : 0.f);
     A[lane * lda + j] = l;
+    cb[j * CL + ((lane - j) & 31)] = (lane >= j) ? l : 0.f;
+    if (lane == 0) rp[j] = r;
+    __syncwarp();
+    float wv[32];
 #pragma unroll
-    for (int t = 1; t < 32; ++t) {
-      const T lkj = __shfl_sync(FULL, l, (j + t) & 31);
-      if (j + t <= lane) a[t] = fma(-l, lkj, a[t]);
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(&cb[j * CL + 4 * q]);
+      wv[4 * q] = v.x;
+      wv[4 * q + 1] = v.y;
+      wv[4 * q + 2] = v.z;
+      wv[4 * q + 3] = v.w;
     }
+#pragma unroll
+    for (int t = 1; t < 32; ++t) a[t] = fmaf(-l, wv[t], a[t]);
 #pragma unroll
     for (int t = 0; t < 31; ++t) a[t] = a[t + 1];
-    a[31] = T(0);
+    a[31] = 0.f;
   }
   __syncwarp();
-  T b[32];
+  float b[32];
 #pragma unroll
-  for (int t = 0; t < 32; ++t) b[t] = (t == lane) ? T(1) : T(0);
+  for (int t = 0; t < 32; ++t) b[t] = (t == lane) ? 1.f : 0.f;
 #pragma unroll 1
   for (int k = 0; k < 32; ++k) {
-    const T lkk = A[k * lda + k];
-    const T xk = (lkk > T(0)) ? b[0] / lkk : T(0);
+    const float xk = b[0] * rp[k];
     Xo[k * ldx + lane] = xk;
+    float wv[32];
 #pragma unroll
-    for (int t = 1; t < 32; ++t) {
-      const T lik = (k + t < 32) ? A[(k + t) * lda + k] : T(0);
-      b[t] = fma(-lik, xk, b[t]);
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(&cb[k * CL + 4 * q]);
+      wv[4 * q] = v.x;
+      wv[4 * q + 1] = v.y;
+      wv[4 * q + 2] = v.z;
+      wv[4 * q + 3] = v.w;
     }
 #pragma unroll
+    for (int t = 1; t < 32; ++t) b[t] = fmaf(-wv[t], xk, b[t]);
+#pragma unroll
     for (int t = 0; t < 31; ++t) b[t] = b[t + 1];
-    b[31] = T(0);
+    b[31] = 0.f;
   }
   __syncwarp();
   return kept;
@@ -258,8 +278,9 @@ __device__ inline int leaf64_core(float* S, float* X, float tol) {
   const bool act = tid < 256;
   const int warp = tid >> 5;
   __shared__ int s_kept;
+  __shared__ __align__(16) float s_cb[32 * 36 + 32];
   int k1 = 0;
-  if (warp == 0) k1 = warp_chol32<float>(S, LD, X, LD, tol);
+  if (warp == 0) k1 = warp_chol32(S, LD, X, LD, tol, s_cb);
   __syncthreads();
   // L21 = G21 X11^T: 4 outputs per thread (row i, columns c4..c4+3)
   const int i = (tid >> 3) & 31, c4 = (tid & 7) * 4;
@@ -289,7 +310,7 @@ __device__ inline int leaf64_core(float* S, float* X, float tol) {
   }
   __syncthreads();
   int k2 = 0;
-  if (warp == 0) k2 = warp_chol32<float>(S + H * LD + H, LD, X + H * LD + H, LD, tol);
+  if (warp == 0) k2 = warp_chol32(S + H * LD + H, LD, X + H * LD + H, LD, tol, s_cb);
   if (tid == 0) s_kept = k1 + k2;
   __syncthreads();
   // T = L21 X11 (X11 lower: t >= c), kept in X21's place for now

@@ -372,14 +372,14 @@ bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t 
 // trailing update of the right-looking order; the products are exact FP32.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kStepLD = 68;   // leaf tiles S and X
+constexpr int kStepLD = 68;   // leaf tiles S and X; k-major product tiles
 constexpr int kStepKC = 32;   // K chunk of the products
-constexpr int kStepALD = 33;  // product tiles (row-major, 32 + 1)
 
-// acc += A B^T for 64 x 64 outputs, A = rows of Ab, B = rows of Bb (row
-// major, ld), K a multiple of 32.  Thread (ty, tx) = (tid / 16, tid % 16)
-// holds rows ty + 16 a and columns tx + 16 b.  The next K chunk is loaded
-// into registers while the current one is multiplied.
+// acc += A B^T for 64 x 64 outputs, A = 64 rows of Ab, B = 64 rows of Bb (row
+// major, ld), K a multiple of 32.  The K chunk goes to shared memory k-major
+// (As[k][row], ld 68) so that thread (ty, tx) = (tid / 16, tid % 16), which
+// holds rows 4 ty.. and columns 4 tx.., reads two float4 per k.  The next
+// chunk is loaded into registers while the current one is multiplied.
 __device__ void step_prod64(const float* Ab, const float* Bb, int64_t ld, int K, float (&acc)[4][4],
                             float* As, float* Bs) {
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -398,22 +398,20 @@ __device__ void step_prod64(const float* Ab, const float* Bb, int64_t ld, int K,
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int e = tid + 256 * q, r = e >> 5, c = e & 31;
-      As[r * kStepALD + c] = ra[q];
-      Bs[r * kStepALD + c] = rb[q];
+      As[c * kStepLD + r] = ra[q];
+      Bs[c * kStepLD + r] = rb[q];
     }
     __syncthreads();
     if (k0 + kStepKC < K) fetch(k0 + kStepKC);
 #pragma unroll 8
     for (int k = 0; k < kStepKC; ++k) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[(ty + 16 * i) * kStepALD + k];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[(tx + 16 * j) * kStepALD + k];
+      const float4 a = *reinterpret_cast<const float4*>(&As[k * kStepLD + 4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[k * kStepLD + 4 * tx]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -424,11 +422,11 @@ __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t 
                                                         float* Linv, int64_t J0, int64_t j0,
                                                         const float* maxdiag, double tol_rel,
                                                         int* kept) {
-  extern __shared__ float step_smem[];
-  float* S = step_smem;                     // 64 x 68: D, then L_jj
+  extern __shared__ __align__(16) float step_smem[];
+  float* S = step_smem;                     // 64 x 68: D, then L_jj; then X^T
   float* X = S + 64 * kStepLD;              // 64 x 68: L_jj^{-1}
-  float* As = X + 64 * kStepLD;             // 64 x 33
-  float* Bs = As + 64 * kStepALD;           // 64 x 33
+  float* As = X + 64 * kStepLD;             // 32 x 68 (k-major)
+  float* Bs = As + kStepKC * kStepLD;       // 32 x 68
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int K = (int)(j0 - J0);
   const float tol = (float)(tol_rel * (double)(*maxdiag));
@@ -437,13 +435,17 @@ __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t 
   float acc[4][4] = {};
   step_prod64(Ljj, Ljj, w, K, acc, As, Bs);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
+    const int r = 4 * ty + i;
+    const float4 g = *reinterpret_cast<const float4*>(&G[(j0 + r) * w + j0 + 4 * tx]);
+    const float gv[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int r = ty + 16 * i, c = tx + 16 * j;
-      S[r * kStepLD + c] = (c <= r) ? G[(j0 + r) * w + j0 + c] - acc[i][j] : 0.f;
+      const int c = 4 * tx + j;
+      S[r * kStepLD + c] = (c <= r) ? gv[j] - acc[i][j] : 0.f;
       X[r * kStepLD + c] = 0.f;
     }
+  }
   __syncthreads();
   const int nk = leaf64_core(S, X, tol);
   if (blockIdx.x == 0) {
@@ -462,36 +464,42 @@ __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t 
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
   step_prod64(L + r0 * w + J0, Ljj, w, K, acc, As, Bs);
-  float* Pt = As;  // 64 x 65 (spans As and Bs), P = G[R, j0:j1] - acc
+  // P^T (k-major over As and Bs, 64 x 68) and X^T (over S, no longer needed)
+  float* PT = As;
+  float* XT = S;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
+    const int r = 4 * ty + i;
+    const float4 g = *reinterpret_cast<const float4*>(&G[(r0 + r) * w + j0 + 4 * tx]);
+    const float gv[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = ty + 16 * i, c = tx + 16 * j;
-      Pt[r * 65 + c] = G[(r0 + r) * w + j0 + c] - acc[i][j];
-    }
+    for (int j = 0; j < 4; ++j) PT[(4 * tx + j) * kStepLD + r] = gv[j] - acc[i][j];
+  }
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int c = e >> 6, t = e & 63;
+    XT[t * kStepLD + c] = X[c * kStepLD + t];
+  }
   __syncthreads();
   // L[R, j0:j1] = P X^T (X lower: X[c][t] = 0 for t > c)
   float o[4][4] = {};
+#pragma unroll 8
   for (int t = 0; t < 64; ++t) {
-    float a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = Pt[(ty + 16 * i) * 65 + t];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = X[(tx + 16 * j) * kStepLD + t];
+    const float4 a = *reinterpret_cast<const float4*>(&PT[t * kStepLD + 4 * ty]);
+    const float4 b = *reinterpret_cast<const float4*>(&XT[t * kStepLD + 4 * tx]);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) o[i][j] = fmaf(a[i], b[j], o[i][j]);
+      for (int j = 0; j < 4; ++j) o[i][j] = fmaf(av[i], bv[j], o[i][j]);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) L[(r0 + ty + 16 * i) * w + j0 + tx + 16 * j] = o[i][j];
+    *reinterpret_cast<float4*>(&L[(r0 + 4 * ty + i) * w + j0 + 4 * tx]) =
+        make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
 }
 
 size_t chol_step_smem() {
-  return (size_t)(2 * 64 * kStepLD + 2 * 64 * kStepALD) * sizeof(float);
+  return (size_t)(2 * 64 * kStepLD + 2 * kStepKC * kStepLD) * sizeof(float);
 }
 
 bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_t J0, int64_t j0,
