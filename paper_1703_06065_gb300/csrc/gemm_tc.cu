@@ -53,8 +53,16 @@ constexpr int BM = 128;
 // Epilogue warps: 4 (one per TMEM lane quarter) for the store variants; 8
 // for the residual, whose epilogue streams X from HBM and needs the extra
 // loads in flight (two warps per lane quarter, each on half the columns).
-template <int EPI> __host__ __device__ constexpr int epi_warps() { return EPI == 2 ? 8 : 4; }
-template <int EPI> __host__ __device__ constexpr int threads_of() { return 64 + 32 * epi_warps<EPI>(); }
+// Epilogue warps.  The grouped residual (short K: bound by reading X) has
+// eight and gives up a pipeline stage for their transpose tiles; the
+// single-GEMM residual (long K: bound by the MMA feed) keeps four warps and
+// the fourth stage.
+template <int EPI, bool G> __host__ __device__ constexpr int epi_warps() {
+  return (EPI == 2 && G) ? 8 : 4;
+}
+template <int EPI, bool G> __host__ __device__ constexpr int threads_of() {
+  return 64 + 32 * epi_warps<EPI, G>();
+}
 constexpr int kStageABytes = BM * 128;  // 128 rows (or MN elements) x 128 bytes of K
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -333,22 +341,22 @@ __device__ __forceinline__ Unit locate(const Maps& maps, const Params& p, const 
   }
 }
 
-template <int BN, int EPI> struct StageCfg {
+template <int BN, int EPI, bool G> struct StageCfg {
   static constexpr int kStageBBytes = BN * 128;
   static constexpr int kStageBytes = kStageABytes + kStageBBytes;
-  // 192 KB of stages; the residual keeps 160 KB and gives the rest to its
-  // eight per-warp 32 x 36 transpose tiles (four for the store epilogue)
-  static constexpr int kStages = (EPI == 2 ? 163840 : 196608) / kStageBytes;
+  // 192 KB of stages and one 32 x 36 transpose tile per epilogue warp (an
+  // eight-warp residual keeps 160 KB of stages)
+  static constexpr int kStages = (epi_warps<EPI, G>() == 8 ? 163840 : 196608) / kStageBytes;
   static constexpr int kTmemCols = 2 * BN;
-  static constexpr int kStageOut = (EPI == 2 ? 8 : 4) * 32 * 36 * 4;
+  static constexpr int kStageOut = epi_warps<EPI, G>() * 32 * 36 * 4;
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 512 + kStageOut;
 };
 
 template <int BN, int KIND, int EPI, bool GROUPED>
-__global__ void __launch_bounds__(threads_of<EPI>(), 1)
+__global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
     tc_gemm_kernel(const __grid_constant__ Maps maps, const __grid_constant__ Params p,
                    const Group grp) {
-  using SC = StageCfg<BN, EPI>;
+  using SC = StageCfg<BN, EPI, GROUPED>;
   using KC = KindCfg<KIND>;
   constexpr int S = SC::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -363,7 +371,7 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(tmem_slot + 4);  // 2 per epilogue warp
   float* stage_out = reinterpret_cast<float*>(smem + S * SC::kStageBytes + 512);
-  constexpr int EW = epi_warps<EPI>();
+  constexpr int EW = epi_warps<EPI, GROUPED>();
   int* const status = GROUPED ? grp.status : p.status;
   if constexpr (!GROUPED) {
     if (p.run_flag && *p.run_flag == 0) return;  // uniform: the whole CTA leaves
@@ -641,6 +649,10 @@ __global__ void __launch_bounds__(threads_of<EPI>(), 1)
         if (lane == 0) {
           P->partials[2 * (kResidSlots * (int64_t)w.uu + ew)] = e2;
           P->partials[2 * (kResidSlots * (int64_t)w.uu + ew) + 1] = x2;
+          for (int sl = ew + EW; sl < kResidSlots; sl += EW) {  // slots no warp uses
+            P->partials[2 * (kResidSlots * (int64_t)w.uu + sl)] = 0.0;
+            P->partials[2 * (kResidSlots * (int64_t)w.uu + sl) + 1] = 0.0;
+          }
         }
         e2 = 0.0;
         x2 = 0.0;
@@ -996,7 +1008,7 @@ bool make_map(CUtensorMap* map, const Operand& op, int kind, int box_rows_mn, in
 template <int BN, int KIND, int EPI, bool GROUPED>
 bcur_status_t launch_inst(const Maps& maps, const Params& p, const Group& grp, int grid,
                           cudaStream_t s) {
-  using SC = StageCfg<BN, EPI>;
+  using SC = StageCfg<BN, EPI, GROUPED>;
   static bool attr = false;
   if (!attr) {
     BCUR_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, KIND, EPI, GROUPED>,
@@ -1004,7 +1016,7 @@ bcur_status_t launch_inst(const Maps& maps, const Params& p, const Group& grp, i
                                        SC::kSmemBytes));
     attr = true;
   }
-  tc_gemm_kernel<BN, KIND, EPI, GROUPED><<<grid, threads_of<EPI>(), SC::kSmemBytes, s>>>(maps, p,
+  tc_gemm_kernel<BN, KIND, EPI, GROUPED><<<grid, threads_of<EPI, GROUPED>(), SC::kSmemBytes, s>>>(maps, p,
                                                                                      grp);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;

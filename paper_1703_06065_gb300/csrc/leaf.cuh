@@ -29,17 +29,22 @@ __device__ __forceinline__ bool residual_needs_refine(double rel_err) {
 // its direction: the column of L and the row of L^{-1} are zero.  Writes L64
 // and Linv64 (FP64) and LinvT (T), all w x w with zeros above the diagonal;
 // *kept = number of kept pivots.  Every thread of the block must call it.
+// Right-looking, two barriers per column (scale the column by 1/L_jj; update
+// the trailing lower part on a 16 x (threads / 16) grid).  L^{-1} by forward
+// substitution, one column per thread, kept in the strictly upper part of S
+// (X[r][c] at S[c][r + 1], which the factorisation never touches).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void chol_small_body(const double* G, int w, double tol_rel, double* L64,
                                 double* Linv64, T* LinvT, int* kept, double* S) {
   const int ld = w + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int ty = tid >> 4, tx = tid & 15, nty = nt >> 4;
   for (int e = tid; e < w * w; e += nt) {
     const int i = e / w, j = e % w;
     S[i * ld + j] = (j <= i) ? G[i * w + j] : 0.0;
   }
-  __shared__ double s_tol, s_piv;
+  __shared__ double s_tol;
   __shared__ int s_kept;
   __syncthreads();
   if (tid == 0) {
@@ -50,48 +55,45 @@ __device__ void chol_small_body(const double* G, int w, double tol_rel, double* 
   }
   __syncthreads();
   for (int j = 0; j < w; ++j) {
+    const double d = S[j * ld + j];
+    const bool keep = d > s_tol && d > 0.0;
+    const double p = keep ? sqrt(d) : 0.0;
+    const double inv = keep ? 1.0 / p : 0.0;
+    for (int i = j + 1 + tid; i < w; i += nt) S[i * ld + j] *= inv;
+    __syncthreads();
     if (tid == 0) {
-      const double d = S[j * ld + j];
-      double p = 0.0;
-      if (d > s_tol && d > 0.0) { p = sqrt(d); s_kept++; }
       S[j * ld + j] = p;
-      s_piv = p;
+      if (keep) s_kept++;
     }
-    __syncthreads();
-    const double p = s_piv;
-    for (int i = j + 1 + tid; i < w; i += nt) S[i * ld + j] = (p > 0.0) ? S[i * ld + j] / p : 0.0;
-    __syncthreads();
-    const int rem = w - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int a = e / rem, b = e % rem;
-      if (b <= a) {
-        const int i = j + 1 + a, i2 = j + 1 + b;
-        S[i * ld + i2] -= S[i * ld + j] * S[i2 * ld + j];
-      }
+    for (int a = j + 1 + ty; a < w; a += nty) {
+      const double la = S[a * ld + j];
+      for (int b = j + 1 + tx; b <= a; b += 16) S[a * ld + b] = fma(-la, S[b * ld + j], S[a * ld + b]);
     }
     __syncthreads();
   }
-  for (int e = tid; e < w * w; e += nt) {
-    const int i = e / w, j = e % w;
-    L64[e] = (j <= i) ? S[i * ld + j] : 0.0;
-  }
-  // L^{-1} by forward substitution, one column per thread; dropped rows -> 0.
   for (int c = tid; c < w; c += nt) {
-    for (int i = 0; i < w; ++i) {
-      double x = 0.0;
-      if (i >= c) {
-        const double lii = S[i * ld + i];
-        if (lii > 0.0) {
-          double acc = (i == c) ? 1.0 : 0.0;
-          for (int k = c; k < i; ++k) acc -= S[i * ld + k] * Linv64[k * w + c];
-          x = acc / lii;
-        }
+    double* xc = S + c * ld + 1;  // xc[k] = X[k][c], k >= c
+    for (int r = c; r < w; ++r) {
+      const double* lr = S + r * ld;
+      double a0 = (r == c) ? 1.0 : 0.0, a1 = 0.0;
+      int k = c;
+      for (; k + 1 < r; k += 2) {
+        a0 = fma(-lr[k], xc[k], a0);
+        a1 = fma(-lr[k + 1], xc[k + 1], a1);
       }
-      Linv64[i * w + c] = x;
-      LinvT[i * w + c] = (T)x;
+      if (k < r) a0 = fma(-lr[k], xc[k], a0);
+      const double lrr = lr[r];
+      xc[r] = (lrr > 0.0) ? (a0 + a1) / lrr : 0.0;
     }
   }
   __syncthreads();
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, j = e % w;
+    L64[e] = (j <= i) ? S[i * ld + j] : 0.0;
+    const double x = (j <= i) ? S[j * ld + i + 1] : 0.0;
+    Linv64[e] = x;
+    LinvT[e] = (T)x;
+  }
   if (tid == 0 && kept) *kept = s_kept;
 }
 
