@@ -109,17 +109,39 @@ __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcu
 //   apply: X' = L^{-1} X (FP32), optionally also as BF16 for the next
 //          product with A.
 // ---------------------------------------------------------------------------
+// The Gram is symmetric and only its lower part is read: threads 0..135
+// each own one R x R tile (ti >= tj) of the 16 x 16 tile grid, threads
+// 136..255 the 120 tiles above it, which they only zero.  All 256 threads
+// load; the next 64-column slice is fetched into registers while the
+// current one is multiplied.
+__device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
+  ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  tj = t - ti * (ti + 1) / 2;
+}
+
 template <int LP>
 __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chunks, int sel) {
   constexpr int R = LP / 16;          // R x R outputs per thread
+  constexpr int NL = LP * 64 / 256;   // slice elements loaded per thread
   const int b = find_item(chunks, blockIdx.x);
   const Item& I = items[b];
   const int ch = blockIdx.x - chunks.prefix[b];
   const float* X = panel(I, sel);
   const int64_t h = panel_h(I, sel), ld = panel_ld(I, sel);
-  constexpr int TLD = LP + 4;         // XsT[c][r]: column c of the chunk, rows r
+  constexpr int TLD = LP + 4;         // XsT[c][r]: column c of the slice, rows r
   __shared__ __align__(16) float XsT[64 * TLD];
-  const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
+  const int tid = threadIdx.x;
+  const bool lower = tid < 136;
+  int ti, tj;
+  if (lower) {
+    tri_tile(tid, ti, tj);
+  } else {  // strictly lower (a + 1, b) with b <= a, transposed: (b, a + 1)
+    int a2, b2;
+    tri_tile(tid - 136, a2, b2);
+    ti = b2;
+    tj = a2 + 1;
+  }
   float acc[R][R];
 #pragma unroll
   for (int a = 0; a < R; ++a)
@@ -127,26 +149,39 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
     for (int c = 0; c < R; ++c) acc[a][c] = 0.f;
   const int64_t c_begin = (int64_t)ch * CH;
   const int64_t c_end = c_begin + CH < h ? c_begin + CH : h;
+  float rx[NL];
+  auto fetch = [&](int64_t c0) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = tid + 256 * q, r = e / 64, c = e % 64;
+      rx[q] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
+    }
+  };
+  fetch(c_begin);
   for (int64_t c0 = c_begin; c0 < c_end; c0 += 64) {
-    for (int e = tid; e < LP * 64; e += 256) {
-      const int r = e / 64, c = e % 64;
-      XsT[c * TLD + r] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = tid + 256 * q, r = e / 64, c = e % 64;
+      XsT[c * TLD + r] = rx[q];
     }
     __syncthreads();
+    if (c0 + 64 < c_end) fetch(c0 + 64);
+    if (lower) {
 #pragma unroll 4
-    for (int c = 0; c < 64; ++c) {
-      float a[R], bb[R];
+      for (int c = 0; c < 64; ++c) {
+        float a[R], bb[R];
 #pragma unroll
-      for (int q = 0; q < R; q += 4) {
-        const float4 a4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + R * ti + q]);
-        const float4 b4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + R * tj + q]);
-        a[q] = a4.x; a[q + 1] = a4.y; a[q + 2] = a4.z; a[q + 3] = a4.w;
-        bb[q] = b4.x; bb[q + 1] = b4.y; bb[q + 2] = b4.z; bb[q + 3] = b4.w;
+        for (int q = 0; q < R; q += 4) {
+          const float4 a4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + R * ti + q]);
+          const float4 b4 = *reinterpret_cast<const float4*>(&XsT[c * TLD + R * tj + q]);
+          a[q] = a4.x; a[q + 1] = a4.y; a[q + 2] = a4.z; a[q + 3] = a4.w;
+          bb[q] = b4.x; bb[q + 1] = b4.y; bb[q + 2] = b4.z; bb[q + 3] = b4.w;
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+#pragma unroll
+          for (int p = 0; p < R; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
       }
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-#pragma unroll
-        for (int p = 0; p < R; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
     }
     __syncthreads();
   }
@@ -154,7 +189,7 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
 #pragma unroll
   for (int q = 0; q < R; ++q)
 #pragma unroll
-    for (int p = 0; p < R; ++p) out[(R * ti + q) * LP + R * tj + p] = acc[q][p];
+    for (int p = 0; p < R; ++p) out[(R * ti + q) * LP + R * tj + p] = lower ? acc[q][p] : 0.f;
 }
 
 template <int LP>
@@ -185,48 +220,97 @@ __global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, 
   }
 }
 
+// apply: a CTA takes AP columns in slices of 64; thread (ti, tj) forms rows
+// RR ti.. (RR = LP / 16) and columns 4 tj.. of the slice as a small GEMM from
+// shared memory (L^{-1} transposed, the slice row-major), summing t = 0..r in
+// increasing order and stopping at the last nonzero column of its rows.  The
+// next slice is fetched into registers while the current one is multiplied.
 template <int LP>
-__global__ void __launch_bounds__(AP, LP == 64 ? 2 : 1) sapply_kernel(const Item* items,
-                                                                      Work chunks, int src,
-                                                                      int dst, int write_bf16) {
+__global__ void __launch_bounds__(256) sapply_kernel(const Item* items, Work chunks, int src,
+                                                     int dst, int write_bf16) {
+  constexpr int RR = LP / 16;         // rows per thread
+  constexpr int LLD = LP + 4;         // LsT[t][r] = L^{-1}[r][t]
+  constexpr int XLD = 64 + 4;         // Xs[t][c]
+  constexpr int NL = LP * 64 / 256;   // slice elements loaded per thread
   const int b = find_item(chunks, blockIdx.x);
   const Item& I = items[b];
   const int ch = blockIdx.x - chunks.prefix[b];
-  extern __shared__ __align__(16) float Ls[];  // LP x LP
-  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Ls[e] = I.LinvT[e];
-  __syncthreads();
+  extern __shared__ __align__(16) float apply_smem[];
+  float* LsT = apply_smem;            // LP x LLD
+  float* Xs = LsT + LP * LLD;         // LP x XLD
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  for (int e = tid; e < LP * LP; e += 256) {
+    const int r = e / LP, t = e % LP;
+    LsT[t * LLD + r] = I.LinvT[e];
+  }
   const int64_t h = panel_h(I, src), ld = panel_ld(I, src);
-  const int64_t j = (int64_t)ch * AP + threadIdx.x;
-  if (j >= h) return;
   const float* X = panel(I, src);
   float* Y = panel(I, dst);
   bf16* Yb = write_bf16 ? (src < PN0 ? I.Qh : I.Zh) : nullptr;
-  float x[LP];
+  const int64_t c_begin = (int64_t)ch * AP;
+  const int64_t c_end = c_begin + AP < h ? c_begin + AP : h;
+  const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(Yb) & 7) == 0);
+  float rx[NL];
+  auto fetch = [&](int64_t c0) {
 #pragma unroll
-  for (int t = 0; t < LP; ++t) x[t] = X[t * ld + j];
-  // rows in groups of 16; each output sums t = 0..r in increasing order,
-  // reading L^{-1} four entries at a time
-#pragma unroll
-  for (int r0 = 0; r0 < LP; r0 += 16) {
-    float acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-#pragma unroll
-    for (int t = 0; t < r0 + 16; t += 4)
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        if (t > r0 + q) continue;
-        const float4 l4 = *reinterpret_cast<const float4*>(&Ls[(r0 + q) * LP + t]);
-        acc[q] = fmaf(l4.x, x[t], acc[q]);
-        if (t + 1 <= r0 + q) acc[q] = fmaf(l4.y, x[t + 1], acc[q]);
-        if (t + 2 <= r0 + q) acc[q] = fmaf(l4.z, x[t + 2], acc[q]);
-        if (t + 3 <= r0 + q) acc[q] = fmaf(l4.w, x[t + 3], acc[q]);
-      }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      Y[(r0 + q) * ld + j] = acc[q];
-      if (Yb) Yb[(r0 + q) * ld + j] = __float2bfloat16_rn(acc[q]);
+    for (int q = 0; q < NL; ++q) {
+      const int e = tid + 256 * q, r = e / 64, c = e % 64;
+      rx[q] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
     }
+  };
+  fetch(c_begin);
+  const int tmax = RR * ti + RR;      // L^{-1}[r][t] = 0 for t > r
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += 64) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = tid + 256 * q, r = e / 64, c = e % 64;
+      Xs[r * XLD + c] = rx[q];
+    }
+    __syncthreads();
+    if (c0 + 64 < c_end) fetch(c0 + 64);
+    float acc[RR][4];
+#pragma unroll
+    for (int q = 0; q < RR; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+#pragma unroll 4
+    for (int t = 0; t < tmax; ++t) {
+      float a[RR];
+#pragma unroll
+      for (int q = 0; q < RR; q += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&LsT[t * LLD + RR * ti + q]);
+        a[q] = a4.x; a[q + 1] = a4.y; a[q + 2] = a4.z; a[q + 3] = a4.w;
+      }
+      const float4 b4 = *reinterpret_cast<const float4*>(&Xs[t * XLD + 4 * tj]);
+      const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int q = 0; q < RR; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(a[q], bv[p], acc[q][p]);
+    }
+    const int64_t col = c0 + 4 * tj;
+#pragma unroll
+    for (int q = 0; q < RR; ++q) {
+      const int64_t off = (int64_t)(RR * ti + q) * ld + col;
+      if (vec && col + 3 < c_end) {
+        *reinterpret_cast<float4*>(Y + off) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+        if (Yb) {
+          bf16 hv[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) hv[p] = __float2bfloat16_rn(acc[q][p]);
+          *reinterpret_cast<uint2*>(Yb + off) = *reinterpret_cast<const uint2*>(hv);
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          if (col + p >= c_end) break;
+          Y[off + p] = acc[q][p];
+          if (Yb) Yb[off + p] = __float2bfloat16_rn(acc[q][p]);
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -630,10 +714,10 @@ bcur_status_t chol_lp(const Item* items, int B, int sel, int pass, int want_lb, 
 template <int LP>
 bcur_status_t apply_lp(const Item* items, Work chunks, int total, int src, int dst,
                        int write_bf16, cudaStream_t s) {
-  const size_t smem = (size_t)LP * LP * sizeof(float);
+  const size_t smem = (size_t)LP * (LP + 4 + 64 + 4) * sizeof(float);
   static bool attr = false;
   BCUR_TRY(allow_smem(sapply_kernel<LP>, smem, attr));
-  sapply_kernel<LP><<<total, AP, smem, s>>>(items, chunks, src, dst, write_bf16);
+  sapply_kernel<LP><<<total, 256, smem, s>>>(items, chunks, src, dst, write_bf16);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
