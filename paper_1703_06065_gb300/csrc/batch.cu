@@ -195,25 +195,28 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
 template <int LP>
 __global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, int pass,
                                                     int want_lb) {
-  extern __shared__ double S[];  // LP x (LP + 1)
+  extern __shared__ double S[];  // l x (l + 1)
   const Item& I = items[blockIdx.x];
   const int nch = sel < PN0 ? I.chunks_m : I.chunks_n;
+  const int l = I.l;  // panel rows l..LP-1 are zero: only the leading l x l block is factored
   for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
+    const int i = e / LP, j = e % LP;
     double g = 0.0;
-    for (int c = 0; c < nch; ++c) g += (double)I.gpart[(int64_t)c * LP * LP + e];
+    if (i < l && j <= i)
+      for (int c = 0; c < nch; ++c) g += (double)I.gpart[(int64_t)c * LP * LP + e];
     I.G64[e] = g;
   }
   __syncthreads();
   double* L = pass ? I.L64b : I.L64a;
-  chol_small_body<float>(I.G64, LP, 64.0 * 1.1920928955078125e-07, L, I.Linv64, I.LinvT, nullptr,
-                         S);
+  chol_small_body<float>(I.G64, l, LP, 64.0 * 1.1920928955078125e-07, L, I.Linv64, I.LinvT,
+                         nullptr, S);
   if (want_lb && pass == 1) {
     __syncthreads();
     // L_B = L_a L_b: X = L_a Q' and Q' = L_b Q give X = L_a L_b Q
     for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
       const int i = e / LP, j = e % LP;
       double acc = 0.0;
-      if (j <= i)
+      if (i < l && j <= i)
         for (int k = j; k <= i; ++k) acc += I.L64a[i * LP + k] * I.L64b[k * LP + j];
       I.Lb[e] = acc;
     }

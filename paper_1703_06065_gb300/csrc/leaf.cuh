@@ -24,10 +24,12 @@ __device__ __forceinline__ bool residual_needs_refine(double rel_err) {
 
 // ---------------------------------------------------------------------------
 // Small FP64 Cholesky with the drop rule, and its inverse (w <= 128).
-// S: shared memory of w * (w + 1) doubles.  G (w x w, ld w): only the lower
-// part is read.  A pivot d with d <= tol_rel * max_i G_ii (or d <= 0) drops
-// its direction: the column of L and the row of L^{-1} are zero.  Writes L64
-// and Linv64 (FP64) and LinvT (T), all w x w with zeros above the diagonal;
+// S: shared memory of w * (w + 1) doubles.  G (w x w, ld ld >= w): only the
+// lower part is read.  A pivot d with d <= tol_rel * max_i G_ii (or d <= 0)
+// drops its direction: the column of L and the row of L^{-1} are zero.
+// Writes L64 and Linv64 (FP64) and LinvT (T), all ld x ld with zeros above
+// the diagonal and outside the leading w x w block (a zero-padded G gives the
+// same result as factoring it whole: the padding pivots are dropped);
 // *kept = number of kept pivots.  Every thread of the block must call it.
 // Right-looking, two barriers per column (scale the column by 1/L_jj; update
 // the trailing lower part on a 16 x (threads / 16) grid).  L^{-1} by forward
@@ -35,14 +37,14 @@ __device__ __forceinline__ bool residual_needs_refine(double rel_err) {
 // (X[r][c] at S[c][r + 1], which the factorisation never touches).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void chol_small_body(const double* G, int w, double tol_rel, double* L64,
+__device__ void chol_small_body(const double* G, int w, int ldio, double tol_rel, double* L64,
                                 double* Linv64, T* LinvT, int* kept, double* S) {
   const int ld = w + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ty = tid >> 4, tx = tid & 15, nty = nt >> 4;
   for (int e = tid; e < w * w; e += nt) {
     const int i = e / w, j = e % w;
-    S[i * ld + j] = (j <= i) ? G[i * w + j] : 0.0;
+    S[i * ld + j] = (j <= i) ? G[i * ldio + j] : 0.0;
   }
   __shared__ double s_tol;
   __shared__ int s_kept;
@@ -87,10 +89,11 @@ __device__ void chol_small_body(const double* G, int w, double tol_rel, double* 
     }
   }
   __syncthreads();
-  for (int e = tid; e < w * w; e += nt) {
-    const int i = e / w, j = e % w;
-    L64[e] = (j <= i) ? S[i * ld + j] : 0.0;
-    const double x = (j <= i) ? S[j * ld + i + 1] : 0.0;
+  for (int e = tid; e < ldio * ldio; e += nt) {
+    const int i = e / ldio, j = e % ldio;
+    const bool in = i < w && j <= i;
+    L64[e] = in ? S[i * ld + j] : 0.0;
+    const double x = in ? S[j * ld + i + 1] : 0.0;
     Linv64[e] = x;
     LinvT[e] = (T)x;
   }

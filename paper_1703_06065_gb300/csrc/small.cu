@@ -94,7 +94,7 @@ template <typename T>
 __global__ void chol_small_kernel(const double* G, int w, double tol_rel, double* L64,
                                   double* Linv64, T* LinvT, int* kept) {
   extern __shared__ double S[];
-  chol_small_body<T>(G, w, tol_rel, L64, Linv64, LinvT, kept, S);
+  chol_small_body<T>(G, w, w, tol_rel, L64, Linv64, LinvT, kept, S);
 }
 
 template <typename T>
