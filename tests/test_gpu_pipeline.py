@@ -181,6 +181,24 @@ def test_haar_tensor_core_paths(sp, fp, score_tol):
     assert np.linalg.norm(cur_gpu - cur_orc) <= 1e-3 * np.linalg.norm(A)
 
 
+def test_fit_with_several_outer_cholesky_panels():
+    """c = 1536 and r = 1280 selected columns / rows: the blocked Cholesky of
+    each Gram runs over three outer panels of 512 columns, so the
+    left-looking steps read the columns of earlier panels through the outer
+    trailing updates.  The decomposition must still reproduce the oracle's
+    CUR and relative error."""
+    p = bi.scaled_haar(3072, 4096, 128, k=20, p=10, q=2, g_col=12, g_row=10, seed=17, rank=400,
+                       noise=1e-4)
+    ref, gpu, plan = run_problem(p, "bf16", "bf16x3")
+    assert abs(gpu["err"][1] - ref["rel"]) <= 1e-3
+    c, r = gpu["rank"][0], gpu["rank"][1]
+    assert c == 1536 and r == 1280
+    cur_gpu = gpu["C"][:, :c] @ gpu["U"][:c, :r] @ gpu["R"][:r]
+    cur_orc = ref["C"] @ ref["U"] @ ref["R"]
+    A = p.matrix().astype(np.float64)
+    assert np.linalg.norm(cur_gpu - cur_orc) <= 1e-3 * np.linalg.norm(A)
+
+
 def test_residual_refines_when_the_error_is_small():
     """Exactly rank-8 data: the true relative error is at the FP32 storage
     level, far below what one BF16 term resolves (about 3e-3 here).  The plan
