@@ -614,8 +614,53 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
         e2 += (double)se;
         x2 += (double)sx;
       };
+      // A whole tile (every row and column inside X, X 16-byte aligned) takes
+      // the short path: one pointer per lane, no masks, d = x - alpha a by
+      // one FMA, FP32 sums over the warp's share of the tile.
+      const bool whole = vec_ok && rbase + 32 <= Mm && w.n0 + cbeg + CW <= Nm;
+      if (whole) {
+        const float* xl = Xp + (int64_t)(rbase + lr) * ldx + w.n0 + lc;
+        const int64_t st4 = 4 * ldx;
+        auto load_w = [&](float4 (&xv)[8], int c) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) xv[i] = __ldcs(reinterpret_cast<const float4*>(xl + i * st4 + c));
+        };
+        float se = 0.f, sx = 0.f;
+        auto reduce_w = [&](const float4 (&xv)[8], const float4 (&av)[8]) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float xs[4] = {xv[i].x, xv[i].y, xv[i].z, xv[i].w};
+            const float as[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float d = fmaf(-alpha, as[j], xs[j]);
+              se = fmaf(d, d, se);
+              sx = fmaf(xs[j], xs[j], sx);
+            }
+          }
+        };
 #pragma unroll 1
-      for (int c = cbeg; c < cbeg + CW; c += 64) {
+        for (int c = cbeg; c < cbeg + CW; c += 64) {
+          float4 xa[8], aa[8];
+          if constexpr (CW >= 64) {
+            float4 xb[8];
+            load_w(xa, c);
+            load_w(xb, c + 32);
+            read_acc(aa, c);
+            reduce_w(xa, aa);
+            read_acc(aa, c + 32);
+            reduce_w(xb, aa);
+          } else {
+            load_w(xa, c);
+            read_acc(aa, c);
+            reduce_w(xa, aa);
+          }
+        }
+        e2 += (double)se;
+        x2 += (double)sx;
+      }
+#pragma unroll 1
+      for (int c = cbeg; !whole && c < cbeg + CW; c += 64) {
         float4 xa[8], aa[8];
         if constexpr (CW >= 64) {
           float4 xb[8];
