@@ -32,9 +32,13 @@ __device__ __forceinline__ bool residual_needs_refine(double rel_err) {
 // same result as factoring it whole: the padding pivots are dropped);
 // *kept = number of kept pivots.  Every thread of the block must call it.
 // Right-looking, two barriers per column (scale the column by 1/L_jj; update
-// the trailing lower part on a 16 x (threads / 16) grid).  L^{-1} by forward
-// substitution, one column per thread, kept in the strictly upper part of S
-// (X[r][c] at S[c][r + 1], which the factorisation never touches).
+// the trailing lower part on a 16 x (threads / 16) grid).  Each pivot's
+// square root and reciprocal are taken once, by the thread that finishes the
+// diagonal entry (FP64 sqrt and divide are long sequences on this GPU's FP64
+// pipe), and published by the barrier that ends the column.  L^{-1} by
+// forward substitution, one column per thread, multiplying by the stored
+// reciprocals, kept in the strictly upper part of S (X[r][c] at S[c][r + 1],
+// which the factorisation never touches).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void chol_small_body(const double* G, int w, int ldio, double tol_rel, double* L64,
@@ -48,28 +52,37 @@ __device__ void chol_small_body(const double* G, int w, int ldio, double tol_rel
   }
   __shared__ double s_tol;
   __shared__ int s_kept;
+  __shared__ double s_p[128], s_inv[128];  // L_jj and 1 / L_jj (0 when dropped)
+  auto pivot = [&](int j, double tol) {
+    const double d = S[j * ld + j];
+    const bool keep = d > tol && d > 0.0;
+    const double p = keep ? sqrt(d) : 0.0;
+    s_p[j] = p;
+    s_inv[j] = keep ? 1.0 / p : 0.0;
+  };
   __syncthreads();
   if (tid == 0) {
     double mx = 0.0;
     for (int i = 0; i < w; ++i) mx = fmax(mx, S[i * ld + i]);
     s_tol = tol_rel * mx;
     s_kept = 0;
+    pivot(0, tol_rel * mx);
   }
   __syncthreads();
   for (int j = 0; j < w; ++j) {
-    const double d = S[j * ld + j];
-    const bool keep = d > s_tol && d > 0.0;
-    const double p = keep ? sqrt(d) : 0.0;
-    const double inv = keep ? 1.0 / p : 0.0;
+    const double inv = s_inv[j];
     for (int i = j + 1 + tid; i < w; i += nt) S[i * ld + j] *= inv;
     __syncthreads();
     if (tid == 0) {
-      S[j * ld + j] = p;
-      if (keep) s_kept++;
+      S[j * ld + j] = s_p[j];
+      if (s_p[j] > 0.0) s_kept++;
     }
     for (int a = j + 1 + ty; a < w; a += nty) {
       const double la = S[a * ld + j];
-      for (int b = j + 1 + tx; b <= a; b += 16) S[a * ld + b] = fma(-la, S[b * ld + j], S[a * ld + b]);
+      for (int b = j + 1 + tx; b <= a; b += 16) {
+        S[a * ld + b] = fma(-la, S[b * ld + j], S[a * ld + b]);
+        if (a == j + 1 && b == j + 1) pivot(j + 1, s_tol);  // the next diagonal entry is final
+      }
     }
     __syncthreads();
   }
@@ -84,8 +97,7 @@ __device__ void chol_small_body(const double* G, int w, int ldio, double tol_rel
         a1 = fma(-lr[k + 1], xc[k + 1], a1);
       }
       if (k < r) a0 = fma(-lr[k], xc[k], a0);
-      const double lrr = lr[r];
-      xc[r] = (lrr > 0.0) ? (a0 + a1) / lrr : 0.0;
+      xc[r] = (a0 + a1) * s_inv[r];
     }
   }
   __syncthreads();
