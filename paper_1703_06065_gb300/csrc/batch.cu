@@ -439,30 +439,30 @@ __global__ void __launch_bounds__(256) gather_r_kernel(const Item* items,
 // it (L_iJ = G_iJ L_JJ^{-T}, kept in shared memory), update the trailing
 // lower triangle in place.  Then L^{-1} block row by block row:
 // X_IJ = -X_II sum_{J <= K < I} L_IK X_KJ.  Writes L, L^{-1} (zeros above the
-// diagonal) and L^{-1} as a BF16 pair.
+// diagonal) and L^{-1} as a BF16 pair.  Every 64 x 64 x 64 product reads its
+// left operand k-major (A^T[t][row]) and its right operand row-major
+// (B[t][col]) from shared memory, two float4 per k for a thread's 4 x 4
+// outputs.
 // ---------------------------------------------------------------------------
-constexpr int WLD = NB + 4;   // leaf leading dimension (potrf_leaf<float, 64>)
-constexpr int PLD = NB + 1;
-// Shared memory: leaf L and L^{-1}, the transposed inverse (later reused for
-// the three tiles of the inverse phase), and the panel below the leaf, whose
-// height depends on the largest w of the launch.
-constexpr int kWideBase = 2 * NB * WLD + NB * PLD;
-static_assert(3 * NB * PLD <= kWideBase, "inverse tiles must fit in the leaf area");
+constexpr int WLD = NB + 4;   // leading dimension of every 64-wide tile (potrf_leaf's too)
+constexpr int RLD = WMAX - NB + 4;  // the k-major panel: PsT[t][i], i < w - NB
+// Shared memory: leaf L and L^{-1}, X^T, and the k-major panel below the leaf
+// (its width depends on the largest w of the launch); the inverse phase
+// reuses the first four tiles' worth.
+constexpr int kWideBase = 3 * NB * WLD;
 constexpr size_t wide_smem(int wmax) {
-  return (size_t)(kWideBase + (wmax - NB) * PLD) * sizeof(float);
+  return (size_t)(kWideBase + NB * (wmax - NB + 4)) * sizeof(float);
 }
+static_assert(4 * NB * WLD <= kWideBase + NB * (NB + 4), "inverse tiles must fit");
 
-__device__ __forceinline__ void tile_acc(const float* Arow, int lda, const float* Bcol, int ldb,
-                                         int ti, int tj, float (&acc)[4][4]) {
-  // acc[q][p] += sum_t A[4ti+q][t] * B[t][4tj+p], t < NB
+// acc[q][p] += sum_{t < kn} AT[t][4 ti + q] * B[t][4 tj + p]  (lda, ldb multiples of 4)
+__device__ __forceinline__ void tile_acc_k(const float* AT, int lda, const float* B, int ldb,
+                                           int ti, int tj, int kn, float (&acc)[4][4]) {
 #pragma unroll 4
-  for (int t = 0; t < NB; ++t) {
-    float a[4], bb[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      a[q] = Arow[(4 * ti + q) * lda + t];
-      bb[q] = Bcol[t * ldb + 4 * tj + q];
-    }
+  for (int t = 0; t < kn; ++t) {
+    const float4 a4 = *reinterpret_cast<const float4*>(&AT[t * lda + 4 * ti]);
+    const float4 b4 = *reinterpret_cast<const float4*>(&B[t * ldb + 4 * tj]);
+    const float a[4] = {a4.x, a4.y, a4.z, a4.w}, bb[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -470,17 +470,42 @@ __device__ __forceinline__ void tile_acc(const float* Arow, int lda, const float
   }
 }
 
+// 64 x 64 tile of a row-major global matrix (ld) into shared memory:
+// transposed (dst[c][r] = src[r][c]) or as is (dst[r][c]), ld of dst WLD.
+__device__ __forceinline__ void load_tile(const float* src, int64_t ld, float* dst, bool transpose) {
+  const int tid = threadIdx.x;
+  float4 v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = tid + 256 * q, r = e >> 4, c4 = (e & 15) * 4;
+    v[q] = *reinterpret_cast<const float4*>(src + (int64_t)r * ld + c4);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = tid + 256 * q, r = e >> 4, c4 = (e & 15) * 4;
+    if (transpose) {
+      dst[(c4 + 0) * WLD + r] = v[q].x;
+      dst[(c4 + 1) * WLD + r] = v[q].y;
+      dst[(c4 + 2) * WLD + r] = v[q].z;
+      dst[(c4 + 3) * WLD + r] = v[q].w;
+    } else {
+      *reinterpret_cast<float4*>(&dst[r * WLD + c4]) = v[q];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) wchol_kernel(const Item* items, const int* entries,
                                                     int pass) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   float* S = sm;              // NB x WLD: leaf L
   float* X = S + NB * WLD;    // NB x WLD: leaf L^{-1}
-  float* XT = X + NB * WLD;   // NB x PLD: XT[t][c] = X[c][t]
-  float* Ps = XT + NB * PLD;  // (w - NB) x PLD panel
+  float* XT = X + NB * WLD;   // NB x WLD: XT[t][c] = X[c][t]
+  float* PsT = XT + NB * WLD; // NB x pld: PsT[t][i] = panel row i, column t
   const int e0 = entries[blockIdx.x];
   const Item& I = items[e0 >> 1];
   const int side = e0 & 1;
   const int w = side ? I.rpad : I.cpad;
+  const int pld = w - NB + 4;
   float* G = side ? I.GR : I.GC;
   float* L = side ? I.LR[pass] : I.LC[pass];
   float* Li = side ? I.LRi[pass] : I.LCi[pass];
@@ -511,32 +536,41 @@ __global__ void __launch_bounds__(256) wchol_kernel(const Item* items, const int
       const int i = e / NB, c = e % NB;
       L[(int64_t)(j0 + i) * w + j0 + c] = c <= i ? S[i * WLD + c] : 0.f;
       Li[(int64_t)(j0 + i) * w + j0 + c] = c <= i ? X[i * WLD + c] : 0.f;
-      XT[c * PLD + i] = X[i * WLD + c];
+      XT[c * WLD + i] = X[i * WLD + c];
     }
     const int R = w - j0 - NB;
     if (R > 0) {
-      for (int e = tid; e < R * NB; e += 256) {
-        const int i = e / NB, c = e % NB;
-        Ps[i * PLD + c] = G[(int64_t)(j0 + NB + i) * w + j0 + c];
+      for (int r0 = 0; r0 < R; r0 += NB) {
+        const float* src = G + (int64_t)(j0 + NB + r0) * w + j0;
+        float4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + 256 * q, r = e >> 4, c4 = (e & 15) * 4;
+          v[q] = *reinterpret_cast<const float4*>(src + (int64_t)r * w + c4);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + 256 * q, r = e >> 4, c4 = (e & 15) * 4;
+          PsT[(c4 + 0) * pld + r0 + r] = v[q].x;
+          PsT[(c4 + 1) * pld + r0 + r] = v[q].y;
+          PsT[(c4 + 2) * pld + r0 + r] = v[q].z;
+          PsT[(c4 + 3) * pld + r0 + r] = v[q].w;
+        }
       }
       __syncthreads();
-      // panel: L_iJ = G_iJ X_JJ^T, 64 rows at a time, in place
+      // panel: L_iJ = G_iJ X_JJ^T, 64 rows at a time, in place (k-major)
       for (int r0 = 0; r0 < R; r0 += NB) {
-        float acc[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
-        tile_acc(Ps + r0 * PLD, PLD, XT, PLD, ti, tj, acc);
+        float acc[4][4] = {};
+        tile_acc_k(PsT + r0, pld, XT, WLD, ti, tj, NB, acc);
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 4; ++q) {
+          const int i = r0 + 4 * ti + q;
+          *reinterpret_cast<float4*>(&L[(int64_t)(j0 + NB + i) * w + j0 + 4 * tj]) =
+              make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int i = r0 + 4 * ti + q, c = 4 * tj + p;
-            Ps[i * PLD + c] = acc[q][p];
-            L[(int64_t)(j0 + NB + i) * w + j0 + c] = acc[q][p];
-          }
+          for (int p = 0; p < 4; ++p) PsT[(4 * tj + p) * pld + i] = acc[q][p];
+        }
         __syncthreads();
       }
       // trailing update of the lower triangle, tile (bi, bj), bj <= bi
@@ -545,95 +579,74 @@ __global__ void __launch_bounds__(256) wchol_kernel(const Item* items, const int
         int bi = 0;
         while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
         const int bj = t - bi * (bi + 1) / 2;
-        float acc[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+        float acc[4][4] = {};
         // sum_t P[bi*NB + a][t] P[bj*NB + b][t]
-#pragma unroll 4
-        for (int tt = 0; tt < NB; ++tt) {
-          float a[4], bb[4];
+        tile_acc_k(PsT + bi * NB, pld, PsT + bj * NB, pld, ti, tj, NB, acc);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            a[q] = Ps[(bi * NB + 4 * ti + q) * PLD + tt];
-            bb[q] = Ps[(bj * NB + 4 * tj + q) * PLD + tt];
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(a[q], bb[p], acc[q][p]);
+        for (int q = 0; q < 4; ++q) {
+          const int64_t row = j0 + NB + bi * NB + 4 * ti + q;
+          float4* g = reinterpret_cast<float4*>(&G[row * w + j0 + NB + bj * NB + 4 * tj]);
+          float4 o = *g;
+          o.x -= acc[q][0];
+          o.y -= acc[q][1];
+          o.z -= acc[q][2];
+          o.w -= acc[q][3];
+          *g = o;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int64_t row = j0 + NB + bi * NB + 4 * ti + q;
-            const int64_t col = j0 + NB + bj * NB + 4 * tj + p;
-            G[row * w + col] -= acc[q][p];
-          }
       }
     }
     __syncthreads();
   }
   // L^{-1}: off-diagonal blocks by block rows (tiles in the leaf area)
-  float* TA = sm;
-  float* TB = sm + NB * PLD;
-  float* TT = sm + 2 * NB * PLD;
+  float* TAT = sm;             // L_IK^T
+  float* TB = sm + NB * WLD;   // X_KJ
+  float* TT = sm + 2 * NB * WLD;  // sum_K L_IK X_KJ
+  float* TXT = sm + 3 * NB * WLD; // X_II^T
   for (int Ib = 1; Ib < nbk; ++Ib) {
+    load_tile(Li + (int64_t)(Ib * NB) * w + Ib * NB, w, TXT, true);
     for (int Jb = 0; Jb < Ib; ++Jb) {
-      float acc[4][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc[q][p] = 0.f;
+      float acc[4][4] = {};
       for (int Kb = Jb; Kb < Ib; ++Kb) {
-        for (int e = tid; e < NB * NB; e += 256) {
-          const int i = e / NB, c = e % NB;
-          TA[i * PLD + c] = L[(int64_t)(Ib * NB + i) * w + Kb * NB + c];
-          TB[i * PLD + c] = Li[(int64_t)(Kb * NB + i) * w + Jb * NB + c];
-        }
+        load_tile(L + (int64_t)(Ib * NB) * w + Kb * NB, w, TAT, true);
+        load_tile(Li + (int64_t)(Kb * NB) * w + Jb * NB, w, TB, false);
         __syncthreads();
-        tile_acc(TA, PLD, TB, PLD, ti, tj, acc);
+        tile_acc_k(TAT, WLD, TB, WLD, ti, tj, NB, acc);
         __syncthreads();
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) TT[(4 * ti + q) * PLD + 4 * tj + p] = acc[q][p];
-      for (int e = tid; e < NB * NB; e += 256) {
-        const int i = e / NB, c = e % NB;
-        TA[i * PLD + c] = Li[(int64_t)(Ib * NB + i) * w + Ib * NB + c];
-      }
+        *reinterpret_cast<float4*>(&TT[(4 * ti + q) * WLD + 4 * tj]) =
+            make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
       __syncthreads();
-      float acc2[4][4];
+      float acc2[4][4] = {};
+      tile_acc_k(TXT, WLD, TT, WLD, ti, tj, NB, acc2);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc2[q][p] = 0.f;
-      tile_acc(TA, PLD, TT, PLD, ti, tj, acc2);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-          Li[(int64_t)(Ib * NB + 4 * ti + q) * w + Jb * NB + 4 * tj + p] = -acc2[q][p];
+        *reinterpret_cast<float4*>(&Li[(int64_t)(Ib * NB + 4 * ti + q) * w + Jb * NB + 4 * tj]) =
+            make_float4(-acc2[q][0], -acc2[q][1], -acc2[q][2], -acc2[q][3]);
       __syncthreads();
     }
   }
-  // zeros above the block diagonal, then the BF16 pair of L^{-1}
-  for (int64_t e = tid; e < (int64_t)w * w; e += 256) {
-    const int i = (int)(e / w), c = (int)(e % w);
+  // zeros above the block diagonal, then the BF16 pair of L^{-1} (four per thread)
+  const int w4 = w / 4;
+  for (int e = tid; e < w * w4; e += 256) {
+    const int i = e / w4, c = (e - i * w4) * 4;
+    const int64_t off = (int64_t)i * w + c;
+    float4 lv = *reinterpret_cast<const float4*>(&Li[off]);
     if (c / NB > i / NB) {
-      L[e] = 0.f;
-      Li[e] = 0.f;
+      *reinterpret_cast<float4*>(&L[off]) = make_float4(0.f, 0.f, 0.f, 0.f);
+      lv = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(&Li[off]) = lv;
     }
-  }
-  __syncthreads();
-  for (int64_t e = tid; e < (int64_t)w * w; e += 256) {
-    const float v = Li[e];
-    const bf16 h = __float2bfloat16_rn(v);
-    Lh[e] = h;
-    Ll[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    const float vv[4] = {lv.x, lv.y, lv.z, lv.w};
+    bf16 h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      h[p] = __float2bfloat16_rn(vv[p]);
+      l[p] = __float2bfloat16_rn(vv[p] - __bfloat162float(h[p]));
+    }
+    *reinterpret_cast<uint2*>(&Lh[off]) = *reinterpret_cast<const uint2*>(h);
+    *reinterpret_cast<uint2*>(&Ll[off]) = *reinterpret_cast<const uint2*>(l);
   }
   if (tid == 0) I.kept[side * 2 + pass] = kept;
 }
