@@ -336,21 +336,39 @@ __global__ void __launch_bounds__(128) scores_kernel(const Item* items, const bc
   const float* P = col ? I.Pn0 : I.Pm0;
   const int64_t h = col ? I.n : I.m, ld = col ? I.ldn : I.ldm;
   const int k = I.k;
-  extern __shared__ float Fs[];  // LP x LP
+  extern __shared__ __align__(16) float FsT[];  // LP x LP, FsT[t][i] = F[i][t]
   __shared__ double red[4];
-  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) Fs[e] = F[e];
+  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
+    const int i = e / LP, t = e % LP;
+    FsT[t * LP + i] = F[e];
+  }
   __syncthreads();
   const int64_t j0 = (int64_t)g * I.s;
   const int64_t j1 = j0 + I.s < h ? j0 + I.s : h;
   double acc = 0.0;
-  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+  // Blocks narrower than the CTA split the k rows of V^T among thread groups
+  // (group tg takes t = tg, tg + groups, ...); wider ones take a column per
+  // thread.  The mapping depends only on s, so the order of every sum is a
+  // function of the decomposition alone.
+  const int nt = (int)blockDim.x;
+  const int groups = I.s >= nt ? 1 : nt / I.s;
+  const int span = groups == 1 ? nt : I.s;
+  const int tg = groups == 1 ? 0 : (int)threadIdx.x / I.s;
+  const int jc = groups == 1 ? (int)threadIdx.x : (int)threadIdx.x % I.s;
+  for (int64_t j = j0 + jc; tg < groups && j < j1; j += span) {
     float p[LP];
 #pragma unroll
     for (int i = 0; i < LP; ++i) p[i] = P[i * ld + j];
-    for (int t = 0; t < k; ++t) {
+    for (int t = tg; t < k; t += groups) {
       float v = 0.f;
 #pragma unroll
-      for (int i = 0; i < LP; ++i) v = fmaf(Fs[i * LP + t], p[i], v);
+      for (int i = 0; i < LP; i += 4) {  // broadcast float4 reads of row t of F^T
+        const float4 f = *reinterpret_cast<const float4*>(&FsT[t * LP + i]);
+        v = fmaf(f.x, p[i], v);
+        v = fmaf(f.y, p[i + 1], v);
+        v = fmaf(f.z, p[i + 2], v);
+        v = fmaf(f.w, p[i + 3], v);
+      }
       acc = fma((double)v, (double)v, acc);
     }
   }
@@ -424,8 +442,29 @@ __global__ void __launch_bounds__(256) gather_r_kernel(const Item* items,
   const float* A = io[b].A;
   bf16* hr = I.XRh[0] + (int64_t)rr * I.ldn;
   bf16* lr = I.XRl[0] + (int64_t)rr * I.ldn;
+  const float* src = A + (int64_t)(row >= 0 ? row : 0) * I.lda;
+  // four per thread when the row is 16-byte aligned (n, lda, ldn multiples of 4)
+  const bool v4 = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (I.n % 4 == 0) &&
+                  ((reinterpret_cast<uintptr_t>(hr) & 7) == 0) &&
+                  ((reinterpret_cast<uintptr_t>(lr) & 7) == 0);
+  if (v4) {
+    for (int64_t j = 4 * (int64_t)threadIdx.x; j < I.n; j += 4 * (int64_t)blockDim.x) {
+      const float4 v = row >= 0 ? *reinterpret_cast<const float4*>(src + j)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+      bf16 h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        h[q] = __float2bfloat16_rn(vv[q]);
+        l[q] = __float2bfloat16_rn(vv[q] - __bfloat162float(h[q]));
+      }
+      *reinterpret_cast<uint2*>(hr + j) = *reinterpret_cast<const uint2*>(h);
+      *reinterpret_cast<uint2*>(lr + j) = *reinterpret_cast<const uint2*>(l);
+    }
+    return;
+  }
   for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x) {
-    const float v = row >= 0 ? A[(int64_t)row * I.lda + j] : 0.f;
+    const float v = row >= 0 ? src[j] : 0.f;
     const bf16 h = __float2bfloat16_rn(v);
     hr[j] = h;
     lr[j] = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -445,7 +484,6 @@ __global__ void __launch_bounds__(256) gather_r_kernel(const Item* items,
 // outputs.
 // ---------------------------------------------------------------------------
 constexpr int WLD = NB + 4;   // leading dimension of every 64-wide tile (potrf_leaf's too)
-constexpr int RLD = WMAX - NB + 4;  // the k-major panel: PsT[t][i], i < w - NB
 // Shared memory: leaf L and L^{-1}, X^T, and the k-major panel below the leaf
 // (its width depends on the largest w of the launch); the inverse phase
 // reuses the first four tiles' worth.
