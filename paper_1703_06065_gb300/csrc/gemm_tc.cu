@@ -543,16 +543,27 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
       if (w.skip) continue;
       const bool has_acc = w.klo < w.khi;
       const uint32_t acc = tu & 1, use = tu >> 1;
-      if (has_acc) {
-        if (!mbar_wait(&tfull[acc], use & 1, status, abort_flag)) { ok = false; break; }
-        tc_fence_after();
-      }
       const int Mm = P->Mm, Nm = P->Nm;
       const float alpha = P->alpha;
       const int64_t ldx = P->ldx;
       const int rbase = w.m0 + quarter * 32;
       const float* const Xp = P->X;
       const bool vec_ok = ((reinterpret_cast<uintptr_t>(Xp) & 15) == 0) && (ldx % 4 == 0);
+      const bool whole = vec_ok && rbase + 32 <= Mm && w.n0 + cbeg + CW <= Nm;
+      if (whole && lc == 0) {
+        // X does not depend on the MMA: while the accumulator is still being
+        // formed, ask L2 for every 128-byte row piece this warp will read
+        // (one lane per piece, no registers held).
+        const float* xr = Xp + (int64_t)(rbase + lr) * ldx + w.n0 + cbeg;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          for (int c = 0; c < CW; c += 32)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(xr + 4 * i * ldx + c));
+      }
+      if (has_acc) {
+        if (!mbar_wait(&tfull[acc], use & 1, status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+      }
       // rows rbase + lr + 4 i (i < 8), columns col0 + lc .. + 3
       auto load_x = [&](float4 (&xv)[8], int col0) {
         const int col = col0 + lc;
@@ -617,7 +628,6 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
       // A whole tile (every row and column inside X, X 16-byte aligned) takes
       // the short path: one pointer per lane, no masks, d = x - alpha a by
       // one FMA, FP32 sums over the warp's share of the tile.
-      const bool whole = vec_ok && rbase + 32 <= Mm && w.n0 + cbeg + CW <= Nm;
       if (whole) {
         const float* xl = Xp + (int64_t)(rbase + lr) * ldx + w.n0 + lc;
         const int64_t st4 = 4 * ldx;
