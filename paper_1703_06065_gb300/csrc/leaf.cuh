@@ -200,25 +200,23 @@ __device__ int potrf_leaf(const T* G, int64_t ldg, T* S, T* X, T tol) {
 }
 
 // ---------------------------------------------------------------------------
-// One warp: Cholesky with the drop rule and the inverse of a 32 x 32 FP32
-// block held in shared memory (lower part of A, ld lda; factored in place,
-// zeros written above the diagonal).  Lane i owns row i in registers as a
-// window that slides one column per step: at step j, a[t] holds entry
-// (i, j + t), so the register indices stay compile-time constants while the
-// step loop stays rolled (unrolling the steps would make it bound on
-// instruction fetch).  Step j: pivot d from lane j by shuffle; drop rule
-// d <= tol or d <= 0; r = 1/sqrt(d) (rsqrtf), L_jj = d r, l_ij = a_ij r.
-// Column j is also written to cb row j, shifted (cb[j][t] = L[j + t][j], zero
-// past the block), so that the update a[t] -= l_i l_{j+t} reads it with eight
-// broadcast float4 loads.  Entries above the diagonal are updated too (their
-// lanes carry l = 0 from then on, so they never feed back; A gets zeros
-// there).  L^{-1} by forward substitution, one column per lane, with the same
-// sliding window: x_k = b_k r_k, then b_{k+t} -= L[k+t][k] x_k from cb row k.
-// A dropped pivot zeroes its column of L and its row of L^{-1}.  cb: 32 x 36
-// + 32 floats of shared scratch for this warp.  Returns the number of kept
+// One warp: Cholesky with the drop rule of a 32 x 32 FP32 block held in
+// shared memory (lower part of A, ld lda; factored in place, zeros written
+// above the diagonal).  Lane i owns row i in registers as a window that
+// slides one column per step: at step j, a[t] holds entry (i, j + t), so the
+// register indices stay compile-time constants while the step loop stays
+// rolled (unrolling the steps would make it bound on instruction fetch).
+// Step j: pivot d from lane j by shuffle; drop rule d <= tol or d <= 0;
+// r = 1/sqrt(d) (rsqrtf), L_jj = d r, l_ij = a_ij r.  Column j is also
+// written to cb row j, shifted (cb[j][t] = L[j + t][j], zero past the
+// block), so that the update a[t] -= l_i l_{j+t} reads it with eight
+// broadcast float4 loads, and r to cb's reciprocal row.  Entries above the
+// diagonal are updated too (their lanes carry l = 0 from then on, so they
+// never feed back; A gets zeros there).  A dropped pivot zeroes its column.
+// cb: 32 x 36 + 32 floats of shared scratch.  Returns the number of kept
 // pivots (same in every lane).
 // ---------------------------------------------------------------------------
-__device__ inline int warp_chol32(float* A, int lda, float* Xo, int ldx, float tol, float* cb) {
+__device__ inline int warp_chol32_fact(float* A, int lda, float tol, float* cb) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int CL = 36;
   float* rp = cb + 32 * CL;  // 1 / L_jj (0 when dropped)
@@ -255,13 +253,22 @@ __device__ inline int warp_chol32(float* A, int lda, float* Xo, int ldx, float t
     a[31] = 0.f;
   }
   __syncwarp();
-  float b[32];
-#pragma unroll
-  for (int t = 0; t < 32; ++t) b[t] = (t == lane) ? 1.f : 0.f;
+  return kept;
+}
+
+// One warp: forward substitution with the factor left in cb by
+// warp_chol32_fact.  Lane c solves L y = b (b: its 32 right-hand-side values
+// in registers) with the same sliding window: y_k = b_k r_k, then
+// b_{k+t} -= L[k+t][k] y_k from cb row k; y_k goes to out[k * so + c * sl].
+// With b = e_c this is column c of L^{-1} (a dropped pivot gives a zero row).
+__device__ inline void warp_fwd32(const float* cb, float (&b)[32], float* out, int so, int sl) {
+  constexpr int CL = 36;
+  const float* rp = cb + 32 * CL;
+  const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int k = 0; k < 32; ++k) {
     const float xk = b[0] * rp[k];
-    Xo[k * ldx + lane] = xk;
+    out[k * so + lane * sl] = xk;
     float wv[32];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -278,12 +285,13 @@ __device__ inline int warp_chol32(float* A, int lda, float* Xo, int ldx, float t
     b[31] = 0.f;
   }
   __syncwarp();
-  return kept;
 }
 
 // The 64 x 64 leaf in FP32 from two warp-level 32 x 32 factorisations:
-//   L11 = chol(G11), X11 = L11^{-1};  L21 = G21 X11^T;
-//   L22 = chol(G22 - L21 L21^T), X22 = L22^{-1};  X21 = -X22 (L21 X11).
+//   L11 = chol(G11);  X11 = L11^{-1} and L21 = G21 L11^{-T} by forward
+//   substitution, side by side in warps 0 and 1;  L22 = chol(G22 - L21 L21^T)
+//   in warp 0 while the other warps form T = L21 X11;  X22 = L22^{-1};
+//   X21 = -X22 T.
 // leaf64_core starts from the block already in shared memory (S: lower part,
 // zeros above the diagonal, LD = 68; X: zeros) after a block barrier; it
 // leaves S = L and X = L^{-1} (threads 0..255 work, all must call it).  A
@@ -293,27 +301,26 @@ __device__ inline int leaf64_core(float* S, float* X, float tol) {
   constexpr int LD = 68, H = 32;
   const int tid = threadIdx.x;
   const bool act = tid < 256;
-  const int warp = tid >> 5;
+  const int warp = tid >> 5, lane = tid & 31;
   __shared__ int s_kept;
   __shared__ __align__(16) float s_cb[32 * 36 + 32];
   int k1 = 0;
-  if (warp == 0) k1 = warp_chol32(S, LD, X, LD, tol, s_cb);
+  if (warp == 0) k1 = warp_chol32_fact(S, LD, tol, s_cb);
   __syncthreads();
-  // L21 = G21 X11^T: 4 outputs per thread (row i, columns c4..c4+3)
-  const int i = (tid >> 3) & 31, c4 = (tid & 7) * 4;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  if (act) {
+  if (warp == 0) {  // X11 = L11^{-1}, column `lane`
+    float b[32];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = c4 + q;
-      for (int t = 0; t <= c; ++t) acc[q] = fmaf(S[(H + i) * LD + t], X[c * LD + t], acc[q]);
-    }
+    for (int t = 0; t < 32; ++t) b[t] = (t == lane) ? 1.f : 0.f;
+    warp_fwd32(s_cb, b, X, LD, 1);
+  } else if (warp == 1) {  // row `lane` of L21 = G21 L11^{-T}, in place
+    float b[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) b[t] = S[(H + lane) * LD + t];
+    __syncwarp();
+    warp_fwd32(s_cb, b, S + H * LD, 1, LD);
   }
   __syncthreads();
-  if (act)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) S[(H + i) * LD + c4 + q] = acc[q];
-  __syncthreads();
+  const int i = (tid >> 3) & 31, c4 = (tid & 7) * 4;
   // G22 -= L21 L21^T (lower part)
   if (act) {
 #pragma unroll
@@ -327,25 +334,26 @@ __device__ inline int leaf64_core(float* S, float* X, float tol) {
   }
   __syncthreads();
   int k2 = 0;
-  if (warp == 0) k2 = warp_chol32(S + H * LD + H, LD, X + H * LD + H, LD, tol, s_cb);
-  if (tid == 0) s_kept = k1 + k2;
-  __syncthreads();
-  // T = L21 X11 (X11 lower: t >= c), kept in X21's place for now
-  if (act) {
+  if (warp == 0) {
+    k2 = warp_chol32_fact(S + H * LD + H, LD, tol, s_cb);
+    float b[32];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = c4 + q;
+    for (int t = 0; t < 32; ++t) b[t] = (t == lane) ? 1.f : 0.f;
+    warp_fwd32(s_cb, b, X + H * LD + H, LD, 1);
+  } else if (act) {
+    // T = L21 X11 (X11 lower: t >= c), in X21's place; warp 0 touches only
+    // the (2, 2) blocks meanwhile
+    for (int e = tid - 32; e < H * H; e += 224) {
+      const int r = e >> 5, c = e & 31;
       float t2 = 0.f;
-      for (int t = c; t < H; ++t) t2 = fmaf(S[(H + i) * LD + t], X[t * LD + c], t2);
-      acc[q] = t2;
+      for (int t = c; t < H; ++t) t2 = fmaf(S[(H + r) * LD + t], X[t * LD + c], t2);
+      X[(H + r) * LD + c] = t2;
     }
   }
-  __syncthreads();
-  if (act)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) X[(H + i) * LD + c4 + q] = acc[q];
+  if (tid == 0) s_kept = k1 + k2;
   __syncthreads();
   // X21 = -X22 T (X22 lower: t <= i)
+  float acc[4];
   if (act) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
