@@ -19,10 +19,11 @@
 // three products are consecutive K-slices of one accumulation: iteration i
 // of a tile's K loop handles K-block klo + i/3 with the operand pair i%3.
 //
-// CTA = 6 warps, persistent over a static tile schedule:
+// CTA = 6 warps (10 for the grouped residual), persistent over a static tile
+// schedule:
 //   warp 0      TMA producer (one elected thread)
 //   warp 1      TMEM allocator + MMA issuer (one elected thread)
-//   warps 2..5  epilogue: tcgen05.ld from TMEM (each warp owns the 32 TMEM
+//   warps 2..   epilogue: tcgen05.ld from TMEM (each warp owns the 32 TMEM
 //               lanes of its rank within the warpgroup), then store, split-K
 //               partial store, or fused residual reduction.
 // Every mbarrier wait is bounded (2 s on %globaltimer); a wait that runs out
@@ -50,13 +51,11 @@ namespace bcur {
 namespace tc {
 
 constexpr int BM = 128;
-// Epilogue warps: 4 (one per TMEM lane quarter) for the store variants; 8
-// for the residual, whose epilogue streams X from HBM and needs the extra
-// loads in flight (two warps per lane quarter, each on half the columns).
-// Epilogue warps.  The grouped residual (short K: bound by reading X) has
-// eight and gives up a pipeline stage for their transpose tiles; the
-// single-GEMM residual (long K: bound by the MMA feed) keeps four warps and
-// the fourth stage.
+// Epilogue warps: 4 (one per TMEM lane quarter).  The grouped residual,
+// whose short-K tiles are bound by streaming X from HBM, has 8 (two warps per
+// lane quarter, each on half the columns) and gives up a pipeline stage for
+// their transpose tiles; the single-GEMM residual (long K, bound by the MMA
+// feed) keeps 4 warps and the fourth stage.
 template <int EPI, bool G> __host__ __device__ constexpr int epi_warps() {
   return (EPI == 2 && G) ? 8 : 4;
 }
