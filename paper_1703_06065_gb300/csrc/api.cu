@@ -46,7 +46,7 @@ struct bcur_plan_s {
   std::vector<int64_t> col_off, row_off;
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;      // second lane: the R-side QR runs beside the C side
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_stagger = nullptr;
   int64_t m = 0, n = 0, lda = 0;
   int k = 0, l = 0, q = 0;
   int64_t ldm = 0, ldn = 0;      // padded panel leading dims
@@ -600,7 +600,7 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float*
 // pr[0] (input, then result) and pr[1] (intermediate) ping-pong.
 bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, int64_t h,
                            int64_t ld, float* G, float* L1, float* L1i, float* L2, float* L2i,
-                           int parts, int* kept) {
+                           int parts, int* kept, cudaEvent_t after_gram = nullptr) {
   const bool lo = parts == 3;
   S16 Li16 = s16(P, ln.Lih, ln.Lil, lo);
   auto g16 = [&](bcur_plan_t, GemmDesc d, int pr2) { return g16_on(P, ln, d, pr2); };
@@ -612,6 +612,7 @@ bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, 
     g.D = G;
     g.out_lower = 1;
     BCUR_TRY(g16(P, g, parts));
+    if (pass == 0 && after_gram) BCUR_CUDA_TRY(cudaEventRecord(after_gram, ln.s));
     BCUR_TRY(chol_inv_blocked16(P, ln, G, Ls[pass], Lis[pass], w, parts, kept + pass,
                                 drop_tol<float>(h)));
     GemmDesc a = mk16(w, h, w, Li16, w, 0, src, ld, 0, ld);  // Li16 holds L^{-1} already
@@ -751,12 +752,16 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   int* kept = P->at<int>(P->o.kept);
   // The QR factors of C and R^T are independent: the R side runs on the
   // second lane (fork / join through events, so this also works in a graph).
+  // The R side starts when the C side's first Gram is done, so that each
+  // side's latency-bound Cholesky steps run beside the other side's GEMMs
+  // instead of beside each other.
   const Lane l0 = lane_of(P, 0), l1 = lane_of(P, 1);
   BCUR_CUDA_TRY(cudaEventRecord(P->ev_fork, s));
   BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_fork, 0));
   BCUR_TRY(wide_cqr2_16(P, l0, XC, cw, m, ldm, P->at<float>(P->o.GC), P->at<float>(P->o.L1C),
                         P->at<float>(P->o.L1Ci), P->at<float>(P->o.L2C), P->at<float>(P->o.L2Ci),
-                        parts, kept + 4));
+                        parts, kept + 4, P->ev_stagger));
+  BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_stagger, 0));
   BCUR_TRY(wide_cqr2_16(P, l1, XR, rw, n, ldn, P->at<float>(P->o.GR), P->at<float>(P->o.L1R),
                         P->at<float>(P->o.L1Ri), P->at<float>(P->o.L2R), P->at<float>(P->o.L2Ri),
                         parts, kept + 6));
@@ -1127,6 +1132,7 @@ bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
     BCUR_CUDA_TRY(cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking));
     BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    BCUR_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_stagger, cudaEventDisableTiming));
   }
   P->ws = (char*)ws;
   P->ws_bytes = bytes;
@@ -1268,6 +1274,7 @@ void bcur_destroy(bcur_plan_t P) {
   }
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->ev_stagger) cudaEventDestroy(P->ev_stagger);
   delete P;
 }
 
