@@ -597,10 +597,13 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float*
 }
 
 // Wide Cholesky-QR2 of a BF16-pair panel X (w x h): X = L1 L2 Q.  The pairs
-// pr[0] (input, then result) and pr[1] (intermediate) ping-pong.
+// pr[0] (input, then result) and pr[1] (intermediate) ping-pong.  With
+// second_apply false the second pass stops at L2: pr[1] keeps Q1 = L1^{-1} X
+// (Q = L2^{-1} Q1 is then applied to the small products instead).
 bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, int64_t h,
                            int64_t ld, float* G, float* L1, float* L1i, float* L2, float* L2i,
-                           int parts, int* kept, cudaEvent_t after_gram = nullptr) {
+                           int parts, int* kept, cudaEvent_t after_gram = nullptr,
+                           bool second_apply = true) {
   const bool lo = parts == 3;
   S16 Li16 = s16(P, ln.Lih, ln.Lil, lo);
   auto g16 = [&](bcur_plan_t, GemmDesc d, int pr2) { return g16_on(P, ln, d, pr2); };
@@ -615,6 +618,7 @@ bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, 
     if (pass == 0 && after_gram) BCUR_CUDA_TRY(cudaEventRecord(after_gram, ln.s));
     BCUR_TRY(chol_inv_blocked16(P, ln, G, Ls[pass], Lis[pass], w, parts, kept + pass,
                                 drop_tol<float>(h)));
+    if (pass == 1 && !second_apply) break;
     GemmDesc a = mk16(w, h, w, Li16, w, 0, src, ld, 0, ld);  // Li16 holds L^{-1} already
     a.Dh = dst.h;
     a.Dl = dst.l;
@@ -760,50 +764,66 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_fork, 0));
   BCUR_TRY(wide_cqr2_16(P, l0, XC, cw, m, ldm, P->at<float>(P->o.GC), P->at<float>(P->o.L1C),
                         P->at<float>(P->o.L1Ci), P->at<float>(P->o.L2C), P->at<float>(P->o.L2Ci),
-                        parts, kept + 4, P->ev_stagger));
+                        parts, kept + 4, P->ev_stagger, false));
   BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_stagger, 0));
   BCUR_TRY(wide_cqr2_16(P, l1, XR, rw, n, ldn, P->at<float>(P->o.GR), P->at<float>(P->o.L1R),
                         P->at<float>(P->o.L1Ri), P->at<float>(P->o.L2R), P->at<float>(P->o.L2Ri),
-                        parts, kept + 6));
+                        parts, kept + 6, nullptr, false));
   BCUR_CUDA_TRY(cudaEventRecord(P->ev_join, P->stream2));
   BCUR_CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
-  // W = A Q_R (m x r);  M = Q_C^T W (c x r)
+  // The second Cholesky-QR pass stops at L2: with Q1 = X L1^{-T} (the pairs
+  // XC[1], XR[1]) and Q = Q1 L2^{-T}, every product by Q becomes a product by
+  // Q1 and a small triangular one.  W1 = A Q1_R (m x r); M1 = Q1_C^T W1
+  // (c x r);
+  //   M2 = L2C^{-T} L2C^{-1} M1 L2R^{-T} L2R^{-1}, so Q_C M Q_R^T = Q1_C M2 Q1_R^T
+  //        (M = Q_C^T A Q_R; the residual uses M2 with Q1);
+  //   U  = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1} = L1C^{-T} M2 L1R^{-1}.
   S16 A16 = s16(P, P->o.A16h, P->o.A16l, lo);
   S16 W16 = s16(P, P->o.Wh, P->o.Wl, lo);
   S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
   BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
   {
-    GemmDesc g = mk16(m, rw, n, A16, ldn, 0, XR[0], ldn, 1, rw);
+    GemmDesc g = mk16(m, rw, n, A16, ldn, 0, XR[1], ldn, 1, rw);
     g.Dh = W16.h;
     g.Dl = W16.l;
     BCUR_TRY(g16(P, g, parts));
-    GemmDesc g2 = mk16(cw, rw, m, XC[0], ldm, 0, W16, rw, 0, rw);
-    g2.D = P->at<float>(P->o.Mb);
+    GemmDesc g2 = mk16(cw, rw, m, XC[1], ldm, 0, W16, rw, 0, rw);
     g2.Dh = M16.h;
     g2.Dl = M16.l;
     BCUR_TRY(g16(P, g2, parts));
   }
-  // U = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1}
   S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
   S16 U1 = s16(P, P->o.U1h, P->o.U1l, lo);
   S16 U2 = s16(P, P->o.U2h, P->o.U2l, lo);
   float* Uf = P->at<float>(P->o.U2);
+  auto tri = [&](GemmDesc d, S16 out, float* outf) {
+    d.Dh = out.h;
+    d.Dl = out.l;
+    d.D = outf;
+    return g16(P, d, parts);
+  };
   BCUR_TRY(split(P, P->at<float>(P->o.L2Ri), rw, rw, rw, Li16, rw));
-  GemmDesc g1 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 0, rw);
-  g1.Dh = U1.h; g1.Dl = U1.l; g1.triB = 1;
-  BCUR_TRY(g16(P, g1, parts));
-  BCUR_TRY(split(P, P->at<float>(P->o.L1Ri), rw, rw, rw, Li16, rw));
-  GemmDesc g2 = mk16(cw, rw, rw, U1, rw, 0, Li16, rw, 0, rw);
-  g2.Dh = U2.h; g2.Dl = U2.l; g2.triB = 1;
-  BCUR_TRY(g16(P, g2, parts));
+  GemmDesc t1 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 1, rw);  // M1 L2R^{-T}
+  t1.triB = 2;
+  BCUR_TRY(tri(t1, U1, nullptr));
+  GemmDesc t2 = mk16(cw, rw, rw, U1, rw, 0, Li16, rw, 0, rw);   // ... L2R^{-1}
+  t2.triB = 1;
+  BCUR_TRY(tri(t2, U2, nullptr));
   BCUR_TRY(split(P, P->at<float>(P->o.L2Ci), cw, cw, cw, Li16, cw));
-  GemmDesc g3 = mk16(cw, rw, cw, Li16, cw, 1, U2, rw, 0, rw);
-  g3.Dh = U1.h; g3.Dl = U1.l; g3.triA = 2;
-  BCUR_TRY(g16(P, g3, parts));
+  GemmDesc t3 = mk16(cw, rw, cw, Li16, cw, 0, U2, rw, 0, rw);   // L2C^{-1} ...
+  t3.triA = 1;
+  BCUR_TRY(tri(t3, U1, nullptr));
+  GemmDesc t4 = mk16(cw, rw, cw, Li16, cw, 1, U1, rw, 0, rw);   // M2 = L2C^{-T} ...
+  t4.triA = 2;
+  BCUR_TRY(tri(t4, M16, P->at<float>(P->o.Mb)));
+  BCUR_TRY(split(P, P->at<float>(P->o.L1Ri), rw, rw, rw, Li16, rw));
+  GemmDesc t5 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 0, rw);  // M2 L1R^{-1}
+  t5.triB = 1;
+  BCUR_TRY(tri(t5, U2, nullptr));
   BCUR_TRY(split(P, P->at<float>(P->o.L1Ci), cw, cw, cw, Li16, cw));
-  GemmDesc g4 = mk16(cw, rw, cw, Li16, cw, 1, U1, rw, 0, rw);
-  g4.D = Uf; g4.triA = 2;
-  BCUR_TRY(g16(P, g4, parts));
+  GemmDesc t6 = mk16(cw, rw, cw, Li16, cw, 1, U2, rw, 0, rw);   // U = L1C^{-T} ...
+  t6.triA = 2;
+  BCUR_TRY(tri(t6, S16{}, Uf));
   if (Uout) BCUR_TRY(copy2d<float>(Uf, rw, Uout, P->r_max, P->c_max, P->r_max, s));
   return BCUR_OK;
 }
@@ -822,8 +842,8 @@ bcur_status_t run_error16(bcur_plan_t P, const float* A, double* out) {
   int* flag = P->at<int>(P->o.refine);
   for (int pass = 0; pass < (parts == 3 ? 2 : 1); ++pass) {
     const bool lo = pass == 1;
-    S16 QC = s16(P, P->o.XC16[0], P->o.XC16[1], lo);
-    S16 QR = s16(P, P->o.XR16[0], P->o.XR16[1], lo);
+    S16 QC = s16(P, P->o.XC16[2], P->o.XC16[3], lo);  // Q1_C, Q1_R (with M2, see run_fit16)
+    S16 QR = s16(P, P->o.XR16[2], P->o.XR16[3], lo);
     S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
     S16 Pp = s16(P, P->o.Ph, P->o.Pl, lo);
     GemmDesc g = mk16(m, rw, cw, QC, ldm, 1, M16, rw, 0, rw);
