@@ -57,7 +57,7 @@ struct bcur_batch_s {
     TcGroup g[3];                                // the prepared launches
     int n = 0;
   };
-  MGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[4], gP, gRes, gP3, gRes3;
+  MGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[6], gP, gRes, gP3, gRes3;
   // graph mode: the sequence is captured on a stream of the plan's own and
   // joined to the caller's stream through events
   cudaStream_t gstream = nullptr;
@@ -125,9 +125,10 @@ size_t layout(bcur_batch_t P) {
     for (int i = 0; i < 3; ++i) g.tab[i] = bp.take<char>(gemm_tc_group_bytes(count));
   };
   grp(P->gY, B); grp(P->gZ, B); grp(P->gY2, B);
-  for (int i = 0; i < 2; ++i) { grp(P->gGram[i], 2 * B); grp(P->gApply[i], 2 * B); }
+  for (int i = 0; i < 2; ++i) grp(P->gGram[i], 2 * B);
+  grp(P->gApply[0], 2 * B);  // the second Cholesky-QR pass has no apply
   grp(P->gW, B); grp(P->gM, B);
-  for (int i = 0; i < 4; ++i) grp(P->gU[i], B);
+  for (int i = 0; i < 6; ++i) grp(P->gU[i], B);
   grp(P->gP, B); grp(P->gRes, B); grp(P->gP3, B); grp(P->gRes3, B);
   for (int b = 0; b < B; ++b) {
     Item& I = P->it[b];
@@ -249,7 +250,7 @@ bcur_status_t run_group(const bcur_batch_s::MGroup& g, cudaStream_t s) {
 
 bcur_status_t build_groups(bcur_batch_t P) {
   const int B = P->B;
-  std::vector<GemmDesc> y, z, y2, w, mm, u[4], pp, res, pp3, res3;
+  std::vector<GemmDesc> y, z, y2, w, mm, u[6], pp, res, pp3, res3;
   std::vector<GemmDesc> gram[2], app[2];
   const int64_t LP = P->lp;
   for (int b = 0; b < B; ++b) {
@@ -284,45 +285,52 @@ bcur_status_t build_groups(bcur_batch_t P) {
       d.triA = 1;
       app[pass].push_back(d);
     }
-    // W = A Q_R^T (m x r);  M = Q_C W (c x r)
-    d = g16(m, rp, n, I.Ah, I.Al, ldn, 0, I.XRh[0], I.XRl[0], ldn, 1, rp, 3);
+    // The second Cholesky-QR pass stops at L2 (no apply): Q1 = the pass-0
+    // result (index 1), Q = Q1 L2^{-T}.  W1 = A Q1_R^T (m x r); M1 = Q1_C W1
+    // (c x r); M2 = L2C^{-T} L2C^{-1} M1 L2R^{-T} L2R^{-1}, so that
+    // Q_C M Q_R^T = Q1_C M2 Q1_R^T; U = L1C^{-T} M2 L1R^{-1}.
+    d = g16(m, rp, n, I.Ah, I.Al, ldn, 0, I.XRh[1], I.XRl[1], ldn, 1, rp, 3);
     d.Dh = I.Wh;
     d.Dl = I.Wl;
     w.push_back(d);
-    d = g16(cp, rp, m, I.XCh[0], I.XCl[0], ldm, 0, I.Wh, I.Wl, rp, 0, rp, 3);
-    d.D = I.Mf;
+    d = g16(cp, rp, m, I.XCh[1], I.XCl[1], ldm, 0, I.Wh, I.Wl, rp, 0, rp, 3);
     d.Dh = I.Mh;
     d.Dl = I.Ml;
     mm.push_back(d);
-    // U = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1}
-    d = g16(cp, rp, rp, I.Mh, I.Ml, rp, 0, I.LRih[1], I.LRil[1], rp, 0, rp, 3);
-    d.Dh = I.U1h; d.Dl = I.U1l; d.triB = 1;
+    d = g16(cp, rp, rp, I.Mh, I.Ml, rp, 0, I.LRih[1], I.LRil[1], rp, 1, rp, 3);  // M1 L2R^{-T}
+    d.Dh = I.U1h; d.Dl = I.U1l; d.triB = 2;
     u[0].push_back(d);
-    d = g16(cp, rp, rp, I.U1h, I.U1l, rp, 0, I.LRih[0], I.LRil[0], rp, 0, rp, 3);
+    d = g16(cp, rp, rp, I.U1h, I.U1l, rp, 0, I.LRih[1], I.LRil[1], rp, 0, rp, 3);  // .. L2R^{-1}
     d.Dh = I.U2h; d.Dl = I.U2l; d.triB = 1;
     u[1].push_back(d);
-    d = g16(cp, rp, cp, I.LCih[1], I.LCil[1], cp, 1, I.U2h, I.U2l, rp, 0, rp, 3);
-    d.Dh = I.U1h; d.Dl = I.U1l; d.triA = 2;
+    d = g16(cp, rp, cp, I.LCih[1], I.LCil[1], cp, 0, I.U2h, I.U2l, rp, 0, rp, 3);  // L2C^{-1} ..
+    d.Dh = I.U1h; d.Dl = I.U1l; d.triA = 1;
     u[2].push_back(d);
-    d = g16(cp, rp, cp, I.LCih[0], I.LCil[0], cp, 1, I.U1h, I.U1l, rp, 0, rp, 3);
-    d.D = I.Uf; d.triA = 2;
+    d = g16(cp, rp, cp, I.LCih[1], I.LCil[1], cp, 1, I.U1h, I.U1l, rp, 0, rp, 3);  // M2
+    d.D = I.Mf; d.Dh = I.Mh; d.Dl = I.Ml; d.triA = 2;
     u[3].push_back(d);
-    // P = Q_C^T M (m x r), then sum (A - P Q_R)^2: one BF16 term, and the
+    d = g16(cp, rp, rp, I.Mh, I.Ml, rp, 0, I.LRih[0], I.LRil[0], rp, 0, rp, 3);  // M2 L1R^{-1}
+    d.Dh = I.U2h; d.Dl = I.U2l; d.triB = 1;
+    u[4].push_back(d);
+    d = g16(cp, rp, cp, I.LCih[0], I.LCil[0], cp, 1, I.U2h, I.U2l, rp, 0, rp, 3);  // U
+    d.D = I.Uf; d.triA = 2;
+    u[5].push_back(d);
+    // P = Q1_C^T M2 (m x r), then sum (A - P Q1_R)^2: one BF16 term, and the
     // BF16-pair version for the items the first result flags
-    d = g16(m, rp, cp, I.XCh[0], nullptr, ldm, 1, I.Mh, nullptr, rp, 0, rp, 1);
+    d = g16(m, rp, cp, I.XCh[1], nullptr, ldm, 1, I.Mh, nullptr, rp, 0, rp, 1);
     d.Dh = I.Ph;
     pp.push_back(d);
-    d = g16(m, n, rp, I.Ph, nullptr, rp, 0, I.XRh[0], nullptr, ldn, 0, 0, 1);
+    d = g16(m, n, rp, I.Ph, nullptr, rp, 0, I.XRh[1], nullptr, ldn, 0, 0, 1);
     d.X = nullptr;  // set per run from the io table
     d.ldx = I.lda;
     d.partials = I.partials;
     res.push_back(d);
-    d = g16(m, rp, cp, I.XCh[0], I.XCl[0], ldm, 1, I.Mh, I.Ml, rp, 0, rp, 3);
+    d = g16(m, rp, cp, I.XCh[1], I.XCl[1], ldm, 1, I.Mh, I.Ml, rp, 0, rp, 3);
     d.Dh = I.Ph;
     d.Dl = I.Pl;
     d.run_flag = I.refine;
     pp3.push_back(d);
-    d = g16(m, n, rp, I.Ph, I.Pl, rp, 0, I.XRh[0], I.XRl[0], ldn, 0, 0, 3);
+    d = g16(m, n, rp, I.Ph, I.Pl, rp, 0, I.XRh[1], I.XRl[1], ldn, 0, 0, 3);
     d.X = nullptr;
     d.ldx = I.lda;
     d.partials = I.partials;
@@ -343,9 +351,9 @@ bcur_status_t build_groups(bcur_batch_t P) {
                            {&P->gRes3, &res3, 1, 256}};
   for (int i = 0; i < 2; ++i) {
     jobs.push_back({&P->gGram[i], &gram[i], 0, 0});
-    jobs.push_back({&P->gApply[i], &app[i], 0, 0});
+    if (i == 0) jobs.push_back({&P->gApply[i], &app[i], 0, 0});  // no second apply
   }
-  for (int i = 0; i < 4; ++i) jobs.push_back({&P->gU[i], &u[i], 0, 0});
+  for (int i = 0; i < 6; ++i) jobs.push_back({&P->gU[i], &u[i], 0, 0});
   std::vector<bcur_status_t> st(jobs.size(), BCUR_OK);
   const unsigned hw = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
   int dev = 0;
@@ -447,15 +455,17 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
     for (int c = 0; c < 3; ++c)
       BCUR_TRY(wide_chol(P->d_items, P->wide_entries[c], P->wide_count[c], wmax[c], pass, s));
     BCUR_TRY(mark(P, s, "wide_chol"));
-    BCUR_TRY(run_group(P->gApply[pass], s));
-    BCUR_TRY(mark(P, s, "qr_apply"));
+    if (pass == 0) {  // the second pass stops at L2 (see build_groups)
+      BCUR_TRY(run_group(P->gApply[pass], s));
+      BCUR_TRY(mark(P, s, "qr_apply"));
+    }
   }
   // U = C^+ A R^+
   BCUR_TRY(run_group(P->gW, s));
   BCUR_TRY(mark(P, s, "w_gemm"));
   BCUR_TRY(run_group(P->gM, s));
   BCUR_TRY(mark(P, s, "m_gemm"));
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 6; ++i) {
     BCUR_TRY(run_group(P->gU[i], s));
     BCUR_TRY(mark(P, s, "u_gemm"));
   }
