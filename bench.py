@@ -450,12 +450,7 @@ def main_native(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": p.name, "m": p.m, "n": p.n, "k": p.k, "p": p.p, "q": p.q,
-                       "block": int(p.col_off[1]), "G_col": int(p.col_off.size - 1),
-                       "G_row": int(p.row_off.size - 1), "g_col": p.g_col, "g_row": p.g_row,
-                       "storage": p.storage, "sketch_prec": sp, "fit_prec": fp,
-                       "l2": f"inputs larger than L2 (A = {A.numel() * A.element_size() / 1e9:.2f} GB)",
-                       "parallelism": f"replicas x{world}"},
+            "config": single_config(p, sp, fp, world),
             "rel_err": float(e[1]), "fro_err": float(e[0]),
             "accuracy_gate": gate, "stage_ms": stage_ms, "input_generation_s": round(t_gen, 1),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
@@ -497,6 +492,17 @@ def main_reference_batched(args, world):
     print(json.dumps(line), flush=True)
 
 
+def single_config(p, sp, fp, world):
+    """The config object of a single-matrix workload, shared by both arms."""
+    a_bytes = p.m * p.n * (8 if p.storage == "f64" else 4)
+    return {"workload": p.name, "m": p.m, "n": p.n, "k": p.k, "p": p.p, "q": p.q,
+            "block": int(p.col_off[1]), "G_col": int(p.col_off.size - 1),
+            "G_row": int(p.row_off.size - 1), "g_col": p.g_col, "g_row": p.g_row,
+            "storage": p.storage, "sketch_prec": sp, "fit_prec": fp,
+            "l2": f"inputs larger than L2 (A = {a_bytes / 1e9:.2f} GB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def main_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -512,7 +518,9 @@ def main_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": p.name, "m": p.m, "n": p.n, "k": p.k},
+        "data": "synthetic",
+        "config": single_config(p, args.sketch_prec or ("f64" if p.storage == "f64" else "bf16"),
+                                args.fit_prec or ("f64" if p.storage == "f64" else "bf16x3"), world),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
