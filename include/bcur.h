@@ -54,7 +54,7 @@ typedef enum {
   BCUR_ERANK = 4,       /* a factorisation met a zero pivot it could not drop  */
   BCUR_ENONFINITE = 5,  /* NaN or Inf met in the data                          */
   BCUR_ETIMEOUT = 6,    /* a bounded device-side wait gave up                  */
-  BCUR_ENOTSUP = 7,     /* combination not supported by this build / device    */
+  BCUR_ENOTSUP = 7,     /* combination not supported by the library / device  */
   BCUR_ESTATE = 8       /* call out of order (e.g. bcur_fit before a workspace) */
 } bcur_status_t;
 
