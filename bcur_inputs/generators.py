@@ -343,6 +343,21 @@ def scaled_haar(m: int, n: int, s: int, k: int, p: int, q: int, g_col: int, g_ro
                    recipe=dict(kind="haar_spectrum", rank=min(rank, m, n), decay=1.5, noise=noise))
 
 
+def host_sample(full: Problem, factor: int = 4) -> Problem:
+    """A bounded stand-in of a large single-matrix workload for timing the host
+    oracle: the same recipe at 1/factor the size per side, blocks of the same
+    width, and g scaled so that c/n and r/m stay as in the full problem.
+    Problems of at most 8192 x 8192 are returned unchanged."""
+    if full.m <= 8192 and full.n <= 8192:
+        return full
+    m, n = full.m // factor, full.n // factor
+    s = int(full.col_off[1])
+    gs = max(1, full.g_col // factor)
+    r = full.recipe
+    return scaled_haar(m, n, s, k=full.k, p=full.p, q=full.q, g_col=gs, g_row=gs, seed=full.seed,
+                       rank=min(r.get("rank", 200), m), noise=r.get("noise", 1e-4))
+
+
 def _biometric(g: np.random.Generator, name: str, seed: int, m_range=(256, 4096),
                n_range=(1024, 16384), k_range=(5, 50), blocks=(16, 32, 64, 128, 256)) -> Problem:
     s = int(g.choice(list(blocks)))

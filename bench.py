@@ -109,36 +109,47 @@ class Clocks:
 # Oracle timing (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 def oracle_flops(m, n, c, r, l, q):
-    """FLOP model of the FP64 oracle's dominant steps (used to scale a timed
-    sample to the full size): range finder 2(2q+2) m n l; SVD-based pinv of C
-    and R ~ 4 m c^2 + 8 c^3 and 4 n r^2 + 8 r^3; C^+ A R^+ 2 c m n + 2 c n r;
-    C U R 2 m c r + 2 m r n."""
+    """FLOP model of the FP64 oracle's dominant steps, used only when no
+    measured full-size / sample ratio is stored: range finder 2(2q+2) m n l;
+    SVD-based pinv of C and R ~ 4 m c^2 + 8 c^3 and 4 n r^2 + 8 r^3;
+    C^+ A R^+ 2 c m n + 2 c n r; C U R 2 m c r + 2 m r n."""
     return (2 * (2 * q + 2) * m * n * l + 4 * m * c * c + 8 * c ** 3 + 4 * n * r * r + 8 * r ** 3
             + 2 * c * m * n + 2 * c * n * r + 2 * m * c * r + 2 * m * r * n)
 
 
-def oracle_sample(full: bi.Problem):
-    """A bounded sample of the workload for the host oracle: the same recipe
-    at 1/4 the size per side, blocks of the same width, c/n and r/m kept."""
-    if full.m <= 8192 and full.n <= 8192:
-        return full, 1.0
-    f = 4
-    m, n = full.m // f, full.n // f
-    s = int(full.col_off[1])
-    gs = max(1, full.g_col // f)
-    p = bi.scaled_haar(m, n, s, k=full.k, p=full.p, q=full.q, g_col=gs, g_row=gs, seed=full.seed,
-                       rank=min(200, m), noise=full.recipe.get("noise", 1e-4))
+def oracle_scale(full: bi.Problem, p: bi.Problem):
+    """(factor, how) that turns the oracle's time on the bounded sample p into
+    its time on the full problem.  Preferred: the ratio of the two times the
+    committed golden script measured in one process on the same host
+    (tests/golden/<workload>_oracle.json, seconds_oracle / seconds_sample);
+    otherwise the FLOP model above."""
+    if p is full:
+        return 1.0, "the full problem itself"
+    ref_path = os.path.join(ROOT, "tests", "golden", f"{full.name}_oracle.json")
+    if os.path.exists(ref_path):
+        ref = json.load(open(ref_path))
+        if ref.get("seconds_sample") and ref.get("seed") == full.seed and ref.get("k") == full.k:
+            f = float(ref["seconds_oracle"]) / float(ref["seconds_sample"])
+            return f, (f"measured ratio x{f:.1f}: full-size oracle {ref['seconds_oracle']} s vs "
+                       f"this sample {ref['seconds_sample']} s, one process on "
+                       f"{ref.get('cores', '?')} host cores (tests/golden/"
+                       f"{os.path.basename(ref_path)})")
     c_full = int(np.sum(np.sort(np.diff(full.col_off))[::-1][:full.g_col]))
     r_full = int(np.sum(np.sort(np.diff(full.row_off))[::-1][:full.g_row]))
-    scale = oracle_flops(full.m, full.n, c_full, r_full, full.l, full.q) / oracle_flops(
-        m, n, gs * s, gs * s, p.l, p.q)
-    return p, scale
+    cs = int(np.sum(np.sort(np.diff(p.col_off))[::-1][:p.g_col]))
+    rs = int(np.sum(np.sort(np.diff(p.row_off))[::-1][:p.g_row]))
+    f = oracle_flops(full.m, full.n, c_full, r_full, full.l, full.q) / oracle_flops(
+        p.m, p.n, cs, rs, p.l, p.q)
+    return f, f"oracle FLOP model x{f:.1f} (no measured ratio stored)"
 
 
 def time_oracle(full: bi.Problem, steps: int, warmup: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload.  Returns
+    (full-size decompositions/s, description, mean seconds per sample run)."""
     import oracle as orc
 
-    p, scale = oracle_sample(full)
+    p = bi.host_sample(full)
+    scale, how = oracle_scale(full, p)
     A = p.matrix()
     om, uc, ur = p.omega(), p.u_col(), p.u_row()
     times = []
@@ -152,8 +163,7 @@ def time_oracle(full: bi.Problem, steps: int, warmup: int = 0):
     sample = (f"FP64 NumPy oracle, whole pipeline on a {p.m}x{p.n} matrix of the same recipe "
               f"({len(p.col_off) - 1}+{len(p.row_off) - 1} blocks of {int(p.col_off[1])}, "
               f"{p.g_col}+{p.g_row} drawn, k={p.k}, p={p.p}, q={p.q}); mean of {steps} runs "
-              f"{t:.3f} s; decomps/s scaled to {full.m}x{full.n} by the oracle FLOP model "
-              f"(x{scale:.1f})")
+              f"{t:.3f} s; decomps/s of the {full.m}x{full.n} workload by the {how}")
     return 1.0 / (t * scale), sample, t
 
 
@@ -263,32 +273,13 @@ def main_native(args):
         A_h = A.cpu().pin_memory()
         om_h = om.cpu().pin_memory()
         uc_h, ur_h = uc.cpu().pin_memory(), ur.cpu().pin_memory()
-        A_d = torch.empty_like(A)
-        om_d, uc_d, ur_d = torch.empty_like(om), torch.empty_like(uc), torch.empty_like(ur)
-        U_h = torch.empty(Ubuf.shape, dtype=tdt).pin_memory()
-        e_h = torch.empty(3, dtype=torch.float64).pin_memory()
-        cs_h = torch.empty(p.col_off.size - 1, dtype=torch.float64).pin_memory()
-        rs_h = torch.empty(p.row_off.size - 1, dtype=torch.float64).pin_memory()
-        ci_h = torch.empty(p.g_col, dtype=torch.int32).pin_memory()
-        ri_h = torch.empty(p.g_row, dtype=torch.int32).pin_memory()
+        outs = plan.decompose_host(A_h, om_h, uc_h, ur_h)   # allocates the pinned outputs
 
         def e2e_step():
-            A_d.copy_(A_h, non_blocking=True)
-            om_d.copy_(om_h, non_blocking=True)
-            uc_d.copy_(uc_h, non_blocking=True)
-            ur_d.copy_(ur_h, non_blocking=True)
-            cs, rs = plan.scores(A_d, om_d)
-            ci, ri, _, _ = plan.sample(cs, rs, uc_d, ur_d)
-            plan.fit(A_d, ci, ri, U=Ubuf)
-            plan.error(A_d, out=ebuf)
-            U_h.copy_(Ubuf, non_blocking=True)
-            e_h.copy_(ebuf, non_blocking=True)
-            cs_h.copy_(cs, non_blocking=True)
-            rs_h.copy_(rs, non_blocking=True)
-            ci_h.copy_(ci, non_blocking=True)
-            ri_h.copy_(ri, non_blocking=True)
+            # one C-ABI call: H2D of A, Omega and the uniforms, the whole method,
+            # D2H of the scores, indices, U and the error
+            plan.decompose_host(A_h, om_h, uc_h, ur_h, out=outs)
 
-        e2e_step()
         torch.cuda.synchronize()
         barrier()
         k2 = max(1, min(args.steps, 3))
@@ -297,6 +288,7 @@ def main_native(args):
             e2e_step()
         ev1.record(s)
         torch.cuda.synchronize()
+        plan.sync_status()
         ms2 = ev0.elapsed_time(ev1) / k2
         if world > 1:
             import torch.distributed as dist
@@ -305,10 +297,13 @@ def main_native(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms2 = float(t.item())
         h2d = sum(x.numel() * x.element_size() for x in (A_h, om_h, uc_h, ur_h))
-        d2h = sum(x.numel() * x.element_size() for x in (U_h, e_h, cs_h, rs_h, ci_h, ri_h))
+        d2h = sum(x.numel() * x.element_size() for x in outs.values())
         e2e = {"value": world * 1000.0 / ms2, "unit": UNIT, "ms_per_step": ms2,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-        del A_d, A_h
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "api": "bcur_decompose_host (host buffers in, host results out; copies on the "
+                      "plan's stream inside the timed region)",
+               "matches_device_run": bool(abs(float(outs["err"][1]) - float(e[1])) == 0.0)}
+        del A_h, outs
 
     # -- dominant kernel, timed live ---------------------------------------
     # The tensor-core GEMM's store variant takes most of the step; its largest
@@ -339,16 +334,20 @@ def main_native(args):
             ev1.record(s)
             torch.cuda.synchronize()
             kms = ev0.elapsed_time(ev1) / nrep
-            mma = 3 * 2.0 * p.m * p.n * r
-            achieved = mma / (kms * 1e-3) / 1e12
+            alg = 2.0 * p.m * p.n * r              # the method's flops for W = A Q_R
+            mma = 3 * alg                          # issued BF16 MMA flops (three split terms)
+            achieved = alg / (kms * 1e-3) / 1e12
             peak = peaks.get("bf16_tflops", 1968.0)
             roof = {"kernel": "tc_gemm_kernel<256, BF16, store>: W = A Q_R, split BF16 (3 terms)",
                     "bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 3),
                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                     "ms": round(kms, 4),
-                    "algorithmic": f"3 x 2*m*n*r = {mma:.4g} BF16 MMA flop per launch "
-                                   f"(m={p.m}, n={p.n}, r={r}); FP32-equivalent product "
-                                   f"{mma / 3 / (kms * 1e-3) / 1e12:.1f} TFLOP/s",
+                    "algorithmic": f"2*m*n*r = {alg:.4g} flop per launch (m={p.m}, n={p.n}, "
+                                   f"r={r}): the product the method needs, counted once",
+                    "tensor_pipe_frac": round(mma / (kms * 1e-3) / 1e12 / peak, 4),
+                    "tensor_pipe_note": f"issued BF16 MMA work 3 x 2*m*n*r = {mma:.4g} flop "
+                                        f"({mma / (kms * 1e-3) / 1e12:.1f} TFLOP/s): the split "
+                                        "pair's three terms keep about 16 bits",
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst; kernel timed alone)"}
             del Ah, Al, Q, Qh, Ql, Wd
             Pm = (torch.randn(p.m, r, device=dev) / float(np.sqrt(r))).to(torch.bfloat16)
@@ -444,6 +443,10 @@ def main_native(args):
                 roof["traffic"] = tr["dram_bytes_read"] + tr["dram_bytes_write"]
                 roof["traffic_source"] = "profiles/tc_gemm_traffic.json"
 
+    study = None
+    if rank == 0 and p.name == "precision_32768" and not args.no_cpu_baseline:
+        study = precision_study(p, dev)
+
     if rank == 0:
         dtype = sp if sp == fp else f"{sp}/{fp}"
         line = {
@@ -456,6 +459,8 @@ def main_native(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu,
         }
+        if study is not None:
+            line["precision_study"] = study
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -492,6 +497,69 @@ def main_reference_batched(args, world):
     print(json.dumps(line), flush=True)
 
 
+def precision_study(full: bi.Problem, dev):
+    """Per-stage error of each sketch precision against the FP64 oracle, on the
+    bounded sample of the workload that the oracle decomposes in seconds
+    (bcur_inputs.host_sample: the same recipe at 1/4 the size per side,
+    k, p, q unchanged), with the split-BF16 fit:
+      - subspace: sin of the largest principal angle between the GPU's top-k
+        right (and left) singular subspace and the oracle's;
+      - scores: max |l_gpu - l_orc| / max l_orc over both sides;
+      - indices: draws equal to the oracle's (per side, in draw order);
+      - U: ||U_gpu - U_orc||_F / ||U_orc||_F with the oracle's blocks forced;
+      - e: |e_gpu - e_orc| (e = ||A - CUR||_F / ||A||_F)."""
+    import torch
+
+    import oracle as orc
+    import paper_1703_06065_gb300 as pkg
+
+    p = bi.host_sample(full)
+    A = p.matrix()
+    om, uc, ur = p.omega(), p.u_col(), p.u_row()
+    t0 = time.perf_counter()
+    ref = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, om, uc, ur)
+    t_orc = time.perf_counter() - t0
+    At = torch.from_numpy(A).to(dev)
+    omt = torch.from_numpy(np.ascontiguousarray(om.T)).to(dev, torch.float32)
+    uct, urt = torch.from_numpy(uc).to(dev), torch.from_numpy(ur).to(dev)
+    ci_o = torch.tensor(ref["col_idx"], dtype=torch.int32, device=dev)
+    ri_o = torch.tensor(ref["row_idx"], dtype=torch.int32, device=dev)
+
+    def sin_angle(Xg, Xo):
+        q, _ = np.linalg.qr(Xg)
+        d = q - Xo @ (Xo.T @ q)
+        return float(np.linalg.norm(d, 2))
+
+    out = {"sample": f"{p.m}x{p.n}, k={p.k}, p={p.p}, q={p.q}, {p.g_col}+{p.g_row} blocks of "
+                     f"{int(p.col_off[1])}", "oracle_s": round(t_orc, 2), "fit": "bf16x3"}
+    for sp in ("bf16", "fp8", "bf16x3", "f32"):
+        plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
+                        dtype="f32", sketch_prec=sp, fit_prec="bf16x3")
+        cs, rs = plan.scores(At, omt)
+        Vt, Ut, _ = plan.factors()
+        ci, ri, _, _ = plan.sample(cs, rs, uct, urt)
+        U = plan.fit(At, ci_o, ri_o)
+        e = plan.error(At)
+        plan.sync_status()
+        lmax = max(ref["col_scores"].max(), ref["row_scores"].max())
+        sd = max(np.abs(cs.cpu().numpy() - ref["col_scores"]).max(),
+                 np.abs(rs.cpu().numpy() - ref["row_scores"]).max()) / lmax
+        cig, rig = ci.cpu().tolist(), ri.cpu().tolist()
+        c, r = ref["U"].shape
+        Ug = U.double().cpu().numpy()[:c, :r]
+        out[sp] = {
+            "sin_angle_V": sin_angle(Vt.double().cpu().numpy().T, ref["V_k"]),
+            "sin_angle_U": sin_angle(Ut.double().cpu().numpy().T, ref["U_k"]),
+            "score_max_rel": float(sd),
+            "col_idx_equal": sum(a == b for a, b in zip(cig, ref["col_idx"])),
+            "row_idx_equal": sum(a == b for a, b in zip(rig, ref["row_idx"])),
+            "U_rel_fro": float(np.linalg.norm(Ug - ref["U"]) / np.linalg.norm(ref["U"])),
+            "e_abs_diff": abs(float(e[1].item()) - ref["rel"]),
+        }
+        del plan
+    return out
+
+
 def single_config(p, sp, fp, world):
     """The config object of a single-matrix workload, shared by both arms."""
     a_bytes = p.m * p.n * (8 if p.storage == "f64" else 4)
@@ -516,11 +584,15 @@ def main_reference(args):
     v, sample, t = time_oracle(p, steps=steps, warmup=min(args.warmup, 1))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": single_config(p, args.sketch_prec or ("f64" if p.storage == "f64" else "bf16"),
                                 args.fit_prec or ("f64" if p.storage == "f64" else "bf16x3"), world),
+        "step_note": "each timed step is one oracle decomposition of the bounded sample named in "
+                     "cpu_baseline.sample (ms_per_step is its measured time); value is in "
+                     "decompositions/s of the full workload, scaled as that sample states",
+        "full_size_ms_per_decomp": 1000.0 / v,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

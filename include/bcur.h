@@ -183,6 +183,56 @@ bcur_status_t bcur_error(bcur_plan_t plan, const void* A, double* out);
 bcur_status_t bcur_truncate(bcur_plan_t plan, const void* A, int32_t kt, const void* omega,
                             void* Uk, double* out);
 
+/* The whole decomposition (stages 1-6) from host buffers: the call a user
+ * with data in host memory makes.  A (row-major m x n, lda), omega (the
+ * l x n panel, ld n; storage type of A), u_col (g_col) and u_row (g_row)
+ * are host pointers; they are copied on the plan's stream into `staging`
+ * (caller-owned device memory of at least bcur_host_staging_bytes(plan)
+ * bytes, 256-byte aligned), the method runs there as bcur_scores,
+ * bcur_sample, bcur_fit and bcur_error do, and the results are copied back
+ * into host memory: col_scores (G_col doubles), row_scores (G_row),
+ * col_idx (g_col int32), row_idx (g_row int32), U (c_max x r_max in the
+ * storage type of A, c_max / r_max the largest possible c and r for the
+ * descriptor's g; rows past the drawn c and columns past r are zero) and
+ * err (3 doubles, as bcur_error).  Every output but err may be NULL.
+ * Asynchronous like every plan call: the host outputs hold the results once
+ * the plan's stream has been synchronised (bcur_sync_status), and the host
+ * inputs must stay unmodified until then.  Page-locked host memory lets the
+ * copies run at full speed (pageable memory is staged by the runtime).
+ * Errors: BCUR_ESTATE (no workspace), BCUR_EINVAL (NULL input, misaligned
+ * staging), BCUR_ENOMEM (staging too small), and those of the stage calls. */
+size_t bcur_host_staging_bytes(bcur_plan_t plan);
+bcur_status_t bcur_decompose_host(bcur_plan_t plan, const void* A, const void* omega,
+                                  const double* u_col, const double* u_row, void* staging,
+                                  size_t staging_bytes, double* col_scores, double* row_scores,
+                                  int32_t* col_idx, int32_t* row_idx, void* U, double* err);
+
+/* The rank-k comparison of Sec. 4.1: out (device, 2 doubles) receives
+ * ||A - A_k||_F, evaluated as ||A - U_k Sigma_k V_k^T||_F with the top-k
+ * factors of the last bcur_scores (the best rank-k error when the range
+ * finder captured the top-k subspace, slightly above it otherwise), and the
+ * ratio ||A - CUR||_F / ||A - A_k||_F with ||A - CUR||_F from the last
+ * bcur_error.  The fused residual on CUDA cores in the storage precision
+ * (one more pass over A).  Errors: BCUR_ESTATE (no scores or no error yet),
+ * BCUR_EINVAL. */
+bcur_status_t bcur_rank_k_error(bcur_plan_t plan, const void* A, double* out);
+
+/* Boosting (Sec. 3.3): the algorithm is repeated t times with independent
+ * draws and the decomposition with the smallest ||A - CUR||_F is kept.  With
+ * the t runs' outputs laid out contiguously in device memory -- err: t
+ * triples at err_stride doubles (>= 3), U: t blocks of U_bytes bytes,
+ * col_idx: t x g_col, row_idx: t x g_row -- this picks the run on the
+ * device, without a host synchronisation: *best (device int32) = the first
+ * run in order with the smallest err[i * err_stride] (NaN loses), and its U,
+ * indices and error triple are copied to U_best, col_idx_best, row_idx_best,
+ * err_best (device; each may be NULL, as may U).  1 <= t <= 4096.
+ * Errors: BCUR_EINVAL. */
+bcur_status_t bcur_boost_select(int32_t t, const double* err, int64_t err_stride, const void* U,
+                                int64_t U_bytes, const int32_t* col_idx, int32_t g_col,
+                                const int32_t* row_idx, int32_t g_row, void* U_best,
+                                int32_t* col_idx_best, int32_t* row_idx_best, double* err_best,
+                                int32_t* best, void* stream);
+
 /* Sizes of the last fit: c, r, and the number of kept directions of C and
  * R^T.  Host pointers; synchronises the plan's stream. */
 bcur_status_t bcur_rank(bcur_plan_t plan, int64_t* c, int64_t* r, int64_t* rank_c,
@@ -278,16 +328,21 @@ bcur_status_t bcur_residual(const void* X, int64_t ldx, const void* P, int64_t l
  * framework's pool (so a fresh cudaMalloc fails or fragments it), request
  * loops that must never call cudaMalloc/cudaFree (cudaFree synchronises the
  * whole device), and plug-ins that are handed only input and output pointers.
- * Same arguments and result as bcur_residual, minus the workspace: the
- * per-CTA partial sums go to a fixed 1 MiB array inside the library's device
- * image (65536 partial pairs; every GPU that loads the library holds it until
- * the process exits).
+ * Same arguments, data types and result as bcur_residual, minus the
+ * workspace: dtype F64 (prec F64), F32 (prec F32, TF32 or BF16; where the
+ * tensor cores cannot serve the call it runs on the CUDA cores in FP32, as
+ * bcur_residual does) or BF16 (X FP32, P and Q BF16, prec BF16, tensor cores
+ * only: BCUR_ENOTSUP for operands TMA cannot describe).  The per-CTA partial
+ * sums go to a fixed 1 MiB array inside the library's device image (65536
+ * partial pairs; every GPU that loads the library holds it until the process
+ * exits).
  *   - Sizes whose kernel would need more than 65536 partial pairs (FP32:
  *     more than 65536 tiles of 128 x 128 in X; FP64: tiles of 64 x 64) are
  *     rejected with BCUR_ENOMEM before anything is enqueued.
  *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before
- *     any stream capture begins.
+ *     per device, with that device current, and again if the device's
+ *     context has changed since, e.g. after cudaDeviceReset); make that
+ *     first call before any stream capture begins.
  *   - No call allocates or frees device memory.
  *   - All calls share the one array and it keeps the last call's contents;
  *     each call writes every slot it later reads, so nothing needs clearing,
@@ -297,7 +352,46 @@ bcur_status_t bcur_residual_noalloc(const void* X, int64_t ldx, const void* P, i
                                     const void* Q, int64_t ldq, int64_t m, int64_t n, int64_t r,
                                     int32_t dtype, int32_t prec, double* out, void* stream);
 
-/* Dense GEMM on the library's kernels, exposed for testing the tensor-core
+/* Plan-free pieces of the fit, for callers that assemble the method from
+ * stage calls (the row-sharded form, where each rank holds whole row blocks
+ * and the Gram matrices are summed across ranks between the calls).
+ *
+ * bcur_cholesky_inverse: G = L L^T for a symmetric positive semi-definite
+ * w x w matrix (row-major, ld w, lower part read and overwritten by the
+ * blocked factorisation's trailing updates), with the drop rule of the fit:
+ * a pivot at or below tol_rel times the largest diagonal entry (tol_rel <= 0:
+ * 64 units of round-off of dtype) drops its direction (zero row and column
+ * of L and L^{-1}).  L and Linv (w x w, zeros above the diagonal) and *kept
+ * (device int32, the number of kept pivots) are written.  dtype F64 or F32
+ * (CUDA cores, left-looking 64-wide leaves and blocked updates).  w a
+ * multiple of 64 (pad with zero rows and columns: they are dropped), at most
+ * 65536.  workspace: device scratch of at least 256 bytes, 256-byte aligned.
+ *
+ * bcur_svd_small: one-sided Jacobi SVD X = Ut diag(sigma) W^T of a w x w FP64
+ * matrix (row-major), w <= 128, computed in dtype (F64 or F32); Ut and W
+ * row-major w x w in dtype, sigma descending (FP64); work: device scratch of
+ * (w + 1)^2 elements of dtype; status (device int32, may be NULL) records
+ * BCUR_ETIMEOUT if the sweeps do not converge.
+ *
+ * bcur_gather_blocks: the chosen blocks of A (row-major m x n, lda, F64 or
+ * F32): axis 1 gathers columns into C^T (cap x m, ld ldo >= m), axis 0 rows
+ * into R (cap x n, ld ldo >= n); blocks idx (device int32, g entries, in
+ * order) of the partition off (device int64, G + 1 offsets); rows of the
+ * output past the gathered count are zero; map: device scratch of cap + 1
+ * int64 (the gathered count is left in map[cap]).
+ * Errors: BCUR_EINVAL, BCUR_ENOMEM. */
+bcur_status_t bcur_cholesky_inverse(void* G, int64_t w, int32_t dtype, void* L, void* Linv,
+                                    int32_t* kept, double tol_rel, void* workspace,
+                                    size_t workspace_bytes, void* stream);
+bcur_status_t bcur_svd_small(const double* X, int32_t w, int32_t dtype, void* Ut, void* W,
+                             double* sigma, void* work, size_t work_bytes, int32_t* status,
+                             void* stream);
+bcur_status_t bcur_gather_blocks(const void* A, int64_t lda, int64_t m, int64_t n, int32_t dtype,
+                                 int32_t axis, const int64_t* off, int32_t G, const int32_t* idx,
+                                 int32_t g, int64_t cap, void* out, int64_t ldo, void* map,
+                                 void* stream);
+
+/* Dense GEMM on the library's kernels, exposed for testing the tensor-core/* Dense GEMM on the library's kernels, exposed for testing the tensor-core
  * path against the CUDA-core path:  D (M x N, row-major, ldd) = A_op B_op,
  * A_op(i, kk) = transA ? A[kk * lda + i] : A[i * lda + kk],
  * B_op(kk, j) = transB ? B[j * ldb + kk] : B[kk * ldb + j].
@@ -368,6 +462,20 @@ typedef struct {
 
 typedef struct bcur_batch_s* bcur_batch_t;
 
+/* Tile widths of the grouped GEMMs are picked by the library's autotuner:
+ * bcur_batch_set_workspace times, for every GEMM shape class (stage, output
+ * width, rows, K, operand layout) not measured before in this process, a
+ * grouped launch of copies of one GEMM of that class at each candidate width
+ * (64, 128, 256 output columns per tile; 64 or 128 for the skinny sketch
+ * products) and keeps the fastest (the widest within 3% of it).  The choice
+ * depends only on the GEMM's own shape, so a decomposition's results are the
+ * same alone or in any batch.  Environment: BCUR_AUTOTUNE=0 skips the
+ * measurements (fixed widths by output width for unseen shapes);
+ * BCUR_AUTOTUNE_CACHE=<file> loads earlier choices from that JSON file and
+ * writes new ones back.  bcur_autotune_measured() counts the shape classes
+ * measured so far in this process. */
+int32_t bcur_autotune_measured(void);
+
 /* Validate `count` items and size the workspace; q subspace iterations
  * (0..16) for every item.  Allocates no device memory.  Errors: BCUR_EINVAL
  * (an item out of range: l > 128, g > G, g * s > 512, lda < n or not a
@@ -377,7 +485,9 @@ bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int
 
 /* Attach caller-owned device memory (>= workspace_bytes, 256-byte aligned)
  * and build the launch tables in it (tensor maps of every grouped GEMM,
- * work lists).  Synchronous.  Errors: BCUR_EINVAL, BCUR_ENOMEM, BCUR_ECUDA. */
+ * work lists), after the autotuner has chosen the tile widths (above; its
+ * measuring launches run on the plan's own setup stream and use only this
+ * workspace).  Synchronous.  Errors: BCUR_EINVAL, BCUR_ENOMEM, BCUR_ECUDA. */
 bcur_status_t bcur_batch_set_workspace(bcur_batch_t plan, void* workspace, size_t bytes);
 
 /* Run the whole method for every item; io: host array of `count` entries
@@ -422,6 +532,17 @@ void bcur_batch_destroy(bcur_batch_t plan);
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices).  Used to report launches per timed step. */
 uint64_t bcur_launch_count(void);
+
+/* Bound, in nanoseconds, of every wait inside the tensor-core kernels' main
+ * loops (a pipeline stage, an accumulator) on the current device, for the
+ * launches that follow; default 2 s, allowed 1 ns ... 60 s.  A wait that
+ * runs out records BCUR_ETIMEOUT in the status word of the call (returned
+ * by bcur_sync_status / bcur_batch_sync_status); the kernel then waits for
+ * the copies and products it has already issued (always with the full 2 s
+ * bound), releases its tensor memory and returns, so the context stays
+ * usable.  Meant for watchdogs and for tests of that path.  Synchronous.
+ * Errors: BCUR_EINVAL (out of range), BCUR_ECUDA. */
+bcur_status_t bcur_set_wait_budget_ns(uint64_t ns);
 
 /* Library version, "major.minor.patch". */
 const char* bcur_version(void);

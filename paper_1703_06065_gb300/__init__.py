@@ -24,7 +24,7 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "Batch", "alg1", "boosted", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
+__all__ = ["Plan", "Batch", "alg1", "boosted", "boosted_batch", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
            "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
@@ -173,6 +173,48 @@ class Plan:
         _need_cuda(A)
         out = torch.empty(3, dtype=torch.float64, device=A.device) if out is None else out
         _lib.check(self._L.bcur_error(self._h, _ptr(A), _ptr(out)), "bcur_error")
+        return out
+
+    def decompose_host(self, A, omega, u_col, u_row, out=None):
+        """The whole decomposition from host tensors through one C-ABI call
+        (bcur_decompose_host): the inputs are copied to the device on the
+        plan's stream, the method runs there and the results are copied back.
+        ``A``, ``omega`` (l x n panel), ``u_col``, ``u_row``: contiguous CPU
+        tensors (page-locked for full-speed copies).  ``out``: an optional
+        dict of preallocated CPU tensors (keys col_scores, row_scores,
+        col_idx, row_idx, U, err) to fill; the filled dict is returned.  The
+        results are valid once torch's current stream has been synchronised."""
+        torch = _torch()
+        for t in (A, omega, u_col, u_row):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host inputs must be contiguous CPU tensors")
+        if out is None:
+            pin = A.is_pinned()
+            mk = lambda *sh, dtype: torch.empty(*sh, dtype=dtype, pin_memory=pin)  # noqa: E731
+            out = {"col_scores": mk(self.G_col, dtype=torch.float64),
+                   "row_scores": mk(self.G_row, dtype=torch.float64),
+                   "col_idx": mk(self.g_col, dtype=torch.int32),
+                   "row_idx": mk(self.g_row, dtype=torch.int32),
+                   "U": mk(self.c_max, self.r_max, dtype=self.tdtype),
+                   "err": mk(3, dtype=torch.float64)}
+        need = self._L.bcur_host_staging_bytes(self._h)
+        if getattr(self, "_staging", None) is None or self._staging.numel() < need:
+            self._staging = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        _lib.check(self._L.bcur_decompose_host(
+            self._h, _ptr(A), _ptr(omega), _ptr(u_col), _ptr(u_row), _ptr(self._staging),
+            c_size_t(self._staging.numel()), _ptr(out.get("col_scores")),
+            _ptr(out.get("row_scores")), _ptr(out.get("col_idx")), _ptr(out.get("row_idx")),
+            _ptr(out.get("U")), _ptr(out["err"])), "bcur_decompose_host")
+        return out
+
+    def rank_k_error(self, A):
+        """{||A - A_k||_F, ||A - CUR||_F / ||A - A_k||_F} (device FP64): the
+        rank-k comparison of Sec. 4.1, A_k from the last scores' top-k factors
+        and ||A - CUR||_F from the last error call."""
+        torch = _torch()
+        _need_cuda(A)
+        out = torch.empty(2, dtype=torch.float64, device=A.device)
+        _lib.check(self._L.bcur_rank_k_error(self._h, _ptr(A), _ptr(out)), "bcur_rank_k_error")
         return out
 
     def truncate(self, A, kt: int, omega, want_u: bool = True):
@@ -465,19 +507,66 @@ def alg1(A, col_off, r: int, g: int, u_rows, u_cols, want_u: bool = True):
     return dict(row_idx=ri, col_idx=ci, col_scores=cs, col_prob=cp, U=U, err=err)
 
 
+def _boost_pick(t, err_all, U_all, ci_all, ri_all):
+    """Device-side choice of the run with the smallest ||A - CUR||_F
+    (bcur_boost_select) among t runs stored contiguously."""
+    torch = _torch()
+    dev = err_all.device
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    err = torch.empty(3, dtype=torch.float64, device=dev)
+    ci = torch.empty(ci_all.shape[1], dtype=torch.int32, device=dev)
+    ri = torch.empty(ri_all.shape[1], dtype=torch.int32, device=dev)
+    U = torch.empty(U_all.shape[1:], dtype=U_all.dtype, device=dev) if U_all is not None else None
+    ub = 0 if U_all is None else U_all[0].numel() * U_all.element_size()
+    _lib.check(_lib.load().bcur_boost_select(
+        t, _ptr(err_all), err_all.shape[1], _ptr(U_all), ub, _ptr(ci_all), ci_all.shape[1],
+        _ptr(ri_all), ri_all.shape[1], _ptr(U), _ptr(ci), _ptr(ri), _ptr(err), _ptr(best),
+        _stream()), "bcur_boost_select")
+    return dict(col_idx=ci, row_idx=ri, U=U, err=err), best
+
+
 def boosted(plan: Plan, A, omegas, u_cols, u_rows):
-    """Boosting (Sec. 3.3): run the decomposition once per (omega, u_col, u_row)
-    triple and keep the run with the smallest ||A - CUR||_F.  Returns the
-    chosen run's outputs and the index of the run."""
-    best, best_i, best_e = None, -1, float("inf")
+    """Boosting (Sec. 3.3): the decomposition is repeated once per (omega,
+    u_col, u_row) triple and the run with the smallest ||A - CUR||_F is kept.
+    The runs write into contiguous device buffers and the library picks the
+    best one on the device, so nothing waits for the host.  Returns the
+    chosen run's outputs (device tensors col_idx, row_idx, U, err) and its
+    index (device int32 tensor of one element)."""
+    torch = _torch()
+    t = len(omegas)
+    dev = A.device
+    err_all = torch.empty(t, 3, dtype=torch.float64, device=dev)
+    U_all = torch.empty(t, plan.c_max, plan.r_max, dtype=plan.tdtype, device=dev)
+    ci_all = torch.empty(t, plan.g_col, dtype=torch.int32, device=dev)
+    ri_all = torch.empty(t, plan.g_row, dtype=torch.int32, device=dev)
     for i, (om, uc, ur) in enumerate(zip(omegas, u_cols, u_rows)):
-        res = decompose(plan, A, om, uc, ur)
-        e = float(res["err"][0].item())
-        if e < best_e:
-            best, best_i, best_e = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in res.items()}, i, e
-    return best, best_i
+        cs, rs = plan.scores(A, om)
+        _lib.check(plan._L.bcur_sample(plan._h, _ptr(cs), _ptr(rs), _ptr(uc), _ptr(ur),
+                                       _ptr(ci_all[i]), _ptr(ri_all[i]), c_void_p(0), c_void_p(0)),
+                   "bcur_sample")
+        plan.fit(A, ci_all[i], ri_all[i], U=U_all[i])
+        plan.error(A, out=err_all[i])
+    return _boost_pick(t, err_all, U_all, ci_all, ri_all)
 
 
+def boosted_batch(item: dict, A, omegas, u_cols, u_rows, q: int = 2, use_graph: bool = False):
+    """Boosting (Sec. 3.3) in one batched pass: the t independent runs on the
+    same resident A (FP32) are the t members of one Batch (every stage one
+    launch over all runs, BF16 sketch and split-BF16 fit), and the run with
+    the smallest ||A - CUR||_F is picked on the device.  ``item`` holds the
+    Batch keys m, n, k, p, block, g_col, g_row.  Returns the chosen run's
+    outputs (device tensors col_idx, row_idx, U, err), its index (device
+    int32 tensor) and the Batch (reusable for further draws)."""
+    t = len(omegas)
+    b = Batch([item] * t, q=q)
+    out = b.run([A] * t, omegas, u_cols, u_rows, want_u=True, use_graph=use_graph)
+    # identical items: the batch's flat output buffers are t runs side by side
+    fl = out["flat"]
+    c, r = b.c_max[0], b.r_max[0]
+    best, idx = _boost_pick(t, fl["err"][0][:3 * t].view(t, 3), fl["U"][0][:t * c * r].view(t, c, r),
+                            fl["col_idx"][0][:t * item["g_col"]].view(t, item["g_col"]),
+                            fl["row_idx"][0][:t * item["g_row"]].view(t, item["g_row"]))
+    return best, idx, b
 def decompose(plan: Plan, A, omega, u_col, u_row, col_idx=None, row_idx=None):
     """All stages on one matrix; returns a dict of device tensors."""
     cs, rs = plan.scores(A, omega)

@@ -29,7 +29,10 @@ EXPORTS = [
     "bcur_alg1_workspace", "bcur_alg1", "bcur_truncate", "bcur_batch_plan",
     "bcur_batch_set_workspace", "bcur_batch_run", "bcur_batch_dims", "bcur_batch_sync_status",
     "bcur_batch_destroy", "bcur_batch_profile", "bcur_batch_profile_count",
-    "bcur_batch_profile_entry", "bcur_batch_set_stream",
+    "bcur_batch_profile_entry", "bcur_batch_set_stream", "bcur_host_staging_bytes",
+    "bcur_decompose_host", "bcur_set_wait_budget_ns", "bcur_autotune_measured",
+    "bcur_rank_k_error", "bcur_boost_select", "bcur_cholesky_inverse", "bcur_svd_small",
+    "bcur_gather_blocks",
 ]
 
 
@@ -121,6 +124,30 @@ def load():
                                         c_int64, c_int64, c_int64, c_int32, c_int32, c_void_p,
                                         c_void_p]
     L.bcur_residual_noalloc.restype = st
+    L.bcur_host_staging_bytes.argtypes = [c_void_p]
+    L.bcur_host_staging_bytes.restype = c_size_t
+    L.bcur_decompose_host.argtypes = [c_void_p] + [c_void_p] * 5 + [c_size_t] + [c_void_p] * 6
+    L.bcur_decompose_host.restype = st
+    L.bcur_set_wait_budget_ns.argtypes = [ctypes.c_uint64]
+    L.bcur_set_wait_budget_ns.restype = st
+    L.bcur_autotune_measured.argtypes = []
+    L.bcur_autotune_measured.restype = c_int32
+    L.bcur_rank_k_error.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.bcur_rank_k_error.restype = st
+    L.bcur_boost_select.argtypes = [c_int32, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
+                                    c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p]
+    L.bcur_boost_select.restype = st
+    L.bcur_cholesky_inverse.argtypes = [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p,
+                                        c_double, c_void_p, c_size_t, c_void_p]
+    L.bcur_cholesky_inverse.restype = st
+    L.bcur_svd_small.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_size_t, c_void_p, c_void_p]
+    L.bcur_svd_small.restype = st
+    L.bcur_gather_blocks.argtypes = [c_void_p, c_int64, c_int64, c_int64, c_int32, c_int32,
+                                     c_void_p, c_int32, c_void_p, c_int32, c_int64, c_void_p,
+                                     c_int64, c_void_p, c_void_p]
+    L.bcur_gather_blocks.restype = st
     L.bcur_gemm.argtypes = [c_int64, c_int64, c_int64, c_void_p, c_int64, c_int32, c_void_p,
                             c_int64, c_int32, c_void_p, c_int64, c_int32, c_int32, c_void_p]
     L.bcur_gemm.restype = st

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbcur.so")
 SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "small.cu", "noalloc.cu", "alg1.cu", "batch.cu",
-           "batch_api.cu"]
+           "batch_api.cu", "autotune.cu", "boost.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

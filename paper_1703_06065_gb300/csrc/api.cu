@@ -75,7 +75,7 @@ struct bcur_plan_s {
   bool bf16_path = false;
   size_t tc_scratch_bytes = 0;
   int64_t n_partials = 0;
-  bool have_scores = false, have_fit = false;
+  bool have_scores = false, have_fit = false, have_error = false;
   template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
 };
 
@@ -934,6 +934,26 @@ bcur_status_t run_truncate(bcur_plan_t P, const T* A, int kt, const T* omega, T*
   return finish_residual(P->at<double>(P->o.partials), np, out, 0, s);
 }
 
+// ||A - U_k Sigma_k V_k^T||_F from the factors of the last bcur_scores (the
+// fused residual with P = U_k, Q = Sigma_k V_k^T; CUDA cores, storage
+// precision) and its ratio to the last ||A - CUR||_F.
+template <typename T>
+bcur_status_t run_rank_k(bcur_plan_t P, const T* A, double* out) {
+  cudaStream_t s = P->stream;
+  const int k = P->k;
+  const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
+  T* Q = P->at<T>(P->o.Pn2);
+  BCUR_TRY(copy2d<T>(P->at<T>(P->o.Vp), ldn, Q, ldn, k, n, s));
+  BCUR_TRY(scale_rows_by<T>(Q, k, n, ldn, P->at<double>(P->o.sigma), s));
+  GemmDesc r = mk(m, n, k, P->at<T>(P->o.Up), ldm, 1, Q, ldn, 0, nullptr, 0);
+  r.X = A;
+  r.ldx = P->lda;
+  r.partials = P->at<double>(P->o.partials);
+  int64_t np = 0;
+  BCUR_TRY(gemm_simt_resid<T>(r, s, &np));
+  return rank_k_ratio(P->at<double>(P->o.result), P->at<double>(P->o.partials), np, out, s);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -944,6 +964,11 @@ extern "C" {
 const char* bcur_version(void) { return "0.1.0"; }
 
 uint64_t bcur_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+bcur_status_t bcur_set_wait_budget_ns(uint64_t ns) {
+  if (ns == 0 || ns > 60000000000ull) return BCUR_EINVAL;
+  return gemm_tc_set_wait_budget(ns);
+}
 
 bcur_status_t bcur_gemm_split(int64_t M, int64_t N, int64_t K, const void* A_hi, const void* A_lo,
                               int64_t lda, int32_t transA, const void* B_hi, const void* B_lo,
@@ -1230,6 +1255,7 @@ bcur_status_t bcur_fit(bcur_plan_t P, const void* A, const int32_t* ci, const in
   else
     st = run_fit<float>(P, (const float*)A, ci, ri, (float*)U, (float*)C, (float*)R);
   P->have_fit = (st == BCUR_OK);
+  P->have_error = false;
   return st;
 }
 
@@ -1237,9 +1263,99 @@ bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {
   if (!P) return BCUR_EINVAL;
   if (!P->ws || !P->have_fit) return BCUR_ESTATE;
   if (!A || !out) return BCUR_EINVAL;
-  if (P->d.a_dtype == BCUR_F64) return run_error<double>(P, (const double*)A, out);
-  if (is_bf16_prec(P->d.fit_prec)) return run_error16(P, (const float*)A, out);
-  return run_error<float>(P, (const float*)A, out);
+  bcur_status_t st;
+  if (P->d.a_dtype == BCUR_F64) st = run_error<double>(P, (const double*)A, out);
+  else if (is_bf16_prec(P->d.fit_prec)) st = run_error16(P, (const float*)A, out);
+  else st = run_error<float>(P, (const float*)A, out);
+  BCUR_TRY(st);
+  // kept for bcur_rank_k_error's ratio
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->at<double>(P->o.result), out, 3 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, P->stream));
+  P->have_error = true;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_rank_k_error(bcur_plan_t P, const void* A, double* out) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws || !P->have_scores || !P->have_error) return BCUR_ESTATE;
+  if (!A || !out) return BCUR_EINVAL;
+  return P->d.a_dtype == BCUR_F64 ? run_rank_k<double>(P, (const double*)A, out)
+                                  : run_rank_k<float>(P, (const float*)A, out);
+}
+
+// --- Plan-free factorisation pieces (used by the row-sharded form) --------
+bcur_status_t bcur_cholesky_inverse(void* G, int64_t w, int32_t dtype, void* L, void* Linv,
+                                    int32_t* kept, double tol_rel, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
+  if (!G || !L || !Linv || !kept || !workspace) return BCUR_EINVAL;
+  if (w < 64 || w % 64 != 0 || w > 65536) return BCUR_EINVAL;
+  if (dtype != BCUR_F64 && dtype != BCUR_F32) return BCUR_EINVAL;
+  if (workspace_bytes < 256 || ((uintptr_t)workspace & 255)) return BCUR_EINVAL;
+  // A minimal plan: the stream, the leaf size and two slots of the caller's
+  // scratch (the largest diagonal entry, a status word).
+  bcur_plan_s P;
+  P.stream = (cudaStream_t)stream;
+  P.nb = 64;
+  P.ws = (char*)workspace;
+  P.ws_bytes = workspace_bytes;
+  P.o.maxdiag = 0;
+  P.o.status = 128;
+  P.o.tc_scratch = 0;
+  P.tc_scratch_bytes = 0;
+  if (dtype == BCUR_F64) {
+    const double tol = tol_rel > 0.0 ? tol_rel : 64.0 * EpsOf<double>::v;
+    return chol_inv_blocked<double>(&P, (double*)G, (double*)L, (double*)Linv, w, BCUR_F64,
+                                    (int*)kept, tol);
+  }
+  const double tol = tol_rel > 0.0 ? tol_rel : 64.0 * EpsOf<float>::v;
+  return chol_inv_blocked<float>(&P, (float*)G, (float*)L, (float*)Linv, w, BCUR_F32, (int*)kept,
+                                 tol);
+}
+
+bcur_status_t bcur_svd_small(const double* X, int32_t w, int32_t dtype, void* Ut, void* W,
+                             double* sigma, void* work, size_t work_bytes, int32_t* status,
+                             void* stream) {
+  if (!X || !Ut || !W || !sigma || !work || w < 1 || w > 128) return BCUR_EINVAL;
+  if (dtype != BCUR_F64 && dtype != BCUR_F32) return BCUR_EINVAL;
+  const size_t esz = dtype == BCUR_F64 ? 8 : 4;
+  if (work_bytes < (size_t)(w + 1) * (w + 1) * esz) return BCUR_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == BCUR_F64)
+    return jacobi_svd_small<double>(X, w, (double*)Ut, (double*)W, sigma, (double*)work,
+                                    (int*)status, s);
+  return jacobi_svd_small<float>(X, w, (float*)Ut, (float*)W, sigma, (float*)work, (int*)status, s);
+}
+
+bcur_status_t bcur_gather_blocks(const void* A, int64_t lda, int64_t m, int64_t n, int32_t dtype,
+                                 int32_t axis, const int64_t* off, int32_t G, const int32_t* idx,
+                                 int32_t g, int64_t cap, void* out, int64_t ldo, void* map,
+                                 void* stream) {
+  if (!A || !off || !idx || !out || !map || m < 1 || n < 1 || lda < n || G < 1 || g < 0)
+    return BCUR_EINVAL;
+  if (dtype != BCUR_F64 && dtype != BCUR_F32) return BCUR_EINVAL;
+  if (axis != 0 && axis != 1) return BCUR_EINVAL;
+  if (cap < 1 || ldo < (axis == 1 ? m : n)) return BCUR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t* mp = static_cast<int64_t*>(map);
+  int64_t* count = mp + cap;
+  BCUR_TRY(expand_blocks(idx, g, off, G, cap, mp, count, s));
+  if (axis == 1) {  // columns: out = C^T (cap x m, ld ldo)
+    return dtype == BCUR_F64
+               ? gather_cols_t<double>((const double*)A, lda, m, mp, cap, (double*)out, ldo, s)
+               : gather_cols_t<float>((const float*)A, lda, m, mp, cap, (float*)out, ldo, s);
+  }
+  return dtype == BCUR_F64
+             ? gather_rows<double>((const double*)A, lda, n, mp, cap, (double*)out, ldo, s)
+             : gather_rows<float>((const float*)A, lda, n, mp, cap, (float*)out, ldo, s);
+}
+
+bcur_status_t bcur_boost_select(int32_t t, const double* err, int64_t err_stride, const void* U,
+                                int64_t U_bytes, const int32_t* col_idx, int32_t g_col,
+                                const int32_t* row_idx, int32_t g_row, void* U_best,
+                                int32_t* col_idx_best, int32_t* row_idx_best, double* err_best,
+                                int32_t* best, void* stream) {
+  return boost_select(t, err, err_stride, U, U_bytes, col_idx, g_col, row_idx, g_row, U_best,
+                      col_idx_best, row_idx_best, err_best, best, (cudaStream_t)stream);
 }
 
 bcur_status_t bcur_truncate(bcur_plan_t P, const void* A, int32_t kt, const void* omega,
@@ -1252,6 +1368,76 @@ bcur_status_t bcur_truncate(bcur_plan_t P, const void* A, int32_t kt, const void
   if (P->d.a_dtype == BCUR_F64)
     return run_truncate<double>(P, (const double*)A, kt, (const double*)omega, (double*)Uk, out);
   return run_truncate<float>(P, (const float*)A, kt, (const float*)omega, (float*)Uk, out);
+}
+
+// --- Whole decomposition from host buffers --------------------------------
+// Staging layout (device, caller-owned): A, Omega panel, the two uniform
+// vectors, scores, indices, U and the error triple, each slice 256-byte
+// aligned.
+struct HostStage {
+  size_t A, om, uc, ur, cs, rs, ci, ri, U, err, total;
+};
+static HostStage host_stage_layout(const bcur_plan_s* P) {
+  Layout L;
+  HostStage h;
+  const size_t e = P->esz;
+  h.A = L.take((size_t)P->m * P->lda * e);
+  h.om = L.take((size_t)P->l * P->n * e);
+  h.uc = L.take((size_t)P->d.g_col * 8);
+  h.ur = L.take((size_t)P->d.g_row * 8);
+  h.cs = L.take((size_t)P->d.G_col * 8);
+  h.rs = L.take((size_t)P->d.G_row * 8);
+  h.ci = L.take((size_t)P->d.g_col * 4);
+  h.ri = L.take((size_t)P->d.g_row * 4);
+  h.U = L.take((size_t)P->c_max * P->r_max * e);
+  h.err = L.take(3 * 8);
+  h.total = L.cur;
+  return h;
+}
+
+size_t bcur_host_staging_bytes(bcur_plan_t P) { return P ? host_stage_layout(P).total : 0; }
+
+bcur_status_t bcur_decompose_host(bcur_plan_t P, const void* A, const void* omega,
+                                  const double* u_col, const double* u_row, void* staging,
+                                  size_t staging_bytes, double* col_scores, double* row_scores,
+                                  int32_t* col_idx, int32_t* row_idx, void* U, double* err) {
+  if (!P) return BCUR_EINVAL;
+  if (!P->ws) return BCUR_ESTATE;
+  if (!A || !omega || !u_col || !u_row || !staging || !err) return BCUR_EINVAL;
+  if ((uintptr_t)staging & 255) return BCUR_EINVAL;
+  const HostStage h = host_stage_layout(P);
+  if (staging_bytes < h.total) return BCUR_ENOMEM;
+  char* base = static_cast<char*>(staging);
+  cudaStream_t s = P->stream;
+  const size_t e = P->esz;
+  auto h2d = [&](size_t off, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  auto d2h = [&](void* dst, size_t off, size_t bytes) {
+    return cudaMemcpyAsync(dst, base + off, bytes, cudaMemcpyDeviceToHost, s);
+  };
+  BCUR_CUDA_TRY(h2d(h.A, A, (size_t)P->m * P->lda * e));
+  BCUR_CUDA_TRY(h2d(h.om, omega, (size_t)P->l * P->n * e));
+  BCUR_CUDA_TRY(h2d(h.uc, u_col, (size_t)P->d.g_col * 8));
+  BCUR_CUDA_TRY(h2d(h.ur, u_row, (size_t)P->d.g_row * 8));
+  const void* Ad = base + h.A;
+  double* cs = reinterpret_cast<double*>(base + h.cs);
+  double* rs = reinterpret_cast<double*>(base + h.rs);
+  int32_t* ci = reinterpret_cast<int32_t*>(base + h.ci);
+  int32_t* ri = reinterpret_cast<int32_t*>(base + h.ri);
+  double* ed = reinterpret_cast<double*>(base + h.err);
+  BCUR_TRY(bcur_scores(P, Ad, base + h.om, cs, rs));
+  BCUR_TRY(bcur_sample(P, cs, rs, reinterpret_cast<const double*>(base + h.uc),
+                       reinterpret_cast<const double*>(base + h.ur), ci, ri, nullptr, nullptr));
+  BCUR_TRY(bcur_fit(P, Ad, ci, ri, U ? base + h.U : nullptr, nullptr, nullptr));
+  BCUR_TRY(bcur_error(P, Ad, ed));
+  if (col_scores) BCUR_CUDA_TRY(d2h(col_scores, h.cs, (size_t)P->d.G_col * 8));
+  if (row_scores) BCUR_CUDA_TRY(d2h(row_scores, h.rs, (size_t)P->d.G_row * 8));
+  if (col_idx) BCUR_CUDA_TRY(d2h(col_idx, h.ci, (size_t)P->d.g_col * 4));
+  if (row_idx) BCUR_CUDA_TRY(d2h(row_idx, h.ri, (size_t)P->d.g_row * 4));
+  if (U) BCUR_CUDA_TRY(d2h(U, h.U, (size_t)P->c_max * P->r_max * e));
+  BCUR_CUDA_TRY(d2h(err, h.err, 3 * 8));
+  return BCUR_OK;
 }
 
 bcur_status_t bcur_rank(bcur_plan_t P, int64_t* c, int64_t* r, int64_t* rank_c, int64_t* rank_r) {

@@ -214,23 +214,16 @@ GemmDesc g16(int64_t M, int64_t N, int64_t K, const void* A, const void* Alo, in
   return g;
 }
 
-// Tile width for one GEMM: from its output width in MMA space (the kernel
-// stores D^T when M < 128 and N >= 2M).
-int pick_bn(const GemmDesc& d, int resid) {
-  const bool swap = !resid && d.M < 128 && d.N >= 2 * d.M;
-  const int64_t Nm = swap ? d.M : d.N;
-  return Nm <= 64 ? 64 : (Nm <= 128 ? 128 : 256);
-}
-
+// Tile width of every GEMM of a stage (from the autotuner, autotune.cu), then
+// one grouped launch per width.
 bcur_status_t prep(bcur_batch_t P, bcur_batch_s::MGroup& g, std::vector<GemmDesc>& ds, int resid,
-                   int BN) {
+                   const std::vector<int>& bns) {
   const int widths[3] = {64, 128, 256};
   g.n = 0;
   for (int wi = 0; wi < 3; ++wi) {
     std::vector<GemmDesc> part;
     for (size_t i = 0; i < ds.size(); ++i) {
-      const int bn = BN ? BN : pick_bn(ds[i], resid);
-      if (bn != widths[wi]) continue;
+      if (bns[i] != widths[wi]) continue;
       part.push_back(ds[i]);
       part.back().status = P->d_status;
     }
@@ -340,20 +333,52 @@ bcur_status_t build_groups(bcur_batch_t P) {
   // The tables are independent: encode them on parallel host threads (the
   // tensor-map encoding is pure host work; the uploads share the plan's setup
   // stream, whose use from several threads is ordered by the runtime).
+  // Candidate tile widths per stage: the skinny sketch products (64 or 128
+  // output rows) try 64 and 128; the residual keeps 256 (its epilogue streams
+  // A, and A is only known per run); every other product tries all three.
   struct Job {
     bcur_batch_s::MGroup* g;
     std::vector<GemmDesc>* ds;
-    int resid, BN;
+    int resid;
+    const char* stage;
+    std::vector<int> cands;
+    std::vector<int> bns;
   };
-  std::vector<Job> jobs = {{&P->gY, &y, 0, 64}, {&P->gZ, &z, 0, 64}, {&P->gY2, &y2, 0, 64},
-                           {&P->gW, &w, 0, 0}, {&P->gM, &mm, 0, 0}, {&P->gP, &pp, 0, 0},
-                           {&P->gRes, &res, 1, 256}, {&P->gP3, &pp3, 0, 0},
-                           {&P->gRes3, &res3, 1, 256}};
+  const std::vector<int> all = {64, 128, 256}, narrow = {64, 128}, wide = {256};
+  std::vector<Job> jobs = {{&P->gY, &y, 0, "sketch_y", narrow, {}},
+                           {&P->gZ, &z, 0, "sketch_z", narrow, {}},
+                           {&P->gY2, &y2, 0, "sketch_y2", narrow, {}},
+                           {&P->gW, &w, 0, "w", all, {}},
+                           {&P->gM, &mm, 0, "m", all, {}},
+                           {&P->gP, &pp, 0, "p", all, {}},
+                           {&P->gRes, &res, 1, "res", wide, {}},
+                           {&P->gP3, &pp3, 0, "p3", all, {}},
+                           {&P->gRes3, &res3, 1, "res3", wide, {}}};
+  static const char* gram_names[2] = {"gram0", "gram1"};
+  static const char* u_names[6] = {"u0", "u1", "u2", "u3", "u4", "u5"};
   for (int i = 0; i < 2; ++i) {
-    jobs.push_back({&P->gGram[i], &gram[i], 0, 0});
-    if (i == 0) jobs.push_back({&P->gApply[i], &app[i], 0, 0});  // no second apply
+    jobs.push_back({&P->gGram[i], &gram[i], 0, gram_names[i], all, {}});
+    if (i == 0) jobs.push_back({&P->gApply[i], &app[i], 0, "apply0", all, {}});  // no second apply
   }
-  for (int i = 0; i < 6; ++i) jobs.push_back({&P->gU[i], &u[i], 0, 0});
+  for (int i = 0; i < 6; ++i) jobs.push_back({&P->gU[i], &u[i], 0, u_names[i], all, {}});
+  // Measuring launches write their tables into the BF16 lo copy of the
+  // largest A (not yet filled: the workspace holds no data before a run).
+  {
+    TuneScratch sc;
+    size_t big = 0;
+    for (int b = 1; b < B; ++b)
+      if (P->it[b].m * P->it[b].ldn > P->it[big].m * P->it[big].ldn) big = b;
+    sc.table = P->it[big].Al;
+    sc.table_bytes = (size_t)P->it[big].m * P->it[big].ldn * sizeof(bf16);
+    sc.status = P->d_status;
+    sc.stream = P->sstream;
+    int dev = 0;
+    BCUR_CUDA_TRY(cudaGetDevice(&dev));
+    BCUR_CUDA_TRY(cudaDeviceGetAttribute(&sc.sms, cudaDevAttrMultiProcessorCount, dev));
+    for (Job& j : jobs) BCUR_TRY(tune_widths(j.stage, *j.ds, j.resid, j.cands, sc, &j.bns));
+    BCUR_CUDA_TRY(cudaMemsetAsync(P->d_status, 0, sizeof(int), P->sstream));
+    BCUR_CUDA_TRY(cudaStreamSynchronize(P->sstream));
+  }
   std::vector<bcur_status_t> st(jobs.size(), BCUR_OK);
   const unsigned hw = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
   int dev = 0;
@@ -368,7 +393,7 @@ bcur_status_t build_groups(bcur_batch_t P) {
         return;
       }
       for (size_t j = t; j < jobs.size(); j += hw)
-        st[j] = prep(P, *jobs[j].g, *jobs[j].ds, jobs[j].resid, jobs[j].BN);
+        st[j] = prep(P, *jobs[j].g, *jobs[j].ds, jobs[j].resid, jobs[j].bns);
     });
   for (auto& th : pool) th.join();
   for (bcur_status_t e : st) BCUR_TRY(e);

@@ -63,7 +63,13 @@ template <int EPI, bool G> __host__ __device__ constexpr int threads_of() {
   return 64 + 32 * epi_warps<EPI, G>();
 }
 constexpr int kStageABytes = BM * 128;  // 128 rows (or MN elements) x 128 bytes of K
+// Bound of the waits that drain the kernel's own asynchronous work before it
+// exits (copies and MMAs in flight): always the full 2 s.
 constexpr uint64_t kWaitNs = 2000000000ull;
+// Bound of the waits of the main loop (a stage, an accumulator); 2 s unless
+// lowered from the host (bcur_set_wait_budget_ns), e.g. by a test that makes
+// a wait run out on purpose.
+__device__ unsigned long long g_wait_budget_ns = 2000000000ull;
 
 enum Epi { EPI_STORE = 0, EPI_PARTIAL = 1, EPI_RESID = 2 };
 
@@ -140,10 +146,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
                                           volatile int* abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = now_ns();
+  const uint64_t budget = *(volatile unsigned long long*)&g_wait_budget_ns;
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (now_ns() - t0 > kWaitNs) {
+    if (now_ns() - t0 > budget) {
       *abort_flag = 1;
       if (status) atomicCAS(status, 0, (int)BCUR_ETIMEOUT);
       return false;
@@ -560,7 +567,10 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(xr + 4 * i * ldx + c));
       }
       if (has_acc) {
-        if (!mbar_wait(&tfull[acc], use & 1, status, abort_flag)) { ok = false; break; }
+        // every lane polls; the warp goes on only if all of them saw the
+        // phase (the tcgen05.ld and shuffles below need the whole warp)
+        const bool got = mbar_wait(&tfull[acc], use & 1, status, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         tc_fence_after();
       }
       // rows rbase + lr + 4 i (i < 8), columns col0 + lc .. + 3
@@ -737,7 +747,8 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
       const bool has_acc = w.klo < w.khi;
       const uint32_t acc = tu & 1, use = tu >> 1;
       if (has_acc) {
-        if (!mbar_wait(&tfull[acc], use & 1, status, abort_flag)) { ok = false; break; }
+        const bool got = mbar_wait(&tfull[acc], use & 1, status, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }  // warp-uniform, as above
         tc_fence_after();
       }
       const int Mm = P->Mm, Nm = P->Nm;
@@ -1350,6 +1361,12 @@ bcur_status_t group_run(const TcGroup& g, cudaStream_t s, int grid) {
 }  // namespace tc
 
 bool gemm_tc_available() { return tc::tc_device_ok(); }
+
+bcur_status_t gemm_tc_set_wait_budget(uint64_t ns) {
+  const unsigned long long v = (unsigned long long)ns;
+  BCUR_CUDA_TRY(cudaMemcpyToSymbol(tc::g_wait_budget_ns, &v, sizeof(v)));
+  return BCUR_OK;
+}
 
 int64_t gemm_tc_resid_ctas(int64_t, int64_t) { return 1024; }
 

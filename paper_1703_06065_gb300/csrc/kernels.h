@@ -3,6 +3,8 @@
 
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace bcur {
@@ -68,6 +70,8 @@ bcur_status_t gemm_tc(const GemmDesc& d, int prec, cudaStream_t s);
 bcur_status_t gemm_tc_resid(const GemmDesc& d, int prec, cudaStream_t s, int64_t* n_partials);
 int64_t gemm_tc_resid_ctas(int64_t M, int64_t N);
 bool gemm_tc_available();
+// Bound of the tensor-core kernels' main-loop waits on the current device.
+bcur_status_t gemm_tc_set_wait_budget(uint64_t ns);
 
 // Grouped tensor-core GEMM: many BF16 GEMMs of different shapes in one
 // persistent launch.  The table (tensor maps + parameters per GEMM, tile
@@ -96,6 +100,23 @@ bcur_status_t gemm_tc_group_run(const TcGroup& g, cudaStream_t s, int grid = 0);
 bcur_status_t gemm_tc_group_patch_x(const TcGroup& g, const void* base, size_t stride,
                                     size_t offset, cudaStream_t s);
 int64_t gemm_tc_units(const GemmDesc& d, int resid, int BN);
+
+// Tile-width autotuner of the grouped GEMMs (autotune.cu).  For each GEMM of
+// a stage, the width to use: from the tuning table (keyed by the stage name
+// and the GEMM's own shape class), measured on a miss when measuring is on
+// and `table` has room for a grouped launch of copies of the GEMM, otherwise
+// the fixed choice by output width.  Synchronises `stream` when it measures.
+struct TuneScratch {
+  void* table = nullptr;      // device memory for the measuring launches' tables
+  size_t table_bytes = 0;
+  int* status = nullptr;
+  cudaStream_t stream = nullptr;
+  int sms = 148;
+};
+bcur_status_t tune_widths(const char* stage, const std::vector<GemmDesc>& ds, int resid,
+                          const std::vector<int>& cands, const TuneScratch& sc,
+                          std::vector<int>* out);
+int tune_fixed_bn(const GemmDesc& d, int resid);
 
 // ---------------------------------------------------------------------------
 // Small kernels
@@ -179,6 +200,18 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
                      cudaStream_t s);
 
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+// Boosting (boost.cu): the run with the smallest err[i * err_stride] among t
+// runs laid out contiguously (first minimum in run order), its index in
+// *best and copies of its outputs (U_bytes per run, g_col / g_row indices,
+// the 3-double error).  Every output may be null.
+bcur_status_t boost_select(int t, const double* err, int64_t err_stride, const void* U,
+                           int64_t U_bytes, const int32_t* ci, int gc, const int32_t* ri, int gr,
+                           void* U_best, int32_t* ci_best, int32_t* ri_best, double* err_best,
+                           int32_t* best, cudaStream_t s);
+// out = {sqrt(sum of partials_k's even entries), cur_err[0] / out[0]}.
+bcur_status_t rank_k_ratio(const double* cur_err, const double* partials_k, int64_t n,
+                           double* out, cudaStream_t s);
 
 template <typename T>
 bcur_status_t scale_rows_by(T* X, int64_t rows, int64_t cols, int64_t ld, const double* sc,

@@ -23,22 +23,55 @@ static __device__ __align__(256) double g_residual_scratch[2 * kMaxPartials];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+struct Cached {
+  void* ctx = nullptr;   // context the address was looked up in
+  double* addr = nullptr;
+};
+Cached g_scratch_addr[kMaxDevices];
+
+using CtxGetCurrentFn = int (*)(void**);  // cuCtxGetCurrent(CUcontext*)
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(ptr);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
 
 // Device address of the array for the current device.  The name above is only
-// a host-side stand-in; the address must come from the runtime, once per
-// device, with that device current.
+// a host-side stand-in; the address must come from the runtime, with that
+// device current.  It is looked up once per device and again whenever the
+// device's current context has changed since (after cudaDeviceReset the
+// module is loaded anew, possibly at another address).
 bcur_status_t scratch_address(double** out) {
   int dev = 0;
   BCUR_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return BCUR_ENOTSUP;
+  auto current = []() -> void* {
+    void* ctx = nullptr;
+    if (auto fn = ctx_get_current()) {
+      if (fn(&ctx) != 0) ctx = nullptr;
+    }
+    return ctx;
+  };
+  void* ctx = current();
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_scratch_addr[dev] == nullptr) {
+  Cached& c = g_scratch_addr[dev];
+  if (c.addr == nullptr || ctx == nullptr || c.ctx != ctx) {
     void* p = nullptr;
     BCUR_CUDA_TRY(cudaGetSymbolAddress(&p, g_residual_scratch));
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    c.addr = static_cast<double*>(p);
+    c.ctx = current();  // the lookup makes the device's primary context current
   }
-  *out = g_scratch_addr[dev];
+  *out = c.addr;
   return BCUR_OK;
 }
 
@@ -56,11 +89,18 @@ extern "C" bcur_status_t bcur_residual_noalloc(const void* X, int64_t ldx, const
   if (ldx < n || ldp < r || ldq < n) return BCUR_EINVAL;
   if (dtype == BCUR_F64 && prec != BCUR_F64) return BCUR_EINVAL;
   if (dtype == BCUR_F32 && (prec < BCUR_F32 || prec > BCUR_BF16)) return BCUR_EINVAL;
-  if (dtype != BCUR_F64 && dtype != BCUR_F32) return BCUR_EINVAL;
+  if (dtype == BCUR_BF16 && prec != BCUR_BF16) return BCUR_EINVAL;
+  if (dtype != BCUR_F64 && dtype != BCUR_F32 && dtype != BCUR_BF16) return BCUR_EINVAL;
   // Every kernel that may serve the call must fit its partials in the array.
-  int64_t need = dtype == BCUR_F64 ? gemm_simt_resid_ctas<double>(m, n)
-                                   : gemm_simt_resid_ctas<float>(m, n);
-  if (dtype == BCUR_F32 && prec != BCUR_F32) need = std::max(need, gemm_tc_resid_ctas(m, n));
+  int64_t need = 0;
+  if (dtype == BCUR_F64) {
+    need = gemm_simt_resid_ctas<double>(m, n);
+  } else if (dtype == BCUR_BF16) {
+    need = gemm_tc_resid_ctas(m, n);
+  } else {
+    need = gemm_simt_resid_ctas<float>(m, n);
+    if (prec != BCUR_F32) need = std::max(need, gemm_tc_resid_ctas(m, n));
+  }
   if (need > kMaxPartials) return BCUR_ENOMEM;
 
   double* scratch = nullptr;
@@ -75,6 +115,9 @@ extern "C" bcur_status_t bcur_residual_noalloc(const void* X, int64_t ldx, const
   int64_t np = 0;
   if (dtype == BCUR_F64) {
     BCUR_TRY(gemm_simt_resid<double>(g, s, &np));
+  } else if (dtype == BCUR_BF16) {  // X FP32, P and Q BF16: tensor cores only
+    g.ab_bf16 = 1;
+    BCUR_TRY(gemm_tc_resid(g, prec, s, &np));
   } else {
     bcur_status_t st = BCUR_ENOTSUP;
     if (prec == BCUR_TF32 || prec == BCUR_BF16) st = gemm_tc_resid(g, prec, s, &np);

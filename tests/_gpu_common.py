@@ -89,3 +89,61 @@ def run_problem(p, sketch_prec=None, fit_prec=None, A=None, force_oracle_idx=Tru
     gpu.update(U=U.double().cpu().numpy(), C=C.double().cpu().numpy().T,
                R=R.double().cpu().numpy(), err=e.cpu().numpy(), rank=plan.rank())
     return ref, gpu, plan
+
+
+# Unit round-offs of the arithmetic the precisions stand for: one BF16 term
+# (8 significant bits), e4m3 (4 bits), a BF16 hi/lo pair (about 16 bits,
+# including the dropped lo*lo term and FP32 accumulation) and FP32 with its
+# accumulation over long sums.
+UNIT = {"bf16": 2.0 ** -8, "fp8": 2.0 ** -4, "bf16x3": 2.0 ** -16, "f32": 2.0 ** -22}
+
+
+def score_bound(A, k, u, lmax, safety=2.0):
+    """First-order bound on |l_gpu - l_oracle| for block scores computed from
+    a sketch at unit round-off u.
+
+    Independent roundings of A and of each orthonormal panel (relative size
+    u / sqrt(3) on average) perturb the coupling between the k-th and
+    (k+1)-th singular pairs of A by about
+        de = u / sqrt(3) * (||A||_F / sqrt(m n) + sigma_1 / sqrt(min(m, n)));
+    the top-k subspace then turns by s = safety * de / (sigma_k - sigma_{k+1})
+    (Wedin), and a block score l_g = ||E_g^T V_k||_F^2 moves by at most
+    2 sqrt(l_g k) s + (k + l_g) s^2 (write V' = V W + V_perp Z with
+    ||Z||_F <= sqrt(k) s).  Returned as a bound for the largest score lmax."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    sv = np.linalg.svd(A, compute_uv=False)
+    de = u / np.sqrt(3.0) * (np.linalg.norm(A) / np.sqrt(m * n) + sv[0] / np.sqrt(min(m, n)))
+    s = safety * de / (sv[k - 1] - sv[k])
+    return 2.0 * np.sqrt(lmax * k) * s + (k + lmax) * s * s
+
+
+def u_bound(C, R, rel_err, u):
+    """First-order bound on ||U_gpu - U||_F / ||U||_F for U = C^+ A R^+ computed
+    with unit round-off u by a backward-stable least-squares solve on each
+    side: u (2 kappa / cos(theta) + kappa^2 tan(theta)) per side (the
+    least-squares perturbation theorem, e.g. Golub and Van Loan, Thm. 5.3.1),
+    kappa the condition number of C (resp. R), sin(theta) the relative
+    residual ||A - CUR||_F / ||A||_F."""
+    def kappa(X):
+        sv = np.linalg.svd(np.asarray(X, dtype=np.float64), compute_uv=False)
+        return sv[0] / sv[-1]
+    c = np.sqrt(max(1.0 - rel_err ** 2, 1e-30))
+    t = rel_err / c
+    return u * sum(2.0 * kp / c + kp * kp * t for kp in (kappa(C), kappa(R)))
+
+
+def assert_indices_to_first_tie(ref, gpu, p):
+    """Block indices equal the oracle's bit for bit up to the first draw whose
+    x = u T lies within the score perturbation of an oracle CDF boundary.
+    The GPU's prefix sums and total differ from the oracle's by at most the
+    L1 norm of the score difference, so a draw farther than twice that from
+    every boundary must pick the same block.  Returns the checked draws."""
+    out = {}
+    for side, u, g in (("col", p.u_col(), p.g_col), ("row", p.u_row(), p.g_row)):
+        d1 = float(np.sum(np.abs(np.asarray(gpu[f"{side}_scores"]) - ref[f"{side}_scores"])))
+        tol = 2.0 * d1 + 1e-12 * float(np.sum(ref[f"{side}_scores"]))
+        n_ok = tie_draws(ref[f"{side}_scores"], u, g, p.replacement, tol)
+        assert gpu[f"{side}_idx"][:n_ok] == list(ref[f"{side}_idx"][:n_ok]), side
+        out[side] = n_ok
+    return out

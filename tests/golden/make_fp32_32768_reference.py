@@ -3,8 +3,12 @@
 Runs only the oracle (host, NumPy/LAPACK) on the stored FP32 matrix that
 ``bcur_inputs.fp32_32768()`` (or ``precision_32768()``, k = 100, p = 20,
 q = 3) draws, and stores block scores, block indices, the top singular values
-and the residual in ``<workload>_oracle.json`` next to this file.  Needs about
-45 GB of host memory and a few minutes on 16 cores.
+and the residual in ``<workload>_oracle.json`` next to this file.  It also
+times the oracle on the bounded sample that the benchmark times
+(``bcur_inputs.host_sample``: the same recipe at 1/4 the size per side), in
+the same process on the same host cores, so that the benchmark can scale its
+sample's time to the full size by a measured ratio.  Needs about 45 GB of
+host memory and a few minutes on 16 cores.
 
     python tests/golden/make_fp32_32768_reference.py [fp32_32768 | precision_32768]
 """
@@ -38,11 +42,19 @@ def main():
                sigma=[float(x) for x in r["sigma"]], err=float(r["err"]), rel=float(r["rel"]),
                norm_a=float(np.linalg.norm(A.astype(np.float64))),
                seconds_generate=round(t1 - t0, 1), seconds_oracle=round(t2 - t1, 1))
+    ps = bi.host_sample(p)
+    As = ps.matrix()
+    t3 = time.time()
+    orc.block_cur(As, ps.col_off, ps.row_off, ps.k, ps.q, ps.g_col, ps.g_row, ps.omega(),
+                  ps.u_col(), ps.u_row())
+    t4 = time.time()
+    out.update(seconds_sample=round(t4 - t3, 2), sample=f"{ps.m}x{ps.n}, g {ps.g_col}+{ps.g_row}",
+               cores=os.cpu_count())
     path = os.path.join(HERE, f"{p.name}_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
-    print(json.dumps({k: out[k] for k in ("rel", "err", "col_idx", "row_idx",
-                                          "seconds_generate", "seconds_oracle")}))
+    print(json.dumps({k: out[k] for k in ("rel", "err", "col_idx", "row_idx", "seconds_generate",
+                                          "seconds_oracle", "seconds_sample", "cores")}))
 
 
 if __name__ == "__main__":

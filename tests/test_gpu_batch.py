@@ -223,3 +223,39 @@ def test_nonfinite_item_is_reported():
     with pytest.raises(pkg.BcurError) as e:
         b.sync_status()
     assert e.value.status == 5
+
+
+def test_autotuned_tile_widths_are_measured_once_and_cached(tmp_path, monkeypatch):
+    """The autotuner times each GEMM shape class once and keeps its choice in
+    the process table and in the JSON cache file; a second plan of the same
+    shapes measures nothing and gives bit for bit the same results."""
+    import json
+
+    import paper_1703_06065_gb300 as pkg
+
+    device()
+    L = pkg.load()
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("BCUR_AUTOTUNE_CACHE", str(cache))
+    # shapes no other test uses, so that their classes are new to the table
+    probs = [bi.Problem(f"tune_{i}", m, n, k=k, p=10, q=2, col_off=bi.uniform_blocks(n, s),
+                        row_off=bi.uniform_blocks(m, s), g_col=g, g_row=g, seed=40 + i,
+                        storage="f32", recipe=dict(kind="ar1_mixture", rank=k, phi=0.95,
+                                                   noise=0.05))
+             for i, (m, n, k, s, g) in enumerate([(2944, 5120, 17, 160, 3), (1408, 9216, 9, 96, 4)])]
+    n0 = L.bcur_autotune_measured()
+    b1, ins, r1 = _run(probs)
+    n1 = L.bcur_autotune_measured()
+    assert n1 > n0
+    table = json.loads(cache.read_text())
+    assert table and all(v in (64, 128, 256) for v in table.values())
+    assert any(k.startswith("w|") for k in table) and any(k.startswith("sketch_y|") for k in table)
+    b2 = pkg.Batch([_item(p) for p in probs], q=2)
+    assert L.bcur_autotune_measured() == n1           # every class came from the table
+    o2 = b2.run(*ins)
+    b2.sync_status()
+    r2 = [_host(o2, i) for i in range(len(probs))]
+    for a, b in zip(r1, r2):
+        for key in a:
+            if a[key] is not None:
+                np.testing.assert_array_equal(a[key], b[key])

@@ -45,6 +45,7 @@ def test_boosting_keeps_the_smallest_error():
     ucs = [to_dev(bi.uniforms(p.g_col, sd, 3)) for sd in seeds]
     urs = [to_dev(bi.uniforms(p.g_row, sd, 4)) for sd in seeds]
     best, i = pkg.boosted(plan, to_dev(A), oms, ucs, urs)
+    i = int(i.item())
     errs = []
     for sd in seeds:
         r = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row,
@@ -53,3 +54,53 @@ def test_boosting_keeps_the_smallest_error():
         errs.append(r["err"])
     assert i == int(np.argmin(errs))
     assert abs(float(best["err"][0]) - min(errs)) <= 1e-9 * min(errs)
+    # the chosen run's outputs are that run's: its indices are the oracle's
+    sd = seeds[i]
+    r = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row,
+                      bi.rademacher(p.n, p.l, sd), bi.uniforms(p.g_col, sd, 3),
+                      bi.uniforms(p.g_row, sd, 4))
+    assert best["col_idx"].cpu().tolist() == list(r["col_idx"])
+    assert best["row_idx"].cpu().tolist() == list(r["row_idx"])
+
+
+def test_boosting_in_one_batched_pass():
+    """t = 4 independent draws on the same resident FP32 matrix run as the
+    members of one batch; the device picks the smallest error, which must be
+    the run the FP64 oracle ranks first (the four errors are well apart) and
+    meet the 1e-3 gate."""
+    import paper_1703_06065_gb300 as pkg
+
+    device()
+    p = bi.Problem("boost_f32", 768, 1536, k=8, p=8, q=2, col_off=bi.uniform_blocks(1536, 64),
+                   row_off=bi.uniform_blocks(768, 64), g_col=3, g_row=3, seed=5, storage="f32",
+                   recipe=dict(kind="ar1_mixture", rank=8, phi=0.95, noise=0.05))
+    A = p.matrix()
+    seeds = [21, 22, 23, 24]
+    oms = [to_dev(np.ascontiguousarray(bi.rademacher(p.n, p.l, sd).T), torch.float32) for sd in seeds]
+    ucs = [to_dev(bi.uniforms(p.g_col, sd, 3)) for sd in seeds]
+    urs = [to_dev(bi.uniforms(p.g_row, sd, 4)) for sd in seeds]
+    item = dict(m=p.m, n=p.n, k=p.k, p=p.p, block=64, g_col=p.g_col, g_row=p.g_row)
+    best, idx, _ = pkg.boosted_batch(item, to_dev(A), oms, ucs, urs)
+    refs = [orc.block_cur(A.astype(np.float64), p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row,
+                          bi.rademacher(p.n, p.l, sd), bi.uniforms(p.g_col, sd, 3),
+                          bi.uniforms(p.g_row, sd, 4)) for sd in seeds]
+    rel = [r["rel"] for r in refs]
+    i = int(idx.item())
+    order = np.argsort(rel)
+    if rel[order[1]] - rel[order[0]] > 2e-3:   # a clear winner: the device must find it
+        assert i == int(order[0])
+    assert abs(float(best["err"][1]) - rel[i]) <= 1e-3
+    assert float(best["err"][1]) <= min(rel) + 1e-3
+
+
+def test_rank_k_ratio_against_the_oracle():
+    """||A - A_k||_F from the plan's top-k factors equals the exact tail of the
+    spectrum (the range finder is exact for the rank-10 + small-noise recipe
+    with q = 2), and the ratio ||A - CUR||_F / ||A - A_k||_F follows."""
+    p = bi.plain_fp64_512x1024()
+    ref, gpu, plan = run_problem(p)
+    A = p.matrix()
+    out = plan.rank_k_error(to_dev(A)).cpu().numpy()
+    tail = orc.tail_norm(A, p.k)
+    assert abs(out[0] - tail) <= 1e-6 * tail
+    assert abs(out[1] - ref["err"] / tail) <= 1e-6 * ref["err"] / tail
