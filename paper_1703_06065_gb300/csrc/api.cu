@@ -743,16 +743,17 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
                          P->at<int64_t>(P->o.colmap), counts, s));
   BCUR_TRY(expand_blocks(ri, P->d.g_row, P->at<int64_t>(P->o.row_off), P->d.G_row, rw,
                          P->at<int64_t>(P->o.rowmap), counts + 1, s));
-  float* Cp = P->at<float>(P->o.Cp0);
-  float* Rp = P->at<float>(P->o.Rp0);
-  BCUR_TRY(gather_cols_t<float>(A, lda, m, P->at<int64_t>(P->o.colmap), cw, Cp, ldm, s));
-  BCUR_TRY(gather_rows<float>(A, lda, n, P->at<int64_t>(P->o.rowmap), rw, Rp, ldn, s));
-  if (Cout) BCUR_TRY(copy2d<float>(Cp, ldm, Cout, m, P->c_max, m, s));
-  if (Rout) BCUR_TRY(copy2d<float>(Rp, ldn, Rout, n, P->r_max, n, s));
+  const int64_t* colmap = P->at<int64_t>(P->o.colmap);
+  const int64_t* rowmap = P->at<int64_t>(P->o.rowmap);
+  // C^T and R are gathered straight into their BF16 pairs (one read of the
+  // chosen columns / rows of A, one write of the pair); the FP32 copies the
+  // caller may ask for are gathered into its buffers.
+  if (Cout) BCUR_TRY(gather_cols_t<float>(A, lda, m, colmap, P->c_max, Cout, m, s));
+  if (Rout) BCUR_TRY(gather_rows<float>(A, lda, n, rowmap, P->r_max, Rout, n, s));
   S16 XC[2] = {s16(P, P->o.XC16[0], P->o.XC16[1], lo), s16(P, P->o.XC16[2], P->o.XC16[3], lo)};
   S16 XR[2] = {s16(P, P->o.XR16[0], P->o.XR16[1], lo), s16(P, P->o.XR16[2], P->o.XR16[3], lo)};
-  BCUR_TRY(split(P, Cp, ldm, cw, m, XC[0], ldm));
-  BCUR_TRY(split(P, Rp, ldn, rw, n, XR[0], ldn));
+  BCUR_TRY(gather_cols_pair(A, lda, m, colmap, cw, XC[0].h, XC[0].l, ldm, s));
+  BCUR_TRY(gather_rows_pair(A, lda, n, rowmap, rw, XR[0].h, XR[0].l, ldn, s));
   int* kept = P->at<int>(P->o.kept);
   // The QR factors of C and R^T are independent: the R side runs on the
   // second lane (fork / join through events, so this also works in a graph).

@@ -228,6 +228,17 @@ bcur_status_t quant_rows_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t
 bcur_status_t transpose_u8(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t cols, uint8_t* T,
                            int64_t ldt, cudaStream_t s);
 
+// Gathers that write the BF16 pair (hi = bf16(a), lo = bf16(a - hi); lo may
+// be null) directly: rows R[rr] = A[map[rr]] (R cap x n, ld ldo) and the
+// transposed columns C^T[cc] = A[:, map[cc]] (C^T cap x m, ld ldo, even).
+// Entries with map < 0 give zeros.
+bcur_status_t gather_rows_pair(const float* A, int64_t lda, int64_t n, const int64_t* map,
+                               int64_t cap, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                               cudaStream_t s);
+bcur_status_t gather_cols_pair(const float* A, int64_t lda, int64_t m, const int64_t* map,
+                               int64_t cap, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                               cudaStream_t s);
+
 // Split an FP32 matrix (rows x cols, ldx) into BF16 pairs: hi = bf16(x),
 // lo = bf16(x - hi) (round to nearest even both times); outputs have
 // leading dimension ldo; lo may be null (hi only).

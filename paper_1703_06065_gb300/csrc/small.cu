@@ -903,6 +903,139 @@ bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols
 }
 
 // ---------------------------------------------------------------------------
+// Gathers straight into BF16 pairs (the split-BF16 fit's operands): each
+// element of A is read once and written once as hi = bf16(a), lo =
+// bf16(a - hi), with no FP32 copy of C or R in between.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split2(float a, float b, __nv_bfloat162* h, __nv_bfloat162* l) {
+  *h = __floats2bfloat162_rn(a, b);
+  const float2 f = __bfloat1622float2(*h);
+  *l = __floats2bfloat162_rn(a - f.x, b - f.y);
+}
+
+// R[rr][j] = A[map[rr]][j] as a pair (zero rows where map < 0).  vec: A rows
+// 16-byte aligned (lda % 4 == 0, A aligned) and ldo % 4 == 0 (8-byte aligned
+// outputs): four elements per thread, float4 in, two bf16x2 out per part.
+__global__ void gather_rows_pair_kernel(const float* A, int64_t lda, int64_t n, const int64_t* map,
+                                        __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                                        int vec) {
+  const int64_t rr = blockIdx.y;
+  const int64_t row = map[rr];
+  const float* src = A + (row >= 0 ? row : 0) * lda;
+  __nv_bfloat16* dh = hi + rr * ldo;
+  __nv_bfloat16* dl = lo ? lo + rr * ldo : nullptr;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    for (int64_t q = tid; q < n4; q += nth) {
+      const float4 v = row >= 0 ? __ldcs(reinterpret_cast<const float4*>(src) + q)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      __nv_bfloat162 h[2], l[2];
+      split2(v.x, v.y, &h[0], &l[0]);
+      split2(v.z, v.w, &h[1], &l[1]);
+      reinterpret_cast<uint2*>(dh)[q] = *reinterpret_cast<const uint2*>(h);
+      if (dl) reinterpret_cast<uint2*>(dl)[q] = *reinterpret_cast<const uint2*>(l);
+    }
+    done = 4 * n4;
+  }
+  for (int64_t j = done + tid; j < n; j += nth) {
+    const float a = row >= 0 ? src[j] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(a);
+    dh[j] = h;
+    if (dl) dl[j] = __float2bfloat16_rn(a - __bfloat162float(h));
+  }
+}
+
+// C^T[cc][i] = A[i][map[cc]] as a pair, 64 x 64 tiles through shared memory.
+// A tile whose 64 gathered columns are consecutive in A and start on a
+// 16-byte boundary is read as float4 rows; other tiles (block boundaries
+// inside the tile, blocks drawn out of order, ragged sizes) element by
+// element.  Output rows past cap are not written; map < 0 gives zeros.
+__global__ void __launch_bounds__(256) gather_cols_pair_kernel(const float* A, int64_t lda,
+                                                               int64_t m, const int64_t* map,
+                                                               int64_t cap, __nv_bfloat16* hi,
+                                                               __nv_bfloat16* lo, int64_t ldo,
+                                                               int a_vec) {
+  __shared__ float t[64][65];
+  const int64_t i0 = (int64_t)blockIdx.x * 64, cc0 = (int64_t)blockIdx.y * 64;
+  const int tid = threadIdx.x;
+  const int64_t c0 = map[cc0];
+  int ok = a_vec && c0 >= 0 && (c0 % 4) == 0 && cc0 + 63 < cap;
+  if (ok) ok = (map[cc0 + (tid & 63)] == c0 + (tid & 63));
+  ok = __syncthreads_and(ok);
+  if (ok) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int r = (tid >> 4) + 16 * it, q = tid & 15;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + r < m) v = __ldcs(reinterpret_cast<const float4*>(A + (i0 + r) * lda + c0) + q);
+      t[r][4 * q] = v.x;
+      t[r][4 * q + 1] = v.y;
+      t[r][4 * q + 2] = v.z;
+      t[r][4 * q + 3] = v.w;
+    }
+  } else {
+    for (int e = tid; e < 64 * 64; e += 256) {
+      const int r = e >> 6, c = e & 63;
+      const int64_t cc = cc0 + c, i = i0 + r;
+      const int64_t col = cc < cap ? map[cc] : -1;
+      t[r][c] = (col >= 0 && i < m) ? A[i * lda + col] : 0.f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int c = (tid >> 5) + 8 * it, ip = tid & 31;
+    const int64_t cc = cc0 + c, i = i0 + 2 * ip;
+    if (cc >= cap || i >= m) continue;
+    __nv_bfloat16* dh = hi + cc * ldo + i;
+    __nv_bfloat16* dl = lo ? lo + cc * ldo + i : nullptr;
+    if (i + 1 < m) {
+      __nv_bfloat162 h, l;
+      split2(t[2 * ip][c], t[2 * ip + 1][c], &h, &l);
+      *reinterpret_cast<__nv_bfloat162*>(dh) = h;
+      if (dl) *reinterpret_cast<__nv_bfloat162*>(dl) = l;
+    } else {
+      const float a = t[2 * ip][c];
+      const __nv_bfloat16 h = __float2bfloat16_rn(a);
+      dh[0] = h;
+      if (dl) dl[0] = __float2bfloat16_rn(a - __bfloat162float(h));
+    }
+  }
+}
+
+bcur_status_t gather_rows_pair(const float* A, int64_t lda, int64_t n, const int64_t* map,
+                               int64_t cap, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                               cudaStream_t s) {
+  if (cap <= 0 || n <= 0) return BCUR_OK;
+  if (cap > 65535) return BCUR_EINVAL;
+  const int vec = (lda % 4 == 0) && ((uintptr_t)A % 16 == 0) && (ldo % 4 == 0) &&
+                  ((uintptr_t)hi % 8 == 0) && (!lo || (uintptr_t)lo % 8 == 0);
+  const int64_t per_row = vec ? n / 4 : n;
+  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(ceil_div(per_row, 256), 16));
+  gather_rows_pair_kernel<<<dim3((unsigned)gx, (unsigned)cap), 256, 0, s>>>(A, lda, n, map, hi,
+                                                                            lo, ldo, vec);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+bcur_status_t gather_cols_pair(const float* A, int64_t lda, int64_t m, const int64_t* map,
+                               int64_t cap, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo,
+                               cudaStream_t s) {
+  if (cap <= 0 || m <= 0) return BCUR_OK;
+  if (ceil_div(cap, 64) > 65535 || ldo % 2 != 0 || (uintptr_t)hi % 4 != 0 ||
+      (lo && (uintptr_t)lo % 4 != 0))
+    return BCUR_EINVAL;
+  const int a_vec = (lda % 4 == 0) && ((uintptr_t)A % 16 == 0);
+  dim3 grid((unsigned)ceil_div(m, 64), (unsigned)ceil_div(cap, 64));
+  gather_cols_pair_kernel<<<grid, 256, 0, s>>>(A, lda, m, map, cap, hi, lo, ldo, a_vec);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Instantiations
 // ---------------------------------------------------------------------------
 #define BCUR_INST(T)                                                                              \
