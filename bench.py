@@ -858,10 +858,13 @@ def main_serving(args):
     pkg.load()
     reqs = bi.serving_requests(args.rate, args.duration, seed=4 + 1000 * rank)
     srv = serve.Server(hbm_budget=args.hbm_budget, lanes=3, max_batch=128, heavy_lanes=2,
-                       max_heavy_batch=8)
+                       max_heavy_batch=16, draw=bi.generators.request_inputs_device)
     # warm-up: the kernels, the allocator and the plan builders on the first requests
     warm = bi.serving_requests(args.rate, 0.05, seed=99)
     srv.run(warm, realtime=False)
+    # tile widths of shape classes first met during the timed run are the
+    # fixed ones: no autotuner measurements inside the timed region
+    os.environ["BCUR_AUTOTUNE"] = "0"
     clocks = Clocks(local)
     clocks.start()
     t0 = time.perf_counter()
@@ -911,7 +914,9 @@ def main_serving(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16/bf16x3", "data": "synthetic",
             "config": {"workload": "serving", "rate_per_s": args.rate, "duration_s": args.duration,
                        "requests": len(reqs), "heavy": int(sum(r.heavy for r in reqs)),
-                       "lanes": "3 light + 2 heavy streams", "hbm_budget_gb": args.hbm_budget / 1e9},
+                       "lanes": "3 light + 2 heavy streams, batched groups (up to 128 "
+                                "light, 16 heavy)",
+                       "hbm_budget_gb": args.hbm_budget / 1e9},
             "latency": {k: round(v, 3) for k, v in st.items() if k.endswith("_ms")},
             "completed": st["requests"], "wall_s": round(wall, 2), "groups": jobs,
             "clocks": clk, "baseline_one_at_a_time": base,
@@ -979,8 +984,8 @@ def main():
     ap.add_argument("--count", type=int, default=BATCH_COUNT,
                     help="batched workload: decompose only the first COUNT matrices (profiling)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
-    ap.add_argument("--duration", type=float, default=10.0,
-                    help="serving: seconds of arrivals (the full workload is 60)")
+    ap.add_argument("--duration", type=float, default=60.0,
+                    help="serving: seconds of arrivals")
     ap.add_argument("--hbm-budget", type=float, default=160e9, help="serving: admission budget")
     ap.add_argument("--kernel", default=None, choices=["wgemm"],
                     help="time one kernel instead of the workload (profiling)")

@@ -74,7 +74,7 @@ class Plan:
                  row_off: Sequence[int], g_col: int, g_row: int, dtype: str = "f32",
                  lda: Optional[int] = None, replacement: bool = False,
                  sketch_prec: Optional[str] = None, fit_prec: Optional[str] = None,
-                 device=None):
+                 device=None, workspace=None):
         torch = _torch()
         L = _lib.load()
         self._L = L
@@ -105,7 +105,12 @@ class Plan:
         self.workspace_bytes = ws.value
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
-        self._ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=dev)
+        if workspace is not None:   # caller-owned device memory (e.g. a serving arena)
+            if workspace.numel() < ws.value:
+                raise ValueError(f"workspace of {workspace.numel()} bytes < {ws.value} needed")
+            self._ws = workspace
+        else:
+            self._ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=dev)
         _lib.check(L.bcur_set_workspace(h, _ptr(self._ws), c_size_t(self._ws.numel())),
                    "bcur_set_workspace")
         self.c_max = self._max_sum(self._col_off, g_col, replacement)
@@ -143,14 +148,17 @@ class Plan:
         _lib.check(self._L.bcur_factors(self._h, _ptr(Vt), _ptr(Ut), _ptr(sig)), "bcur_factors")
         return Vt, Ut, sig
 
-    def sample(self, cs, rs, u_col, u_row):
+    def sample(self, cs, rs, u_col, u_row, out=None):
         torch = _torch()
         _need_cuda(cs, rs, u_col, u_row)
         dev = cs.device
-        ci = torch.empty(self.g_col, dtype=torch.int32, device=dev)
-        ri = torch.empty(self.g_row, dtype=torch.int32, device=dev)
-        cp = torch.empty(self.g_col, dtype=torch.float64, device=dev)
-        rp = torch.empty(self.g_row, dtype=torch.float64, device=dev)
+        if out is not None:
+            ci, ri, cp, rp = out
+        else:
+            ci = torch.empty(self.g_col, dtype=torch.int32, device=dev)
+            ri = torch.empty(self.g_row, dtype=torch.int32, device=dev)
+            cp = torch.empty(self.g_col, dtype=torch.float64, device=dev)
+            rp = torch.empty(self.g_row, dtype=torch.float64, device=dev)
         _lib.check(self._L.bcur_sample(self._h, _ptr(cs), _ptr(rs), _ptr(u_col), _ptr(u_row),
                                        _ptr(ci), _ptr(ri), _ptr(cp), _ptr(rp)), "bcur_sample")
         return ci, ri, cp, rp

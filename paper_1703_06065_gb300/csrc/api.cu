@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -1417,7 +1418,26 @@ bcur_status_t bcur_decompose_host(bcur_plan_t P, const void* A, const void* omeg
   auto d2h = [&](void* dst, size_t off, size_t bytes) {
     return cudaMemcpyAsync(dst, base + off, bytes, cudaMemcpyDeviceToHost, s);
   };
-  BCUR_CUDA_TRY(h2d(h.A, A, (size_t)P->m * P->lda * e));
+  // A, the one large input: read by the SMs over the host link when the
+  // page-locked buffer is mapped into the device's address space (measured
+  // faster than the copy engines on GB300), otherwise copied.
+  // BCUR_H2D=copy forces the copy engines.
+  {
+    const size_t abytes = (size_t)P->m * P->lda * e;
+    void* mapped = nullptr;
+    const char* mode = getenv("BCUR_H2D");
+    const bool want_sm = !(mode && strcmp(mode, "copy") == 0);
+    bool done = false;
+    if (want_sm && abytes % 16 == 0 &&
+        cudaHostGetDevicePointer(&mapped, const_cast<void*>(A), 0) == cudaSuccess && mapped &&
+        ((uintptr_t)mapped & 15) == 0) {
+      BCUR_TRY(copy_bytes_sm(mapped, base + h.A, abytes, P->sms, s));
+      done = true;
+    } else {
+      cudaGetLastError();  // a buffer that is not mapped is not an error here
+    }
+    if (!done) BCUR_CUDA_TRY(h2d(h.A, A, abytes));
+  }
   BCUR_CUDA_TRY(h2d(h.om, omega, (size_t)P->l * P->n * e));
   BCUR_CUDA_TRY(h2d(h.uc, u_col, (size_t)P->d.g_col * 8));
   BCUR_CUDA_TRY(h2d(h.ur, u_row, (size_t)P->d.g_row * 8));

@@ -406,29 +406,65 @@ __global__ void sample_kernel(const Item* items, const bcur_batch_io_t* io) {
 }
 
 // C^T panel (cpad x m) and R (rpad x n) as BF16 pairs, straight from A.
-__global__ void gather_c_kernel(const Item* items, const bcur_batch_io_t* io, Work tiles) {
+// C^T of one decomposition as a BF16 pair, 64 x 64 tiles (rows i of A, gathered
+// columns cc) through shared memory.  A tile whose 64 columns are consecutive
+// in A and start on a 16-byte boundary reads float4 row pieces; other tiles
+// (a block boundary inside the tile, blocks of 16 or 32 drawn out of order)
+// read element by element.  Stores are two BF16 per thread and part.
+__global__ void __launch_bounds__(256) gather_c_kernel(const Item* items,
+                                                       const bcur_batch_io_t* io, Work tiles) {
   const int b = find_item(tiles, blockIdx.x);
   const Item& I = items[b];
   const int t = blockIdx.x - tiles.prefix[b];
-  const int ti = (int)((I.m + 31) / 32);
-  const int64_t i0 = (int64_t)(t % ti) * 32, c0 = (int64_t)(t / ti) * 32;
-  __shared__ float tile[32][33];
-  const int x = threadIdx.x;
-  const int64_t cc = c0 + x;
-  const int col = cc < I.cpad ? I.colmap[cc] : -1;
+  const int ti = (int)((I.m + 63) / 64);
+  const int64_t i0 = (int64_t)(t % ti) * 64, c0 = (int64_t)(t / ti) * 64;
+  __shared__ float tile[64][65];
+  const int tid = threadIdx.x;
   const float* A = io[b].A;
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t i = i0 + y;
-    tile[y][x] = (col >= 0 && i < I.m) ? A[i * I.lda + col] : 0.f;
+  const int first = I.colmap[c0];
+  int ok = first >= 0 && (first % 4) == 0 && c0 + 63 < I.cpad && (I.lda % 4) == 0 &&
+           ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  if (ok) ok = I.colmap[c0 + (tid & 63)] == first + (tid & 63);
+  ok = __syncthreads_and(ok);
+  if (ok) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int r = (tid >> 4) + 16 * it, q = tid & 15;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + r < I.m)
+        v = __ldcs(reinterpret_cast<const float4*>(A + (i0 + r) * I.lda + first) + q);
+      tile[r][4 * q] = v.x;
+      tile[r][4 * q + 1] = v.y;
+      tile[r][4 * q + 2] = v.z;
+      tile[r][4 * q + 3] = v.w;
+    }
+  } else {
+    for (int e = tid; e < 64 * 64; e += 256) {
+      const int r = e >> 6, c = e & 63;
+      const int64_t cc = c0 + c, i = i0 + r;
+      const int col = cc < I.cpad ? I.colmap[cc] : -1;
+      tile[r][c] = (col >= 0 && i < I.m) ? A[i * I.lda + col] : 0.f;
+    }
   }
   __syncthreads();
-  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t c = c0 + y, i = i0 + x;
-    if (c < I.cpad && i < I.m) {
-      const float v = tile[x][y];
-      const bf16 h = __float2bfloat16_rn(v);
-      I.XCh[0][c * I.ldm + i] = h;
-      I.XCl[0][c * I.ldm + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int c = (tid >> 5) + 8 * it, ip = tid & 31;
+    const int64_t cc = c0 + c, i = i0 + 2 * ip;
+    if (cc >= I.cpad || i >= I.m) continue;
+    bf16* dh = I.XCh[0] + cc * I.ldm + i;
+    bf16* dl = I.XCl[0] + cc * I.ldm + i;
+    const float v0 = tile[2 * ip][c];
+    if (i + 1 < I.m) {
+      const float v1 = tile[2 * ip + 1][c];
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      const float2 f = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162*>(dh) = h;
+      *reinterpret_cast<__nv_bfloat162*>(dl) = __floats2bfloat162_rn(v0 - f.x, v1 - f.y);
+    } else {
+      const bf16 h = __float2bfloat16_rn(v0);
+      dh[0] = h;
+      dl[0] = __float2bfloat16_rn(v0 - __bfloat162float(h));
     }
   }
 }
@@ -820,7 +856,7 @@ bcur_status_t sample(const Item* items, const bcur_batch_io_t* io, int B, cudaSt
 
 bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, int ctotal,
                      Work rrows, int rtotal, cudaStream_t s) {
-  gather_c_kernel<<<ctotal, dim3(32, 8), 0, s>>>(items, io, ctiles);
+  gather_c_kernel<<<ctotal, 256, 0, s>>>(items, io, ctiles);
   BCUR_LAUNCH_CHECK();
   gather_r_kernel<<<rtotal, 256, 0, s>>>(items, io, rrows);
   BCUR_LAUNCH_CHECK();

@@ -570,7 +570,7 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
     am[b] = (int)ceil_div(I.m, AP);
     an[b] = (int)ceil_div(I.n, AP);
     bl[b] = I.Gc + I.Gr;
-    ct[b] = (int)(ceil_div(I.cpad, 32) * ceil_div(I.m, 32));
+    ct[b] = (int)(ceil_div(I.cpad, 64) * ceil_div(I.m, 64));
     rr[b] = I.rpad;
     ur[b] = I.cmax;
   }

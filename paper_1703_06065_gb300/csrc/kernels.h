@@ -200,6 +200,9 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
                      cudaStream_t s);
 
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
+// dst = src (bytes, both 16-byte aligned, bytes a multiple of 16) by the SMs;
+// src may be mapped host memory.
+bcur_status_t copy_bytes_sm(const void* src, void* dst, size_t bytes, int sms, cudaStream_t s);
 
 // Boosting (boost.cu): the run with the smallest err[i * err_stride] among t
 // runs laid out contiguously (first minimum in run order), its index in

@@ -10,6 +10,8 @@
 
 #include <cuda_fp8.h>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 #include "leaf.cuh"
 
@@ -520,31 +522,53 @@ bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_
 }
 
 // ---------------------------------------------------------------------------
-// Block leverage scores (Def. 2): one CTA per block, FP64 accumulation in a
-// fixed order (strided per thread, xor-tree per warp, warps in order).
+// Block leverage scores (Def. 2): one thread-block cluster of kScoreCtas CTAs
+// per block g.  CTA q of the cluster sums F[j, t]^2 over its slice of the
+// block's columns j (every row t, consecutive threads on consecutive j, so
+// each row piece is one coalesced read) in FP64; the CTA's partial is formed
+// in a fixed order (per thread, xor-tree per warp, warps in order), and CTA 0
+// adds the cluster's partials in rank order through distributed shared
+// memory, so the score does not depend on scheduling.
 // ---------------------------------------------------------------------------
+constexpr int kScoreCtas = 8;
+
 template <typename T>
-__global__ void block_scores_kernel(const T* Ft, int k, int64_t ldf, const int64_t* off,
-                                    double* scores, int* status) {
-  const int g = blockIdx.x;
+__global__ void __cluster_dims__(kScoreCtas, 1, 1) __launch_bounds__(256)
+    block_scores_kernel(const T* Ft, int k, int64_t ldf, const int64_t* off, double* scores,
+                        int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int g = blockIdx.y;
+  const int q = (int)cluster.block_rank();
   const int64_t j0 = off[g], size = off[g + 1] - off[g];
-  const int64_t total = size * k;
+  const int64_t chunk = (size + kScoreCtas - 1) / kScoreCtas;
+  const int64_t a = j0 + q * chunk, b = min(j0 + size, a + chunk);
   double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    const int64_t t = e / size, j = j0 + e % size;
-    const double v = (double)Ft[t * ldf + j];
-    acc = fma(v, v, acc);
+  for (int t = 0; t < k; ++t) {
+    const T* row = Ft + (int64_t)t * ldf;
+    for (int64_t j = a + threadIdx.x; j < b; j += blockDim.x) {
+      const double v = (double)row[j];
+      acc = fma(v, v, acc);
+    }
   }
   acc = warp_sum(acc);
   __shared__ double r[32];
+  __shared__ double part;
   if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += r[w];
+    part = sum;
+  }
+  cluster.sync();  // every CTA's partial is written
+  if (q == 0 && threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int c = 0; c < kScoreCtas; ++c) sum += *cluster.map_shared_rank(&part, c);
     scores[g] = sum;
     if (!isfinite(sum)) dev_set_status(status, (int)BCUR_ENONFINITE);
   }
+  cluster.sync();  // the partials stay alive until CTA 0 has read them
 }
 
 template <typename T>
@@ -552,7 +576,9 @@ bcur_status_t block_scores(const T* Ft, int k, int64_t h, int64_t ldf, const int
                            double* scores, int* status, cudaStream_t s) {
   (void)h;
   if (G <= 0) return BCUR_OK;
-  block_scores_kernel<T><<<G, 256, 0, s>>>(Ft, k, ldf, off, scores, status);
+  if (G > 65535) return BCUR_EINVAL;
+  block_scores_kernel<T><<<dim3(kScoreCtas, (unsigned)G), 256, 0, s>>>(Ft, k, ldf, off, scores,
+                                                                       status);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
@@ -680,6 +706,37 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
   if (rows <= 0 || cols <= 0) return BCUR_OK;
   BCUR_CUDA_TRY(cudaMemcpy2DAsync(dst, ldd * sizeof(T), src, lds * sizeof(T), cols * sizeof(T),
                                   rows, cudaMemcpyDeviceToDevice, s));
+  return BCUR_OK;
+}
+
+// Copy of `bytes` bytes by the SMs: 16 bytes per thread and step, many
+// loads in flight per SM.  Used to bring a page-locked host buffer that is
+// mapped into the device's address space into device memory with the SMs
+// reading it over the host link (the copy engines are the alternative).
+__global__ void __launch_bounds__(256) copy_bytes_kernel(const uint4* __restrict__ src,
+                                                         uint4* __restrict__ dst, int64_t n16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = __ldcs(src + i), b = __ldcs(src + i + stride);
+    const uint4 c = __ldcs(src + i + 2 * stride), d = __ldcs(src + i + 3 * stride);
+    __stcs(dst + i, a);
+    __stcs(dst + i + stride, b);
+    __stcs(dst + i + 2 * stride, c);
+    __stcs(dst + i + 3 * stride, d);
+  }
+  for (; i < n16; i += stride) __stcs(dst + i, __ldcs(src + i));
+}
+
+bcur_status_t copy_bytes_sm(const void* src, void* dst, size_t bytes, int sms, cudaStream_t s) {
+  if (((uintptr_t)src | (uintptr_t)dst | bytes) & 15) return BCUR_EINVAL;
+  const int64_t n16 = (int64_t)(bytes / 16);
+  if (n16 == 0) return BCUR_OK;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)sms,
+                                                                 (n16 + 255) / 256));
+  copy_bytes_kernel<<<blocks, 256, 0, s>>>(static_cast<const uint4*>(src),
+                                           static_cast<uint4*>(dst), n16);
+  BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 

@@ -9,9 +9,14 @@ Requests arrive over time (each a matrix to decompose).  The loop
   into a batched decomposition (every stage one launch over the whole group,
   :class:`Batch`) as soon as a lane is free, so requests that arrive while
   others are on the GPU join the next group.  Heavy requests (l = k + p > 64,
-  which need 128-row panels) are grouped among themselves on lanes of their
-  own, so that they neither widen the panels of the light groups nor hold
-  them up;
+  which need 128-row panels) run on lanes of their own, so that they neither
+  widen the panels of the light groups nor hold them up.  By default they
+  are grouped into batches of their own (up to ``max_heavy_batch``: a
+  group's per-matrix factorisations run side by side, so a 16384^2 request
+  costs about 3.3 ms in a group of eight against 13 ms alone); with
+  ``heavy_plan=True`` each heavy lane instead keeps one single-matrix plan
+  (:class:`Plan`) and runs its heavy requests one after another (about
+  9.4 ms each for 16384^2, k = 64);
 * retires a group when its completion event has fired, returning its memory
   to the budget.
 
@@ -29,7 +34,7 @@ from typing import Callable, Dict, List, Optional
 
 import numpy as np
 
-from . import Batch, _lib
+from . import Batch, Plan, _lib
 
 LIGHT_L = 64   # requests with l = k + p above this are heavy (128-row panels)
 
@@ -103,17 +108,21 @@ class _Req:
 class Server:
     """Continuous batching over `lanes` CUDA streams with an HBM budget.
 
-    `draw(problem, device)` returns the request's inputs on the device: the
-    matrix A (FP32, row-major), the test matrix as an l x n panel and the two
-    vectors of uniforms; by default all drawn on the device from the
-    request's seed (biometric recipe, Rademacher test matrix).
+    `draw(problem, device, out)` returns the request's inputs on the device:
+    the matrix A (FP32, row-major, written into ``out``, an m x n view of the
+    arena), the test matrix as an l x n panel and the two vectors of
+    uniforms.  The caller supplies it (the benchmark and the tests draw every
+    input on the device from the request's seed).
     """
 
     def __init__(self, hbm_budget: float = 160e9, lanes: int = 3, max_batch: int = 128,
                  heavy_lanes: int = 2, max_heavy_batch: int = 8, heavy_share: float = 0.6,
                  builders: int = 4, keep_u: bool = False,
-                 keep_inputs: Callable = None, draw: Callable = None, device=None):
+                 keep_inputs: Callable = None, draw: Callable = None, device=None,
+                 heavy_plan: bool = False):
         torch = _torch()
+        if draw is None:
+            raise ValueError("Server needs draw(problem, device, out) for the requests' inputs")
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.budget = float(hbm_budget)
@@ -121,7 +130,8 @@ class Server:
         self.max_heavy_batch = max_heavy_batch
         self.keep_u = keep_u
         self.keep_inputs = keep_inputs or (lambda r: False)
-        self.draw = draw or self._draw
+        self.draw = draw
+        self.heavy_plan = heavy_plan
         self.gen_stream = torch.cuda.Stream(device=self.device)
         self.light = [{"stream": torch.cuda.Stream(device=self.device), "job": None}
                       for _ in range(lanes)]
@@ -139,13 +149,6 @@ class Server:
 
         self.pool = ThreadPoolExecutor(max_workers=builders)
         self.building = {False: collections.deque(), True: collections.deque()}
-
-    # -- inputs ---------------------------------------------------------------
-    @staticmethod
-    def _draw(p, device, out):
-        import bcur_inputs as bi
-
-        return bi.generators.request_inputs_device(p, device, out=out)
 
     def _footprint(self, q) -> float:
         """Matrix + panels + this request's share of a workspace."""
@@ -221,12 +224,75 @@ class Server:
         lane["job"] = dict(kind="heavy" if reqs[0].r.heavy else "light", reqs=reqs, batch=b,
                            host=host, start=start, done=done, ws=(ws_off, ws_bytes))
 
+    def _heavy_lane_plan(self, lane, p):
+        """The lane's single-matrix plan for this heavy shape (built on first
+        use with its workspace and outputs in the arena, kept for the run)."""
+        torch = self.torch
+        key = (p.m, p.n, p.k, p.p, p.q, int(p.col_off[1]), p.g_col, p.g_row)
+        pl = lane.get("plan")
+        if pl is not None and pl["key"] == key:
+            return pl
+        if pl is not None:  # another heavy shape: the idle lane's plan is replaced
+            self.arena.release(*pl["ws"])
+            self.budget += pl["ws"][1]
+            lane["plan"] = None
+        with torch.cuda.stream(lane["stream"]):
+            need = _plan_workspace(p)
+            off = self.arena.alloc(need)
+            if off is None:
+                return None
+            plan = Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
+                        dtype="f32", sketch_prec="bf16", fit_prec="bf16x3", device=self.device,
+                        workspace=self.arena.view(off, need))
+        dev = self.device
+        outs = dict(cs=torch.empty(plan.G_col, dtype=torch.float64, device=dev),
+                    rs=torch.empty(plan.G_row, dtype=torch.float64, device=dev),
+                    ci=torch.empty(plan.g_col, dtype=torch.int32, device=dev),
+                    ri=torch.empty(plan.g_row, dtype=torch.int32, device=dev),
+                    cp=torch.empty(plan.g_col, dtype=torch.float64, device=dev),
+                    rp=torch.empty(plan.g_row, dtype=torch.float64, device=dev),
+                    U=torch.empty(plan.c_max, plan.r_max, device=dev),
+                    err=torch.empty(3, dtype=torch.float64, device=dev))
+        self.budget -= need   # held by the lane for the rest of the run
+        lane["plan"] = dict(key=key, plan=plan, outs=outs, ws=(off, need))
+        return lane["plan"]
+
+    def _start_heavy(self, lane, q, pl):
+        """Run one heavy request on `lane` with the lane's plan."""
+        torch = self.torch
+        s = lane["stream"]
+        plan, o = pl["plan"], pl["outs"]
+        with torch.cuda.stream(s):
+            s.wait_event(q.ready)
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(s)
+            plan.scores(q.A, q.omega, out=(o["cs"], o["rs"]))
+            plan.sample(o["cs"], o["rs"], q.u_col, q.u_row, out=(o["ci"], o["ri"], o["cp"], o["rp"]))
+            plan.fit(q.A, o["ci"], o["ri"], U=o["U"])
+            plan.error(q.A, out=o["err"])
+            host = {}
+            for k, src in (("err", o["err"]), ("col_idx", o["ci"]), ("row_idx", o["ri"]),
+                           ("U", o["U"] if self.keep_u else None)):
+                if src is None:
+                    host[k] = [None]
+                    continue
+                h = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
+                h.copy_(src, non_blocking=True)
+                host[k] = [h]
+            done = torch.cuda.Event(enable_timing=True)
+            done.record(s)
+        lane["job"] = dict(kind="heavy", reqs=[q], batch=None, plan=plan, host=host,
+                           start=start, done=done, ws=None)
+
     def _retire(self, lane, t_start_ev):
         job = lane["job"]
         t_done = t_start_ev.elapsed_time(job["done"]) / 1000.0
         self.jobs.append((job["kind"], len(job["reqs"]),
                           t_start_ev.elapsed_time(job["start"]) / 1000.0, t_done))
-        job["batch"].sync_status()
+        if job["batch"] is not None:
+            job["batch"].sync_status()
+        else:
+            job["plan"].sync_status()
         for i, q in enumerate(job["reqs"]):
             h = job["host"]
             q.t_done = t_done
@@ -241,7 +307,8 @@ class Server:
                 self.in_heavy -= q.bytes
             self.arena.release(q.a_off, 4 * q.r.problem.m * q.r.problem.n)
             q.A = q.omega = q.u_col = q.u_row = None
-        self.arena.release(*job["ws"])
+        if job["ws"] is not None:
+            self.arena.release(*job["ws"])
         job["batch"] = None
         lane["job"] = None
         return job["reqs"]
@@ -299,9 +366,19 @@ class Server:
                         self.in_heavy += q.bytes
                     (heavy if cls else light).append(q)
                     progressed = True
-            # dispatch on free lanes
+            # heavy requests one at a time on each free heavy lane's plan
+            if self.heavy_plan:
+                for lane in self.heavy:
+                    if lane["job"] is None and heavy:
+                        pl = self._heavy_lane_plan(lane, heavy[0].r.problem)
+                        if pl is not None:
+                            self._start_heavy(lane, heavy.popleft(), pl)
+                            progressed = True
+            # dispatch groups on free lanes
             for cls, lanes_, queue, cap in ((True, self.heavy, heavy, self.max_heavy_batch),
                                             (False, self.light, light, self.max_batch)):
+                if cls and self.heavy_plan:
+                    continue
                 # keep one group per lane being planned ahead of time
                 bq = self.building[cls]
                 while queue and len(bq) < len(lanes_):
@@ -323,6 +400,31 @@ class Server:
                 else:
                     time.sleep(5e-5)
         return done
+
+
+def _plan_workspace(p) -> int:
+    """Workspace bytes of a single-matrix plan (BF16 sketch, split-BF16 fit)."""
+    import ctypes
+
+    L = _lib.load()
+    col_off = np.ascontiguousarray(np.asarray(p.col_off, dtype=np.int64))
+    row_off = np.ascontiguousarray(np.asarray(p.row_off, dtype=np.int64))
+    d = _lib.Desc()
+    d.m, d.n, d.lda = p.m, p.n, p.n
+    d.a_dtype = _lib.BCUR_F32
+    d.k, d.p, d.q = p.k, p.p, p.q
+    d.G_col = len(col_off) - 1
+    d.col_off = col_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.G_row = len(row_off) - 1
+    d.row_off = row_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.g_col, d.g_row = p.g_col, p.g_row
+    d.replacement = 0
+    d.sketch_prec, d.fit_prec = _lib.BCUR_BF16, _lib.BCUR_BF16X3
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _lib.check(L.bcur_plan(ctypes.byref(d), None, ctypes.byref(h), ctypes.byref(ws)), "bcur_plan")
+    L.bcur_destroy(h)
+    return int(ws.value)
 
 
 def _batch_workspace(item: dict, q: int) -> int:

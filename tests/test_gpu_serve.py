@@ -24,6 +24,7 @@ def _server(**kw):
 
     device()
     kw.setdefault("hbm_budget", 8e9)
+    kw.setdefault("draw", bi.generators.request_inputs_device)
     return serve.Server(**kw)
 
 
@@ -34,6 +35,7 @@ def test_serving_alone_and_in_the_mix_agree():
     assert any(r.heavy for r in reqs) and sum(not r.heavy for r in reqs) > 20
     srv = _server(lanes=3, max_batch=32, keep_u=True)
     done = srv.run(reqs, realtime=True, timeout=120.0)
+    assert any(k == "heavy" for k, *_ in srv.jobs)
     assert len(done) == len(reqs)
     stats = serve.latency_stats(done)
     assert stats["p50_ms"] > 0 and stats["p99_ms"] >= stats["p50_ms"]
@@ -87,3 +89,22 @@ def test_admission_respects_the_budget():
     assert len(done) == len(reqs)
     assert peak[0] <= srv.budget + 1e-6
     assert srv.in_use == pytest.approx(0.0, abs=1e-3)
+
+
+def test_heavy_requests_batched_path_agrees_with_the_plan_path():
+    """Heavy requests are grouped into batches by default; with heavy_plan=True
+    each heavy lane runs them one at a time on a single-matrix plan.  Both
+    meet the oracle's error gate on the same inputs."""
+    reqs = [r for r in _requests(rate=400.0, duration=0.6, heavy_frac=0.5) if r.heavy][:2]
+    assert reqs
+    keep = lambda r: True  # noqa: E731
+    a = _server(lanes=1, max_batch=8, keep_inputs=keep, heavy_plan=True).run(reqs,
+                                                                             realtime=False)
+    b = _server(lanes=1, max_batch=8, keep_inputs=keep).run(reqs, realtime=False)
+    for qa, qb in zip(sorted(a, key=lambda q: q.r.rid), sorted(b, key=lambda q: q.r.rid)):
+        p = qa.r.problem
+        A, om, uc, ur = qa.result["inputs"]
+        ref = orc.block_cur(A.astype(np.float64), p.col_off, p.row_off, p.k, p.q, p.g_col,
+                            p.g_row, om.T.astype(np.float64), uc, ur)
+        for q in (qa, qb):
+            assert abs(q.result["err"][1] - ref["rel"]) <= 1e-3
