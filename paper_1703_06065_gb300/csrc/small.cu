@@ -524,8 +524,8 @@ bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_
 // ---------------------------------------------------------------------------
 // Block leverage scores (Def. 2): one thread-block cluster of kScoreCtas CTAs
 // per block g.  CTA q of the cluster sums F[j, t]^2 over its slice of the
-// block's columns j (every row t, consecutive threads on consecutive j, so
-// each row piece is one coalesced read) in FP64; the CTA's partial is formed
+// block's columns j (every row t; consecutive threads on consecutive j
+// within a row piece, so each piece is a coalesced read) in FP64; the CTA's partial is formed
 // in a fixed order (per thread, xor-tree per warp, warps in order), and CTA 0
 // adds the cluster's partials in rank order through distributed shared
 // memory, so the score does not depend on scheduling.
@@ -543,13 +543,15 @@ __global__ void __cluster_dims__(kScoreCtas, 1, 1) __launch_bounds__(256)
   const int64_t j0 = off[g], size = off[g + 1] - off[g];
   const int64_t chunk = (size + kScoreCtas - 1) / kScoreCtas;
   const int64_t a = j0 + q * chunk, b = min(j0 + size, a + chunk);
+  // the slice's k x len elements spread over all threads (a narrow slice
+  // still gives every thread several independent loads in flight)
+  const int len = b > a ? (int)(b - a) : 0;
+  const int total = k * len;
   double acc = 0.0;
-  for (int t = 0; t < k; ++t) {
-    const T* row = Ft + (int64_t)t * ldf;
-    for (int64_t j = a + threadIdx.x; j < b; j += blockDim.x) {
-      const double v = (double)row[j];
-      acc = fma(v, v, acc);
-    }
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int t = e / len, j = e - t * len;
+    const double v = (double)Ft[(int64_t)t * ldf + a + j];
+    acc = fma(v, v, acc);
   }
   acc = warp_sum(acc);
   __shared__ double r[32];
