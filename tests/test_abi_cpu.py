@@ -162,3 +162,49 @@ def test_batch_plan_rejects_empty_and_bad_q(lib):
     w1 = _batch_plan(lib, [_GOOD])[1]
     w2 = _batch_plan(lib, [_GOOD, _GOOD])[1]
     assert w2 > w1
+
+
+def test_new_entry_points_validate_on_the_host(lib):
+    """Every argument error of the plan-free, boosting, host-buffer and
+    settings calls is refused before anything touches the GPU."""
+    d, keep = _desc()
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    assert lib.bcur_plan(ctypes.byref(d), None, ctypes.byref(h), ctypes.byref(ws)) == 0
+    p = ctypes.c_void_p(0x1000)
+    # host-buffer decomposition: no workspace yet, then a null plan
+    assert lib.bcur_host_staging_bytes(h) >= 256 * 512 * 4
+    assert lib.bcur_decompose_host(h, p, p, p, p, p, 1 << 40, None, None, None, None, None,
+                                   p) == 8                       # ESTATE
+    assert lib.bcur_decompose_host(None, p, p, p, p, p, 1 << 40, None, None, None, None, None,
+                                   p) == 1
+    assert lib.bcur_host_staging_bytes(None) == 0
+    assert lib.bcur_rank_k_error(h, p, p) == 8                   # no scores / error yet
+    assert lib.bcur_rank_k_error(None, p, p) == 1
+    lib.bcur_destroy(h)
+    # plan-free factorisation pieces
+    assert lib.bcur_cholesky_inverse(p, 100, 0, p, p, p, ctypes.c_double(0.0), p, 256,
+                                     None) == 1                  # w not a multiple of 64
+    assert lib.bcur_cholesky_inverse(p, 128, 3, p, p, p, ctypes.c_double(0.0), p, 256,
+                                     None) == 1                  # dtype
+    assert lib.bcur_cholesky_inverse(p, 128, 0, p, p, p, ctypes.c_double(0.0), p, 128,
+                                     None) == 1                  # scratch too small
+    assert lib.bcur_cholesky_inverse(None, 128, 0, p, p, p, ctypes.c_double(0.0), p, 256,
+                                     None) == 1
+    assert lib.bcur_svd_small(p, 129, 0, p, p, p, p, 1 << 20, None, None) == 1
+    assert lib.bcur_svd_small(p, 64, 0, p, p, p, p, 64, None, None) == 2  # work too small
+    off = p
+    assert lib.bcur_gather_blocks(p, 10, 8, 16, 0, 1, off, 2, p, 1, 8, p, 8, p, None) == 1  # lda < n
+    assert lib.bcur_gather_blocks(p, 16, 8, 16, 0, 2, off, 2, p, 1, 8, p, 8, p, None) == 1  # axis
+    assert lib.bcur_gather_blocks(p, 16, 8, 16, 0, 1, off, 2, p, 1, 8, p, 4, p, None) == 1  # ldo < m
+    # boosting's choice
+    assert lib.bcur_boost_select(0, p, 3, None, 0, None, 0, None, 0, None, None, None, None,
+                                 None, None) == 1                # t < 1
+    assert lib.bcur_boost_select(2, p, 2, None, 0, None, 0, None, 0, None, None, None, None,
+                                 None, None) == 1                # stride < 3
+    assert lib.bcur_boost_select(2, p, 3, None, 0, None, 4, None, 0, None, p, None, None,
+                                 None, None) == 1                # output without input
+    # settings
+    assert lib.bcur_set_wait_budget_ns(0) == 1
+    assert lib.bcur_set_wait_budget_ns(61_000_000_000) == 1
+    assert lib.bcur_autotune_measured() == 0
