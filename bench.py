@@ -567,7 +567,9 @@ def single_config(p, sp, fp, world):
             "block": int(p.col_off[1]), "G_col": int(p.col_off.size - 1),
             "G_row": int(p.row_off.size - 1), "g_col": p.g_col, "g_row": p.g_row,
             "storage": p.storage, "sketch_prec": sp, "fit_prec": fp,
-            "l2": f"inputs larger than L2 (A = {a_bytes / 1e9:.2f} GB)",
+            "l2": (f"inputs larger than L2 (A = {a_bytes / 1e9:.2f} GB)" if a_bytes > 129e6 else
+                   f"A = {a_bytes / 1e6:.1f} MB fits in L2 and is not flushed between steps: a "
+                   f"latency figure for the small case"),
             "parallelism": f"replicas x{world}"}
 
 

@@ -272,6 +272,14 @@ bcur_status_t bcur_block_stable_rank(const void* Ft, int32_t dtype, int32_t k, i
                                      int64_t ldf, const int64_t* off, int32_t G, double* ratio,
                                      void* workspace, size_t workspace_bytes, void* stream);
 
+/* The incoherence of the same definition section, mu = (m / k) max_i
+ * ||U_k^T e_i||^2, from the panel U_k^T (k x m, row-major, ld >= m; dtype
+ * F64 or F32; e.g. bcur_factors' Ut): squared row norms in FP64, the
+ * maximum taken order-independently.  out: one device double; scratch: 8
+ * bytes of device memory (overwritten).  Errors: BCUR_EINVAL. */
+bcur_status_t bcur_incoherence(const void* Ut, int32_t dtype, int32_t k, int64_t m, int64_t ld,
+                               double* out, void* scratch, void* stream);
+
 /* The paper's Algorithm 1 as printed (Sec. 3.1), one call:
  *   1. r rows of A drawn uniformly with replacement (p_i = 1/m, the inverse-CDF
  *      rule of bcur_sample on equal scores, uniforms u_rows) and

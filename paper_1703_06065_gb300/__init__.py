@@ -419,12 +419,16 @@ def block_stable_rank(Ft, off):
 
 
 def incoherence(Ut):
-    """mu = (m/k) max_i ||U_k^T e_i||^2 (Sec. 3.2) from the panel U_k^T (k x m)."""
+    """mu = (m/k) max_i ||U_k^T e_i||^2 (Sec. 3.2) from the panel U_k^T (k x m):
+    a device FP64 tensor of one element (bcur_incoherence)."""
     torch = _torch()
+    _need_cuda(Ut)
     k, m = Ut.shape
-    off = torch.arange(m + 1, dtype=torch.int64, device=Ut.device)
-    lev = block_scores(Ut, off)
-    return (m / k) * lev.max()
+    out = torch.empty(1, dtype=torch.float64, device=Ut.device)
+    scratch = torch.empty(1, dtype=torch.int64, device=Ut.device)
+    _lib.check(_lib.load().bcur_incoherence(_ptr(Ut), _dtype_code(Ut), k, m, m, _ptr(out),
+                                            _ptr(scratch), _stream()), "bcur_incoherence")
+    return out[0]
 
 
 def sample_blocks(scores, u, g: int, replacement: bool = False):

@@ -32,7 +32,7 @@ EXPORTS = [
     "bcur_batch_profile_entry", "bcur_batch_set_stream", "bcur_host_staging_bytes",
     "bcur_decompose_host", "bcur_set_wait_budget_ns", "bcur_autotune_measured",
     "bcur_rank_k_error", "bcur_boost_select", "bcur_cholesky_inverse", "bcur_svd_small",
-    "bcur_gather_blocks",
+    "bcur_gather_blocks", "bcur_incoherence",
 ]
 
 
@@ -148,6 +148,9 @@ def load():
                                      c_void_p, c_int32, c_void_p, c_int32, c_int64, c_void_p,
                                      c_int64, c_void_p, c_void_p]
     L.bcur_gather_blocks.restype = st
+    L.bcur_incoherence.argtypes = [c_void_p, c_int32, c_int32, c_int64, c_int64, c_void_p,
+                                   c_void_p, c_void_p]
+    L.bcur_incoherence.restype = st
     L.bcur_gemm.argtypes = [c_int64, c_int64, c_int64, c_void_p, c_int64, c_int32, c_void_p,
                             c_int64, c_int32, c_void_p, c_int64, c_int32, c_int32, c_void_p]
     L.bcur_gemm.restype = st

@@ -1534,6 +1534,15 @@ bcur_status_t bcur_block_stable_rank(const void* Ft, int32_t dtype, int32_t k, i
   return BCUR_EINVAL;
 }
 
+bcur_status_t bcur_incoherence(const void* Ut, int32_t dtype, int32_t k, int64_t m, int64_t ld,
+                               double* out, void* scratch, void* stream) {
+  if (!Ut || !out || !scratch) return BCUR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == BCUR_F64) return incoherence<double>((const double*)Ut, k, m, ld, out, scratch, s);
+  if (dtype == BCUR_F32) return incoherence<float>((const float*)Ut, k, m, ld, out, scratch, s);
+  return BCUR_EINVAL;
+}
+
 bcur_status_t bcur_sample_blocks(const double* scores, int32_t G, const double* u, int32_t g,
                                  int32_t replacement, int32_t* idx, double* prob, void* stream) {
   if (!scores || !u || !idx) return BCUR_EINVAL;

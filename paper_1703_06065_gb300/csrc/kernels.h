@@ -161,6 +161,12 @@ template <typename T>
 bcur_status_t block_scores(const T* Ft, int k, int64_t h, int64_t ldf, const int64_t* off,
                            int G, double* scores, int* status, cudaStream_t s);
 
+// mu = (m / k) max_i ||U_k^T e_i||^2 from the panel U_k^T (k x m, ld); out is
+// one device double; scratch: 8 bytes of device memory.
+template <typename T>
+bcur_status_t incoherence(const T* Ut, int k, int64_t m, int64_t ld, double* out, void* scratch,
+                          cudaStream_t s);
+
 // Per-block ||F_g||_F^2 / ||F_g||_2^2 (block stable rank terms, Sec. 3.2).
 template <typename T>
 bcur_status_t block_stable_rank(const T* Ft, int k, int64_t ldf, const int64_t* off, int G,

@@ -534,12 +534,12 @@ constexpr int kScoreCtas = 8;
 
 template <typename T>
 __global__ void __cluster_dims__(kScoreCtas, 1, 1) __launch_bounds__(256)
-    block_scores_kernel(const T* Ft, int k, int64_t ldf, const int64_t* off, double* scores,
-                        int* status) {
+    block_scores_kernel(const T* Ft, int k, int64_t ldf, const int64_t* off, int G,
+                        double* scores, int* status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  const int g = blockIdx.y;
   const int q = (int)cluster.block_rank();
+  for (int g = blockIdx.y; g < G; g += gridDim.y) {
   const int64_t j0 = off[g], size = off[g + 1] - off[g];
   const int64_t chunk = (size + kScoreCtas - 1) / kScoreCtas;
   const int64_t a = j0 + q * chunk, b = min(j0 + size, a + chunk);
@@ -571,6 +571,7 @@ __global__ void __cluster_dims__(kScoreCtas, 1, 1) __launch_bounds__(256)
     if (!isfinite(sum)) dev_set_status(status, (int)BCUR_ENONFINITE);
   }
   cluster.sync();  // the partials stay alive until CTA 0 has read them
+  }
 }
 
 template <typename T>
@@ -578,12 +579,55 @@ bcur_status_t block_scores(const T* Ft, int k, int64_t h, int64_t ldf, const int
                            double* scores, int* status, cudaStream_t s) {
   (void)h;
   if (G <= 0) return BCUR_OK;
-  if (G > 65535) return BCUR_EINVAL;
-  block_scores_kernel<T><<<dim3(kScoreCtas, (unsigned)G), 256, 0, s>>>(Ft, k, ldf, off, scores,
-                                                                       status);
+  block_scores_kernel<T><<<dim3(kScoreCtas, (unsigned)std::min(G, 32768)), 256, 0, s>>>(
+      Ft, k, ldf, off, G, scores, status);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
+
+// mu = (m / k) max_i ||U_k^T e_i||^2 (Sec. 3.2): each thread forms the FP64
+// squared norms of its columns of the panel U_k^T; the maximum is taken with
+// an atomic max on the bit pattern (non-negative doubles order like their
+// bits), so the result does not depend on the order.
+template <typename T>
+__global__ void incoherence_kernel(const T* Ut, int k, int64_t m, int64_t ld,
+                                   unsigned long long* out_bits) {
+  double mx = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int t = 0; t < k; ++t) {
+      const double v = (double)Ut[(int64_t)t * ld + i];
+      acc = fma(v, v, acc);
+    }
+    mx = fmax(mx, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void incoherence_finish_kernel(const unsigned long long* bits, double scale,
+                                          double* out) {
+  *out = scale * __longlong_as_double((long long)*bits);
+}
+
+template <typename T>
+bcur_status_t incoherence(const T* Ut, int k, int64_t m, int64_t ld, double* out, void* scratch,
+                          cudaStream_t s) {
+  if (k < 1 || m < 1 || ld < m) return BCUR_EINVAL;
+  unsigned long long* bits = static_cast<unsigned long long*>(scratch);
+  BCUR_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(*bits), s));
+  const int blocks = (int)std::min<int64_t>((m + 255) / 256, 1024);
+  incoherence_kernel<T><<<blocks, 256, 0, s>>>(Ut, k, m, ld, bits);
+  BCUR_LAUNCH_CHECK();
+  incoherence_finish_kernel<<<1, 1, 0, s>>>(bits, (double)m / (double)k, out);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+template bcur_status_t incoherence<float>(const float*, int, int64_t, int64_t, double*, void*,
+                                          cudaStream_t);
+template bcur_status_t incoherence<double>(const double*, int, int64_t, int64_t, double*, void*,
+                                           cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Inverse-CDF sampling, one thread: the arithmetic must be the sequential

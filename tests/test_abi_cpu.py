@@ -204,6 +204,8 @@ def test_new_entry_points_validate_on_the_host(lib):
                                  None, None) == 1                # stride < 3
     assert lib.bcur_boost_select(2, p, 3, None, 0, None, 4, None, 0, None, p, None, None,
                                  None, None) == 1                # output without input
+    assert lib.bcur_incoherence(None, 0, 4, 16, 16, p, p, None) == 1
+    assert lib.bcur_incoherence(p, 3, 4, 16, 16, p, p, None) == 1        # dtype
     # settings
     assert lib.bcur_set_wait_budget_ns(0) == 1
     assert lib.bcur_set_wait_budget_ns(61_000_000_000) == 1
