@@ -109,11 +109,15 @@ __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcu
 //   apply: X' = L^{-1} X (FP32), optionally also as BF16 for the next
 //          product with A.
 // ---------------------------------------------------------------------------
-// The Gram is symmetric and only its lower part is read: threads 0..135
-// each own one R x R tile (ti >= tj) of the 16 x 16 tile grid, threads
-// 136..255 the 120 tiles above it, which they only zero.  All 256 threads
-// load; the next 64-column slice is fetched into registers while the
-// current one is multiplied.
+// The Gram is symmetric and only its lower part is read.  Its rows past the
+// item's l are zero, so only the lower R x R tiles of the leading
+// nb = ceil(l / R) tile rows are formed: T = nb (nb + 1) / 2 tiles.  The 256
+// threads are split into G = 256 / T groups of T: thread (g, t) forms tile t
+// over the slice columns c = g, g + G, ..., and the groups' partial tiles are
+// added in group order at the end (so the sum order depends only on l, never
+// on the rest of the batch).  Work and loads scale with l^2, not with the
+// panel height LP.  The next 64-column slice is fetched into registers while
+// the current one is multiplied.
 __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
   ti = 0;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
@@ -121,27 +125,27 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
 }
 
 template <int LP>
-__global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chunks, int sel) {
-  constexpr int R = LP / 16;          // R x R outputs per thread
+__global__ void __launch_bounds__(256, LP == 64 ? 2 : 1) sgram_kernel(const Item* items,
+                                                                      Work chunks, int sel) {
+  constexpr int R = LP / 16;          // R x R outputs per tile
   constexpr int NL = LP * 64 / 256;   // slice elements loaded per thread
+  constexpr int TLD = LP + 4;         // XsT[c][r]: column c of the slice, rows r
+  constexpr int SMEM = (64 * TLD > 136 * R * R) ? 64 * TLD : 136 * R * R;
   const int b = find_item(chunks, blockIdx.x);
   const Item& I = items[b];
   const int ch = blockIdx.x - chunks.prefix[b];
   const float* X = panel(I, sel);
   const int64_t h = panel_h(I, sel), ld = panel_ld(I, sel);
-  constexpr int TLD = LP + 4;         // XsT[c][r]: column c of the slice, rows r
-  __shared__ __align__(16) float XsT[64 * TLD];
+  const int l = I.l;
+  __shared__ __align__(16) float XsT[SMEM];
   const int tid = threadIdx.x;
-  const bool lower = tid < 136;
-  int ti, tj;
-  if (lower) {
-    tri_tile(tid, ti, tj);
-  } else {  // strictly lower (a + 1, b) with b <= a, transposed: (b, a + 1)
-    int a2, b2;
-    tri_tile(tid - 136, a2, b2);
-    ti = b2;
-    tj = a2 + 1;
-  }
+  const int nb = (l + R - 1) / R;
+  const int T = nb * (nb + 1) / 2;
+  const int G = 256 / T;
+  const int g = tid / T, t = tid - g * T;
+  const bool active = g < G;
+  int ti = 0, tj = 0;
+  if (active) tri_tile(t, ti, tj);
   float acc[R][R];
 #pragma unroll
   for (int a = 0; a < R; ++a)
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
       const int e = tid + 256 * q, r = e / 64, c = e % 64;
-      rx[q] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
+      rx[q] = (r < l && c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
     }
   };
   fetch(c_begin);
@@ -166,9 +170,9 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
     }
     __syncthreads();
     if (c0 + 64 < c_end) fetch(c0 + 64);
-    if (lower) {
-#pragma unroll 4
-      for (int c = 0; c < 64; ++c) {
+    if (active) {
+#pragma unroll 2
+      for (int c = g; c < 64; c += G) {
         float a[R], bb[R];
 #pragma unroll
         for (int q = 0; q < R; q += 4) {
@@ -185,11 +189,28 @@ __global__ void __launch_bounds__(256) sgram_kernel(const Item* items, Work chun
     }
     __syncthreads();
   }
-  float* out = I.gpart + (int64_t)ch * LP * LP;
+  // groups 1 .. G-1 hand their partial tiles to group 0, in group order
+  for (int gg = 1; gg < G; ++gg) {
+    if (active && g == gg)
 #pragma unroll
-  for (int q = 0; q < R; ++q)
+      for (int q = 0; q < R; ++q)
 #pragma unroll
-    for (int p = 0; p < R; ++p) out[(R * ti + q) * LP + R * tj + p] = lower ? acc[q][p] : 0.f;
+        for (int p = 0; p < R; ++p) XsT[(t * R + q) * R + p] = acc[q][p];
+    __syncthreads();
+    if (active && g == 0)
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int p = 0; p < R; ++p) acc[q][p] += XsT[(t * R + q) * R + p];
+    __syncthreads();
+  }
+  if (active && g == 0) {
+    float* out = I.gpart + (int64_t)ch * LP * LP;
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int p = 0; p < R; ++p) out[(R * ti + q) * LP + R * tj + p] = acc[q][p];
+  }
 }
 
 template <int LP>
@@ -229,7 +250,7 @@ __global__ void __launch_bounds__(256) schol_kernel(const Item* items, int sel, 
 // increasing order and stopping at the last nonzero column of its rows.  The
 // next slice is fetched into registers while the current one is multiplied.
 template <int LP>
-__global__ void __launch_bounds__(256) sapply_kernel(const Item* items, Work chunks, int src,
+__global__ void __launch_bounds__(256, LP == 64 ? 3 : 2) sapply_kernel(const Item* items, Work chunks, int src,
                                                      int dst, int write_bf16) {
   constexpr int RR = LP / 16;         // rows per thread
   constexpr int LLD = LP + 4;         // LsT[t][r] = L^{-1}[r][t]
@@ -247,6 +268,7 @@ __global__ void __launch_bounds__(256) sapply_kernel(const Item* items, Work chu
     LsT[t * LLD + r] = I.LinvT[e];
   }
   const int64_t h = panel_h(I, src), ld = panel_ld(I, src);
+  const int l = I.l;
   const float* X = panel(I, src);
   float* Y = panel(I, dst);
   bf16* Yb = write_bf16 ? (src < PN0 ? I.Qh : I.Zh) : nullptr;
@@ -259,11 +281,13 @@ __global__ void __launch_bounds__(256) sapply_kernel(const Item* items, Work chu
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
       const int e = tid + 256 * q, r = e / 64, c = e % 64;
-      rx[q] = (c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
+      rx[q] = (r < l && c0 + c < c_end) ? X[r * ld + c0 + c] : 0.f;
     }
   };
   fetch(c_begin);
-  const int tmax = RR * ti + RR;      // L^{-1}[r][t] = 0 for t > r
+  // L^{-1}[r][t] = 0 for t > r, and rows and columns past l are zero: rows
+  // r >= l of the result are zero without a product
+  const int tmax = RR * ti < l ? min(RR * ti + RR, l) : 0;
   for (int64_t c0 = c_begin; c0 < c_end; c0 += 64) {
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
@@ -355,10 +379,12 @@ __global__ void __launch_bounds__(128) scores_kernel(const Item* items, const bc
   const int span = groups == 1 ? nt : I.s;
   const int tg = groups == 1 ? 0 : (int)threadIdx.x / I.s;
   const int jc = groups == 1 ? (int)threadIdx.x : (int)threadIdx.x % I.s;
+  // rows of the panel past l are zero: only the leading l4 are read
+  const int l4 = (I.l + 3) & ~3;
   for (int64_t j = j0 + jc; tg < groups && j < j1; j += span) {
     float p[LP];
 #pragma unroll
-    for (int i = 0; i < LP; ++i) p[i] = P[i * ld + j];
+    for (int i = 0; i < LP; ++i) p[i] = i < l4 ? P[i * ld + j] : 0.f;
     for (int t = tg; t < k; t += groups) {
       float v = 0.f;
 #pragma unroll

@@ -102,9 +102,13 @@ bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, int re
 }  // namespace batch
 
 // Batched Jacobi SVD (small.cu): `batch` independent w x w problems stored
-// contiguously (X, Ut, W, jwork at stride w*w, sigma at stride w).
+// contiguously (X, Ut, W, jwork at stride w*w, sigma at stride w).  With
+// wdim (device, one int per problem) only each problem's leading
+// wdim[b] x wdim[b] block is factored (the rest of X must be zero); the
+// outputs past it are zeros (W: identity there).
 template <typename T>
 bcur_status_t jacobi_svd_batched(const double* X, int w, T* Ut, T* W, double* sigma, T* jwork,
-                                 int* status, int batch, cudaStream_t s);
+                                 int* status, int batch, cudaStream_t s,
+                                 const int* wdim = nullptr);
 
 }  // namespace bcur

@@ -43,6 +43,7 @@ struct bcur_batch_s {
   double* Lb_all = nullptr;
   float *Ut_all = nullptr, *W_all = nullptr, *jw_all = nullptr;
   double* sig_all = nullptr;
+  int* d_l = nullptr;    // l = k + p of every item (the Jacobi's own width)
   bcur_batch_io_t* h_io = nullptr;  // pinned staging of the io table
   cudaEvent_t ev_io = nullptr;
   WorkList rows8, chunks_m, chunks_n, apply_m, apply_n, blocks, ctiles, rrows, urows;
@@ -117,6 +118,7 @@ size_t layout(bcur_batch_t P) {
   P->W_all = bp.take<float>((size_t)B * LP * LP);
   P->jw_all = bp.take<float>((size_t)B * LP * LP);
   P->sig_all = bp.take<double>((size_t)B * LP);
+  P->d_l = bp.take<int>(B);
   WorkList* wls[] = {&P->rows8, &P->chunks_m, &P->chunks_n, &P->apply_m, &P->apply_n,
                      &P->blocks, &P->ctiles, &P->rrows, &P->urows};
   for (WorkList* w : wls) w->d = bp.take<int>(B + 1);
@@ -462,7 +464,7 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   BCUR_TRY(mark(P, s, "sketch_gemm"));
   BCUR_TRY(orth(P, PN0, PN1, true, s));
   BCUR_TRY(jacobi_svd_batched<float>(P->Lb_all, P->lp, P->Ut_all, P->W_all, P->sig_all,
-                                     P->jw_all, P->d_status, B, s));
+                                     P->jw_all, P->d_status, B, s, P->d_l));
   BCUR_TRY(mark(P, s, "jacobi"));
   BCUR_TRY(scores(P->d_items, P->d_io, P->blocks.w(), P->blocks.total, P->d_status, P->lp, s));
   BCUR_TRY(mark(P, s, "scores"));
@@ -598,6 +600,10 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
     }
   }
   BCUR_CUDA_TRY(cudaMemcpyAsync(P->d_items, P->it.data(), (size_t)B * sizeof(Item),
+                                cudaMemcpyHostToDevice, P->sstream));
+  std::vector<int> ls(B);
+  for (int b = 0; b < B; ++b) ls[b] = P->it[b].l;
+  BCUR_CUDA_TRY(cudaMemcpyAsync(P->d_l, ls.data(), (size_t)B * sizeof(int),
                                 cudaMemcpyHostToDevice, P->sstream));
   BCUR_CUDA_TRY(cudaMemsetAsync(P->d_status, 0, sizeof(int), P->sstream));
   BCUR_CUDA_TRY(cudaMemsetAsync(P->d_io, 0, (size_t)B * sizeof(bcur_batch_io_t), P->sstream));

@@ -147,23 +147,28 @@ __device__ __forceinline__ int rr_player(int pos, int round, int wp) {
 }
 
 template <typename T>
-__global__ void jacobi_svd_kernel(const double* X, int w, T* Ut, T* W, double* sigma, T* J,
-                                  int* status) {
+__global__ void jacobi_svd_kernel(const double* X, int ws, T* Ut, T* W, double* sigma, T* J,
+                                  int* status, const int* wdim) {
   extern __shared__ unsigned char smem_raw[];
+  // ws: the stride of the stored w x w matrices; w: the leading block that is
+  // factored (a batch entry's own width when wdim is given; the rest of the
+  // stored matrix is zero and its outputs are written as zeros)
+  const int64_t b = blockIdx.x;
+  const int w = wdim ? min(ws, max(1, wdim[b])) : ws;
   T* Xs = reinterpret_cast<T*>(smem_raw);  // column-major: column p at Xs[p * w]
   const int wp = w + (w & 1);
   {  // batch: one matrix per CTA
-    const int64_t b = blockIdx.x;
-    X += b * w * w;
-    if (Ut) Ut += b * w * w;
-    if (W) W += b * w * w;
-    sigma += b * w;
-    J += b * wp * wp;
+    const int64_t wsp = ws + (ws & 1);
+    X += b * ws * ws;
+    if (Ut) Ut += b * ws * ws;
+    if (W) W += b * ws * ws;
+    sigma += b * ws;
+    J += b * wsp * wsp;
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   for (int e = tid; e < wp * w; e += blockDim.x) {
     const int p = e / w, i = e % w;
-    Xs[e] = (p < w) ? (T)X[i * w + p] : T(0);
+    Xs[e] = (p < w) ? (T)X[i * ws + p] : T(0);
   }
   for (int e = tid; e < wp * wp; e += blockDim.x) J[e] = (e / wp == e % wp) ? T(1) : T(0);
   __shared__ int s_rot;
@@ -236,14 +241,15 @@ __global__ void jacobi_svd_kernel(const double* X, int w, T* Ut, T* W, double* s
     if (sweep == max_sweeps && status) atomicCAS(status, 0, (int)BCUR_ETIMEOUT);
   }
   __syncthreads();
-  for (int e = tid; e < w * w; e += blockDim.x) {
-    const int i = e / w, t = e % w;
-    const int p = s_order[t];
-    const double sg = s_sig[p];
-    if (Ut) Ut[i * w + t] = sg > 0.0 ? (T)((double)Xs[p * w + i] / sg) : T(0);
-    if (W) W[i * w + t] = J[(int64_t)p * wp + i];
+  for (int e = tid; e < ws * ws; e += blockDim.x) {
+    const int i = e / ws, t = e % ws;
+    const bool in = i < w && t < w;
+    const int p = in ? s_order[t] : 0;
+    const double sg = in ? s_sig[p] : 0.0;
+    if (Ut) Ut[e] = (in && sg > 0.0) ? (T)((double)Xs[p * w + i] / sg) : T(0);
+    if (W) W[e] = in ? J[(int64_t)p * wp + i] : T(i == t ? 1 : 0);
   }
-  for (int t = tid; t < w; t += blockDim.x) sigma[t] = s_sig[s_order[t]];
+  for (int t = tid; t < ws; t += blockDim.x) sigma[t] = t < w ? s_sig[s_order[t]] : 0.0;
 }
 
 template <typename T>
@@ -259,14 +265,14 @@ bcur_status_t jacobi_svd_small(const double* X, int w, T* Ut, T* W, double* sigm
     attr_set = true;
   }
   const int warps = wp / 2 < 32 ? (wp / 2 < 1 ? 1 : wp / 2) : 32;
-  jacobi_svd_kernel<T><<<1, warps * 32, smem, s>>>(X, w, Ut, W, sigma, jwork, status);
+  jacobi_svd_kernel<T><<<1, warps * 32, smem, s>>>(X, w, Ut, W, sigma, jwork, status, nullptr);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 
 template <typename T>
 bcur_status_t jacobi_svd_batched(const double* X, int w, T* Ut, T* W, double* sigma, T* jwork,
-                                 int* status, int batch, cudaStream_t s) {
+                                 int* status, int batch, cudaStream_t s, const int* wdim) {
   if (w < 2 || w > 128 || (w & 1) || batch < 1) return BCUR_EINVAL;
   const size_t smem = (size_t)w * w * sizeof(T);
   static bool attr_set = false;
@@ -276,12 +282,12 @@ bcur_status_t jacobi_svd_batched(const double* X, int w, T* Ut, T* W, double* si
     attr_set = true;
   }
   const int warps = w / 2 < 32 ? w / 2 : 32;
-  jacobi_svd_kernel<T><<<batch, warps * 32, smem, s>>>(X, w, Ut, W, sigma, jwork, status);
+  jacobi_svd_kernel<T><<<batch, warps * 32, smem, s>>>(X, w, Ut, W, sigma, jwork, status, wdim);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 template bcur_status_t jacobi_svd_batched<float>(const double*, int, float*, float*, double*,
-                                                 float*, int*, int, cudaStream_t);
+                                                 float*, int*, int, cudaStream_t, const int*);
 
 // ---------------------------------------------------------------------------
 // Blocked Cholesky pieces (working precision T)
@@ -852,7 +858,7 @@ bcur_status_t block_stable_rank(const T* Ft, int k, int64_t ldf, const int64_t* 
   }
   const int warps = kp / 2 < 32 ? (kp / 2 < 1 ? 1 : kp / 2) : 32;
   jacobi_svd_kernel<double><<<G, warps * 32, smem, s>>>(gram, k, nullptr, nullptr, sig, jw,
-                                                        nullptr);
+                                                        nullptr, nullptr);
   BCUR_LAUNCH_CHECK();
   stable_rank_finish_kernel<<<(G + 127) / 128, 128, 0, s>>>(gram, sig, k, G, ratio);
   BCUR_LAUNCH_CHECK();
