@@ -242,9 +242,16 @@ def uniform_blocks(n: int, s: int) -> np.ndarray:
     return off
 
 
-def blocks_to_sample(k: int, s: int, G: int) -> int:
-    """Number of blocks per side for the batched workloads: min(ceil(2k/s)+1, ceil(G/2))."""
-    return int(min(-(-2 * k // s) + 1, -(-G // 2)))
+def blocks_to_sample(k: int, s: int, G: int, other: int = None) -> int:
+    """Number of blocks per side for the batched workloads:
+    min(ceil(2k/s)+1, ceil(G/2)), and (given the length `other` of the other
+    side: m for column blocks, n for row blocks) at most floor(other/(2s)),
+    at least 1, so that C (m x c) and R (r x n) stay tall, c <= m/2 and
+    r <= n/2."""
+    g = min(-(-2 * k // s) + 1, -(-G // 2))
+    if other is not None:
+        g = min(g, max(1, other // (2 * s)))
+    return int(g)
 
 
 # ----------------------------------------------------------------------------
@@ -361,20 +368,22 @@ def host_sample(full: Problem, factor: int = 4) -> Problem:
 def _biometric(g: np.random.Generator, name: str, seed: int, m_range=(256, 4096),
                n_range=(1024, 16384), k_range=(5, 50), blocks=(16, 32, 64, 128, 256)) -> Problem:
     s = int(g.choice(list(blocks)))
-    m = int(g.integers(m_range[0], m_range[1] + 1)) // s * s
-    n = int(g.integers(n_range[0], n_range[1] + 1)) // s * s
+    # at least two blocks per side: with one, the draw is forced and C or R is all of A
+    m = max(int(g.integers(m_range[0], m_range[1] + 1)) // s * s, 2 * s)
+    n = max(int(g.integers(n_range[0], n_range[1] + 1)) // s * s, 2 * s)
     k = int(g.integers(k_range[0], k_range[1] + 1))
     Gc, Gr = n // s, m // s
     return Problem(name, m, n, k=k, p=10, q=2,
                    col_off=uniform_blocks(n, s), row_off=uniform_blocks(m, s),
-                   g_col=blocks_to_sample(k, s, Gc), g_row=blocks_to_sample(k, s, Gr),
+                   g_col=blocks_to_sample(k, s, Gc, m), g_row=blocks_to_sample(k, s, Gr, n),
                    seed=seed, storage="f32",
                    recipe=dict(kind="ar1_mixture", rank=k, phi=0.95, noise=0.05))
 
 
 def batched_biometric(count: int = 512, seed: int = 3, m_range=(256, 4096), n_range=(1024, 16384),
                       k_range=(5, 50), blocks=(16, 32, 64, 128, 256)) -> List[Problem]:
-    """Uneven batch: m~U[256,4096], n~U[1024,16384] (rounded down to s), s in {16..256}, k~U[5,50].
+    """Uneven batch: m~U[256,4096], n~U[1024,16384] (rounded down to s, at least 2s),
+    s in {16..256}, k~U[5,50].
 
     The ranges can be narrowed for test-sized batches; the defaults are the
     512-matrix biometric workload."""

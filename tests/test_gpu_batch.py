@@ -259,3 +259,29 @@ def test_autotuned_tile_widths_are_measured_once_and_cached(tmp_path, monkeypatc
         for key in a:
             if a[key] is not None:
                 np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_worst_conditioned_members_of_the_batch_meet_the_gate():
+    """The members of the 512-matrix batch whose C or R is worst conditioned
+    (kappa from 410 to 860; 105 and 325 are 512-row members at the two-block
+    minimum, c = m/2): batched together, each must meet the 1e-3 error gate
+    against the FP64 oracle, with the oracle's blocks up to the first tie."""
+    import paper_1703_06065_gb300 as pkg
+
+    device()
+    allp = bi.batched_biometric(512, seed=3)
+    picks = [allp[i] for i in (314, 418, 65, 387, 105, 325)]
+    b = pkg.Batch([_item(p) for p in picks], q=2)
+    As = [p.matrix_device(torch.device("cuda")) for p in picks]
+    oms = [to_dev(p.omega().T, torch.float32) for p in picks]
+    o = b.run(As, oms, [to_dev(p.u_col()) for p in picks], [to_dev(p.u_row()) for p in picks])
+    b.sync_status()
+    for i, p in enumerate(picks):
+        A = As[i].double().cpu().numpy()
+        ref = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(),
+                            p.u_col(), p.u_row())
+        e = float(o["err"][i][1].item())
+        assert abs(e - ref["rel"]) <= 1e-3, (p.name, e, ref["rel"])
+        for side, u, g in (("col", p.u_col(), p.g_col), ("row", p.u_row(), p.g_row)):
+            n_ok = _tie_free_draws(ref[f"{side}_scores"], o[f"{side}_scores"][i].cpu().numpy(), u, g)
+            assert o[f"{side}_idx"][i].cpu().tolist()[:n_ok] == list(ref[f"{side}_idx"][:n_ok])
