@@ -200,10 +200,12 @@ def main_native(args):
         dist.init_process_group("nccl", device_id=dev)
     pkg.load()
     p = workload(args.workload, rank)
-    # FP32 data: BF16 sketch (re-orthonormalised after every product) and a
-    # split-BF16 fit on tensor cores; FP64 data stays FP64.
+    # FP32 data: BF16 sketch (re-orthonormalised after every product) and the
+    # adaptive split-BF16 fit on tensor cores (split Cholesky-QR; one-term core
+    # products and residual, redone with three terms on the device when the
+    # error is small); FP64 data stays FP64.
     sp = args.sketch_prec or ("f64" if p.storage == "f64" else "bf16")
-    fp = args.fit_prec or ("f64" if p.storage == "f64" else "bf16x3")
+    fp = args.fit_prec or ("f64" if p.storage == "f64" else "bf16x3a")
     tdt = torch.float64 if p.storage == "f64" else torch.float32
 
     # inputs resident in HBM before the timed region; the host draws exactly the
@@ -259,6 +261,7 @@ def main_native(args):
     plan.sync_status()
     ms = ev0.elapsed_time(ev1) / args.steps
     e = ebuf.cpu().numpy()
+    fit_terms = plan.fit_terms()[0]   # BF16 terms of the fit's core products
     if world > 1:
         import torch.distributed as dist
 
@@ -320,34 +323,44 @@ def main_native(args):
         r = plan.r_max
         nrep = 3
         if fp.startswith("bf16"):
+            # W = A Q_R as the fit ran it: three split terms, or one BF16 term
+            # when the adaptive fit kept one
+            terms = 1 if fit_terms == 1 else 3
             Ah = A.to(torch.bfloat16)
             Al = (A - Ah.float()).to(torch.bfloat16)
             Q = torch.randn(r, p.n, device=dev, dtype=torch.float32) / float(np.sqrt(p.n))
             Qh = Q.to(torch.bfloat16)
             Ql = (Q - Qh.float()).to(torch.bfloat16)
             Wd = torch.empty(p.m, r, device=dev, dtype=torch.float32)
-            pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=Wd)
+
+            def wgemm():
+                if terms == 3:
+                    pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=Wd)
+                else:
+                    pkg.gemm(Ah, Qh, False, True, prec="bf16", out=Wd)
+
+            wgemm()
             torch.cuda.synchronize()
             ev0.record(s)
             for _ in range(nrep):
-                pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=Wd)
+                wgemm()
             ev1.record(s)
             torch.cuda.synchronize()
             kms = ev0.elapsed_time(ev1) / nrep
             alg = 2.0 * p.m * p.n * r              # the method's flops for W = A Q_R
-            mma = 3 * alg                          # issued BF16 MMA flops (three split terms)
+            mma = terms * alg                      # issued BF16 MMA flops
             achieved = alg / (kms * 1e-3) / 1e12
             peak = peaks.get("bf16_tflops", 1968.0)
-            roof = {"kernel": "tc_gemm_kernel<256, BF16, store>: W = A Q_R, split BF16 (3 terms)",
+            what = "split BF16 (3 terms)" if terms == 3 else "one BF16 term (adaptive fit)"
+            roof = {"kernel": f"tc_gemm_kernel<256, BF16, store>: W = A Q_R, {what}",
                     "bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 3),
                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                     "ms": round(kms, 4),
                     "algorithmic": f"2*m*n*r = {alg:.4g} flop per launch (m={p.m}, n={p.n}, "
                                    f"r={r}): the product the method needs, counted once",
                     "tensor_pipe_frac": round(mma / (kms * 1e-3) / 1e12 / peak, 4),
-                    "tensor_pipe_note": f"issued BF16 MMA work 3 x 2*m*n*r = {mma:.4g} flop "
-                                        f"({mma / (kms * 1e-3) / 1e12:.1f} TFLOP/s): the split "
-                                        "pair's three terms keep about 16 bits",
+                    "tensor_pipe_note": f"issued BF16 MMA work {terms} x 2*m*n*r = {mma:.4g} "
+                                        f"flop ({mma / (kms * 1e-3) / 1e12:.1f} TFLOP/s)",
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst; kernel timed alone)"}
             del Ah, Al, Q, Qh, Ql, Wd
             Pm = (torch.randn(p.m, r, device=dev) / float(np.sqrt(r))).to(torch.bfloat16)
@@ -459,6 +472,8 @@ def main_native(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu,
         }
+        if fp.startswith("bf16"):
+            line["config"]["fit_terms"] = fit_terms
         if study is not None:
             line["precision_study"] = study
         print(json.dumps(line), flush=True)
@@ -531,10 +546,12 @@ def precision_study(full: bi.Problem, dev):
         return float(np.linalg.norm(d, 2))
 
     out = {"sample": f"{p.m}x{p.n}, k={p.k}, p={p.p}, q={p.q}, {p.g_col}+{p.g_row} blocks of "
-                     f"{int(p.col_off[1])}", "oracle_s": round(t_orc, 2), "fit": "bf16x3"}
-    for sp in ("bf16", "fp8", "bf16x3", "f32"):
+                     f"{int(p.col_off[1])}", "oracle_s": round(t_orc, 2),
+           "fit": "bf16x3 (keys: sketch precision), bf16x3a for the key sketch/fit"}
+    for sp, fp in (("bf16", "bf16x3"), ("fp8", "bf16x3"), ("bf16x3", "bf16x3"), ("f32", "bf16x3"),
+                   ("bf16", "bf16x3a")):
         plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
-                        dtype="f32", sketch_prec=sp, fit_prec="bf16x3")
+                        dtype="f32", sketch_prec=sp, fit_prec=fp)
         cs, rs = plan.scores(At, omt)
         Vt, Ut, _ = plan.factors()
         ci, ri, _, _ = plan.sample(cs, rs, uct, urt)
@@ -547,7 +564,8 @@ def precision_study(full: bi.Problem, dev):
         cig, rig = ci.cpu().tolist(), ri.cpu().tolist()
         c, r = ref["U"].shape
         Ug = U.double().cpu().numpy()[:c, :r]
-        out[sp] = {
+        key = sp if fp == "bf16x3" else f"{sp}/{fp}"
+        out[key] = {
             "sin_angle_V": sin_angle(Vt.double().cpu().numpy().T, ref["V_k"]),
             "sin_angle_U": sin_angle(Ut.double().cpu().numpy().T, ref["U_k"]),
             "score_max_rel": float(sd),
@@ -556,6 +574,8 @@ def precision_study(full: bi.Problem, dev):
             "U_rel_fro": float(np.linalg.norm(Ug - ref["U"]) / np.linalg.norm(ref["U"])),
             "e_abs_diff": abs(float(e[1].item()) - ref["rel"]),
         }
+        if fp == "bf16x3a":
+            out[key]["fit_terms"] = plan.fit_terms()[0]
         del plan
     return out
 
@@ -590,7 +610,7 @@ def main_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": single_config(p, args.sketch_prec or ("f64" if p.storage == "f64" else "bf16"),
-                                args.fit_prec or ("f64" if p.storage == "f64" else "bf16x3"), world),
+                                args.fit_prec or ("f64" if p.storage == "f64" else "bf16x3a"), world),
         "step_note": "each timed step is one oracle decomposition of the bounded sample named in "
                      "cpu_baseline.sample (ms_per_step is its measured time); value is in "
                      "decompositions/s of the full workload, scaled as that sample states",

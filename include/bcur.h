@@ -70,14 +70,29 @@ typedef enum {
  *   BCUR_FP8    : sketch only (FP32 storage): tcgen05 kind::f8f6f4 on e4m3
  *                 roughly 4-bit operands, A scaled per row and each skinny
  *                 panel per row (amax / 448), the scales undone exactly in
- *                 the products' epilogue; FP32 accumulation. */
+ *                 the products' epilogue; FP32 accumulation.
+ *   BCUR_BF16X3A: fit only (FP32 storage), adaptive: the Cholesky-QR of C
+ *                 and R^T as BCUR_BF16X3; the core products (W = A Q_R,
+ *                 M = Q_C^T W and the triangular products that turn M into
+ *                 U) and the residual ||A - CUR||_F first with one BF16 term
+ *                 each, all taken by bcur_fit.  When that residual is too
+ *                 coarse for the relative error e it reports, i.e. when one
+ *                 term's rounding (2^-8) could move e by more than 2.5e-4
+ *                 ((2^-8)^2 / (2 e) > 2.5e-4, e < 0.031), the device redoes
+ *                 the same products and the residual with three terms.  e
+ *                 depends on errors in M only at second order (their
+ *                 contribution Q_C dM Q_R^T is orthogonal to A - Q_C M Q_R^T);
+ *                 U at first order, so with one term U carries BF16 rounding
+ *                 amplified by the conditioning of C and R.  bcur_fit_terms
+ *                 reports the choice; bcur_error returns the fit's residual. */
 typedef enum {
   BCUR_F64 = 0,
   BCUR_F32 = 1,
   BCUR_TF32 = 2,
   BCUR_BF16 = 3,
   BCUR_BF16X3 = 4,
-  BCUR_FP8 = 5
+  BCUR_FP8 = 5,
+  BCUR_BF16X3A = 6
 } bcur_prec_t;
 
 typedef struct {
@@ -164,10 +179,21 @@ bcur_status_t bcur_sample(bcur_plan_t plan, const double* col_scores, const doub
 bcur_status_t bcur_fit(bcur_plan_t plan, const void* A, const int32_t* col_idx,
                        const int32_t* row_idx, void* U, void* C, void* R);
 
+/* The BF16 terms the last bcur_fit took for its core products (W = A Q_R,
+ * M = Q_C^T W and the triangular products that give U): 1 or 3 with
+ * fit_prec BCUR_BF16X3A (decided on the device), 3 with BCUR_BF16X3, 0 on
+ * CUDA cores.  rel_err_estimate (host, optional) receives the relative error
+ * of the one-term residual the adaptive choice was made from (-1 for the
+ * other precisions).  Synchronises the plan's stream.
+ * Errors: BCUR_EINVAL (NULL plan or terms), BCUR_ESTATE (no fit yet). */
+bcur_status_t bcur_fit_terms(bcur_plan_t plan, int32_t* terms, double* rel_err_estimate);
+
 /* Stage 6: residual of the last fit.  out (device, 3 doubles) receives
  * ||A - CUR||_F, ||A - CUR||_F / ||A||_F and ||A||_F.  CUR is never stored:
  * the Frobenius sum is reduced inside the GEMM epilogue in a fixed order, so
- * repeated calls give bit-identical results. */
+ * repeated calls give bit-identical results.  With fit_prec BCUR_BF16X3A the
+ * fit has already taken this residual; called with the same A pointer (whose
+ * contents must not have changed since bcur_fit), bcur_error copies it. */
 bcur_status_t bcur_error(bcur_plan_t plan, const void* A, double* out);
 
 /* Rank-kt truncation of the last fit's U (Sec. 4.1: U_k, the best rank-k

@@ -176,6 +176,17 @@ class Plan:
             return U, C, R
         return U
 
+    def fit_terms(self):
+        """(terms, estimate): the BF16 terms the last fit took for its core
+        products (1 or 3 for fit_prec "bf16x3a", decided on the device; 3 for
+        "bf16x3"; 0 on CUDA cores) and the relative-error estimate the
+        adaptive choice was made from (-1 when none was taken)."""
+        t = ctypes.c_int32(0)
+        e = ctypes.c_double(-1.0)
+        _lib.check(self._L.bcur_fit_terms(self._h, ctypes.byref(t), ctypes.byref(e)),
+                   "bcur_fit_terms")
+        return int(t.value), float(e.value)
+
     def error(self, A, out=None):
         torch = _torch()
         _need_cuda(A)

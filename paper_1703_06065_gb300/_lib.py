@@ -13,9 +13,9 @@ from ctypes import POINTER, c_double, c_int32, c_int64, c_size_t, c_void_p
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbcur.so")
 
-BCUR_F64, BCUR_F32, BCUR_TF32, BCUR_BF16, BCUR_BF16X3, BCUR_FP8 = 0, 1, 2, 3, 4, 5
+BCUR_F64, BCUR_F32, BCUR_TF32, BCUR_BF16, BCUR_BF16X3, BCUR_FP8, BCUR_BF16X3A = range(7)
 PREC = {"f64": BCUR_F64, "f32": BCUR_F32, "tf32": BCUR_TF32, "bf16": BCUR_BF16,
-        "bf16x3": BCUR_BF16X3, "fp8": BCUR_FP8}
+        "bf16x3": BCUR_BF16X3, "fp8": BCUR_FP8, "bf16x3a": BCUR_BF16X3A}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ENONFINITE",
           6: "ETIMEOUT", 7: "ENOTSUP", 8: "ESTATE"}
 
@@ -32,7 +32,7 @@ EXPORTS = [
     "bcur_batch_profile_entry", "bcur_batch_set_stream", "bcur_host_staging_bytes",
     "bcur_decompose_host", "bcur_set_wait_budget_ns", "bcur_autotune_measured",
     "bcur_rank_k_error", "bcur_boost_select", "bcur_cholesky_inverse", "bcur_svd_small",
-    "bcur_gather_blocks", "bcur_incoherence",
+    "bcur_gather_blocks", "bcur_incoherence", "bcur_fit_terms",
 ]
 
 
@@ -100,6 +100,8 @@ def load():
     L.bcur_fit.restype = st
     L.bcur_error.argtypes = [c_void_p, c_void_p, c_void_p]
     L.bcur_error.restype = st
+    L.bcur_fit_terms.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_double)]
+    L.bcur_fit_terms.restype = st
     L.bcur_rank.argtypes = [c_void_p] + [POINTER(c_int64)] * 4
     L.bcur_rank.restype = st
     L.bcur_sync_status.argtypes = [c_void_p]

@@ -68,6 +68,9 @@ struct bcur_plan_s {
     // BF16 tensor-core path
     size_t A16h, A16l, Om16h, Om16l, Qm16h, Qm16l, Zn16h, Zn16l, XC16[4], XR16[4], Lh, Ll, Lih,
         Lil, T1h, T1l, Pnh, Pnl, Wh, Wl, Mh, Ml, U1h, U1l, U2h, U2l, Ph, Pl, refine;
+    // adaptive split fit: its refinement flag; the one-term, three-term and
+    // chosen residuals it took
+    size_t fit_flag, fit_err;
     // FP8 sketch
     size_t A8, A8T, sA, X8m, X8n, sx;
     // per-lane temporaries of the second lane
@@ -77,13 +80,15 @@ struct bcur_plan_s {
   size_t tc_scratch_bytes = 0;
   int64_t n_partials = 0;
   bool have_scores = false, have_fit = false, have_error = false;
+  // adaptive split fit: the A its residual was taken of (bcur_error reuses it)
+  const void* fit_A = nullptr;
   template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
 };
 
 namespace {
 
 bool is_tc_prec(int p) { return p == BCUR_TF32 || p == BCUR_BF16; }
-bool is_bf16_prec(int p) { return p == BCUR_BF16 || p == BCUR_BF16X3; }
+bool is_bf16_prec(int p) { return p == BCUR_BF16 || p == BCUR_BF16X3 || p == BCUR_BF16X3A; }
 
 // The Cholesky updates must keep the working precision's accuracy: a Gram
 // matrix with condition number kappa^2 loses kappa^2 * u in them.
@@ -433,7 +438,7 @@ struct S16 {
   S16 off(int64_t e) const { return {h + e, l ? l + e : nullptr}; }
 };
 
-int parts_of(int prec) { return prec == BCUR_BF16X3 ? 3 : 1; }
+int parts_of(int prec) { return (prec == BCUR_BF16X3 || prec == BCUR_BF16X3A) ? 3 : 1; }
 
 S16 s16(bcur_plan_t P, size_t oh, size_t ol, bool with_lo) {
   return {P->at<bf16>(oh), with_lo ? P->at<bf16>(ol) : nullptr};
@@ -732,6 +737,9 @@ bcur_status_t run_scores8(bcur_plan_t P, const float* A, const float* omega, dou
 }
 
 // Stages 4-5 on tensor cores.
+bcur_status_t resid16(bcur_plan_t P, const float* A, bool split3, int* flag, const int* run,
+                      double* out, int mode);
+
 bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const int32_t* ri,
                         float* Uout, float* Cout, float* Rout) {
   cudaStream_t s = P->stream;
@@ -780,54 +788,100 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   //   M2 = L2C^{-T} L2C^{-1} M1 L2R^{-T} L2R^{-1}, so Q_C M Q_R^T = Q1_C M2 Q1_R^T
   //        (M = Q_C^T A Q_R; the residual uses M2 with Q1);
   //   U  = L1C^{-T} L2C^{-T} M L2R^{-1} L1R^{-1} = L1C^{-T} M2 L1R^{-1}.
+  // Adaptive form (BCUR_BF16X3A): the products up to M2 and the residual
+  // ||A - Q1_C M2 Q1_R^T||_F first with one BF16 term; when that residual is
+  // too coarse for the error it reports (residual_needs_refine, decided on
+  // the device) the same launches are redone with three terms (gated by the
+  // flag, always enqueued so the sequence stays capturable), and the two
+  // products after M2 take the flag's term count.  The residual is kept for
+  // bcur_error.
+  const bool adapt = P->d.fit_prec == BCUR_BF16X3A;
   S16 A16 = s16(P, P->o.A16h, P->o.A16l, lo);
   S16 W16 = s16(P, P->o.Wh, P->o.Wl, lo);
   S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
-  BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
-  {
-    GemmDesc g = mk16(m, rw, n, A16, ldn, 0, XR[1], ldn, 1, rw);
-    g.Dh = W16.h;
-    g.Dl = W16.l;
-    BCUR_TRY(g16(P, g, parts));
-    GemmDesc g2 = mk16(cw, rw, m, XC[1], ldm, 0, W16, rw, 0, rw);
-    g2.Dh = M16.h;
-    g2.Dl = M16.l;
-    BCUR_TRY(g16(P, g2, parts));
-  }
   S16 Li16 = s16(P, P->o.Lih, P->o.Lil, lo);
   S16 U1 = s16(P, P->o.U1h, P->o.U1l, lo);
   S16 U2 = s16(P, P->o.U2h, P->o.U2l, lo);
   float* Uf = P->at<float>(P->o.U2);
-  auto tri = [&](GemmDesc d, S16 out, float* outf) {
+  int* flag = P->at<int>(P->o.fit_flag);
+  double* ferr = P->at<double>(P->o.fit_err);
+  BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
+  auto tri = [&](GemmDesc d, S16 out, float* outf, int pr, const int* run, const int* terms) {
     d.Dh = out.h;
     d.Dl = out.l;
     d.D = outf;
-    return g16(P, d, parts);
+    d.run_flag = run;
+    d.parts_flag = terms;
+    return g16(P, d, pr);
   };
-  BCUR_TRY(split(P, P->at<float>(P->o.L2Ri), rw, rw, rw, Li16, rw));
-  GemmDesc t1 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 1, rw);  // M1 L2R^{-T}
-  t1.triB = 2;
-  BCUR_TRY(tri(t1, U1, nullptr));
-  GemmDesc t2 = mk16(cw, rw, rw, U1, rw, 0, Li16, rw, 0, rw);   // ... L2R^{-1}
-  t2.triB = 1;
-  BCUR_TRY(tri(t2, U2, nullptr));
-  BCUR_TRY(split(P, P->at<float>(P->o.L2Ci), cw, cw, cw, Li16, cw));
-  GemmDesc t3 = mk16(cw, rw, cw, Li16, cw, 0, U2, rw, 0, rw);   // L2C^{-1} ...
-  t3.triA = 1;
-  BCUR_TRY(tri(t3, U1, nullptr));
-  GemmDesc t4 = mk16(cw, rw, cw, Li16, cw, 1, U1, rw, 0, rw);   // M2 = L2C^{-T} ...
-  t4.triA = 2;
-  BCUR_TRY(tri(t4, M16, P->at<float>(P->o.Mb)));
+  // W1, M1 and M2 with pr terms (launches skipped unless *run when run is set)
+  auto to_m2 = [&](int pr, const int* run) -> bcur_status_t {
+    BCUR_TRY(tri(mk16(m, rw, n, A16, ldn, 0, XR[1], ldn, 1, rw), W16, nullptr, pr, run, nullptr));
+    BCUR_TRY(tri(mk16(cw, rw, m, XC[1], ldm, 0, W16, rw, 0, rw), M16, nullptr, pr, run, nullptr));
+    BCUR_TRY(split(P, P->at<float>(P->o.L2Ri), rw, rw, rw, Li16, rw));
+    GemmDesc t1 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 1, rw);  // M1 L2R^{-T}
+    t1.triB = 2;
+    BCUR_TRY(tri(t1, U1, nullptr, pr, run, nullptr));
+    GemmDesc t2 = mk16(cw, rw, rw, U1, rw, 0, Li16, rw, 0, rw);   // ... L2R^{-1}
+    t2.triB = 1;
+    BCUR_TRY(tri(t2, U2, nullptr, pr, run, nullptr));
+    BCUR_TRY(split(P, P->at<float>(P->o.L2Ci), cw, cw, cw, Li16, cw));
+    GemmDesc t3 = mk16(cw, rw, cw, Li16, cw, 0, U2, rw, 0, rw);   // L2C^{-1} ...
+    t3.triA = 1;
+    BCUR_TRY(tri(t3, U1, nullptr, pr, run, nullptr));
+    GemmDesc t4 = mk16(cw, rw, cw, Li16, cw, 1, U1, rw, 0, rw);   // M2 = L2C^{-T} ...
+    t4.triA = 2;
+    return tri(t4, M16, P->at<float>(P->o.Mb), pr, run, nullptr);
+  };
+  if (adapt) {
+    BCUR_TRY(to_m2(1, nullptr));
+    BCUR_TRY(resid16(P, A, false, flag, nullptr, ferr, 2));
+    BCUR_TRY(to_m2(3, flag));
+    BCUR_TRY(resid16(P, A, true, flag, flag, ferr + 3, 3));
+    BCUR_TRY(select_result(ferr, ferr + 3, flag, ferr + 6, s));
+  } else {
+    BCUR_TRY(to_m2(parts, nullptr));
+  }
+  const int* dyn = adapt ? flag : nullptr;
   BCUR_TRY(split(P, P->at<float>(P->o.L1Ri), rw, rw, rw, Li16, rw));
-  GemmDesc t5 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 0, rw);  // M2 L1R^{-1}
+  GemmDesc t5 = mk16(cw, rw, rw, M16, rw, 0, Li16, rw, 0, rw);    // M2 L1R^{-1}
   t5.triB = 1;
-  BCUR_TRY(tri(t5, U2, nullptr));
+  BCUR_TRY(tri(t5, U2, nullptr, parts, nullptr, dyn));
   BCUR_TRY(split(P, P->at<float>(P->o.L1Ci), cw, cw, cw, Li16, cw));
-  GemmDesc t6 = mk16(cw, rw, cw, Li16, cw, 1, U2, rw, 0, rw);   // U = L1C^{-T} ...
+  GemmDesc t6 = mk16(cw, rw, cw, Li16, cw, 1, U2, rw, 0, rw);     // U = L1C^{-T} ...
   t6.triA = 2;
-  BCUR_TRY(tri(t6, S16{}, Uf));
+  BCUR_TRY(tri(t6, S16{}, Uf, parts, nullptr, dyn));
   if (Uout) BCUR_TRY(copy2d<float>(Uf, rw, Uout, P->r_max, P->c_max, P->r_max, s));
   return BCUR_OK;
+}
+
+// One pass of the tensor-core residual: P = Q1_C M2 (m x r) and
+// sum (A - P Q1_R^T)^2 in the GEMM epilogue, with one BF16 term (split3
+// false) or BF16 pairs; launches skipped unless *run when run is set; the
+// partial sums reduced into out (finish_residual mode, refinement flag).
+bcur_status_t resid16(bcur_plan_t P, const float* A, bool split3, int* flag, const int* run,
+                      double* out, int mode) {
+  const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
+  const int64_t cw = P->c_pad, rw = P->r_pad;
+  S16 QC = s16(P, P->o.XC16[2], P->o.XC16[3], split3);  // Q1_C, Q1_R (with M2, see run_fit16)
+  S16 QR = s16(P, P->o.XR16[2], P->o.XR16[3], split3);
+  S16 M16 = s16(P, P->o.Mh, P->o.Ml, split3);
+  S16 Pp = s16(P, P->o.Ph, P->o.Pl, split3);
+  GemmDesc g = mk16(m, rw, cw, QC, ldm, 1, M16, rw, 0, rw);
+  g.Dh = Pp.h;
+  g.Dl = Pp.l;
+  g.run_flag = run;
+  BCUR_TRY(g16(P, g, split3 ? 3 : 1));
+  GemmDesc r = mk16(m, n, rw, Pp, rw, 0, QR, ldn, 0, 0);
+  r.X = A;
+  r.ldx = P->lda;
+  r.partials = P->at<double>(P->o.partials);
+  r.parts = split3 ? 3 : 1;
+  r.status = P->at<int>(P->o.status);
+  r.run_flag = run;
+  int64_t np = 0;
+  BCUR_TRY(gemm_tc_resid(r, BCUR_BF16, P->stream, &np));
+  return finish_residual(P->at<double>(P->o.partials), np, out, mode, P->stream, flag);
 }
 
 // Stage 6 on tensor cores: P = Q_C^T M, then sum (A - P Q_R)^2 in the GEMM
@@ -836,35 +890,18 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
 // (residual_needs_refine, decided on the device), P and the residual are
 // recomputed with BF16 pairs.  The second pair of launches is always
 // enqueued (the sequence stays capturable) and does nothing unless the flag
-// is set.
+// is set.  The adaptive fit has taken this residual already: for the same A
+// it is copied.
 bcur_status_t run_error16(bcur_plan_t P, const float* A, double* out) {
-  const int64_t m = P->m, n = P->n, ldm = P->ldm, ldn = P->ldn;
-  const int64_t cw = P->c_pad, rw = P->r_pad;
+  if (P->d.fit_prec == BCUR_BF16X3A && A == P->fit_A) {
+    BCUR_CUDA_TRY(cudaMemcpyAsync(out, P->at<double>(P->o.fit_err) + 6, 3 * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, P->stream));
+    return BCUR_OK;
+  }
   const int parts = parts_of(P->d.fit_prec);
   int* flag = P->at<int>(P->o.refine);
-  for (int pass = 0; pass < (parts == 3 ? 2 : 1); ++pass) {
-    const bool lo = pass == 1;
-    S16 QC = s16(P, P->o.XC16[2], P->o.XC16[3], lo);  // Q1_C, Q1_R (with M2, see run_fit16)
-    S16 QR = s16(P, P->o.XR16[2], P->o.XR16[3], lo);
-    S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
-    S16 Pp = s16(P, P->o.Ph, P->o.Pl, lo);
-    GemmDesc g = mk16(m, rw, cw, QC, ldm, 1, M16, rw, 0, rw);
-    g.Dh = Pp.h;
-    g.Dl = Pp.l;
-    if (pass == 1) g.run_flag = flag;
-    BCUR_TRY(g16(P, g, lo ? 3 : 1));
-    GemmDesc r = mk16(m, n, rw, Pp, rw, 0, QR, ldn, 0, 0);
-    r.X = A;
-    r.ldx = P->lda;
-    r.partials = P->at<double>(P->o.partials);
-    r.parts = lo ? 3 : 1;
-    r.status = P->at<int>(P->o.status);
-    if (pass == 1) r.run_flag = flag;
-    int64_t np = 0;
-    BCUR_TRY(gemm_tc_resid(r, BCUR_BF16, P->stream, &np));
-    const int mode = parts == 3 ? (pass == 0 ? 2 : 3) : 0;
-    BCUR_TRY(finish_residual(P->at<double>(P->o.partials), np, out, mode, P->stream, flag));
-  }
+  BCUR_TRY(resid16(P, A, false, flag, nullptr, out, parts == 3 ? 2 : 0));
+  if (parts == 3) BCUR_TRY(resid16(P, A, true, flag, flag, out, 3));
   return BCUR_OK;
 }
 
@@ -1015,9 +1052,10 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
   if (!d->replacement && (d->g_col > d->G_col || d->g_row > d->G_row)) return BCUR_EINVAL;
   if (d->sketch_prec == BCUR_FP8 && d->a_dtype != BCUR_F32) return BCUR_EINVAL;
   if (d->fit_prec == BCUR_FP8) return BCUR_EINVAL;  // FP8 is a sketch precision only
+  if (d->sketch_prec == BCUR_BF16X3A) return BCUR_EINVAL;  // the adaptive form is a fit's
   for (int p : {d->sketch_prec, d->fit_prec}) {
     if (p == BCUR_FP8) continue;
-    if (p < BCUR_F64 || p > BCUR_BF16X3) return BCUR_EINVAL;
+    if (p < BCUR_F64 || p > BCUR_BF16X3A) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F64 && p != BCUR_F64) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F32 && p == BCUR_F64) return BCUR_EINVAL;
     if (p == BCUR_TF32) return BCUR_ENOTSUP;
@@ -1113,7 +1151,7 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
   if (P->bf16_path) {
     const size_t h2 = 2;  // bytes per BF16
     const int64_t wm = std::max(cw, rw);
-    const bool s3 = d->sketch_prec == BCUR_BF16X3, f3 = d->fit_prec == BCUR_BF16X3;
+    const bool s3 = d->sketch_prec == BCUR_BF16X3, f3 = parts_of(d->fit_prec) == 3;
     const bool any3 = s3 || f3;
     o.A16h = L.take(P->m * P->ldn * h2);
     o.A16l = L.take(any3 ? P->m * P->ldn * h2 : 0);
@@ -1145,6 +1183,8 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
       o.Ph = L.take(P->m * rw * h2);
       o.Pl = L.take(P->m * rw * h2);
       o.refine = L.take(sizeof(int));
+      o.fit_flag = L.take(sizeof(int));
+      o.fit_err = L.take(9 * sizeof(double));
       o.Lh2 = L.take(wm * wm * h2);
       o.Ll2 = L.take(wm * wm * h2);
       o.Lih2 = L.take(wm * wm * h2);
@@ -1197,6 +1237,7 @@ bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
                                 P->row_off.size() * 8, cudaMemcpyHostToDevice, s));
   BCUR_CUDA_TRY(cudaStreamSynchronize(s));
   P->have_scores = P->have_fit = false;
+  P->fit_A = nullptr;
   return BCUR_OK;
 }
 
@@ -1258,7 +1299,32 @@ bcur_status_t bcur_fit(bcur_plan_t P, const void* A, const int32_t* ci, const in
     st = run_fit<float>(P, (const float*)A, ci, ri, (float*)U, (float*)C, (float*)R);
   P->have_fit = (st == BCUR_OK);
   P->have_error = false;
+  P->fit_A = (st == BCUR_OK && P->d.fit_prec == BCUR_BF16X3A) ? A : nullptr;
   return st;
+}
+
+bcur_status_t bcur_fit_terms(bcur_plan_t P, int32_t* terms, double* est) {
+  if (!P || !terms) return BCUR_EINVAL;
+  if (!P->ws || !P->have_fit) return BCUR_ESTATE;
+  if (est) *est = -1.0;
+  if (P->d.a_dtype == BCUR_F64 || !is_bf16_prec(P->d.fit_prec)) {
+    *terms = 0;
+    return BCUR_OK;
+  }
+  if (P->d.fit_prec != BCUR_BF16X3A) {
+    *terms = parts_of(P->d.fit_prec);
+    return BCUR_OK;
+  }
+  int flag = 0;
+  double e1[3] = {-1.0, -1.0, -1.0};
+  BCUR_CUDA_TRY(cudaMemcpyAsync(&flag, P->at<int>(P->o.fit_flag), sizeof(int),
+                                cudaMemcpyDeviceToHost, P->stream));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(e1, P->at<double>(P->o.fit_err), sizeof(e1),
+                                cudaMemcpyDeviceToHost, P->stream));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  *terms = flag ? 3 : 1;
+  if (est) *est = e1[1];
+  return BCUR_OK;
 }
 
 bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {

@@ -95,6 +95,7 @@ struct Params {
   double* partials;      // per-CTA {sum (X - acc)^2, sum X^2}
   int* status;
   const int* run_flag;   // when non-null and 0 at launch: nothing to do
+  const int* parts_flag; // parts = 3, non-null and 0 at launch: one term (hi x hi)
   const float* scale_m;  // optional per-row / per-column factors of the output
   const float* scale_n;  //   (MMA space), applied after alpha
 };
@@ -276,6 +277,12 @@ __device__ __forceinline__ int snake(int u, int total) {
   return (round < full_rounds && (round & 1)) ? round * G + (G - 1 - c) : u;
 }
 
+// BF16 terms of a GEMM's products: the producer and the MMA issuer read the
+// same flag (written by an earlier launch) and so agree on the K loop.
+__device__ __forceinline__ int terms_of(const Params& p) {
+  return (p.parts == 3 && p.parts_flag && *p.parts_flag == 0) ? 1 : p.parts;
+}
+
 template <int BN, int KIND>
 __device__ __forceinline__ Unit decode_unit(const Params& p, int uu) {
   constexpr int BK = KindCfg<KIND>::bk;
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
             last = M;
           }
         }
-        const int parts = P->parts, a_mn = P->a_mn, b_mn = P->b_mn;
+        const int parts = terms_of(*P), a_mn = P->a_mn, b_mn = P->b_mn;
         const int n_it = (w.khi - w.klo) * parts;
         for (int i = 0; i < n_it; ++i, ++it) {
           const int kb = w.klo + i / parts, part = i % parts;
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
         const Maps* M;
         const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M, lcache);
         if (w.skip || w.klo >= w.khi) continue;
-        const int parts = P->parts, a_mn = P->a_mn, b_mn = P->b_mn;
+        const int parts = terms_of(*P), a_mn = P->a_mn, b_mn = P->b_mn;
         const uint32_t id = idesc(KIND, a_mn, b_mn, BM, BN);
         const uint32_t acc = tu & 1, use = tu >> 1;
         if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, status, abort_flag)) { ok = false; break; }
@@ -1195,6 +1202,7 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
   p.X = (const float*)d.X; p.ldx = d.ldx; p.partials = d.partials;
   p.status = d.status;
   p.run_flag = d.run_flag;
+  p.parts_flag = parts == 3 ? d.parts_flag : nullptr;
   p.scale_m = swap ? d.scale_n : d.scale_m;
   p.scale_n = swap ? d.scale_m : d.scale_n;
   p.ksplit = 1;

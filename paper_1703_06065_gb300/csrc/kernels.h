@@ -51,6 +51,9 @@ struct GemmDesc {
   // Optional device flag: when it reads 0 at launch the GEMM does nothing
   // (tensor-core path; in a grouped launch per GEMM).
   const int* run_flag = nullptr;
+  // Optional device flag for a split product (parts = 3): when it reads 0 at
+  // launch the product is taken with one term, A_hi B_hi.
+  const int* parts_flag = nullptr;
   // FP8 e4m3 operands (prec BCUR_FP8; A and B K-major, one term), and
   // optional per-row (M) / per-column (N) factors of the result, applied
   // after alpha (tensor-core store only).
@@ -196,6 +199,9 @@ bcur_status_t gather_rows(const T* A, int64_t lda, int64_t n, const int64_t* map
 // residual_needs_refine); mode 3: as mode 0, written only when *flag != 0.
 bcur_status_t finish_residual(const double* partials, int64_t n, double* out, int mode,
                               cudaStream_t s, int* flag = nullptr);
+// out[0..2] = *flag ? r1[0..2] : r0[0..2] (device pointers).
+bcur_status_t select_result(const double* r0, const double* r1, const int* flag, double* out,
+                            cudaStream_t s);
 
 template <typename Tin, typename Tout>
 bcur_status_t convert(const Tin* in, Tout* out, int64_t count, cudaStream_t s);

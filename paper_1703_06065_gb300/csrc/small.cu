@@ -89,6 +89,19 @@ bcur_status_t finish_residual(const double* partials, int64_t n, double* out, in
   return BCUR_OK;
 }
 
+__global__ void select_result_kernel(const double* r0, const double* r1, const int* flag,
+                                     double* out) {
+  const int i = threadIdx.x;
+  if (i < 3) out[i] = *flag ? r1[i] : r0[i];
+}
+
+bcur_status_t select_result(const double* r0, const double* r1, const int* flag, double* out,
+                            cudaStream_t s) {
+  select_result_kernel<<<1, 32, 0, s>>>(r0, r1, flag, out);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Small FP64 Cholesky with the drop rule, and its inverse
 // ---------------------------------------------------------------------------

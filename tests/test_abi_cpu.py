@@ -73,7 +73,10 @@ def _plan(lib, **kw):
     (dict(sp=5, fp=4), 0),                   # FP8 sketch, split-BF16 fit
     (dict(sp=1, fp=5), 1),                   # FP8 is a sketch precision only
     (dict(dtype=0, sp=5, fp=0), 1),          # FP8 sketch needs FP32 storage
-    (dict(sp=6, fp=1), 1),
+    (dict(sp=6, fp=1), 1),                   # the adaptive split form is a fit precision
+    (dict(sp=3, fp=6), 0),                   # BF16 sketch, adaptive split-BF16 fit
+    (dict(dtype=0, sp=0, fp=6), 1),          # FP64 data with a BF16 fit
+    (dict(sp=3, fp=7), 1),
     (dict(lda=100), 1),                      # lda < n
     (dict(k=100, p=40), 1),                  # l > 128
     (dict(k=0), 1),
@@ -103,6 +106,10 @@ def test_calls_before_workspace_and_null_plan(lib):
     assert lib.bcur_scores(h, dummy, dummy, dummy, dummy) == 8      # ESTATE
     assert lib.bcur_fit(h, dummy, dummy, dummy, None, None, None) == 8
     assert lib.bcur_error(h, dummy, dummy) == 8
+    t, e = ctypes.c_int32(), ctypes.c_double()
+    assert lib.bcur_fit_terms(h, ctypes.byref(t), ctypes.byref(e)) == 8
+    assert lib.bcur_fit_terms(h, None, None) == 1
+    assert lib.bcur_fit_terms(None, ctypes.byref(t), None) == 1
     assert lib.bcur_set_workspace(h, ctypes.c_void_p(0x1001), ws.value) == 1  # misaligned
     assert lib.bcur_set_workspace(h, ctypes.c_void_p(0x1000), ws.value - 256) == 2
     lib.bcur_destroy(h)
