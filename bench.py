@@ -449,12 +449,14 @@ def main_native(args):
         if os.path.exists(tpath) and fp.startswith("bf16"):
             import hashlib
 
-            tr = json.load(open(tpath))
             src = open(os.path.join(ROOT, "paper_1703_06065_gb300", "csrc", "gemm_tc.cu"), "rb").read()
-            if (tr.get("source_sha256") == hashlib.sha256(src).hexdigest()
-                    and tr.get("m") == p.m and tr.get("n") == p.n and tr.get("r") == plan.r_max):
-                roof["traffic"] = tr["dram_bytes_read"] + tr["dram_bytes_write"]
-                roof["traffic_source"] = "profiles/tc_gemm_traffic.json"
+            sha = hashlib.sha256(src).hexdigest()
+            terms = 1 if fit_terms == 1 else 3
+            for tr in json.load(open(tpath)).get("records", []):
+                if (tr.get("source_sha256") == sha and tr.get("terms") == terms
+                        and tr.get("m") == p.m and tr.get("n") == p.n and tr.get("r") == plan.r_max):
+                    roof["traffic"] = tr["dram_bytes_read"] + tr["dram_bytes_write"]
+                    roof["traffic_source"] = f"profiles/tc_gemm_traffic.json ({terms} term(s))"
 
     study = None
     if rank == 0 and p.name == "precision_32768" and not args.no_cpu_baseline:
@@ -956,8 +958,9 @@ def _sha(rel: str) -> str:
 # Kernel-only mode: one tensor-core GEMM of the fit, for profiling
 # ---------------------------------------------------------------------------
 def main_kernel(args):
-    """W = A Q_R as the fit computes it (split BF16, three terms) on random
-    operands of the given shape, timed with CUDA events; prints one JSON line."""
+    """W = A Q_R as the fit computes it (split BF16, three terms, or one BF16
+    term as the adaptive fit keeps it: --terms) on random operands of the
+    given shape, timed with CUDA events; prints one JSON line."""
     import torch
 
     import paper_1703_06065_gb300 as pkg
@@ -975,21 +978,31 @@ def main_kernel(args):
     Ql = (Q - Qh.float()).to(torch.bfloat16)
     del Q
     W = torch.empty(m, r, device=dev)
+    terms = 1 if args.terms == 1 else 3
+
+    def run():
+        if terms == 3:
+            pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=W)
+        else:
+            pkg.gemm(Ah, Qh, False, True, prec="bf16", out=W)
+
     for _ in range(args.warmup):
-        pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=W)
+        run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("bench_timed")
     e0.record()
     for _ in range(args.steps):
-        pkg.gemm_split(Ah, Al, Qh, Ql, False, True, out=W)
+        run()
     e1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"kernel": "tc_gemm_kernel<256, BF16, store> split BF16 (3 terms)",
-                      "m": m, "n": n, "r": r, "ms": ms,
-                      "bf16_mma_tflops": 3 * 2.0 * m * n * r / (ms * 1e-3) / 1e12}), flush=True)
+    what = "split BF16 (3 terms)" if terms == 3 else "one BF16 term"
+    print(json.dumps({"kernel": f"tc_gemm_kernel<256, BF16, store> {what}",
+                      "m": m, "n": n, "r": r, "terms": terms, "ms": ms,
+                      "bf16_mma_tflops": terms * 2.0 * m * n * r / (ms * 1e-3) / 1e12}),
+          flush=True)
 
 
 def main():
@@ -1012,6 +1025,8 @@ def main():
     ap.add_argument("--kernel", default=None, choices=["wgemm"],
                     help="time one kernel instead of the workload (profiling)")
     ap.add_argument("--shape", default="32768,32768,8192", help="kernel mode: m,n,r")
+    ap.add_argument("--terms", type=int, default=3, choices=[1, 3],
+                    help="kernel mode: BF16 terms of W = A Q_R")
     ap.add_argument("--no-graph", action="store_true",
                     help="batched workload: launch eagerly instead of replaying a CUDA graph")
     args = ap.parse_args()
