@@ -515,10 +515,11 @@ def main_reference_batched(args, world):
 
 
 def precision_study(full: bi.Problem, dev):
-    """Per-stage error of each sketch precision against the FP64 oracle, on the
-    bounded sample of the workload that the oracle decomposes in seconds
-    (bcur_inputs.host_sample: the same recipe at 1/4 the size per side,
-    k, p, q unchanged), with the split-BF16 fit:
+    """Per-stage error of each sketch precision (BF16, FP8 with per-row and with
+    per-128x128-block scales, split BF16, FP32) and of the adaptive fit against
+    the FP64 oracle, on the bounded sample of the workload that the oracle
+    decomposes in seconds (bcur_inputs.host_sample: the same recipe at 1/4 the
+    size per side, k, p, q unchanged), with the split-BF16 fit:
       - subspace: sin of the largest principal angle between the GPU's top-k
         right (and left) singular subspace and the oracle's;
       - scores: max |l_gpu - l_orc| / max l_orc over both sides;
@@ -550,8 +551,8 @@ def precision_study(full: bi.Problem, dev):
     out = {"sample": f"{p.m}x{p.n}, k={p.k}, p={p.p}, q={p.q}, {p.g_col}+{p.g_row} blocks of "
                      f"{int(p.col_off[1])}", "oracle_s": round(t_orc, 2),
            "fit": "bf16x3 (keys: sketch precision), bf16x3a for the key sketch/fit"}
-    for sp, fp in (("bf16", "bf16x3"), ("fp8", "bf16x3"), ("bf16x3", "bf16x3"), ("f32", "bf16x3"),
-                   ("bf16", "bf16x3a")):
+    for sp, fp in (("bf16", "bf16x3"), ("fp8", "bf16x3"), ("fp8b", "bf16x3"), ("bf16x3", "bf16x3"),
+                   ("f32", "bf16x3"), ("bf16", "bf16x3a")):
         plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
                         dtype="f32", sketch_prec=sp, fit_prec=fp)
         cs, rs = plan.scores(At, omt)

@@ -71,6 +71,11 @@ typedef enum {
  *                 roughly 4-bit operands, A scaled per row and each skinny
  *                 panel per row (amax / 448), the scales undone exactly in
  *                 the products' epilogue; FP32 accumulation.
+ *   BCUR_FP8B   : sketch only (FP32 storage): as BCUR_FP8, with one scale
+ *                 per 128 x 128 block of A (block amax / 448) instead of per
+ *                 row; each 128-deep K block of a product with A is scaled by
+ *                 its block's factor as it is summed (FP32), the panels keep
+ *                 their per-row scales.
  *   BCUR_BF16X3A: fit only (FP32 storage), adaptive: the Cholesky-QR of C
  *                 and R^T as BCUR_BF16X3; the core products (W = A Q_R,
  *                 M = Q_C^T W and the triangular products that turn M into
@@ -92,7 +97,8 @@ typedef enum {
   BCUR_BF16 = 3,
   BCUR_BF16X3 = 4,
   BCUR_FP8 = 5,
-  BCUR_BF16X3A = 6
+  BCUR_BF16X3A = 6,
+  BCUR_FP8B = 7
 } bcur_prec_t;
 
 typedef struct {

@@ -13,9 +13,9 @@ from ctypes import POINTER, c_double, c_int32, c_int64, c_size_t, c_void_p
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbcur.so")
 
-BCUR_F64, BCUR_F32, BCUR_TF32, BCUR_BF16, BCUR_BF16X3, BCUR_FP8, BCUR_BF16X3A = range(7)
+BCUR_F64, BCUR_F32, BCUR_TF32, BCUR_BF16, BCUR_BF16X3, BCUR_FP8, BCUR_BF16X3A, BCUR_FP8B = range(8)
 PREC = {"f64": BCUR_F64, "f32": BCUR_F32, "tf32": BCUR_TF32, "bf16": BCUR_BF16,
-        "bf16x3": BCUR_BF16X3, "fp8": BCUR_FP8, "bf16x3a": BCUR_BF16X3A}
+        "bf16x3": BCUR_BF16X3, "fp8": BCUR_FP8, "bf16x3a": BCUR_BF16X3A, "fp8b": BCUR_FP8B}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ENONFINITE",
           6: "ETIMEOUT", 7: "ENOTSUP", 8: "ESTATE"}
 

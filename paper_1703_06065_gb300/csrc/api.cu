@@ -678,14 +678,18 @@ bcur_status_t run_scores16(bcur_plan_t P, const float* A, const float* omega, do
 }
 
 // Stages 1-2 with the products by A on FP8 e4m3 tensor cores.  A is
-// quantised once per row (A = diag(s_A) A8) and kept twice (A8 and its
-// transpose, so both products read K-major operands); each skinny panel is
-// quantised per row before its product, with s_A folded in when the product
-// sums over the rows of A.  All scales come out of the products exactly and
-// are applied in the GEMM epilogue; the panels stay FP32 and are
-// re-orthonormalised after every product as in the BF16 form.
+// quantised once and kept twice (A8 and its transpose, so both products read
+// K-major operands); each skinny panel is quantised per row before its
+// product.  BCUR_FP8: one scale per row of A (A = diag(s_A) A8), folded into
+// the panel when the product sums over the rows of A, so that every scale
+// comes out of the products exactly and is applied in the GEMM epilogue.
+// BCUR_FP8B: one scale per 128 x 128 block of A; a block's scale varies along
+// K, so each 128-deep K block of a product is scaled as it is added (the
+// GEMM's block-scaled path).  The panels stay FP32 and are re-orthonormalised
+// after every product as in the BF16 form.
 bcur_status_t run_scores8(bcur_plan_t P, const float* A, const float* omega, double* cs,
                           double* rs) {
+  const bool blk = P->d.sketch_prec == BCUR_FP8B;
   cudaStream_t s = P->stream;
   const int l = P->l;
   const int64_t m = P->m, n = P->n, lda = P->lda, ldm = P->ldm, ldn = P->ldn;
@@ -700,36 +704,55 @@ bcur_status_t run_scores8(bcur_plan_t P, const float* A, const float* omega, dou
   uint8_t* X8m = P->at<uint8_t>(P->o.X8m);
   uint8_t* X8n = P->at<uint8_t>(P->o.X8n);
   float* sx = P->at<float>(P->o.sx);
-  BCUR_TRY(quant_rows_e4m3(A, lda, m, n, nullptr, A8, ldn8, sA, s));
-  BCUR_TRY(transpose_u8(A8, ldn8, m, n, A8T, ldm8, s));
+  const int64_t gn = (n + 127) / 128;  // column blocks of A (block scales, row-major)
+  if (blk) {
+    BCUR_TRY(quant_blocks_e4m3(A, lda, m, n, A8, ldn8, A8T, ldm8, sA, s));
+  } else {
+    BCUR_TRY(quant_rows_e4m3(A, lda, m, n, nullptr, A8, ldn8, sA, s));
+    BCUR_TRY(transpose_u8(A8, ldn8, m, n, A8T, ldm8, s));
+  }
   // Y^T (l x m) = X^T A^T from the panel X^T (l x n):  D = X8 A8^T, rows
-  // scaled by sx, columns by sA
-  auto prodAt = [&](const float* X, float* Y) {
-    BCUR_TRY(quant_rows_e4m3(X, ldn, l, n, nullptr, X8n, ldn8, sx, s));
+  // scaled by sx, columns by sA (per row), or each K block by its block's
+  // scale (op(B) = A8^T seen as N x K is A8: block (row block, column block))
+  auto prodAt = [&](const float* X, int64_t ldx, float* Y) {
+    BCUR_TRY(quant_rows_e4m3(X, ldx, l, n, nullptr, X8n, ldn8, sx, s));
     GemmDesc g = mk(l, m, n, X8n, ldn8, 0, A8, ldn8, 1, Y, ldm);
     g.ab_fp8 = 1;
     g.scale_m = sx;
-    g.scale_n = sA;
+    if (blk) {
+      g.bscale_b = sA;
+      g.bs_n = gn;
+      g.bs_k = 1;
+    } else {
+      g.scale_n = sA;
+    }
     g.status = P->at<int>(P->o.status);
     return gemm_tc(g, BCUR_FP8, s);
   };
   // Z^T (l x n) = X^T A from the panel X^T (l x m):  X^T diag(s_A) is
-  // quantised, D = X8 A8T^T, rows scaled by sx
+  // quantised (per-row scales) or X^T itself (block scales: op(B) seen as
+  // N x K is A8T, whose block (j, k) is A's block (k, j)), D = X8 A8T^T, rows
+  // scaled by sx
   auto prodA = [&](const float* X, float* Z) {
-    BCUR_TRY(quant_rows_e4m3(X, ldm, l, m, sA, X8m, ldm8, sx, s));
+    BCUR_TRY(quant_rows_e4m3(X, ldm, l, m, blk ? nullptr : sA, X8m, ldm8, sx, s));
     GemmDesc g = mk(l, n, m, X8m, ldm8, 0, A8T, ldm8, 1, Z, ldn);
     g.ab_fp8 = 1;
     g.scale_m = sx;
+    if (blk) {
+      g.bscale_b = sA;
+      g.bs_n = 1;
+      g.bs_k = gn;
+    }
     g.status = P->at<int>(P->o.status);
     return gemm_tc(g, BCUR_FP8, s);
   };
   const int ep = BCUR_F32;
-  BCUR_TRY(prodAt(omega, Pm0));
+  BCUR_TRY(prodAt(omega, n, Pm0));  // the caller's Omega panel has leading dimension n
   BCUR_TRY(orth_panel<float>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, ep, nullptr));
   for (int it = 0; it < P->q; ++it) {
     BCUR_TRY(prodA(Pm0, Pn0));
     BCUR_TRY(orth_panel<float>(P, Pn0, Pn1, l, n, ldn, P->ksplit_n, ep, nullptr));
-    BCUR_TRY(prodAt(Pn0, Pm0));
+    BCUR_TRY(prodAt(Pn0, ldn, Pm0));
     BCUR_TRY(orth_panel<float>(P, Pm0, Pm1, l, m, ldm, P->ksplit_m, ep, nullptr));
   }
   BCUR_TRY(prodA(Pm0, Pn0));
@@ -1050,11 +1073,13 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
     return BCUR_EINVAL;
   if (d->g_col < 1 || d->g_row < 1) return BCUR_EINVAL;
   if (!d->replacement && (d->g_col > d->G_col || d->g_row > d->G_row)) return BCUR_EINVAL;
-  if (d->sketch_prec == BCUR_FP8 && d->a_dtype != BCUR_F32) return BCUR_EINVAL;
-  if (d->fit_prec == BCUR_FP8) return BCUR_EINVAL;  // FP8 is a sketch precision only
+  const bool fp8 = d->sketch_prec == BCUR_FP8 || d->sketch_prec == BCUR_FP8B;
+  if (fp8 && d->a_dtype != BCUR_F32) return BCUR_EINVAL;
+  // FP8 is a sketch precision only
+  if (d->fit_prec == BCUR_FP8 || d->fit_prec == BCUR_FP8B) return BCUR_EINVAL;
   if (d->sketch_prec == BCUR_BF16X3A) return BCUR_EINVAL;  // the adaptive form is a fit's
   for (int p : {d->sketch_prec, d->fit_prec}) {
-    if (p == BCUR_FP8) continue;
+    if (p == BCUR_FP8 || p == BCUR_FP8B) continue;
     if (p < BCUR_F64 || p > BCUR_BF16X3A) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F64 && p != BCUR_F64) return BCUR_EINVAL;
     if (d->a_dtype == BCUR_F32 && p == BCUR_F64) return BCUR_EINVAL;
@@ -1197,11 +1222,12 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
       o.tc_scratch2 = L.take(P->tc_scratch_bytes);
     }
   }
-  if (d->sketch_prec == BCUR_FP8) {
+  if (fp8) {
     const int64_t ldm8 = round_up(P->m, 16), ldn8 = round_up(P->n, 16);
     o.A8 = L.take(P->m * ldn8);
     o.A8T = L.take(P->n * ldm8);
-    o.sA = L.take(P->m * 4);
+    // row scales (FP8) or 128 x 128 block scales (FP8B)
+    o.sA = L.take(4 * std::max<int64_t>(P->m, ((P->m + 127) / 128) * ((P->n + 127) / 128)));
     o.X8m = L.take(l * ldm8);
     o.X8n = L.take(l * ldn8);
     o.sx = L.take(l * 4);
@@ -1251,7 +1277,7 @@ bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, doubl
     st = run_scores<double>(P, (const double*)A, (const double*)omega, cs, rs);
   else if (is_bf16_prec(P->d.sketch_prec))
     st = run_scores16(P, (const float*)A, (const float*)omega, cs, rs);
-  else if (P->d.sketch_prec == BCUR_FP8)
+  else if (P->d.sketch_prec == BCUR_FP8 || P->d.sketch_prec == BCUR_FP8B)
     st = run_scores8(P, (const float*)A, (const float*)omega, cs, rs);
   else
     st = run_scores<float>(P, (const float*)A, (const float*)omega, cs, rs);

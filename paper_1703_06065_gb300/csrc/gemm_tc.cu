@@ -98,6 +98,11 @@ struct Params {
   const int* parts_flag; // parts = 3, non-null and 0 at launch: one term (hi x hi)
   const float* scale_m;  // optional per-row / per-column factors of the output
   const float* scale_n;  //   (MMA space), applied after alpha
+  // FP8 block scales (MMA space): the product of K block kb in M tile tm is
+  // scaled by bscale[tm * bs_sm + kb * bs_sk] before it is added; each K block
+  // is accumulated in its own TMEM buffer and summed in the epilogue.
+  const float* bscale;
+  int bs_sm, bs_sk;
 };
 
 template <int KIND> struct KindCfg;
@@ -501,6 +506,31 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
         if (w.skip || w.klo >= w.khi) continue;
         const int parts = terms_of(*P), a_mn = P->a_mn, b_mn = P->b_mn;
         const uint32_t id = idesc(KIND, a_mn, b_mn, BM, BN);
+        if constexpr (KIND == 2 && BN <= 128 && EPI == EPI_STORE && !GROUPED) {
+          if (P->bscale) {
+            // one K block (one stage) per TMEM buffer, each handed to the
+            // epilogue on its own
+            for (int i = 0; i < w.khi - w.klo; ++i, ++it) {
+              const uint32_t acc = tu & 1, use = tu >> 1;
+              if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, status, abort_flag)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t stage = it % S, round = it / S;
+              if (!mbar_wait(&full[stage], round & 1, status, abort_flag)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + stage * SC::kStageBytes);
+              const uint32_t sb = sa + kStageABytes;
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                tc_mma<KIND>(tmem_base + acc * BN, sdesc(sa + j * 32, 16, 1024),
+                             sdesc(sb + j * 32, 16, 1024), id, j > 0 ? 1u : 0u);
+              tc_commit(&empty[stage]);
+              tc_commit(&tfull[acc]);
+              ++tu;
+            }
+            if (!ok) break;
+            continue;
+          }
+        }
         const uint32_t acc = tu & 1, use = tu >> 1;
         if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, status, abort_flag)) { ok = false; break; }
         tc_fence_after();
@@ -751,6 +781,52 @@ __global__ void __launch_bounds__(threads_of<EPI, GROUPED>(), 1)
       const Maps* M;
       const Unit w = locate<BN, KIND, GROUPED>(maps, p, grp, u, total, P, M, lcache);
       if (w.skip) continue;
+      if constexpr (KIND == 2 && BN <= 128 && EPI == EPI_STORE && !GROUPED) {
+        if (P->bscale) {
+          // block-scaled FP8: acc += scale(tile, kb) * (the K block's product),
+          // in registers; each TMEM buffer is released as soon as it is read
+          float racc[BN];
+#pragma unroll
+          for (int i = 0; i < BN; ++i) racc[i] = 0.f;
+          const int64_t tm = w.m0 / BM;
+          bool good = true;
+          for (int i = 0; i < w.khi - w.klo; ++i) {
+            const uint32_t a2 = tu & 1, u2 = tu >> 1;
+            const bool got = mbar_wait(&tfull[a2], u2 & 1, status, abort_flag);
+            if (!__all_sync(0xffffffffu, got)) { good = false; break; }
+            tc_fence_after();
+            const float sc = P->bscale[tm * P->bs_sm + (int64_t)(w.klo + i) * P->bs_sk];
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) {
+              float v[32];
+              __syncwarp();
+              tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + a2 * BN + c * 32, v);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) racc[c * 32 + j] = fmaf(sc, v[j], racc[c * 32 + j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[a2]);
+            ++tu;
+          }
+          if (!good) { ok = false; break; }
+          // D^T (the block-scaled product runs transposed): lane = row
+          const int row = w.m0 + quarter * 32 + lane;
+          if (row < P->Mm) {
+            const int Nm = P->Nm;
+            const int64_t ldd = P->ldd;
+            const float f = P->alpha * (P->scale_m ? P->scale_m[row] : 1.f);
+            const float* const sn = P->scale_n;
+            float* const Dp = P->D + (int64_t)w.b * P->sD;
+#pragma unroll
+            for (int i = 0; i < BN; ++i) {
+              const int col = w.n0 + i;
+              if (col < Nm) Dp[(int64_t)col * ldd + row] = f * racc[i] * (sn ? sn[col] : 1.f);
+            }
+          }
+          continue;
+        }
+      }
       const bool has_acc = w.klo < w.khi;
       const uint32_t acc = tu & 1, use = tu >> 1;
       if (has_acc) {
@@ -1206,6 +1282,16 @@ bcur_status_t prepare(const GemmDesc& d, int prec, int epi, int BN_force, Prepar
   p.scale_m = swap ? d.scale_n : d.scale_m;
   p.scale_n = swap ? d.scale_m : d.scale_n;
   p.ksplit = 1;
+  if (d.bscale_b) {
+    // op(B) becomes the MMA's A operand (128-row tiles = its 128-row blocks)
+    // and a stage holds one 128-deep K block of e4m3
+    if (kind != 2 || epi != EPI_STORE || !swap || BN > 128 || !d.D || d.Dh || d.Dl ||
+        d.beta != 0.0 || tri_out || batch != 1 || d.bs_n > INT32_MAX || d.bs_k > INT32_MAX)
+      return BCUR_ENOTSUP;
+    p.bscale = d.bscale_b;
+    p.bs_sm = (int)d.bs_n;
+    p.bs_sk = (int)d.bs_k;
+  }
   out->BN = BN;
   out->kind = kind;
   return BCUR_OK;

@@ -60,6 +60,13 @@ struct GemmDesc {
   int ab_fp8 = 0;
   const float* scale_m = nullptr;
   const float* scale_n = nullptr;
+  // FP8 only: one factor per 128 x 128 block of op(B) seen as N x K (the
+  // block holding column j and K index k has factor
+  // bscale_b[(j / 128) * bs_n + (k / 128) * bs_k]); each 128-deep K block's
+  // product is scaled by it before it is added (store epilogue, FP32 D,
+  // M < 128 with N >= 2M so that the product runs transposed).
+  const float* bscale_b = nullptr;
+  int64_t bs_n = 0, bs_k = 0;
 };
 
 template <typename T> bcur_status_t gemm_simt(const GemmDesc& d, cudaStream_t s);
@@ -239,6 +246,13 @@ bcur_status_t scale_rows_by(T* X, int64_t rows, int64_t cols, int64_t ld, const 
 bcur_status_t quant_rows_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t cols,
                               const float* pre, uint8_t* Q, int64_t ldq, float* scale,
                               cudaStream_t s);
+// Blockwise FP8 e4m3 quantisation: for each 128 x 128 block (bi, bj) of X
+// (rows x cols, ldx), scale[bi * ceil(cols/128) + bj] = block amax / 448 (1
+// for an all-zero block) and Q[i][j] = QT[j][i] = e4m3(X_ij / scale of its
+// block) (round to nearest, saturating); Q ld ldq, QT ld ldqt (bytes).
+bcur_status_t quant_blocks_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                                uint8_t* Q, int64_t ldq, uint8_t* QT, int64_t ldqt, float* scale,
+                                cudaStream_t s);
 // Byte matrix transpose: T[j][i] = Q[i][j] (Q rows x cols, ldq; T ld ldt).
 bcur_status_t transpose_u8(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t cols, uint8_t* T,
                            int64_t ldt, cudaStream_t s);

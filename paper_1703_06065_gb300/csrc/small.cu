@@ -947,6 +947,97 @@ bcur_status_t quant_rows_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t
   return BCUR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 -> FP8 e4m3, one scale per 128 x 128 block, written twice (row-major
+// and transposed, so that both products with A read K-major operands).  One
+// CTA per block: the block's amax (fixed-order reduction), scale = amax / 448
+// (1 for an all-zero block), then the quantised bytes through a shared tile.
+// Interior blocks with 16-byte aligned rows move four elements per access.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) quant_blocks_e4m3_kernel(const float* X, int64_t ldx,
+                                                                int64_t rows, int64_t cols,
+                                                                uint8_t* Q, int64_t ldq,
+                                                                uint8_t* QT, int64_t ldqt,
+                                                                float* scale, int64_t lds,
+                                                                int vec) {
+  __shared__ __align__(16) uint8_t tile[128][132];
+  __shared__ float red[8];
+  const int64_t r0 = (int64_t)blockIdx.y * 128, c0 = (int64_t)blockIdx.x * 128;
+  const int tid = threadIdx.x;
+  const bool whole = vec && r0 + 128 <= rows && c0 + 128 <= cols;
+  float mx = 0.f;
+  if (whole) {
+    for (int e = tid; e < 128 * 32; e += 256) {
+      const int i = e >> 5, j4 = (e & 31) * 4;
+      const float4 v = *reinterpret_cast<const float4*>(X + (r0 + i) * ldx + c0 + j4);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+  } else {
+    for (int e = tid; e < 128 * 128; e += 256) {
+      const int i = e >> 7, j = e & 127;
+      if (r0 + i < rows && c0 + j < cols) mx = fmaxf(mx, fabsf(X[(r0 + i) * ldx + c0 + j]));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  float amax = 0.f;
+  for (int i = 0; i < 8; ++i) amax = fmaxf(amax, red[i]);
+  const float sc = amax > 0.f ? amax / 448.f : 1.f;
+  const float inv = 1.f / sc;
+  if (tid == 0) scale[(int64_t)blockIdx.y * lds + blockIdx.x] = sc;
+  auto q8 = [&](float x) {
+    return (uint8_t)__nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3);
+  };
+  if (whole) {
+    for (int e = tid; e < 128 * 32; e += 256) {
+      const int i = e >> 5, j4 = (e & 31) * 4;
+      const float4 v = *reinterpret_cast<const float4*>(X + (r0 + i) * ldx + c0 + j4);
+      const uint8_t b0 = q8(v.x), b1 = q8(v.y), b2 = q8(v.z), b3 = q8(v.w);
+      tile[i][j4] = b0; tile[i][j4 + 1] = b1; tile[i][j4 + 2] = b2; tile[i][j4 + 3] = b3;
+      *reinterpret_cast<uint32_t*>(Q + (r0 + i) * ldq + c0 + j4) =
+          (uint32_t)b0 | ((uint32_t)b1 << 8) | ((uint32_t)b2 << 16) | ((uint32_t)b3 << 24);
+    }
+  } else {
+    for (int e = tid; e < 128 * 128; e += 256) {
+      const int i = e >> 7, j = e & 127;
+      const bool in = r0 + i < rows && c0 + j < cols;
+      const uint8_t b = in ? q8(X[(r0 + i) * ldx + c0 + j]) : (uint8_t)0;
+      tile[i][j] = b;
+      if (in) Q[(r0 + i) * ldq + c0 + j] = b;
+    }
+  }
+  __syncthreads();
+  if (whole) {
+    for (int e = tid; e < 128 * 32; e += 256) {
+      const int j = e >> 5, i4 = (e & 31) * 4;
+      *reinterpret_cast<uint32_t*>(QT + (c0 + j) * ldqt + r0 + i4) =
+          (uint32_t)tile[i4][j] | ((uint32_t)tile[i4 + 1][j] << 8) |
+          ((uint32_t)tile[i4 + 2][j] << 16) | ((uint32_t)tile[i4 + 3][j] << 24);
+    }
+  } else {
+    for (int e = tid; e < 128 * 128; e += 256) {
+      const int j = e >> 7, i = e & 127;
+      if (c0 + j < cols && r0 + i < rows) QT[(c0 + j) * ldqt + r0 + i] = tile[i][j];
+    }
+  }
+}
+
+bcur_status_t quant_blocks_e4m3(const float* X, int64_t ldx, int64_t rows, int64_t cols,
+                                uint8_t* Q, int64_t ldq, uint8_t* QT, int64_t ldqt, float* scale,
+                                cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return BCUR_OK;
+  const int64_t gr = ceil_div(rows, 128), gc = ceil_div(cols, 128);
+  if (gr > 65535 || gc > INT32_MAX) return BCUR_EINVAL;
+  const int vec = (ldx % 4 == 0) && (ldq % 4 == 0) && (ldqt % 4 == 0) &&
+                  ((uintptr_t)X % 16 == 0) && ((uintptr_t)Q % 4 == 0) && ((uintptr_t)QT % 4 == 0);
+  quant_blocks_e4m3_kernel<<<dim3((unsigned)gc, (unsigned)gr), 256, 0, s>>>(
+      X, ldx, rows, cols, Q, ldq, QT, ldqt, scale, gc, vec);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
 __global__ void transpose_u8_kernel(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t cols,
                                     uint8_t* T, int64_t ldt) {
   __shared__ uint8_t tile[64][65];

@@ -76,7 +76,11 @@ def _plan(lib, **kw):
     (dict(sp=6, fp=1), 1),                   # the adaptive split form is a fit precision
     (dict(sp=3, fp=6), 0),                   # BF16 sketch, adaptive split-BF16 fit
     (dict(dtype=0, sp=0, fp=6), 1),          # FP64 data with a BF16 fit
-    (dict(sp=3, fp=7), 1),
+    (dict(sp=7, fp=4), 0),                   # FP8 sketch with 128 x 128 block scales
+    (dict(sp=7, fp=6), 0),
+    (dict(dtype=0, sp=7, fp=0), 1),          # block-scaled FP8 needs FP32 storage
+    (dict(sp=3, fp=7), 1),                   # FP8 is a sketch precision only
+    (dict(sp=8, fp=4), 1),
     (dict(lda=100), 1),                      # lda < n
     (dict(k=100, p=40), 1),                  # l > 128
     (dict(k=0), 1),
