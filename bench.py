@@ -694,7 +694,8 @@ def main_batched(args):
     urs = [torch.from_numpy(p.u_row()).to(dev) for p in probs]
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    batch = pkg.Batch(items, q=2)
+    bfp = args.fit_prec or "bf16x3a"
+    batch = pkg.Batch(items, q=2, fit_prec=bfp)
     graph = not args.no_graph
 
     def barrier():
@@ -734,6 +735,7 @@ def main_batched(args):
     B = len(probs)
     value = world * B * 1000.0 / ms
     launches = batch.launches_per_run
+    terms1 = sum(1 for t in batch.fit_terms() if t == 1)  # items that kept one BF16 term
 
     # -- end to end: every matrix from pinned host memory, results read back ---
     e2e = None
@@ -848,10 +850,11 @@ def main_batched(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/bf16x3", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": f"bf16/{bfp}", "data": "synthetic",
             "config": {"workload": "batched_biometric" if B == BATCH_COUNT
                        else f"batched_biometric[:{B}]", "matrices": B,
-                       "sum_mn": mn, "storage": "f32", "sketch_prec": "bf16", "fit_prec": "bf16x3",
+                       "sum_mn": mn, "storage": "f32", "sketch_prec": "bf16", "fit_prec": bfp,
+                       "fit_terms_1": terms1,
                        "q": 2, "cuda_graph": graph,
                        "l2": f"inputs larger than L2 (A total {4 * mn / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},

@@ -530,6 +530,23 @@ bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int
  * workspace).  Synchronous.  Errors: BCUR_EINVAL, BCUR_ENOMEM, BCUR_ECUDA. */
 bcur_status_t bcur_batch_set_workspace(bcur_batch_t plan, void* workspace, size_t bytes);
 
+/* Fit precision of every item of the batch: BCUR_BF16X3 (the default; every
+ * product of the fit as a split BF16 pair) or BCUR_BF16X3A (the adaptive
+ * form of bcur_plan's fit_prec: each item's core products W, M and M2 and its
+ * residual first with one BF16 term, redone with three for the items whose
+ * one-term residual is too coarse for the error it reports, e < 0.031; the
+ * two products that give U take the item's term count).  An item's choice
+ * depends only on its own data, so its results stay the same alone or in any
+ * batch.  Call before bcur_batch_set_workspace.  Errors: BCUR_EINVAL (NULL
+ * plan or another precision), BCUR_ESTATE (the workspace is already bound). */
+bcur_status_t bcur_batch_set_fit(bcur_batch_t plan, int32_t fit_prec);
+
+/* terms (host, count entries): the BF16 terms each item's core products took
+ * in the last run, 1 or 3 (3 for every item of a BCUR_BF16X3 plan).
+ * Synchronises the plan's stream.  Errors: BCUR_EINVAL, BCUR_ESTATE (no
+ * workspace). */
+bcur_status_t bcur_batch_fit_terms(bcur_batch_t plan, int32_t* terms);
+
 /* Run the whole method for every item; io: host array of `count` entries
  * (read before the call returns).  Asynchronous on the plan's stream.  With
  * use_graph != 0 the launch sequence is captured into a CUDA graph on the

@@ -103,6 +103,8 @@ class Plan:
         _lib.check(L.bcur_plan(byref(d), _stream(), byref(h), byref(ws)), "bcur_plan")
         self._h = h
         self.workspace_bytes = ws.value
+        self.fit_prec = fit_prec
+        _lib.check(L.bcur_batch_set_fit(h, PREC[fit_prec]), "bcur_batch_set_fit")
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         if workspace is not None:   # caller-owned device memory (e.g. a serving arena)
@@ -264,11 +266,13 @@ class Batch:
 
     ``items``: sequence of dicts with keys m, n, k, p, block, g_col, g_row (and
     optionally lda).  Every stage runs as one launch over the whole batch
-    (BF16 sketch, split-BF16 fit, FP32 storage).  The plan and its workspace
-    are built once; :meth:`run` takes per-item device tensors.
+    (BF16 sketch, split-BF16 fit, FP32 storage; ``fit_prec="bf16x3a"`` for
+    the adaptive fit, whose core products start with one BF16 term per item).
+    The plan and its workspace are built once; :meth:`run` takes per-item
+    device tensors.
     """
 
-    def __init__(self, items, q: int = 2, device=None, workspace=None):
+    def __init__(self, items, q: int = 2, device=None, workspace=None, fit_prec: str = "bf16x3"):
         torch = _torch()
         L = _lib.load()
         self._L = L
@@ -288,6 +292,8 @@ class Batch:
         _lib.check(L.bcur_batch_plan(arr, B, q, _stream(), byref(h), byref(ws)), "bcur_batch_plan")
         self._h = h
         self.workspace_bytes = ws.value
+        self.fit_prec = fit_prec
+        _lib.check(L.bcur_batch_set_fit(h, PREC[fit_prec]), "bcur_batch_set_fit")
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         if workspace is not None:
@@ -376,6 +382,14 @@ class Batch:
         _lib.check(self._L.bcur_batch_dims(self._h, 0, byref(c), byref(r), byref(nl)),
                    "bcur_batch_dims")
         return nl.value
+
+    def fit_terms(self):
+        """The BF16 terms each item's core products took in the last run (1 or
+        3; 3 for every item of a "bf16x3" batch)."""
+        out = (ctypes.c_int32 * self.B)()
+        _lib.check(self._L.bcur_batch_fit_terms(self._h, ctypes.cast(out, c_void_p)),
+                   "bcur_batch_fit_terms")
+        return [int(v) for v in out]
 
     def sync_status(self):
         _lib.check(self._L.bcur_batch_sync_status(self._h), "bcur_batch_sync_status")

@@ -32,7 +32,8 @@ EXPORTS = [
     "bcur_batch_profile_entry", "bcur_batch_set_stream", "bcur_host_staging_bytes",
     "bcur_decompose_host", "bcur_set_wait_budget_ns", "bcur_autotune_measured",
     "bcur_rank_k_error", "bcur_boost_select", "bcur_cholesky_inverse", "bcur_svd_small",
-    "bcur_gather_blocks", "bcur_incoherence", "bcur_fit_terms",
+    "bcur_gather_blocks", "bcur_incoherence", "bcur_fit_terms", "bcur_batch_set_fit",
+    "bcur_batch_fit_terms",
 ]
 
 
@@ -102,6 +103,10 @@ def load():
     L.bcur_error.restype = st
     L.bcur_fit_terms.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_double)]
     L.bcur_fit_terms.restype = st
+    L.bcur_batch_set_fit.argtypes = [c_void_p, c_int32]
+    L.bcur_batch_set_fit.restype = st
+    L.bcur_batch_fit_terms.argtypes = [c_void_p, c_void_p]
+    L.bcur_batch_fit_terms.restype = st
     L.bcur_rank.argtypes = [c_void_p] + [POINTER(c_int64)] * 4
     L.bcur_rank.restype = st
     L.bcur_sync_status.argtypes = [c_void_p]

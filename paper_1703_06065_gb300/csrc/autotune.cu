@@ -180,7 +180,8 @@ bcur_status_t tune_widths(const char* stage, const std::vector<GemmDesc>& ds, in
       std::vector<GemmDesc> rep(copies, ds[i]);
       for (auto& r : rep) {
         r.status = sc.status;
-        r.run_flag = nullptr;  // a conditional GEMM is timed as if it runs
+        r.run_flag = nullptr;    // a conditional GEMM is timed as if it runs,
+        r.parts_flag = nullptr;  // with all the terms its class names
       }
       std::vector<std::pair<int, float>> timed;
       for (int bn : cands) {

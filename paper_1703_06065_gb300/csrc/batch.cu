@@ -918,5 +918,17 @@ bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, int re
   return BCUR_OK;
 }
 
+__global__ void fit_terms_kernel(const Item* items, int B, int* terms) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x)
+    terms[b] = *items[b].refine ? 3 : 1;
+}
+
+bcur_status_t fit_terms(const Item* items, int B, int* terms, cudaStream_t s) {
+  if (B < 1) return BCUR_OK;
+  fit_terms_kernel<<<(B + 255) / 256, 256, 0, s>>>(items, B, terms);
+  BCUR_LAUNCH_CHECK();
+  return BCUR_OK;
+}
+
 }  // namespace batch
 }  // namespace bcur

@@ -96,6 +96,8 @@ bcur_status_t wide_chol(const Item* items, const int* entries, int count, int wm
                         cudaStream_t s);
 bcur_status_t copy_u(const Item* items, const bcur_batch_io_t* io, Work urows, int total,
                      cudaStream_t s);
+// terms[b] = 3 when item b's refinement flag is set, else 1 (device array).
+bcur_status_t fit_terms(const Item* items, int B, int* terms, cudaStream_t s);
 bcur_status_t finish(const Item* items, const bcur_batch_io_t* io, int B, int refine,
                      cudaStream_t s);
 

@@ -59,6 +59,12 @@ struct bcur_batch_s {
     int n = 0;
   };
   MGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[6], gP, gRes, gP3, gRes3;
+  // adaptive split fit (BCUR_BF16X3A): one-term W, M and the products to M2;
+  // the three-term groups above then run only for items whose one-term
+  // residual asks for refinement
+  int fit_prec = BCUR_BF16X3;
+  MGroup gW1, gM1, gU1[4];
+  int* d_terms = nullptr;  // per item: terms of its core products (bcur_batch_fit_terms)
   // graph mode: the sequence is captured on a stream of the plan's own and
   // joined to the caller's stream through events
   cudaStream_t gstream = nullptr;
@@ -132,6 +138,9 @@ size_t layout(bcur_batch_t P) {
   grp(P->gW, B); grp(P->gM, B);
   for (int i = 0; i < 6; ++i) grp(P->gU[i], B);
   grp(P->gP, B); grp(P->gRes, B); grp(P->gP3, B); grp(P->gRes3, B);
+  grp(P->gW1, B); grp(P->gM1, B);
+  for (int i = 0; i < 4; ++i) grp(P->gU1[i], B);
+  P->d_terms = bp.take<int>(B);
   for (int b = 0; b < B; ++b) {
     Item& I = P->it[b];
     I.lp = P->lp;
@@ -245,7 +254,8 @@ bcur_status_t run_group(const bcur_batch_s::MGroup& g, cudaStream_t s) {
 
 bcur_status_t build_groups(bcur_batch_t P) {
   const int B = P->B;
-  std::vector<GemmDesc> y, z, y2, w, mm, u[6], pp, res, pp3, res3;
+  std::vector<GemmDesc> y, z, y2, w, mm, u[6], pp, res, pp3, res3, w1, mm1, u1[4];
+  const bool adapt = P->fit_prec == BCUR_BF16X3A;
   std::vector<GemmDesc> gram[2], app[2];
   const int64_t LP = P->lp;
   for (int b = 0; b < B; ++b) {
@@ -310,6 +320,25 @@ bcur_status_t build_groups(bcur_batch_t P) {
     d = g16(cp, rp, cp, I.LCih[0], I.LCil[0], cp, 1, I.U2h, I.U2l, rp, 0, rp, 3);  // U
     d.D = I.Uf; d.triA = 2;
     u[5].push_back(d);
+    if (adapt) {
+      // one-term copies of W1, M1 and the products to M2 (same outputs); the
+      // three-term ones run only where the flag is set, and the last two
+      // products (U) take the flag's term count
+      auto one = [](GemmDesc g) {
+        g.parts = 1;
+        g.A_lo = nullptr;
+        g.B_lo = nullptr;
+        return g;
+      };
+      w1.push_back(one(w.back()));
+      mm1.push_back(one(mm.back()));
+      for (int i = 0; i < 4; ++i) u1[i].push_back(one(u[i].back()));
+      w.back().run_flag = I.refine;
+      mm.back().run_flag = I.refine;
+      for (int i = 0; i < 4; ++i) u[i].back().run_flag = I.refine;
+      u[4].back().parts_flag = I.refine;
+      u[5].back().parts_flag = I.refine;
+    }
     // P = Q1_C^T M2 (m x r), then sum (A - P Q1_R)^2: one BF16 term, and the
     // BF16-pair version for the items the first result flags
     d = g16(m, rp, cp, I.XCh[1], nullptr, ldm, 1, I.Mh, nullptr, rp, 0, rp, 1);
@@ -363,6 +392,11 @@ bcur_status_t build_groups(bcur_batch_t P) {
     if (i == 0) jobs.push_back({&P->gApply[i], &app[i], 0, "apply0", all, {}});  // no second apply
   }
   for (int i = 0; i < 6; ++i) jobs.push_back({&P->gU[i], &u[i], 0, u_names[i], all, {}});
+  if (adapt) {
+    jobs.push_back({&P->gW1, &w1, 0, "w", all, {}});
+    jobs.push_back({&P->gM1, &mm1, 0, "m", all, {}});
+    for (int i = 0; i < 4; ++i) jobs.push_back({&P->gU1[i], &u1[i], 0, u_names[i], all, {}});
+  }
   // Measuring launches write their tables into the BF16 lo copy of the
   // largest A (not yet filled: the workspace holds no data before a run).
   {
@@ -437,6 +471,50 @@ bcur_status_t orth(bcur_batch_t P, int s0, int s1, bool want_lb, cudaStream_t s)
   return BCUR_OK;
 }
 
+// The fit and residual of the adaptive split fit: W1, M1 and M2 and the
+// residual with one BF16 term; the finish sets each item's refinement flag
+// (residual_needs_refine); the three-term launches redo those products and
+// the residual for the flagged items only; the two products that give U take
+// the flag's term count.
+bcur_status_t enqueue_adaptive_fit(bcur_batch_t P, cudaStream_t s) {
+  const int B = P->B;
+  BCUR_TRY(run_group(P->gW1, s));
+  BCUR_TRY(mark(P, s, "w_gemm"));
+  BCUR_TRY(run_group(P->gM1, s));
+  BCUR_TRY(mark(P, s, "m_gemm"));
+  for (int i = 0; i < 4; ++i) {
+    BCUR_TRY(run_group(P->gU1[i], s));
+    BCUR_TRY(mark(P, s, "u_gemm"));
+  }
+  BCUR_TRY(run_group(P->gP, s));
+  BCUR_TRY(mark(P, s, "p_gemm"));
+  BCUR_TRY(run_group(P->gRes, s));
+  BCUR_TRY(mark(P, s, "residual"));
+  BCUR_TRY(finish(P->d_items, P->d_io, B, 0, s));
+  BCUR_TRY(mark(P, s, "finish"));
+  BCUR_TRY(run_group(P->gW, s));
+  BCUR_TRY(mark(P, s, "w_gemm"));
+  BCUR_TRY(run_group(P->gM, s));
+  BCUR_TRY(mark(P, s, "m_gemm"));
+  for (int i = 0; i < 4; ++i) {
+    BCUR_TRY(run_group(P->gU[i], s));
+    BCUR_TRY(mark(P, s, "u_gemm"));
+  }
+  BCUR_TRY(run_group(P->gP3, s));
+  BCUR_TRY(mark(P, s, "p_gemm"));
+  BCUR_TRY(run_group(P->gRes3, s));
+  BCUR_TRY(mark(P, s, "residual"));
+  BCUR_TRY(finish(P->d_items, P->d_io, B, 1, s));
+  BCUR_TRY(mark(P, s, "finish"));
+  for (int i = 4; i < 6; ++i) {
+    BCUR_TRY(run_group(P->gU[i], s));
+    BCUR_TRY(mark(P, s, "u_gemm"));
+  }
+  BCUR_TRY(copy_u(P->d_items, P->d_io, P->urows.w(), P->urows.total, s));
+  BCUR_TRY(mark(P, s, "copy_u"));
+  return BCUR_OK;
+}
+
 // The launch sequence of one run (the io table is already being copied).
 bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   const int B = P->B;
@@ -487,6 +565,7 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
       BCUR_TRY(mark(P, s, "qr_apply"));
     }
   }
+  if (P->fit_prec == BCUR_BF16X3A) return enqueue_adaptive_fit(P, s);
   // U = C^+ A R^+
   BCUR_TRY(run_group(P->gW, s));
   BCUR_TRY(mark(P, s, "w_gemm"));
@@ -696,6 +775,28 @@ bcur_status_t bcur_batch_dims(bcur_batch_t P, int32_t i, int64_t* cmax, int64_t*
   if (cmax) *cmax = P->it[i].cmax;
   if (rmax) *rmax = P->it[i].rmax;
   if (launches_per_run) *launches_per_run = P->launches;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_batch_set_fit(bcur_batch_t P, int32_t fit_prec) {
+  if (!P) return BCUR_EINVAL;
+  if (fit_prec != BCUR_BF16X3 && fit_prec != BCUR_BF16X3A) return BCUR_EINVAL;
+  if (P->bound) return BCUR_ESTATE;
+  P->fit_prec = fit_prec;
+  return BCUR_OK;
+}
+
+bcur_status_t bcur_batch_fit_terms(bcur_batch_t P, int32_t* terms) {
+  if (!P || !terms) return BCUR_EINVAL;
+  if (!P->bound) return BCUR_ESTATE;
+  if (P->fit_prec != BCUR_BF16X3A) {
+    for (int b = 0; b < P->B; ++b) terms[b] = 3;
+    return BCUR_OK;
+  }
+  BCUR_TRY(fit_terms(P->d_items, P->B, P->d_terms, P->stream));
+  BCUR_CUDA_TRY(cudaMemcpyAsync(terms, P->d_terms, (size_t)P->B * sizeof(int),
+                                cudaMemcpyDeviceToHost, P->stream));
+  BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
   return BCUR_OK;
 }
 

@@ -206,6 +206,8 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.bcur_svd_small(p, 64, 0, p, p, p, p, 64, None, None) == 2  # work too small
     off = p
     assert lib.bcur_gather_blocks(p, 10, 8, 16, 0, 1, off, 2, p, 1, 8, p, 8, p, None) == 1  # lda < n
+    assert lib.bcur_batch_set_fit(None, 4) == 1
+    assert lib.bcur_batch_fit_terms(None, p) == 1
     assert lib.bcur_gather_blocks(p, 16, 8, 16, 0, 2, off, 2, p, 1, 8, p, 8, p, None) == 1  # axis
     assert lib.bcur_gather_blocks(p, 16, 8, 16, 0, 1, off, 2, p, 1, 8, p, 4, p, None) == 1  # ldo < m
     # boosting's choice

@@ -285,3 +285,59 @@ def test_worst_conditioned_members_of_the_batch_meet_the_gate():
         for side, u, g in (("col", p.u_col(), p.g_col), ("row", p.u_row(), p.g_row)):
             n_ok = _tie_free_draws(ref[f"{side}_scores"], o[f"{side}_scores"][i].cpu().numpy(), u, g)
             assert o[f"{side}_idx"][i].cpu().tolist()[:n_ok] == list(ref[f"{side}_idx"][:n_ok])
+
+
+def test_adaptive_fit_batch():
+    """fit_prec "bf16x3a": each item's core products and residual start with
+    one BF16 term and are redone with three only where the item's one-term
+    residual is too coarse (e < 0.031).  The biometric members (e near 0.05
+    to 0.1) keep one term and meet the 1e-3 error gate, with CUR within what
+    the least-squares bound of one term implies; an exactly rank-6 member in
+    the same batch takes three terms and then equals, bit for bit, the same
+    item decomposed by a split-BF16 batch; and every item's results are the
+    same alone as in the batch."""
+    import paper_1703_06065_gb300 as pkg
+    from _gpu_common import UNIT, u_bound
+
+    device()
+    probs = _problems()[:4] + [
+        bi.Problem("rank6_exact", 512, 768, k=6, p=10, q=2, col_off=bi.uniform_blocks(768, 64),
+                   row_off=bi.uniform_blocks(512, 64), g_col=3, g_row=3, seed=14, storage="f32",
+                   recipe=dict(kind="small_lowrank", rank=6, noise=0.0))]
+    ins = _inputs(probs)
+    ba = pkg.Batch([_item(p) for p in probs], q=2, fit_prec="bf16x3a")
+    oa = ba.run(*ins)
+    ba.sync_status()
+    ra = [_host(oa, i) for i in range(len(probs))]
+    terms = ba.fit_terms()
+    assert terms[-1] == 3, terms
+    for t, r in zip(terms, ra):   # e > 0.035: the one-term residual cannot ask for pairs
+        if r["err"][1] > 0.035:
+            assert t == 1, (terms, [x["err"][1] for x in ra])
+    for p, r in zip(probs, ra):
+        A = p.matrix().astype(np.float64)
+        ref = orc.block_cur(A, p.col_off, p.row_off, p.k, p.q, p.g_col, p.g_row, p.omega(),
+                            p.u_col(), p.u_row())
+        assert abs(r["err"][1] - ref["rel"]) <= 1e-3, (p.name, r["err"][1], ref["rel"])
+        C = orc.gather_columns(A, p.col_off, list(r["col_idx"]))
+        R = orc.gather_rows(A, p.row_off, list(r["row_idx"]))
+        U = orc.fit_u(A, C, R)
+        e_o = orc.residual(A, C, U, R)[1]
+        c, rr = C.shape[1], R.shape[0]
+        Ug = r["U"][:c, :rr].astype(np.float64)
+        ub = u_bound(C, R, e_o, UNIT["bf16"])
+        bound = np.linalg.norm(C, 2) * np.linalg.norm(R, 2) * ub * np.linalg.norm(U)
+        assert np.linalg.norm(C @ Ug @ R - C @ U @ R) <= bound, p.name
+    b3 = pkg.Batch([_item(probs[-1])], q=2)
+    o3 = b3.run(*[x[-1:] for x in ins])
+    b3.sync_status()
+    r3 = _host(o3, 0)
+    for key in ("U", "err", "col_idx", "row_idx"):
+        np.testing.assert_array_equal(ra[-1][key], r3[key], err_msg=key)
+    for i in (0, 2):
+        b1 = pkg.Batch([_item(probs[i])], q=2, fit_prec="bf16x3a")
+        o1 = b1.run(*[x[i:i + 1] for x in ins])
+        b1.sync_status()
+        r1 = _host(o1, 0)
+        for key in ("U", "err", "col_scores", "col_idx"):
+            np.testing.assert_array_equal(ra[i][key], r1[key], err_msg=key)
