@@ -885,8 +885,10 @@ def main_serving(args):
     dev = torch.device("cuda", local)
     pkg.load()
     reqs = bi.serving_requests(args.rate, args.duration, seed=4 + 1000 * rank)
+    sfp = args.fit_prec or "bf16x3a"
     srv = serve.Server(hbm_budget=args.hbm_budget, lanes=3, max_batch=128, heavy_lanes=2,
-                       max_heavy_batch=16, draw=bi.generators.request_inputs_device)
+                       max_heavy_batch=16, draw=bi.generators.request_inputs_device,
+                       fit_prec=sfp)
     # warm-up: the kernels, the allocator and the plan builders on the first requests
     warm = bi.serving_requests(args.rate, 0.05, seed=99)
     srv.run(warm, realtime=False)
@@ -939,8 +941,9 @@ def main_serving(args):
         line = {
             "metric": METRIC, "value": st["decomps_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/bf16x3", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": f"bf16/{sfp}", "data": "synthetic",
             "config": {"workload": "serving", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "fit_prec": sfp,
                        "requests": len(reqs), "heavy": int(sum(r.heavy for r in reqs)),
                        "lanes": "3 light + 2 heavy streams, batched groups (up to 128 "
                                 "light, 16 heavy)",

@@ -103,8 +103,6 @@ class Plan:
         _lib.check(L.bcur_plan(byref(d), _stream(), byref(h), byref(ws)), "bcur_plan")
         self._h = h
         self.workspace_bytes = ws.value
-        self.fit_prec = fit_prec
-        _lib.check(L.bcur_batch_set_fit(h, PREC[fit_prec]), "bcur_batch_set_fit")
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         if workspace is not None:   # caller-owned device memory (e.g. a serving arena)

@@ -42,7 +42,12 @@ struct Layout {
 
 using namespace bcur;
 
+// Handles are opaque to callers: a tag as the first member lets every entry
+// point refuse a handle of the other kind (a batch plan) or a stale one.
+constexpr uint32_t kPlanTag = 0x50435542u;  // "BUCP"
+
 struct bcur_plan_s {
+  uint32_t tag = kPlanTag;
   bcur_desc_t d;
   std::vector<int64_t> col_off, row_off;
   cudaStream_t stream = nullptr;
@@ -86,6 +91,8 @@ struct bcur_plan_s {
 };
 
 namespace {
+
+bool plan_ok(const bcur_plan_s* P) { return P && P->tag == kPlanTag; }
 
 bool is_tc_prec(int p) { return p == BCUR_TF32 || p == BCUR_BF16; }
 bool is_bf16_prec(int p) { return p == BCUR_BF16 || p == BCUR_BF16X3 || p == BCUR_BF16X3A; }
@@ -1239,7 +1246,7 @@ bcur_status_t bcur_plan(const bcur_desc_t* d, void* stream, bcur_plan_t* out,
 }
 
 bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
-  if (!P || !ws || ((uintptr_t)ws & 255)) return BCUR_EINVAL;
+  if (!plan_ok(P) || !ws || ((uintptr_t)ws & 255)) return BCUR_EINVAL;
   if (bytes < P->need) return BCUR_ENOMEM;
   if (!P->stream2) {
     BCUR_CUDA_TRY(cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking));
@@ -1269,7 +1276,7 @@ bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
 
 bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, double* cs,
                           double* rs) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws) return BCUR_ESTATE;
   if (!A || !omega || !cs || !rs) return BCUR_EINVAL;
   bcur_status_t st;
@@ -1286,7 +1293,7 @@ bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, doubl
 }
 
 bcur_status_t bcur_factors(bcur_plan_t P, void* Vt, void* Ut, double* sigma) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws || !P->have_scores) return BCUR_ESTATE;
   cudaStream_t s = P->stream;
   if (P->d.a_dtype == BCUR_F64) {
@@ -1304,7 +1311,7 @@ bcur_status_t bcur_factors(bcur_plan_t P, void* Vt, void* Ut, double* sigma) {
 
 bcur_status_t bcur_sample(bcur_plan_t P, const double* cs, const double* rs, const double* uc,
                           const double* ur, int32_t* ci, int32_t* ri, double* cp, double* rp) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!cs || !rs || !uc || !ur || !ci || !ri) return BCUR_EINVAL;
   BCUR_TRY(sample_blocks(cs, P->d.G_col, uc, P->d.g_col, P->d.replacement, ci, cp, P->stream));
   BCUR_TRY(sample_blocks(rs, P->d.G_row, ur, P->d.g_row, P->d.replacement, ri, rp, P->stream));
@@ -1313,7 +1320,7 @@ bcur_status_t bcur_sample(bcur_plan_t P, const double* cs, const double* rs, con
 
 bcur_status_t bcur_fit(bcur_plan_t P, const void* A, const int32_t* ci, const int32_t* ri, void* U,
                        void* C, void* R) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws) return BCUR_ESTATE;
   if (!A || !ci || !ri) return BCUR_EINVAL;
   bcur_status_t st;
@@ -1330,7 +1337,7 @@ bcur_status_t bcur_fit(bcur_plan_t P, const void* A, const int32_t* ci, const in
 }
 
 bcur_status_t bcur_fit_terms(bcur_plan_t P, int32_t* terms, double* est) {
-  if (!P || !terms) return BCUR_EINVAL;
+  if (!plan_ok(P) || !terms) return BCUR_EINVAL;
   if (!P->ws || !P->have_fit) return BCUR_ESTATE;
   if (est) *est = -1.0;
   if (P->d.a_dtype == BCUR_F64 || !is_bf16_prec(P->d.fit_prec)) {
@@ -1354,7 +1361,7 @@ bcur_status_t bcur_fit_terms(bcur_plan_t P, int32_t* terms, double* est) {
 }
 
 bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws || !P->have_fit) return BCUR_ESTATE;
   if (!A || !out) return BCUR_EINVAL;
   bcur_status_t st;
@@ -1370,7 +1377,7 @@ bcur_status_t bcur_error(bcur_plan_t P, const void* A, double* out) {
 }
 
 bcur_status_t bcur_rank_k_error(bcur_plan_t P, const void* A, double* out) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws || !P->have_scores || !P->have_error) return BCUR_ESTATE;
   if (!A || !out) return BCUR_EINVAL;
   return P->d.a_dtype == BCUR_F64 ? run_rank_k<double>(P, (const double*)A, out)
@@ -1454,7 +1461,7 @@ bcur_status_t bcur_boost_select(int32_t t, const double* err, int64_t err_stride
 
 bcur_status_t bcur_truncate(bcur_plan_t P, const void* A, int32_t kt, const void* omega,
                             void* Uk, double* out) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws || !P->have_fit) return BCUR_ESTATE;
   if (!A || !omega || !out || kt < 1 || kt > P->k) return BCUR_EINVAL;
   if (P->c_pad > P->ldm || P->r_pad > P->ldn || P->l > std::min(P->c_max, P->r_max))
@@ -1489,13 +1496,13 @@ static HostStage host_stage_layout(const bcur_plan_s* P) {
   return h;
 }
 
-size_t bcur_host_staging_bytes(bcur_plan_t P) { return P ? host_stage_layout(P).total : 0; }
+size_t bcur_host_staging_bytes(bcur_plan_t P) { return plan_ok(P) ? host_stage_layout(P).total : 0; }
 
 bcur_status_t bcur_decompose_host(bcur_plan_t P, const void* A, const void* omega,
                                   const double* u_col, const double* u_row, void* staging,
                                   size_t staging_bytes, double* col_scores, double* row_scores,
                                   int32_t* col_idx, int32_t* row_idx, void* U, double* err) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws) return BCUR_ESTATE;
   if (!A || !omega || !u_col || !u_row || !staging || !err) return BCUR_EINVAL;
   if ((uintptr_t)staging & 255) return BCUR_EINVAL;
@@ -1554,7 +1561,7 @@ bcur_status_t bcur_decompose_host(bcur_plan_t P, const void* A, const void* omeg
 }
 
 bcur_status_t bcur_rank(bcur_plan_t P, int64_t* c, int64_t* r, int64_t* rank_c, int64_t* rank_r) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   if (!P->ws || !P->have_fit) return BCUR_ESTATE;
   int64_t counts[2] = {0, 0};
   int kept[8] = {0};
@@ -1571,7 +1578,7 @@ bcur_status_t bcur_rank(bcur_plan_t P, int64_t* c, int64_t* r, int64_t* rank_c, 
 }
 
 bcur_status_t bcur_sync_status(bcur_plan_t P) {
-  if (!P) return BCUR_EINVAL;
+  if (!plan_ok(P)) return BCUR_EINVAL;
   BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
   if (!P->ws) return BCUR_OK;
   int st = 0;
@@ -1586,7 +1593,7 @@ bcur_status_t bcur_sync_status(bcur_plan_t P) {
 }
 
 void bcur_destroy(bcur_plan_t P) {
-  if (!P) return;
+  if (!plan_ok(P)) return;
   if (P->stream2) {
     cudaStreamSynchronize(P->stream2);
     cudaStreamDestroy(P->stream2);
@@ -1594,6 +1601,7 @@ void bcur_destroy(bcur_plan_t P) {
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
   if (P->ev_stagger) cudaEventDestroy(P->ev_stagger);
+  P->tag = 0;
   delete P;
 }
 

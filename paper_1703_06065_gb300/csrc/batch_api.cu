@@ -26,7 +26,12 @@ struct WorkList {
 
 }  // namespace
 
+// Handles are opaque to callers: a tag as the first member lets every entry
+// point refuse a handle of the other kind (a single-matrix plan) or a stale one.
+constexpr uint32_t kBatchTag = 0x42435542u;  // "BUCB"
+
 struct bcur_batch_s {
+  uint32_t tag = kBatchTag;
   int B = 0, q = 0;
   int lp = 64;  // panel rows: 64, or 128 when some item has l > 64
   std::vector<bcur_batch_item_t> d;
@@ -81,6 +86,8 @@ struct bcur_batch_s {
 };
 
 namespace {
+
+bool batch_ok(const bcur_batch_s* P) { return P && P->tag == kBatchTag; }
 
 // Bump allocator over the workspace; with base == nullptr it only measures.
 struct Bump {
@@ -632,7 +639,7 @@ bcur_status_t bcur_batch_plan(const bcur_batch_item_t* items, int32_t count, int
 }
 
 bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
-  if (!P || !ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return BCUR_EINVAL;
+  if (!batch_ok(P) || !ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return BCUR_EINVAL;
   if (bytes < P->need) return BCUR_ENOMEM;
   if (!gemm_tc_available()) return BCUR_ENOTSUP;
   if (P->exec) { cudaGraphExecDestroy(P->exec); P->exec = nullptr; }
@@ -698,7 +705,7 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t P, void* ws, size_t bytes) {
 }
 
 bcur_status_t bcur_batch_run(bcur_batch_t P, const bcur_batch_io_t* io, int32_t use_graph) {
-  if (!P || !io) return BCUR_EINVAL;
+  if (!batch_ok(P) || !io) return BCUR_EINVAL;
   if (!P->bound) return BCUR_ESTATE;
   for (int b = 0; b < P->B; ++b) {
     const bcur_batch_io_t& e = io[b];
@@ -756,7 +763,7 @@ bcur_status_t bcur_batch_run(bcur_batch_t P, const bcur_batch_io_t* io, int32_t 
 }
 
 bcur_status_t bcur_batch_set_stream(bcur_batch_t P, void* stream) {
-  if (!P) return BCUR_EINVAL;
+  if (!batch_ok(P)) return BCUR_EINVAL;
   if (P->exec) {  // a captured graph belongs to the old stream's sequence: recapture
     cudaGraphExecDestroy(P->exec);
     P->exec = nullptr;
@@ -771,7 +778,7 @@ bcur_status_t bcur_batch_set_stream(bcur_batch_t P, void* stream) {
 
 bcur_status_t bcur_batch_dims(bcur_batch_t P, int32_t i, int64_t* cmax, int64_t* rmax,
                               int64_t* launches_per_run) {
-  if (!P || i < 0 || i >= P->B) return BCUR_EINVAL;
+  if (!batch_ok(P) || i < 0 || i >= P->B) return BCUR_EINVAL;
   if (cmax) *cmax = P->it[i].cmax;
   if (rmax) *rmax = P->it[i].rmax;
   if (launches_per_run) *launches_per_run = P->launches;
@@ -779,7 +786,7 @@ bcur_status_t bcur_batch_dims(bcur_batch_t P, int32_t i, int64_t* cmax, int64_t*
 }
 
 bcur_status_t bcur_batch_set_fit(bcur_batch_t P, int32_t fit_prec) {
-  if (!P) return BCUR_EINVAL;
+  if (!batch_ok(P)) return BCUR_EINVAL;
   if (fit_prec != BCUR_BF16X3 && fit_prec != BCUR_BF16X3A) return BCUR_EINVAL;
   if (P->bound) return BCUR_ESTATE;
   P->fit_prec = fit_prec;
@@ -787,7 +794,7 @@ bcur_status_t bcur_batch_set_fit(bcur_batch_t P, int32_t fit_prec) {
 }
 
 bcur_status_t bcur_batch_fit_terms(bcur_batch_t P, int32_t* terms) {
-  if (!P || !terms) return BCUR_EINVAL;
+  if (!batch_ok(P) || !terms) return BCUR_EINVAL;
   if (!P->bound) return BCUR_ESTATE;
   if (P->fit_prec != BCUR_BF16X3A) {
     for (int b = 0; b < P->B; ++b) terms[b] = 3;
@@ -801,7 +808,7 @@ bcur_status_t bcur_batch_fit_terms(bcur_batch_t P, int32_t* terms) {
 }
 
 bcur_status_t bcur_batch_sync_status(bcur_batch_t P) {
-  if (!P) return BCUR_EINVAL;
+  if (!batch_ok(P)) return BCUR_EINVAL;
   BCUR_CUDA_TRY(cudaStreamSynchronize(P->stream));
   if (!P->bound) return BCUR_OK;
   int st = 0;
@@ -815,15 +822,15 @@ bcur_status_t bcur_batch_sync_status(bcur_batch_t P) {
 }
 
 bcur_status_t bcur_batch_profile(bcur_batch_t P, int32_t enable) {
-  if (!P) return BCUR_EINVAL;
+  if (!batch_ok(P)) return BCUR_EINVAL;
   P->profile = enable != 0;
   return BCUR_OK;
 }
 
-int32_t bcur_batch_profile_count(bcur_batch_t P) { return P ? (P->pn > 0 ? P->pn - 1 : 0) : 0; }
+int32_t bcur_batch_profile_count(bcur_batch_t P) { return batch_ok(P) ? (P->pn > 0 ? P->pn - 1 : 0) : 0; }
 
 bcur_status_t bcur_batch_profile_entry(bcur_batch_t P, int32_t i, const char** label, double* ms) {
-  if (!P || i < 0 || i + 1 >= P->pn || !label || !ms) return BCUR_EINVAL;
+  if (!batch_ok(P) || i < 0 || i + 1 >= P->pn || !label || !ms) return BCUR_EINVAL;
   float t = 0.f;
   BCUR_CUDA_TRY(cudaEventElapsedTime(&t, P->pev[i], P->pev[i + 1]));
   *label = P->plabel[i + 1];
@@ -832,7 +839,7 @@ bcur_status_t bcur_batch_profile_entry(bcur_batch_t P, int32_t i, const char** l
 }
 
 void bcur_batch_destroy(bcur_batch_t P) {
-  if (!P) return;
+  if (!batch_ok(P)) return;
   for (cudaEvent_t e : P->pev) cudaEventDestroy(e);
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
@@ -842,6 +849,7 @@ void bcur_batch_destroy(bcur_batch_t P) {
   if (P->gstream) cudaStreamDestroy(P->gstream);
   if (P->sstream) cudaStreamDestroy(P->sstream);
   if (P->h_io) cudaFreeHost(P->h_io);
+  P->tag = 0;
   delete P;
 }
 

@@ -450,11 +450,26 @@ __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t 
   float* Bs = As + kStepKC * kStepLD;       // 32 x 68
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int K = (int)(j0 - J0);
-  const float tol = (float)(tol_rel * (double)(*maxdiag));
+  // Columns J0 .. j0-64 of L were written by the steps before the previous
+  // one, the last 64 by the previous step.  Launched as a programmatic
+  // dependent of the previous step, this kernel forms the products over the
+  // older columns while that step is still running, then waits for it
+  // (griddepcontrol.wait: the previous grid has completed and its writes are
+  // visible; a no-op for an ordinary launch) and adds the last 64 columns.
+  // The next step may start once every CTA of this one has passed the wait,
+  // so that its early products only read columns complete by then.
+  const int K0 = K >= 64 ? K - 64 : 0;
   const float* Ljj = L + j0 * w + J0;       // rows j0.., columns J0..j0
-  // D, every CTA
+  const int64_t r0 = j0 + 64 * (int64_t)blockIdx.x;
   float acc[4][4] = {};
-  step_prod64(Ljj, Ljj, w, K, acc, As, Bs);
+  float accp[4][4] = {};
+  step_prod64(Ljj, Ljj, w, K0, acc, As, Bs);
+  if (blockIdx.x != 0) step_prod64(L + r0 * w + J0, Ljj, w, K0, accp, As, Bs);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+  step_prod64(Ljj + K0, Ljj + K0, w, K - K0, acc, As, Bs);
+  const float tol = (float)(tol_rel * (double)(*maxdiag));
+  // D, every CTA
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = 4 * ty + i;
@@ -479,12 +494,7 @@ __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t 
     return;
   }
   // the panel rows of this CTA
-  const int64_t r0 = j0 + 64 * (int64_t)blockIdx.x;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  step_prod64(L + r0 * w + J0, Ljj, w, K, acc, As, Bs);
+  step_prod64(L + r0 * w + J0 + K0, Ljj + K0, w, K - K0, accp, As, Bs);
   // P^T (k-major over As and Bs, 64 x 68) and X^T (over S, no longer needed)
   float* PT = As;
   float* XT = S;
@@ -494,7 +504,7 @@ __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t 
     const float4 g = *reinterpret_cast<const float4*>(&G[(r0 + r) * w + j0 + 4 * tx]);
     const float gv[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) PT[(4 * tx + j) * kStepLD + r] = gv[j] - acc[i][j];
+    for (int j = 0; j < 4; ++j) PT[(4 * tx + j) * kStepLD + r] = gv[j] - accp[i][j];
   }
   for (int e = tid; e < 64 * 64; e += 256) {
     const int c = e >> 6, t = e & 63;
@@ -534,8 +544,21 @@ bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_
     attr_set = true;
   }
   const unsigned blocks = (unsigned)((w - j0) / 64);
-  chol_step_kernel<<<blocks, 256, chol_step_smem(), s>>>(G, w, L, Linv, J0, j0, maxdiag, tol_rel,
-                                                        kept);
+  // A step after the first of an outer panel follows the previous step in the
+  // stream: it is launched as that step's programmatic dependent (see the
+  // kernel); the first step of a panel follows other work and waits for it.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = chol_step_smem();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = j0 > J0 ? 1 : 0;
+  BCUR_CUDA_TRY(cudaLaunchKernelEx(&cfg, chol_step_kernel, G, w, L, Linv, J0, j0, maxdiag, tol_rel,
+                                   kept));
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }

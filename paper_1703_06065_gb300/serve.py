@@ -112,14 +112,15 @@ class Server:
     the matrix A (FP32, row-major, written into ``out``, an m x n view of the
     arena), the test matrix as an l x n panel and the two vectors of
     uniforms.  The caller supplies it (the benchmark and the tests draw every
-    input on the device from the request's seed).
+    input on the device from the request's seed).  `fit_prec`: "bf16x3a" (the
+    adaptive split-BF16 fit, the default) or "bf16x3" for every request.
     """
 
     def __init__(self, hbm_budget: float = 160e9, lanes: int = 3, max_batch: int = 128,
                  heavy_lanes: int = 2, max_heavy_batch: int = 8, heavy_share: float = 0.6,
                  builders: int = 4, keep_u: bool = False,
                  keep_inputs: Callable = None, draw: Callable = None, device=None,
-                 heavy_plan: bool = False):
+                 heavy_plan: bool = False, fit_prec: str = "bf16x3a"):
         torch = _torch()
         if draw is None:
             raise ValueError("Server needs draw(problem, device, out) for the requests' inputs")
@@ -132,6 +133,7 @@ class Server:
         self.keep_inputs = keep_inputs or (lambda r: False)
         self.draw = draw
         self.heavy_plan = heavy_plan
+        self.fit_prec = fit_prec  # "bf16x3a": adaptive split-BF16 fit, "bf16x3": all split
         self.gen_stream = torch.cuda.Stream(device=self.device)
         self.light = [{"stream": torch.cuda.Stream(device=self.device), "job": None}
                       for _ in range(lanes)]
@@ -187,7 +189,7 @@ class Server:
         if ws_off is None:
             return None
         view = self.arena.view(ws_off, ws_bytes)
-        fut = self.pool.submit(Batch, items, reqs[0].r.problem.q, self.device, view)
+        fut = self.pool.submit(Batch, items, reqs[0].r.problem.q, self.device, view, self.fit_prec)
         return dict(reqs=reqs, ws=(ws_off, ws_bytes), fut=fut)
 
     def _start_light(self, lane, prep):
@@ -242,7 +244,7 @@ class Server:
             if off is None:
                 return None
             plan = Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
-                        dtype="f32", sketch_prec="bf16", fit_prec="bf16x3", device=self.device,
+                        dtype="f32", sketch_prec="bf16", fit_prec=self.fit_prec, device=self.device,
                         workspace=self.arena.view(off, need))
         dev = self.device
         outs = dict(cs=torch.empty(plan.G_col, dtype=torch.float64, device=dev),

@@ -223,3 +223,26 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.bcur_set_wait_budget_ns(0) == 1
     assert lib.bcur_set_wait_budget_ns(61_000_000_000) == 1
     assert lib.bcur_autotune_measured() == 0
+
+
+def test_handles_of_the_other_kind_are_refused(lib):
+    """Plan and batch handles are both opaque pointers; each carries a tag, so
+    a single-matrix plan passed to a batch call is refused (BCUR_EINVAL) and
+    left intact, instead of being written through as the wrong struct."""
+    d, keep = _desc()
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    assert lib.bcur_plan(ctypes.byref(d), None, ctypes.byref(h), ctypes.byref(ws)) == 0
+    terms = (ctypes.c_int32 * 4)()
+    assert lib.bcur_batch_set_fit(h, 6) == 1
+    assert lib.bcur_batch_fit_terms(h, ctypes.cast(terms, ctypes.c_void_p)) == 1
+    from paper_1703_06065_gb300 import _lib
+
+    io = (_lib.BatchIO * 1)()
+    assert lib.bcur_batch_run(h, io, 0) == 1
+    assert lib.bcur_batch_sync_status(h) == 1
+    assert lib.bcur_batch_profile_count(h) == 0
+    lib.bcur_batch_destroy(h)                     # not a batch: nothing is freed
+    dummy = ctypes.c_void_p(0x1000)
+    assert lib.bcur_scores(h, dummy, dummy, dummy, dummy) == 8   # still a plan (no workspace)
+    lib.bcur_destroy(h)
