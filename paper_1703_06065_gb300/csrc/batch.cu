@@ -46,14 +46,18 @@ __device__ double block_sum(double v, double* red) {
 
 // ---------------------------------------------------------------------------
 // A -> BF16 hi/lo pair (8 rows per CTA) and Omega^T -> BF16 panel (zero rows
-// past l), one launch.
+// past l), one launch.  mode 0: hi and lo; mode 1: hi only (the adaptive fit
+// needs lo only for the items it refines); mode 2: lo only, for the items
+// whose refinement flag is set (the Omega part is not launched).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcur_batch_io_t* io,
-                                                    Work rows8, int total8, int lp) {
+                                                    Work rows8, int total8, int lp, int mode) {
   const int x = blockIdx.x;
   if (x < total8) {
     const int b = find_item(rows8, x);
     const Item& I = items[b];
+    if (mode == 2 && *I.refine == 0) return;  // uniform over the CTA
+    const bool wh = mode != 2, wl = mode != 1;
     const int64_t r0 = (int64_t)(x - rows8.prefix[b]) * 8;
     const float* A = io[b].A;
     const bool v4 = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (I.lda % 4 == 0) &&
@@ -69,19 +73,24 @@ __global__ void __launch_bounds__(256) split_kernel(const Item* items, const bcu
           const float4 v = reinterpret_cast<const float4*>(xr)[c];
           const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y);
           const __nv_bfloat162 h23 = __floats2bfloat162_rn(v.z, v.w);
-          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-          reinterpret_cast<__nv_bfloat162*>(hr)[2 * c] = h01;
-          reinterpret_cast<__nv_bfloat162*>(hr)[2 * c + 1] = h23;
-          reinterpret_cast<__nv_bfloat162*>(lr)[2 * c] = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
-          reinterpret_cast<__nv_bfloat162*>(lr)[2 * c + 1] =
-              __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+          if (wh) {
+            reinterpret_cast<__nv_bfloat162*>(hr)[2 * c] = h01;
+            reinterpret_cast<__nv_bfloat162*>(hr)[2 * c + 1] = h23;
+          }
+          if (wl) {
+            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+            reinterpret_cast<__nv_bfloat162*>(lr)[2 * c] =
+                __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+            reinterpret_cast<__nv_bfloat162*>(lr)[2 * c + 1] =
+                __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+          }
         }
       } else {
         for (int64_t c = threadIdx.x; c < I.n; c += blockDim.x) {
           const float v = xr[c];
           const bf16 h = __float2bfloat16_rn(v);
-          hr[c] = h;
-          lr[c] = __float2bfloat16_rn(v - __bfloat162float(h));
+          if (wh) hr[c] = h;
+          if (wl) lr[c] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
       }
     }
@@ -793,8 +802,10 @@ __global__ void __launch_bounds__(256) finish_kernel(const Item* items, const bc
 }  // namespace
 
 bcur_status_t split_inputs(const Item* items, const bcur_batch_io_t* io, Work rows8, int total8,
-                           int B, int lp, cudaStream_t s) {
-  split_kernel<<<total8 + B * (lp / 8), 256, 0, s>>>(items, io, rows8, total8, lp);
+                           int B, int lp, cudaStream_t s, int mode) {
+  if (mode < 0 || mode > 2) return BCUR_EINVAL;
+  split_kernel<<<total8 + (mode == 2 ? 0 : B * (lp / 8)), 256, 0, s>>>(items, io, rows8, total8,
+                                                                        lp, mode);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }

@@ -78,7 +78,8 @@ __device__ __forceinline__ int find_item(const Work& w, int x) {
 
 // Launchers (batch.cu).  `items` / `io` are device tables of B entries.
 bcur_status_t split_inputs(const Item* items, const bcur_batch_io_t* io, Work rows8, int total8,
-                           int B, int lp, cudaStream_t s);
+                           int B, int lp, cudaStream_t s,
+                           int mode = 0);
 bcur_status_t skinny_gram(const Item* items, Work chunks, int total, int sel, int lp,
                           cudaStream_t s);
 bcur_status_t skinny_chol(const Item* items, int B, int sel, int pass, int want_lb, int lp,

@@ -499,6 +499,8 @@ bcur_status_t enqueue_adaptive_fit(bcur_batch_t P, cudaStream_t s) {
   BCUR_TRY(mark(P, s, "residual"));
   BCUR_TRY(finish(P->d_items, P->d_io, B, 0, s));
   BCUR_TRY(mark(P, s, "finish"));
+  BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->lp, s, 2));
+  BCUR_TRY(mark(P, s, "split"));
   BCUR_TRY(run_group(P->gW, s));
   BCUR_TRY(mark(P, s, "w_gemm"));
   BCUR_TRY(run_group(P->gM, s));
@@ -531,7 +533,9 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
     for (int i = 0; i < g->n; ++i)
       BCUR_TRY(gemm_tc_group_patch_x(g->g[i], P->d_io, sizeof(bcur_batch_io_t),
                                      offsetof(bcur_batch_io_t, A), s));
-  BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->lp, s));
+  // the adaptive fit splits A's lo half later, for the items it refines
+  BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->lp, s,
+                        P->fit_prec == BCUR_BF16X3A ? 1 : 0));
   BCUR_TRY(mark(P, s, "split"));
   // scores: randomized range finder with q subspace iterations (Sec. 3.1)
   BCUR_TRY(run_group(P->gY, s));
