@@ -181,7 +181,10 @@ bcur_status_t bcur_sample(bcur_plan_t plan, const double* col_scores, const doub
  * Directions of C or R^T that are numerically dependent (a pivot of the
  * Cholesky factor of their Gram matrix below the drop tolerance) are dropped:
  * U is then a least-squares minimiser restricted to the kept directions and
- * bcur_rank() reports the kept counts.  Errors: BCUR_ESTATE, BCUR_EINVAL. */
+ * bcur_rank() reports the kept counts.  With fit_prec BCUR_BF16X3A and the
+ * same A pointer as the last bcur_scores call with a BF16 sketch (contents
+ * unchanged in between), the fit reuses the BF16 copy of A that the scores
+ * left in the workspace.  Errors: BCUR_ESTATE, BCUR_EINVAL. */
 bcur_status_t bcur_fit(bcur_plan_t plan, const void* A, const int32_t* col_idx,
                        const int32_t* row_idx, void* U, void* C, void* R);
 

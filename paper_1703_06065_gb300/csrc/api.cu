@@ -85,8 +85,10 @@ struct bcur_plan_s {
   size_t tc_scratch_bytes = 0;
   int64_t n_partials = 0;
   bool have_scores = false, have_fit = false, have_error = false;
-  // adaptive split fit: the A its residual was taken of (bcur_error reuses it)
+  // adaptive split fit: the A its residual was taken of (bcur_error reuses it),
+  // and the A whose BF16 hi copy the last scores call left in the workspace
   const void* fit_A = nullptr;
+  const void* scores_A16 = nullptr;
   template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
 };
 
@@ -835,7 +837,11 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   float* Uf = P->at<float>(P->o.U2);
   int* flag = P->at<int>(P->o.fit_flag);
   double* ferr = P->at<double>(P->o.fit_err);
-  BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
+  // The adaptive form needs A's lo half only if it refines (split then, gated
+  // by the flag), and its hi half is the BF16 sketch's own copy when the
+  // scores were taken of this A.
+  if (!adapt) BCUR_TRY(split(P, A, lda, m, n, A16, ldn));
+  else if (A != P->scores_A16) BCUR_TRY(split_bf16(A, lda, m, n, A16.h, nullptr, ldn, s));
   auto tri = [&](GemmDesc d, S16 out, float* outf, int pr, const int* run, const int* terms) {
     d.Dh = out.h;
     d.Dl = out.l;
@@ -866,6 +872,7 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   if (adapt) {
     BCUR_TRY(to_m2(1, nullptr));
     BCUR_TRY(resid16(P, A, false, flag, nullptr, ferr, 2));
+    BCUR_TRY(split_bf16(A, lda, m, n, nullptr, A16.l, ldn, s, false, flag));
     BCUR_TRY(to_m2(3, flag));
     BCUR_TRY(resid16(P, A, true, flag, flag, ferr + 3, 3));
     BCUR_TRY(select_result(ferr, ferr + 3, flag, ferr + 6, s));
@@ -1271,6 +1278,7 @@ bcur_status_t bcur_set_workspace(bcur_plan_t P, void* ws, size_t bytes) {
   BCUR_CUDA_TRY(cudaStreamSynchronize(s));
   P->have_scores = P->have_fit = false;
   P->fit_A = nullptr;
+  P->scores_A16 = nullptr;
   return BCUR_OK;
 }
 
@@ -1289,6 +1297,8 @@ bcur_status_t bcur_scores(bcur_plan_t P, const void* A, const void* omega, doubl
   else
     st = run_scores<float>(P, (const float*)A, (const float*)omega, cs, rs);
   if (st == BCUR_OK) P->have_scores = true;
+  P->scores_A16 = (st == BCUR_OK && P->d.a_dtype == BCUR_F32 && is_bf16_prec(P->d.sketch_prec))
+                      ? A : nullptr;
   return st;
 }
 

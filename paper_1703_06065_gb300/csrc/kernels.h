@@ -271,7 +271,10 @@ bcur_status_t gather_cols_pair(const float* A, int64_t lda, int64_t m, const int
 // Split an FP32 matrix (rows x cols, ldx) into BF16 pairs: hi = bf16(x),
 // lo = bf16(x - hi) (round to nearest even both times); outputs have
 // leading dimension ldo; lo may be null (hi only).
+// write_hi false: only lo is written (hi may then be null); run_flag (device,
+// optional): nothing is done when it reads 0 at launch.
 bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols,
-                         __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s);
+                         __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s,
+                         bool write_hi = true, const int* run_flag = nullptr);
 
 }  // namespace bcur

@@ -1090,7 +1090,9 @@ bcur_status_t transpose_u8(const uint8_t* Q, int64_t ldq, int64_t rows, int64_t 
 // FP32 -> BF16 hi/lo pairs
 // ---------------------------------------------------------------------------
 __global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int64_t cols,
-                                  __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, int vec4) {
+                                  __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, int vec4,
+                                  int write_hi, const int* run_flag) {
+  if (run_flag && *run_flag == 0) return;
   for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
     const float* xr = X + r * ldx;
     __nv_bfloat16* hr = hi + r * ldo;
@@ -1102,8 +1104,10 @@ __global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int
         const float4 v = reinterpret_cast<const float4*>(xr)[c];
         const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y);
         const __nv_bfloat162 h23 = __floats2bfloat162_rn(v.z, v.w);
-        reinterpret_cast<__nv_bfloat162*>(hr)[2 * c] = h01;
-        reinterpret_cast<__nv_bfloat162*>(hr)[2 * c + 1] = h23;
+        if (write_hi) {
+          reinterpret_cast<__nv_bfloat162*>(hr)[2 * c] = h01;
+          reinterpret_cast<__nv_bfloat162*>(hr)[2 * c + 1] = h23;
+        }
         if (lr) {
           const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
           reinterpret_cast<__nv_bfloat162*>(lr)[2 * c] = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
@@ -1116,7 +1120,7 @@ __global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int
            c += (int64_t)gridDim.x * blockDim.x) {
         const float v = xr[c];
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hr[c] = h;
+        if (write_hi) hr[c] = h;
         if (lr) lr[c] = __float2bfloat16_rn(v - __bfloat162float(h));
       }
     }
@@ -1124,8 +1128,12 @@ __global__ void split_bf16_kernel(const float* X, int64_t ldx, int64_t rows, int
 }
 
 bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols,
-                         __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s) {
+                         __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t ldo, cudaStream_t s,
+                         bool write_hi, const int* run_flag) {
   if (rows <= 0 || cols <= 0) return BCUR_OK;
+  if (!hi && write_hi) return BCUR_EINVAL;
+  if (!hi) hi = lo;  // not written; keeps the address arithmetic valid
+  if (!hi) return BCUR_OK;
   const int vec4 = (cols % 4 == 0) && (ldx % 4 == 0) && (ldo % 4 == 0) &&
                    ((uintptr_t)X % 16 == 0) && ((uintptr_t)hi % 8 == 0) &&
                    (!lo || (uintptr_t)lo % 8 == 0);
@@ -1133,7 +1141,7 @@ bcur_status_t split_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols
   const int64_t gx = std::min<int64_t>(ceil_div(per_row, 256), 64);
   const int64_t gy = std::min<int64_t>(rows, 65535 / std::max<int64_t>(1, 1));
   split_bf16_kernel<<<dim3((unsigned)gx, (unsigned)std::min<int64_t>(gy, 8192)), 256, 0, s>>>(
-      X, ldx, rows, cols, hi, lo, ldo, vec4);
+      X, ldx, rows, cols, hi, lo, ldo, vec4, write_hi ? 1 : 0, run_flag);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }

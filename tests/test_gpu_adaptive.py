@@ -117,3 +117,29 @@ def test_adaptive_fit_is_deterministic():
         plan.sync_status()
         assert t1[0] == want and plan.fit_terms() == t1
         assert torch.equal(U1, U2) and torch.equal(e1, e2)
+
+
+def test_fit_reuses_the_sketch_copy_of_a():
+    """The adaptive fit takes A's BF16 hi half from the sketch when the
+    scores were computed on the same A pointer, and splits A itself
+    otherwise: both give bit-identical U and errors."""
+    import paper_1703_06065_gb300 as pkg
+    from _gpu_common import device, to_dev
+
+    device()
+    p = bi.scaled_haar(1536, 2048, 64, k=10, p=10, q=2, g_col=6, g_row=5, seed=7, rank=120,
+                       noise=1e-4)
+    A = to_dev(p.matrix(), torch.float32)
+    A2 = A.clone()
+    om = to_dev(p.omega().T, torch.float32)
+    out = []
+    for Ascores in (A, A2):
+        plan = pkg.Plan(p.m, p.n, p.k, p.p, p.q, p.col_off, p.row_off, p.g_col, p.g_row,
+                        dtype="f32", sketch_prec="bf16", fit_prec="bf16x3a")
+        cs, rs = plan.scores(Ascores, om)
+        ci, ri, _, _ = plan.sample(cs, rs, to_dev(p.u_col()), to_dev(p.u_row()))
+        U = plan.fit(A, ci, ri).clone()
+        e = plan.error(A).clone()
+        plan.sync_status()
+        out.append((U, e))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
