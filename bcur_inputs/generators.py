@@ -23,6 +23,7 @@ are not available):
 from __future__ import annotations
 
 import math
+import threading
 from dataclasses import dataclass, field
 from typing import List, Optional
 
@@ -134,34 +135,98 @@ def ar1_factors(m: int, n: int, k: int, phi: float, seed: int):
     return load, x
 
 
+_AR1_CACHE: dict = {}
+_GEN_CACHE = threading.local()
+
+
+def _ar1_mats(phi: float, B: int, nc: int, device):
+    """Cached pieces of the chunked AR(1) recurrence, formed on the device:
+    T^T (B x B, T = phi^(i - j) on and below the diagonal), S^T (S = phi^(B (i - j))
+    over chunks; lower-triangular Toeplitz, so the leading nc x nc block of a
+    larger one is the same) and phi^(i + 1)."""
+    import torch
+
+    key = (float(phi), B, str(device))
+    got = _AR1_CACHE.get(key)
+    if got is None or got[1].shape[0] < nc:
+        size = max(nc, 128 if got is None else 2 * got[1].shape[0])
+        i = torch.arange(B, device=device, dtype=torch.float32)
+        d = i.view(B, 1) - i.view(1, B)
+        T = torch.where(d >= 0, torch.pow(phi, d.clamp(min=0)), torch.zeros_like(d))
+        jj = torch.arange(size, device=device, dtype=torch.float32)
+        dj = jj.view(size, 1) - jj.view(1, size)
+        S = torch.where(dj >= 0, torch.pow(phi ** B, dj.clamp(min=0)), torch.zeros_like(dj))
+        got = (T.t().contiguous(), S.t().contiguous(), torch.pow(phi, i + 1))
+        _AR1_CACHE[key] = got
+    return got[0], got[1][:nc, :nc], got[2]
+
+
+def ar1_series_chunked(e, phi: float, chunk: int = 128):
+    """The AR(1) rows x_0 = e_0, x_t = phi x_{t-1} + sqrt(1 - phi^2) e_t of a
+    k x n innovation matrix e (torch, any device), computed as a chunked linear
+    recurrence: inside each chunk of `chunk` steps the solution from a zero
+    start is one product with the lower-triangular matrix of powers
+    phi^(i - j); the chunks' end values are joined by a second small product
+    over chunks, and each chunk adds its predecessor's end value times
+    phi^(i + 1).  Two matrix products in place of a sequential scan; exact up
+    to FP32 rounding (no truncation)."""
+    import torch
+
+    k, n = e.shape
+    B = chunk
+    nc = (n + B - 1) // B
+    Tt, St, pw = _ar1_mats(phi, B, nc, e.device)
+    src = torch.zeros(k, nc * B, device=e.device, dtype=torch.float32)
+    src[:, :n].copy_(e).mul_(math.sqrt(1.0 - phi * phi))
+    src[:, 0] = e[:, 0]
+    y = (src.view(k * nc, B) @ Tt).view(k, nc, B)       # each chunk from a zero start
+    z = y[:, :, B - 1] @ St                             # chunk end values, k x nc
+    y[:, 1:, :].addcmul_(z[:, :-1].unsqueeze(2), pw.view(1, 1, B))
+    return y.view(k, nc * B)[:, :n]
+
+
+def _device_generator(device):
+    """One reusable torch generator per thread and device (reseeded per use)."""
+    import torch
+
+    gens = getattr(_GEN_CACHE, "gens", None)
+    if gens is None:
+        gens = _GEN_CACHE.gens = {}
+    key = str(device)
+    g = gens.get(key)
+    if g is None:
+        g = gens[key] = torch.Generator(device=device)
+    return g
+
+
 def ar1_mixture_stream(m: int, n: int, k: int, phi: float, noise: float, seed: int,
                        device="cuda", out=None):
     """The biometric-like recipe drawn entirely on the device (the serving
     workload, where every request's matrix is drawn at admission): L and the
-    innovations from a seeded torch generator, and the AR(1) series
-    x_t = phi^t e_0 + c sum_{1 <= s <= t} phi^(t-s) e_s, c = sqrt(1 - phi^2),
-    as a causal convolution with the kernel phi^j truncated where phi^j falls
-    below 1e-16 of the first tap.  FP32."""
+    innovations from a seeded torch generator, the AR(1) series by
+    :func:`ar1_series_chunked`, A = noise * N(0,1) + L X.  FP32."""
     import torch
-    import torch.nn.functional as F
 
-    gen = torch.Generator(device=device)
+    gen = _device_generator(device)
     gen.manual_seed(int(seed) * 1000003 + STREAM_MATRIX)
-    L = torch.randn(m, k, generator=gen, device=device) / math.sqrt(k)
+    L = torch.randn(m, k, generator=gen, device=device).mul_(1.0 / math.sqrt(k))
     e = torch.randn(k, n, generator=gen, device=device)
-    J = min(n, int(math.ceil(math.log(1e-16) / math.log(phi))) + 1)
-    taps = phi ** torch.arange(J - 1, -1, -1, device=device, dtype=torch.float32)
-    inner = torch.cat([torch.zeros(k, 1, device=device), e[:, 1:]], dim=1)
-    conv = F.conv1d(F.pad(inner.unsqueeze(1), (J - 1, 0)), taps.view(1, 1, J)).squeeze(1)
-    powers = phi ** torch.arange(n, device=device, dtype=torch.float32)
-    x = math.sqrt(1.0 - phi * phi) * conv + e[:, :1] * powers
+    x = ar1_series_chunked(e, phi)
     # A = noise * N(0,1) + L x, formed in place (out: a preallocated m x n buffer)
     a = torch.empty(m, n, device=device) if out is None else out
     if noise:
         a.normal_(0.0, noise, generator=gen)
     else:
         a.zero_()
-    a.addmm_(L, x)
+    # the rank-k product on tensor cores with TF32 inputs and FP32 accumulation:
+    # A is still exactly rank k plus noise (the product of TF32-rounded
+    # factors); an FP32 product cost about as much as decomposing the request
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a.addmm_(L, x)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
     return a
 
 
@@ -175,12 +240,11 @@ def request_inputs_device(p: "Problem", device="cuda", out=None):
     r = p.recipe
     A = ar1_mixture_stream(p.m, p.n, r["rank"], r["phi"], r["noise"], p.seed, device=device,
                            out=out)
-    gen = torch.Generator(device=device)
+    gen = _device_generator(device)
     gen.manual_seed(int(p.seed) * 1000003 + STREAM_OMEGA)
-    om = torch.randint(0, 2, (p.l, p.n), generator=gen, device=device).float().mul_(2.0).sub_(1.0)
-    uc = torch.rand(p.g_col, generator=gen, device=device, dtype=torch.float64)
-    ur = torch.rand(p.g_row, generator=gen, device=device, dtype=torch.float64)
-    return A, om, uc, ur
+    om = torch.empty(p.l, p.n, device=device).bernoulli_(0.5, generator=gen).mul_(2.0).sub_(1.0)
+    u = torch.rand(p.g_col + p.g_row, generator=gen, device=device, dtype=torch.float64)
+    return A, om, u[:p.g_col], u[p.g_col:]
 
 
 def ar1_mixture_device(m: int, n: int, k: int, phi: float, noise: float, seed: int,
