@@ -434,7 +434,7 @@ bcur_status_t bcur_gather_blocks(const void* A, int64_t lda, int64_t m, int64_t 
                                  int32_t g, int64_t cap, void* out, int64_t ldo, void* map,
                                  void* stream);
 
-/* Dense GEMM on the library's kernels, exposed for testing the tensor-core/* Dense GEMM on the library's kernels, exposed for testing the tensor-core
+/* Dense GEMM on the library's kernels, exposed for testing the tensor-core
  * path against the CUDA-core path:  D (M x N, row-major, ldd) = A_op B_op,
  * A_op(i, kk) = transA ? A[kk * lda + i] : A[i * lda + kk],
  * B_op(kk, j) = transB ? B[j * ldb + kk] : B[kk * ldb + j].
@@ -448,6 +448,24 @@ bcur_status_t bcur_gather_blocks(const void* A, int64_t lda, int64_t m, int64_t 
 bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                         int32_t transA, const void* B, int64_t ldb, int32_t transB, void* D,
                         int64_t ldd, int32_t dtype, int32_t prec, void* stream);
+
+/* FP8 e4m3 product with one factor per 128 x 128 block of B (the block-scaled
+ * path of the FP8B sketch, exposed for testing):
+ *   D[i][j] = scale_m[i] * sum_kb bscale[(j / 128) * bs_n + kb * bs_k]
+ *                               * sum_{k in K block kb} A[i][k] B[j][k],
+ * K blocks of 128.  A (M x K, ld lda bytes) and B (N x K, ld ldb bytes) are
+ * e4m3 bytes, both K-major; scale_m (M floats) may be NULL (1); bscale holds
+ * the ceil(N/128) x ceil(K/128) block factors with the given strides
+ * (elements); D (M x N, FP32, row-major, ldd).  Every 128-deep K block is
+ * accumulated in FP32 in its own tensor-memory buffer and added, scaled, in
+ * FP32.  Needs M < 128 and N >= 2 M (the product runs transposed, B's blocks
+ * along the 128-row tiles), lda and ldb multiples of 16, 16-byte aligned
+ * bases.  Errors: BCUR_EINVAL (NULL operand, negative size), BCUR_ENOTSUP
+ * (shape or layout outside the above, or no sm_103 tensor cores). */
+bcur_status_t bcur_gemm_fp8_blocks(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                                   const void* B, int64_t ldb, const float* scale_m,
+                                   const float* bscale, int64_t bs_n, int64_t bs_k, float* D,
+                                   int64_t ldd, void* stream);
 
 /* D (M x N, FP32, row-major, ldd) = A B with both operands as BF16 hi/lo
  * pairs (x = hi + lo): A_hi B_hi + A_hi B_lo + A_lo B_hi on the tcgen05

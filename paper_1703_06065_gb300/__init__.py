@@ -24,7 +24,7 @@ import numpy as np
 from . import _lib
 from ._lib import BCUR_BF16, BCUR_F32, BCUR_F64, BCUR_TF32, PREC, BcurError  # noqa: F401
 
-__all__ = ["Plan", "Batch", "alg1", "boosted", "boosted_batch", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split",
+__all__ = ["Plan", "Batch", "alg1", "boosted", "boosted_batch", "block_scores", "block_stable_rank", "incoherence", "sample_blocks", "residual", "gemm", "gemm_split", "gemm_fp8_blocks",
            "decompose", "load", "BcurError", "PREC"]
 
 load = _lib.load
@@ -497,6 +497,21 @@ def gemm(A, B, transA: bool = False, transB: bool = False, prec: str = None, out
     _lib.check(_lib.load().bcur_gemm(M, N, K, _ptr(A), A.shape[1], int(transA), _ptr(B),
                                      B.shape[1], int(transB), _ptr(D), D.shape[1], code, prec,
                                      _stream()), "bcur_gemm")
+    return D
+
+
+def gemm_fp8_blocks(A8, B8, bscale, scale_m=None, out=None):
+    """D = diag(scale_m) sum over 128-deep K blocks kb of bscale[j/128, kb] A8[:, kb] B8[:, kb]^T
+    (e4m3 A8: M x K, B8: N x K, both K-major; bscale: ceil(N/128) x ceil(K/128) FP32)."""
+    torch = _torch()
+    _need_cuda(A8, B8, bscale)
+    M, K = A8.shape
+    N = B8.shape[0]
+    D = torch.empty(M, N, dtype=torch.float32, device=A8.device) if out is None else out
+    _lib.check(_lib.load().bcur_gemm_fp8_blocks(M, N, K, _ptr(A8), A8.stride(0), _ptr(B8),
+                                                B8.stride(0), _ptr(scale_m), _ptr(bscale),
+                                                bscale.stride(0), bscale.stride(1), _ptr(D),
+                                                D.stride(0), _stream()), "bcur_gemm_fp8_blocks")
     return D
 
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "bcur_decompose_host", "bcur_set_wait_budget_ns", "bcur_autotune_measured",
     "bcur_rank_k_error", "bcur_boost_select", "bcur_cholesky_inverse", "bcur_svd_small",
     "bcur_gather_blocks", "bcur_incoherence", "bcur_fit_terms", "bcur_batch_set_fit",
-    "bcur_batch_fit_terms",
+    "bcur_batch_fit_terms", "bcur_gemm_fp8_blocks",
 ]
 
 
@@ -107,6 +107,10 @@ def load():
     L.bcur_batch_set_fit.restype = st
     L.bcur_batch_fit_terms.argtypes = [c_void_p, c_void_p]
     L.bcur_batch_fit_terms.restype = st
+    L.bcur_gemm_fp8_blocks.argtypes = [c_int64, c_int64, c_int64, c_void_p, c_int64, c_void_p,
+                                       c_int64, c_void_p, c_void_p, c_int64, c_int64, c_void_p,
+                                       c_int64, c_void_p]
+    L.bcur_gemm_fp8_blocks.restype = st
     L.bcur_rank.argtypes = [c_void_p] + [POINTER(c_int64)] * 4
     L.bcur_rank.restype = st
     L.bcur_sync_status.argtypes = [c_void_p]

@@ -1696,6 +1696,22 @@ bcur_status_t bcur_residual(const void* X, int64_t ldx, const void* Pm, int64_t 
   return finish_residual((const double*)workspace, np, out, 1, s);
 }
 
+bcur_status_t bcur_gemm_fp8_blocks(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                                   const void* B, int64_t ldb, const float* scale_m,
+                                   const float* bscale, int64_t bs_n, int64_t bs_k, float* D,
+                                   int64_t ldd, void* stream) {
+  if (!A || !B || !bscale || !D || M < 0 || N < 0 || K < 0) return BCUR_EINVAL;
+  if (M == 0 || N == 0) return BCUR_OK;
+  if (K == 0 || !(M < 128 && N >= 2 * M)) return BCUR_ENOTSUP;
+  GemmDesc g = mk(M, N, K, A, lda, 0, B, ldb, 1, D, ldd);
+  g.ab_fp8 = 1;
+  g.scale_m = scale_m;
+  g.bscale_b = bscale;
+  g.bs_n = bs_n;
+  g.bs_k = bs_k;
+  return gemm_tc(g, BCUR_FP8, (cudaStream_t)stream);
+}
+
 bcur_status_t bcur_gemm(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                         int32_t transA, const void* B, int64_t ldb, int32_t transB, void* D,
                         int64_t ldd, int32_t dtype, int32_t prec, void* stream) {

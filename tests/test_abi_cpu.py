@@ -208,6 +208,10 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.bcur_gather_blocks(p, 10, 8, 16, 0, 1, off, 2, p, 1, 8, p, 8, p, None) == 1  # lda < n
     assert lib.bcur_batch_set_fit(None, 4) == 1
     assert lib.bcur_batch_fit_terms(None, p) == 1
+    assert lib.bcur_gemm_fp8_blocks(4, 16, 32, None, 32, p, 32, None, p, 1, 1, p, 16, None) == 1
+    assert lib.bcur_gemm_fp8_blocks(4, 16, 32, p, 32, p, 32, None, None, 1, 1, p, 16, None) == 1
+    assert lib.bcur_gemm_fp8_blocks(200, 500, 32, p, 32, p, 32, None, p, 1, 1, p, 500,
+                                    None) == 7          # M >= 128: not the transposed path
     assert lib.bcur_gather_blocks(p, 16, 8, 16, 0, 2, off, 2, p, 1, 8, p, 8, p, None) == 1  # axis
     assert lib.bcur_gather_blocks(p, 16, 8, 16, 0, 1, off, 2, p, 1, 8, p, 4, p, None) == 1  # ldo < m
     # boosting's choice

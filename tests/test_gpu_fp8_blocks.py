@@ -68,3 +68,43 @@ def test_block_scales_keep_quiet_column_blocks_that_row_scales_lose():
         assert np.max(np.abs(gpu["row_scores"] - refb["row_scores"])) <= bound
         loud = [g for g in range(len(p.col_off) - 1) if g not in qblocks]
         assert np.max(np.abs(gpu["col_scores"][loud] - refb["col_scores"][loud])) <= bound
+
+
+@pytest.mark.parametrize("M,N,K", [(20, 700, 1000), (64, 1024, 768), (120, 4096, 333)])
+def test_block_scaled_fp8_gemm_is_exact_to_fp32_accumulation(M, N, K):
+    """The block-scaled FP8 product against an FP64 product of the same e4m3
+    operands and factors: D = diag(s_m) sum_kb s_B(j/128, kb) A_kb B_kb^T.
+    Products of e4m3 values are exact in FP32, so the only rounding is the
+    FP32 accumulation of each 128-deep K block and of the scaled sum; block
+    factors spread over six orders of magnitude and ragged M, N, K (K not a
+    multiple of 128 or of 16) are covered."""
+    import paper_1703_06065_gb300 as pkg
+    from _gpu_common import device
+
+    torch = pytest.importorskip("torch")
+    dev = device()
+    g = torch.Generator(device="cpu").manual_seed(M + N + K)
+    Kp = (K + 15) // 16 * 16
+    A = (torch.randn(M, Kp, generator=g) * 40).clamp(-440, 440)
+    B = (torch.randn(N, Kp, generator=g) * 40).clamp(-440, 440)
+    A8 = A.to(torch.float8_e4m3fn).to(dev)[:, :K]
+    B8 = B.to(torch.float8_e4m3fn).to(dev)[:, :K]
+    gn, gk = (N + 127) // 128, (K + 127) // 128
+    bs = (10.0 ** (torch.rand(gn, gk, generator=g) * 6 - 3)).to(dev)
+    sm = (torch.rand(M, generator=g) + 0.5).to(dev)
+    D = pkg.gemm_fp8_blocks(A8, B8, bs, scale_m=sm)
+    torch.cuda.synchronize()
+    Ad = A8.double().cpu()
+    Bd = B8.double().cpu()
+    ref = torch.zeros(M, N, dtype=torch.float64)
+    for kb in range(gk):
+        k0, k1 = 128 * kb, min(K, 128 * kb + 128)
+        part = Ad[:, k0:k1] @ Bd[:, k0:k1].T
+        ref += part * bs.double().cpu()[:, kb].repeat_interleave(128)[:N].view(1, N)
+    ref *= sm.double().cpu().view(M, 1)
+    # FP32 rounding of each block sum (at most 128 terms: 128 * 2^-24 = 7.6e-6 of
+    # the block's sum of |products|) and of the scaled accumulation, bounded
+    # with the largest factor for every block
+    scale = (Ad.abs() @ Bd.abs().T) * bs.double().cpu().max() * sm.double().cpu().max()
+    err = (D.double().cpu() - ref).abs()
+    assert torch.all(err <= 1e-5 * scale + 1e-30), float((err / (scale + 1e-30)).max())
