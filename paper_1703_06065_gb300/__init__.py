@@ -504,7 +504,9 @@ def gemm_fp8_blocks(A8, B8, bscale, scale_m=None, out=None):
     """D = diag(scale_m) sum over 128-deep K blocks kb of bscale[j/128, kb] A8[:, kb] B8[:, kb]^T
     (e4m3 A8: M x K, B8: N x K, both K-major; bscale: ceil(N/128) x ceil(K/128) FP32)."""
     torch = _torch()
-    _need_cuda(A8, B8, bscale)
+    for t in (A8, B8, bscale):   # row views with padded leading dimensions are fine
+        if not t.is_cuda or t.stride(-1) != 1:
+            raise ValueError("operands must be CUDA tensors with unit inner stride")
     M, K = A8.shape
     N = B8.shape[0]
     D = torch.empty(M, N, dtype=torch.float32, device=A8.device) if out is None else out
