@@ -508,12 +508,16 @@ bcur_status_t g16(bcur_plan_t P, GemmDesc d, int parts) { return g16_on(P, lane_
 // panels (FP32 diagonal factorisation and panel solve on CUDA cores, the
 // update of the rest of the outer panel on tensor cores).  The inverse is
 // assembled by doubling (X21 = -X22 L21 X11) on tensor cores.  Tensor-core
-// products use `parts` BF16 terms.
+// products use `parts` BF16 terms.  run (optional device flag, the 64-column
+// step path only): every launch does nothing when *run reads 0.
 constexpr int64_t kOuter = 1024;
 constexpr int64_t kOuterStep = 512;
 
+bool chol_steps_apply(bcur_plan_t P, int64_t w) { return P->nb == 64 && w % 64 == 0; }
+
 bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float* L, float* Li,
-                                 int64_t w, int parts, int* kept, double tol) {
+                                 int64_t w, int parts, int* kept, double tol,
+                                 const int* run = nullptr) {
   cudaStream_t s = ln.s;
   const int nb = P->nb;
   const bool lo = parts == 3;
@@ -523,18 +527,24 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float*
   S16 Li16 = s16(P, ln.Lih, ln.Lil, lo);
   S16 T1 = s16(P, ln.T1h, ln.T1l, lo);
   auto split = [&](bcur_plan_t, const float* X, int64_t ldx, int64_t rows, int64_t cols, S16 out,
-                   int64_t ldo) { return split_on(s, X, ldx, rows, cols, out, ldo); };
-  auto g16 = [&](bcur_plan_t, GemmDesc d, int pr) { return g16_on(P, ln, d, pr); };
-  BCUR_TRY(fill_zero(L, (size_t)w * w * sizeof(float), s));
-  BCUR_TRY(fill_zero(Li, (size_t)w * w * sizeof(float), s));
-  BCUR_TRY(fill_zero(kept, sizeof(int), s));
-  BCUR_TRY(max_diag<float>(G, w, w, md, s));
-  const bool step = nb == 64 && w % 64 == 0;
+                   int64_t ldo) {
+    return split_bf16(X, ldx, rows, cols, out.h, out.l, ldo, s, true, run);
+  };
+  auto g16 = [&](bcur_plan_t, GemmDesc d, int pr) {
+    d.run_flag = run;
+    return g16_on(P, ln, d, pr);
+  };
+  const bool step = chol_steps_apply(P, w);
+  if (run && !step) return BCUR_EINVAL;  // the gated form needs the step path
+  BCUR_TRY(fill_zero_if(L, (size_t)w * w * sizeof(float), run, s));
+  BCUR_TRY(fill_zero_if(Li, (size_t)w * w * sizeof(float), run, s));
+  BCUR_TRY(fill_zero_if(kept, sizeof(int), run, s));
+  BCUR_TRY(max_diag<float>(G, w, w, md, s, run));
   const int64_t outer = step ? kOuterStep : kOuter;
   for (int64_t J0 = 0; J0 < w; J0 += outer) {
     const int64_t J1 = std::min(w, J0 + outer);
     for (int64_t j0 = J0; step && j0 < J1; j0 += nb)
-      BCUR_TRY(chol_step(G, w, L, Li, J0, j0, md, tol, kept, s));
+      BCUR_TRY(chol_step(G, w, L, Li, J0, j0, md, tol, kept, s, run));
     for (int64_t j0 = J0; !step && j0 < J1; j0 += nb) {
       BCUR_TRY(potrf_diag<float>(G, w, L, w, Li, w, j0, nb, md, tol, kept, s));
       const int64_t j1 = j0 + nb;
@@ -614,11 +624,13 @@ bcur_status_t chol_inv_blocked16(bcur_plan_t P, const Lane& ln, float* G, float*
 // Wide Cholesky-QR2 of a BF16-pair panel X (w x h): X = L1 L2 Q.  The pairs
 // pr[0] (input, then result) and pr[1] (intermediate) ping-pong.  With
 // second_apply false the second pass stops at L2: pr[1] keeps Q1 = L1^{-1} X
-// (Q = L2^{-1} Q1 is then applied to the small products instead).
+// (Q = L2^{-1} Q1 is then applied to the small products instead).  parts2:
+// the terms of the second pass's Gram and factorisation (0: parts).
 bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, int64_t h,
                            int64_t ld, float* G, float* L1, float* L1i, float* L2, float* L2i,
                            int parts, int* kept, cudaEvent_t after_gram = nullptr,
-                           bool second_apply = true) {
+                           bool second_apply = true, int parts2 = 0) {
+  if (parts2 > 0 && parts2 != parts && second_apply) return BCUR_EINVAL;
   const bool lo = parts == 3;
   S16 Li16 = s16(P, ln.Lih, ln.Lil, lo);
   auto g16 = [&](bcur_plan_t, GemmDesc d, int pr2) { return g16_on(P, ln, d, pr2); };
@@ -626,12 +638,13 @@ bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, 
   float* Lis[2] = {L1i, L2i};
   for (int pass = 0; pass < 2; ++pass) {
     S16 src = pr[pass], dst = pr[1 - pass];
+    const int pt = (pass == 1 && parts2 > 0) ? parts2 : parts;
     GemmDesc g = mk16(w, w, h, src, ld, 0, src, ld, 1, w);
     g.D = G;
     g.out_lower = 1;
-    BCUR_TRY(g16(P, g, parts));
+    BCUR_TRY(g16(P, g, pt));
     if (pass == 0 && after_gram) BCUR_CUDA_TRY(cudaEventRecord(after_gram, ln.s));
-    BCUR_TRY(chol_inv_blocked16(P, ln, G, Ls[pass], Lis[pass], w, parts, kept + pass,
+    BCUR_TRY(chol_inv_blocked16(P, ln, G, Ls[pass], Lis[pass], w, pt, kept + pass,
                                 drop_tol<float>(h)));
     if (pass == 1 && !second_apply) break;
     GemmDesc a = mk16(w, h, w, Li16, w, 0, src, ld, 0, ld);  // Li16 holds L^{-1} already
@@ -641,6 +654,22 @@ bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, 
     BCUR_TRY(g16(P, a, parts));
   }
   return BCUR_OK;
+}
+
+// The second Cholesky-QR pass of wide_cqr2_16 again with three terms (the
+// Gram Q1^T Q1 of the pair q1 and its factorisation into L2, L2i), every
+// launch gated by the device flag run: the refinement of the adaptive fit,
+// whose first pass took one term.  Same launches as the split fit's second
+// pass, so a refined result is the split fit's bit for bit.
+bcur_status_t redo_second_pass(bcur_plan_t P, S16 q1, int64_t w, int64_t h, int64_t ld, float* G,
+                               float* L2, float* L2i, int* kept, const int* run) {
+  const Lane ln = lane_of(P, 0);
+  GemmDesc g = mk16(w, w, h, q1, ld, 0, q1, ld, 1, w);
+  g.D = G;
+  g.out_lower = 1;
+  g.run_flag = run;
+  BCUR_TRY(g16_on(P, ln, g, 3));
+  return chol_inv_blocked16(P, ln, G, L2, L2i, w, 3, kept, drop_tol<float>(h), run);
 }
 
 // Stages 1-2 with the products by A on tensor cores.
@@ -802,15 +831,22 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   // side's latency-bound Cholesky steps run beside the other side's GEMMs
   // instead of beside each other.
   const Lane l0 = lane_of(P, 0), l1 = lane_of(P, 1);
+  // The adaptive form takes the second pass's Gram Q1^T Q1 (near I) and its
+  // factorisation with one BF16 term first: like M, it enters e only at
+  // second order and U at first order at one term's level; the refinement
+  // redoes that pass with three terms (redo_second_pass).
+  const bool adapt = P->d.fit_prec == BCUR_BF16X3A;
+  const bool pass2_one = adapt && chol_steps_apply(P, cw) && chol_steps_apply(P, rw);
+  const int parts2 = pass2_one ? 1 : parts;
   BCUR_CUDA_TRY(cudaEventRecord(P->ev_fork, s));
   BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_fork, 0));
   BCUR_TRY(wide_cqr2_16(P, l0, XC, cw, m, ldm, P->at<float>(P->o.GC), P->at<float>(P->o.L1C),
                         P->at<float>(P->o.L1Ci), P->at<float>(P->o.L2C), P->at<float>(P->o.L2Ci),
-                        parts, kept + 4, P->ev_stagger, false));
+                        parts, kept + 4, P->ev_stagger, false, parts2));
   BCUR_CUDA_TRY(cudaStreamWaitEvent(P->stream2, P->ev_stagger, 0));
   BCUR_TRY(wide_cqr2_16(P, l1, XR, rw, n, ldn, P->at<float>(P->o.GR), P->at<float>(P->o.L1R),
                         P->at<float>(P->o.L1Ri), P->at<float>(P->o.L2R), P->at<float>(P->o.L2Ri),
-                        parts, kept + 6, nullptr, false));
+                        parts, kept + 6, nullptr, false, parts2));
   BCUR_CUDA_TRY(cudaEventRecord(P->ev_join, P->stream2));
   BCUR_CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
   // The second Cholesky-QR pass stops at L2: with Q1 = X L1^{-T} (the pairs
@@ -824,10 +860,9 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
   // ||A - Q1_C M2 Q1_R^T||_F first with one BF16 term; when that residual is
   // too coarse for the error it reports (residual_needs_refine, decided on
   // the device) the same launches are redone with three terms (gated by the
-  // flag, always enqueued so the sequence stays capturable), and the two
-  // products after M2 take the flag's term count.  The residual is kept for
-  // bcur_error.
-  const bool adapt = P->d.fit_prec == BCUR_BF16X3A;
+  // flag, always enqueued so the sequence stays capturable), after the second
+  // QR pass when it took one term, and the two products after M2 take the
+  // flag's term count.  The residual is kept for bcur_error.
   S16 A16 = s16(P, P->o.A16h, P->o.A16l, lo);
   S16 W16 = s16(P, P->o.Wh, P->o.Wl, lo);
   S16 M16 = s16(P, P->o.Mh, P->o.Ml, lo);
@@ -873,6 +908,12 @@ bcur_status_t run_fit16(bcur_plan_t P, const float* A, const int32_t* ci, const 
     BCUR_TRY(to_m2(1, nullptr));
     BCUR_TRY(resid16(P, A, false, flag, nullptr, ferr, 2));
     BCUR_TRY(split_bf16(A, lda, m, n, nullptr, A16.l, ldn, s, false, flag));
+    if (pass2_one) {
+      BCUR_TRY(redo_second_pass(P, XC[1], cw, m, ldm, P->at<float>(P->o.GC),
+                                P->at<float>(P->o.L2C), P->at<float>(P->o.L2Ci), kept + 5, flag));
+      BCUR_TRY(redo_second_pass(P, XR[1], rw, n, ldn, P->at<float>(P->o.GR),
+                                P->at<float>(P->o.L2R), P->at<float>(P->o.L2Ri), kept + 7, flag));
+    }
     BCUR_TRY(to_m2(3, flag));
     BCUR_TRY(resid16(P, A, true, flag, flag, ferr + 3, 3));
     BCUR_TRY(select_result(ferr, ferr + 3, flag, ferr + 6, s));

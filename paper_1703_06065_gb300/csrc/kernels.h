@@ -155,16 +155,19 @@ template <typename T>
 bcur_status_t jacobi_svd_small(const double* X, int w, T* Ut, T* W, double* sigma, T* jwork,
                                int* status, cudaStream_t s);
 
-// Blocked pieces of the wide Cholesky-QR.
+// Blocked pieces of the wide Cholesky-QR.  run (optional device flag): when
+// it reads 0 at launch the kernel does nothing.
 template <typename T>
-bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t s);
+bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t s,
+                       const int* run = nullptr);
 template <typename T>
 bcur_status_t potrf_diag(T* G, int64_t ldg, T* L, int64_t ldl, T* Linv, int64_t ldi, int64_t j0,
                          int nb, const T* maxdiag, double tol_rel, int* kept, cudaStream_t s);
 // One left-looking 64-column step of the blocked FP32 Cholesky (see small.cu):
 // L[j0:, j0:j0+64] and Linv's diagonal block from G and L[:, J0:j0].
 bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_t J0, int64_t j0,
-                        const float* maxdiag, double tol_rel, int* kept, cudaStream_t s);
+                        const float* maxdiag, double tol_rel, int* kept, cudaStream_t s,
+                        const int* run = nullptr);
 
 // Block leverage scores from a panel F^T (k x h).
 template <typename T>
@@ -219,6 +222,9 @@ bcur_status_t copy2d(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t row
                      cudaStream_t s);
 
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s);
+// fill_zero that does nothing when the device flag *run reads 0 at launch
+// (run NULL: always).
+bcur_status_t fill_zero_if(void* p, size_t bytes, const int* run, cudaStream_t s);
 // dst = src (bytes, both 16-byte aligned, bytes a multiple of 16) by the SMs;
 // src may be mapped host memory.
 bcur_status_t copy_bytes_sm(const void* src, void* dst, size_t bytes, int sms, cudaStream_t s);

@@ -306,7 +306,8 @@ template bcur_status_t jacobi_svd_batched<float>(const double*, int, float*, flo
 // Blocked Cholesky pieces (working precision T)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void max_diag_kernel(const T* G, int64_t w, int64_t ldg, T* out) {
+__global__ void max_diag_kernel(const T* G, int64_t w, int64_t ldg, T* out, const int* run) {
+  if (run && *run == 0) return;
   T mx = T(0);
   for (int64_t i = threadIdx.x; i < w; i += blockDim.x) mx = fmax(mx, G[i * ldg + i]);
 #pragma unroll
@@ -322,8 +323,9 @@ __global__ void max_diag_kernel(const T* G, int64_t w, int64_t ldg, T* out) {
 }
 
 template <typename T>
-bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t s) {
-  max_diag_kernel<T><<<1, 1024, 0, s>>>(G, w, ldg, out);
+bcur_status_t max_diag(const T* G, int64_t w, int64_t ldg, T* out, cudaStream_t s,
+                       const int* run) {
+  max_diag_kernel<T><<<1, 1024, 0, s>>>(G, w, ldg, out, run);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
@@ -442,7 +444,11 @@ __device__ void step_prod64(const float* Ab, const float* Bb, int64_t ld, int K,
 __global__ void __launch_bounds__(256) chol_step_kernel(const float* G, int64_t w, float* L,
                                                         float* Linv, int64_t J0, int64_t j0,
                                                         const float* maxdiag, double tol_rel,
-                                                        int* kept) {
+                                                        int* kept, const int* run) {
+  // a gated step (run reads 0) does nothing; the flag was written before the
+  // first step of the factorisation was launched, so every CTA of every step
+  // reads the same value
+  if (run && *run == 0) return;
   extern __shared__ __align__(16) float step_smem[];
   float* S = step_smem;                     // 64 x 68: D, then L_jj; then X^T
   float* X = S + 64 * kStepLD;              // 64 x 68: L_jj^{-1}
@@ -534,7 +540,8 @@ size_t chol_step_smem() {
 }
 
 bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_t J0, int64_t j0,
-                        const float* maxdiag, double tol_rel, int* kept, cudaStream_t s) {
+                        const float* maxdiag, double tol_rel, int* kept, cudaStream_t s,
+                        const int* run) {
   if (w % 64 != 0 || j0 % 64 != 0 || J0 > j0 || (j0 - J0) % 64 != 0 || j0 + 64 > w)
     return BCUR_EINVAL;
   static bool attr_set = false;
@@ -558,7 +565,7 @@ bcur_status_t chol_step(const float* G, int64_t w, float* L, float* Linv, int64_
   cfg.attrs = attr;
   cfg.numAttrs = j0 > J0 ? 1 : 0;
   BCUR_CUDA_TRY(cudaLaunchKernelEx(&cfg, chol_step_kernel, G, w, L, Linv, J0, j0, maxdiag, tol_rel,
-                                   kept));
+                                   kept, run));
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
@@ -831,6 +838,32 @@ bcur_status_t copy_bytes_sm(const void* src, void* dst, size_t bytes, int sms, c
 bcur_status_t fill_zero(void* p, size_t bytes, cudaStream_t s) {
   if (bytes == 0) return BCUR_OK;
   BCUR_CUDA_TRY(cudaMemsetAsync(p, 0, bytes, s));
+  return BCUR_OK;
+}
+
+// Zero `head` bytes at p, then n16 16-byte words, then `tail` bytes, unless
+// *run reads 0.
+__global__ void fill_zero_if_kernel(unsigned char* p, int head, int64_t n16, int tail,
+                                    const int* run) {
+  if (*run == 0) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < head) p[t] = 0;
+  uint4* w = reinterpret_cast<uint4*>(p + head);
+  for (int64_t i = t; i < n16; i += (int64_t)gridDim.x * blockDim.x) w[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (t < tail) p[head + 16 * n16 + t] = 0;
+}
+
+bcur_status_t fill_zero_if(void* p, size_t bytes, const int* run, cudaStream_t s) {
+  if (!run) return fill_zero(p, bytes, s);
+  if (bytes == 0) return BCUR_OK;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const int head = (int)std::min<size_t>(bytes, (16 - (a & 15)) & 15);
+  const int64_t n16 = (int64_t)((bytes - head) / 16);
+  const int tail = (int)(bytes - head - 16 * (size_t)n16);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n16, 256), 1024));
+  fill_zero_if_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<unsigned char*>(p), head, n16,
+                                                       tail, run);
+  BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }
 
@@ -1289,7 +1322,7 @@ bcur_status_t gather_cols_pair(const float* A, int64_t lda, int64_t m, const int
                                        cudaStream_t);                                             \
   template bcur_status_t jacobi_svd_small<T>(const double*, int, T*, T*, double*, T*, int*,       \
                                              cudaStream_t);                                       \
-  template bcur_status_t max_diag<T>(const T*, int64_t, int64_t, T*, cudaStream_t);               \
+  template bcur_status_t max_diag<T>(const T*, int64_t, int64_t, T*, cudaStream_t, const int*);               \
   template bcur_status_t potrf_diag<T>(T*, int64_t, T*, int64_t, T*, int64_t, int64_t, int,       \
                                        const T*, double, int*, cudaStream_t);                     \
   template bcur_status_t block_scores<T>(const T*, int, int64_t, int64_t, const int64_t*, int,    \
