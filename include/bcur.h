@@ -76,17 +76,21 @@ typedef enum {
  *                 row; each 128-deep K block of a product with A is scaled by
  *                 its block's factor as it is summed (FP32), the panels keep
  *                 their per-row scales.
- *   BCUR_BF16X3A: fit only (FP32 storage), adaptive: the Cholesky-QR of C
- *                 and R^T as BCUR_BF16X3; the core products (W = A Q_R,
+ *   BCUR_BF16X3A: fit only (FP32 storage), adaptive: the first pass of
+ *                 the Cholesky-QR of C and R^T as BCUR_BF16X3; the second
+ *                 pass (the Gram of the first pass's factor, near I, and its
+ *                 Cholesky factor), the core products (W = A Q_R,
  *                 M = Q_C^T W and the triangular products that turn M into
  *                 U) and the residual ||A - CUR||_F first with one BF16 term
  *                 each, all taken by bcur_fit.  When that residual is too
  *                 coarse for the relative error e it reports, i.e. when one
  *                 term's rounding (2^-8) could move e by more than 2.5e-4
  *                 ((2^-8)^2 / (2 e) > 2.5e-4, e < 0.031), the device redoes
- *                 the same products and the residual with three terms.  e
- *                 depends on errors in M only at second order (their
- *                 contribution Q_C dM Q_R^T is orthogonal to A - Q_C M Q_R^T);
+ *                 the second pass (when the factor widths are multiples of
+ *                 64), the same products and the residual with three terms.
+ *                 e depends on errors in M and in the second pass's factor
+ *                 only at second order (their contribution Q_C dM Q_R^T is
+ *                 orthogonal to A - Q_C M Q_R^T);
  *                 U at first order, so with one term U carries BF16 rounding
  *                 amplified by the conditioning of C and R.  bcur_fit_terms
  *                 reports the choice; bcur_error returns the fit's residual. */
@@ -189,7 +193,8 @@ bcur_status_t bcur_fit(bcur_plan_t plan, const void* A, const int32_t* col_idx,
                        const int32_t* row_idx, void* U, void* C, void* R);
 
 /* The BF16 terms the last bcur_fit took for its core products (W = A Q_R,
- * M = Q_C^T W and the triangular products that give U): 1 or 3 with
+ * M = Q_C^T W and the triangular products that give U; with BCUR_BF16X3A
+ * also the second Cholesky-QR pass): 1 or 3 with
  * fit_prec BCUR_BF16X3A (decided on the device), 3 with BCUR_BF16X3, 0 on
  * CUDA cores.  rel_err_estimate (host, optional) receives the relative error
  * of the one-term residual the adaptive choice was made from (-1 for the
