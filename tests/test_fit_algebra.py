@@ -45,3 +45,45 @@ def test_folded_second_pass_gives_the_least_squares_core(seed, m, n, c, r):
     Qr = Q1r @ inv(L2r).T
     M = Q.T @ A @ Qr
     assert np.isclose(np.linalg.norm(A - CUR), np.linalg.norm(A - Q @ M @ Qr.T), rtol=1e-10)
+
+
+@pytest.mark.parametrize("seed,m,n,c,r", [(2, 80, 60, 14, 11), (3, 120, 90, 24, 20)])
+def test_second_pass_factor_moves_e_at_second_order_and_u_at_first(seed, m, n, c, r):
+    """The reading behind taking the second pass's Gram G2 = Q1^T Q1 (near I)
+    with one BF16 term: for G2 perturbed by a symmetric eps S (both sides),
+    Q1 (G2 + eps S)^{-1} Q1^T differs from the projector onto range(C) only
+    inside range(C) x range(C), which is orthogonal to A - P_C A P_R, so the
+    relative residual e grows by O(eps^2) while U moves by O(eps).  Doubling
+    eps multiplies the change of e by about 4 and that of U by about 2."""
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((m, n))
+    C = A[:, :c] @ (np.eye(c) + 0.5 * g.standard_normal((c, c)))
+    R = (np.eye(r) + 0.5 * g.standard_normal((r, r))) @ A[:r, :]
+    Q1c, L1c = _chol_qr(C)
+    Q1r, L1r = _chol_qr(R.T)
+    inv = np.linalg.inv
+
+    def sym(k):
+        S = g.standard_normal((k, k))
+        S = S + S.T
+        return S / np.linalg.norm(S, 2)
+
+    Sc, Sr = sym(c), sym(r)
+    M1 = Q1c.T @ A @ Q1r
+
+    def fit(eps):
+        L2c = np.linalg.cholesky(Q1c.T @ Q1c + eps * Sc)
+        L2r = np.linalg.cholesky(Q1r.T @ Q1r + eps * Sr)
+        M2 = inv(L2c).T @ inv(L2c) @ M1 @ inv(L2r).T @ inv(L2r)
+        e = np.linalg.norm(A - Q1c @ M2 @ Q1r.T) / np.linalg.norm(A)
+        return e, inv(L1c).T @ M2 @ inv(L1r)
+
+    e0, U0 = fit(0.0)
+    de, du = [], []
+    for eps in (1e-3, 2e-3):
+        e, U = fit(eps)
+        de.append(e - e0)
+        du.append(np.linalg.norm(U - U0) / np.linalg.norm(U0))
+    assert de[0] > 0 and 3.5 <= de[1] / de[0] <= 4.5, de      # e only grows, as eps^2
+    assert 1.8 <= du[1] / du[0] <= 2.2, du                      # U moves as eps
+    assert de[0] < 1e-3 * du[0], (de, du)                        # second order against first
