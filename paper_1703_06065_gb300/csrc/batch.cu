@@ -604,7 +604,7 @@ __device__ __forceinline__ void load_tile(const float* src, int64_t ld, float* d
 }
 
 __global__ void __launch_bounds__(256) wchol_kernel(const Item* items, const int* entries,
-                                                    int pass) {
+                                                    int pass, int gated) {
   extern __shared__ __align__(16) float sm[];
   float* S = sm;              // NB x WLD: leaf L
   float* X = S + NB * WLD;    // NB x WLD: leaf L^{-1}
@@ -612,6 +612,7 @@ __global__ void __launch_bounds__(256) wchol_kernel(const Item* items, const int
   float* PsT = XT + NB * WLD; // NB x pld: PsT[t][i] = panel row i, column t
   const int e0 = entries[blockIdx.x];
   const Item& I = items[e0 >> 1];
+  if (gated && *I.refine == 0) return;  // uniform over the CTA
   const int side = e0 & 1;
   const int w = side ? I.rpad : I.cpad;
   const int pld = w - NB + 4;
@@ -901,7 +902,7 @@ bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, 
 }
 
 bcur_status_t wide_chol(const Item* items, const int* entries, int count, int wmax, int pass,
-                        cudaStream_t s) {
+                        cudaStream_t s, int gated) {
   if (count < 1) return BCUR_OK;
   if (wmax < NB || wmax > WMAX) return BCUR_EINVAL;
   static bool attr = false;
@@ -910,7 +911,7 @@ bcur_status_t wide_chol(const Item* items, const int* entries, int count, int wm
                                        (int)wide_smem(WMAX)));
     attr = true;
   }
-  wchol_kernel<<<count, 256, wide_smem(wmax), s>>>(items, entries, pass);
+  wchol_kernel<<<count, 256, wide_smem(wmax), s>>>(items, entries, pass, gated);
   BCUR_LAUNCH_CHECK();
   return BCUR_OK;
 }

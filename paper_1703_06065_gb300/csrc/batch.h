@@ -92,9 +92,10 @@ bcur_status_t sample(const Item* items, const bcur_batch_io_t* io, int B, cudaSt
 bcur_status_t gather(const Item* items, const bcur_batch_io_t* io, Work ctiles, int ctotal,
                      Work rrows, int rtotal, cudaStream_t s);
 // entries: (item << 1 | side) of the decompositions in this launch, all with
-// w <= wmax (side 0: C^T with w = cpad, side 1: R with w = rpad).
+// w <= wmax (side 0: C^T with w = cpad, side 1: R with w = rpad).  gated: only
+// the items whose refinement flag is set.
 bcur_status_t wide_chol(const Item* items, const int* entries, int count, int wmax, int pass,
-                        cudaStream_t s);
+                        cudaStream_t s, int gated = 0);
 bcur_status_t copy_u(const Item* items, const bcur_batch_io_t* io, Work urows, int total,
                      cudaStream_t s);
 // terms[b] = 3 when item b's refinement flag is set, else 1 (device array).

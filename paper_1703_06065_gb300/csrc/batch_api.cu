@@ -64,6 +64,9 @@ struct bcur_batch_s {
     int n = 0;
   };
   MGroup gY, gZ, gY2, gGram[2], gApply[2], gW, gM, gU[6], gP, gRes, gP3, gRes3;
+  // adaptive fit: the second Cholesky-QR pass's Grams with one BF16 term
+  // (the three-term gGram[1] then runs only for items the residual refines)
+  MGroup gGram1;
   // adaptive split fit (BCUR_BF16X3A): one-term W, M and the products to M2;
   // the three-term groups above then run only for items whose one-term
   // residual asks for refinement
@@ -141,6 +144,7 @@ size_t layout(bcur_batch_t P) {
   };
   grp(P->gY, B); grp(P->gZ, B); grp(P->gY2, B);
   for (int i = 0; i < 2; ++i) grp(P->gGram[i], 2 * B);
+  grp(P->gGram1, 2 * B);
   grp(P->gApply[0], 2 * B);  // the second Cholesky-QR pass has no apply
   grp(P->gW, B); grp(P->gM, B);
   for (int i = 0; i < 6; ++i) grp(P->gU[i], B);
@@ -263,7 +267,7 @@ bcur_status_t build_groups(bcur_batch_t P) {
   const int B = P->B;
   std::vector<GemmDesc> y, z, y2, w, mm, u[6], pp, res, pp3, res3, w1, mm1, u1[4];
   const bool adapt = P->fit_prec == BCUR_BF16X3A;
-  std::vector<GemmDesc> gram[2], app[2];
+  std::vector<GemmDesc> gram[2], app[2], gram1;
   const int64_t LP = P->lp;
   for (int b = 0; b < B; ++b) {
     const Item& I = P->it[b];
@@ -297,6 +301,15 @@ bcur_status_t build_groups(bcur_batch_t P) {
       d.triA = 1;
       app[pass].push_back(d);
     }
+    if (adapt)  // one-term copies of the second pass's Grams; the pairs only on refinement
+      for (size_t j = gram[1].size() - 2; j < gram[1].size(); ++j) {
+        GemmDesc g1 = gram[1][j];
+        g1.parts = 1;
+        g1.A_lo = nullptr;
+        g1.B_lo = nullptr;
+        gram1.push_back(g1);
+        gram[1][j].run_flag = I.refine;
+      }
     // The second Cholesky-QR pass stops at L2 (no apply): Q1 = the pass-0
     // result (index 1), Q = Q1 L2^{-T}.  W1 = A Q1_R^T (m x r); M1 = Q1_C W1
     // (c x r); M2 = L2C^{-T} L2C^{-1} M1 L2R^{-T} L2R^{-1}, so that
@@ -400,6 +413,7 @@ bcur_status_t build_groups(bcur_batch_t P) {
   }
   for (int i = 0; i < 6; ++i) jobs.push_back({&P->gU[i], &u[i], 0, u_names[i], all, {}});
   if (adapt) {
+    jobs.push_back({&P->gGram1, &gram1, 0, "gram1", all, {}});
     jobs.push_back({&P->gW1, &w1, 0, "w", all, {}});
     jobs.push_back({&P->gM1, &mm1, 0, "m", all, {}});
     for (int i = 0; i < 4; ++i) jobs.push_back({&P->gU1[i], &u1[i], 0, u_names[i], all, {}});
@@ -478,11 +492,21 @@ bcur_status_t orth(bcur_batch_t P, int s0, int s1, bool want_lb, cudaStream_t s)
   return BCUR_OK;
 }
 
+// The wide Cholesky of pass `pass` for every item (gated: only the items whose
+// refinement flag is set), one launch per size class.
+bcur_status_t wide_chol_all(bcur_batch_t P, int pass, cudaStream_t s, int gated) {
+  const int wmax[3] = {128, 256, 512};
+  for (int c = 0; c < 3; ++c)
+    BCUR_TRY(wide_chol(P->d_items, P->wide_entries[c], P->wide_count[c], wmax[c], pass, s, gated));
+  return BCUR_OK;
+}
+
 // The fit and residual of the adaptive split fit: W1, M1 and M2 and the
-// residual with one BF16 term; the finish sets each item's refinement flag
-// (residual_needs_refine); the three-term launches redo those products and
-// the residual for the flagged items only; the two products that give U take
-// the flag's term count.
+// residual with one BF16 term (after a second Cholesky-QR pass with one
+// term); the finish sets each item's refinement flag (residual_needs_refine);
+// the three-term launches redo the second pass, those products and the
+// residual for the flagged items only; the two products that give U take the
+// flag's term count.
 bcur_status_t enqueue_adaptive_fit(bcur_batch_t P, cudaStream_t s) {
   const int B = P->B;
   BCUR_TRY(run_group(P->gW1, s));
@@ -501,6 +525,11 @@ bcur_status_t enqueue_adaptive_fit(bcur_batch_t P, cudaStream_t s) {
   BCUR_TRY(mark(P, s, "finish"));
   BCUR_TRY(split_inputs(P->d_items, P->d_io, P->rows8.w(), P->rows8.total, B, P->lp, s, 2));
   BCUR_TRY(mark(P, s, "split"));
+  // the second Cholesky-QR pass again with three terms, for the refined items
+  BCUR_TRY(run_group(P->gGram[1], s));
+  BCUR_TRY(mark(P, s, "qr_gram"));
+  BCUR_TRY(wide_chol_all(P, 1, s, 1));
+  BCUR_TRY(mark(P, s, "wide_chol"));
   BCUR_TRY(run_group(P->gW, s));
   BCUR_TRY(mark(P, s, "w_gemm"));
   BCUR_TRY(run_group(P->gM, s));
@@ -563,13 +592,13 @@ bcur_status_t enqueue(bcur_batch_t P, cudaStream_t s) {
   BCUR_TRY(gather(P->d_items, P->d_io, P->ctiles.w(), P->ctiles.total, P->rrows.w(),
                   P->rrows.total, s));
   BCUR_TRY(mark(P, s, "gather"));
-  // Cholesky-QR2 of C^T and R, both sides in each launch
+  // Cholesky-QR2 of C^T and R, both sides in each launch (the adaptive fit
+  // takes the second pass's Grams with one term first)
   for (int pass = 0; pass < 2; ++pass) {
-    BCUR_TRY(run_group(P->gGram[pass], s));
+    const bool one = pass == 1 && P->fit_prec == BCUR_BF16X3A;
+    BCUR_TRY(run_group(one ? P->gGram1 : P->gGram[pass], s));
     BCUR_TRY(mark(P, s, "qr_gram"));
-    const int wmax[3] = {128, 256, 512};
-    for (int c = 0; c < 3; ++c)
-      BCUR_TRY(wide_chol(P->d_items, P->wide_entries[c], P->wide_count[c], wmax[c], pass, s));
+    BCUR_TRY(wide_chol_all(P, pass, s, 0));
     BCUR_TRY(mark(P, s, "wide_chol"));
     if (pass == 0) {  // the second pass stops at L2 (see build_groups)
       BCUR_TRY(run_group(P->gApply[pass], s));
