@@ -482,11 +482,6 @@ Lane lane_of(bcur_plan_t P, int i) {
           o.tc_scratch2};
 }
 
-bcur_status_t split_on(cudaStream_t st, const float* X, int64_t ldx, int64_t rows, int64_t cols,
-                       S16 out, int64_t ldo) {
-  return split_bf16(X, ldx, rows, cols, out.h, out.l, ldo, st);
-}
-
 // Tensor-core GEMM on BF16 operands; never falls back (ENOTSUP is an error).
 bcur_status_t g16_on(bcur_plan_t P, const Lane& ln, GemmDesc d, int parts) {
   d.parts = parts;
@@ -659,8 +654,8 @@ bcur_status_t wide_cqr2_16(bcur_plan_t P, const Lane& ln, S16 pr[2], int64_t w, 
 // The second Cholesky-QR pass of wide_cqr2_16 again with three terms (the
 // Gram Q1^T Q1 of the pair q1 and its factorisation into L2, L2i), every
 // launch gated by the device flag run: the refinement of the adaptive fit,
-// whose first pass took one term.  Same launches as the split fit's second
-// pass, so a refined result is the split fit's bit for bit.
+// which took this pass with one term first.  Same launches as the split fit's
+// second pass, so a refined result is the split fit's bit for bit.
 bcur_status_t redo_second_pass(bcur_plan_t P, S16 q1, int64_t w, int64_t h, int64_t ld, float* G,
                                float* L2, float* L2i, int* kept, const int* run) {
   const Lane ln = lane_of(P, 0);
