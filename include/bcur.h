@@ -558,9 +558,10 @@ bcur_status_t bcur_batch_set_workspace(bcur_batch_t plan, void* workspace, size_
 
 /* Fit precision of every item of the batch: BCUR_BF16X3 (the default; every
  * product of the fit as a split BF16 pair) or BCUR_BF16X3A (the adaptive
- * form of bcur_plan's fit_prec: each item's core products W, M and M2 and its
- * residual first with one BF16 term, redone with three for the items whose
- * one-term residual is too coarse for the error it reports, e < 0.031; the
+ * form of bcur_plan's fit_prec: each item's second Cholesky-QR pass Grams,
+ * core products W, M and M2 and its residual first with one BF16 term, redone
+ * with three (with that pass's Cholesky) for the items whose one-term
+ * residual is too coarse for the error it reports, e < 0.031; the
  * two products that give U take the item's term count).  An item's choice
  * depends only on its own data, so its results stay the same alone or in any
  * batch.  Call before bcur_batch_set_workspace.  Errors: BCUR_EINVAL (NULL
