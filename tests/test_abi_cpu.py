@@ -128,14 +128,7 @@ def test_workspace_grows_with_blocks(lib):
 
 
 def _batch_plan(lib, items, q=2):
-    from paper_1703_06065_gb300 import _lib
-
-    arr = (_lib.BatchItem * max(1, len(items)))()
-    for i, it in enumerate(items):
-        a = arr[i]
-        a.m, a.n, a.lda = it["m"], it["n"], it.get("lda", it["n"])
-        a.k, a.p, a.block = it["k"], it["p"], it["block"]
-        a.g_col, a.g_row = it["g_col"], it["g_row"]
+    arr = _lib_batch_items(lib, items)
     h = ctypes.c_void_p()
     ws = ctypes.c_size_t()
     st = lib.bcur_batch_plan(arr, len(items), q, None, ctypes.byref(h), ctypes.byref(ws))
@@ -250,3 +243,87 @@ def test_handles_of_the_other_kind_are_refused(lib):
     dummy = ctypes.c_void_p(0x1000)
     assert lib.bcur_scores(h, dummy, dummy, dummy, dummy) == 8   # still a plan (no workspace)
     lib.bcur_destroy(h)
+
+
+def test_stage_plan_and_batch_calls_refuse_bad_arguments_on_the_host(lib):
+    """The stage calls, the plan calls after bcur_plan and the batch calls
+    refuse NULL operands, out-of-range sizes, a missing or short workspace
+    and calls out of order before any work is enqueued."""
+    p = ctypes.c_void_p(0x1000)
+    F64, F32, BF16 = 0, 1, 3
+    # GEMMs
+    assert lib.bcur_gemm(4, 4, 4, None, 4, 0, p, 4, 0, p, 4, F32, F32, None) == 1
+    assert lib.bcur_gemm(-1, 4, 4, p, 4, 0, p, 4, 0, p, 4, F32, F32, None) == 1
+    assert lib.bcur_gemm(4, 4, 4, p, 4, 0, p, 4, 0, p, 4, F64, F32, None) == 1  # F64 data, F32
+    assert lib.bcur_gemm_split(4, 4, 4, p, None, 4, 0, p, p, 4, 1, p, 4, None) == 1
+    # the fused residual
+    ws_need = lib.bcur_residual_workspace(300, 500, F32)
+    assert ws_need >= 16
+    assert lib.bcur_residual(None, 500, p, 8, p, 500, 300, 500, 8, F32, F32, p, p, ws_need,
+                             None) == 1
+    assert lib.bcur_residual(p, 400, p, 8, p, 500, 300, 500, 8, F32, F32, p, p, ws_need,
+                             None) == 1                                  # ldx < n
+    assert lib.bcur_residual(p, 500, None, 8, p, 500, 300, 500, 8, F32, F32, p, p, ws_need,
+                             None) == 1                                  # r > 0 without P
+    assert lib.bcur_residual(p, 500, p, 8, p, 500, 300, 500, 8, F32, F32, p, p, ws_need - 8,
+                             None) == 2                                  # workspace too small
+    assert lib.bcur_residual_noalloc(p, 500, p, 8, p, 500, 300, 500, 8, BF16, F32, p,
+                                     None) == 1                          # BF16 needs prec BF16
+    assert lib.bcur_residual_noalloc(p, 500, p, 8, p, 500, 300, 500, 8, 9, 9, p, None) == 1
+    # block scores, stable rank, sampling
+    off = (ctypes.c_int64 * 3)(0, 16, 32)
+    assert lib.bcur_block_scores(None, F32, 4, 32, 32, off, 2, p, None) == 1
+    assert lib.bcur_block_scores(p, F32, 4, 32, 16, off, 2, p, None) == 1     # ldf < h
+    assert lib.bcur_block_scores(p, BF16, 4, 32, 32, off, 2, p, None) == 1    # dtype
+    assert lib.bcur_block_stable_rank_workspace(4, 2) > 0
+    assert lib.bcur_block_stable_rank(p, F32, 129, 32, 32, off, 2, p, p, 1 << 20, None) == 1
+    assert lib.bcur_sample_blocks(None, 2, p, 1, 0, p, None, None) == 1
+    assert lib.bcur_sample_blocks(p, 2, p, 3, 0, p, None, None) == 1          # g > G
+    assert lib.bcur_sample_blocks(p, 0, p, 0, 0, p, None, None) == 1          # G < 1
+    # Alg. 1 as printed
+    assert lib.bcur_alg1_workspace(64, 32, None, 2, 8, 1, F32) == 0
+    assert lib.bcur_alg1_workspace(64, 32, off, 2, 8, 1, F32) > 0
+    # plan calls before a workspace, and with NULL arguments
+    d, keep = _desc()
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    assert lib.bcur_plan(ctypes.byref(d), None, ctypes.byref(h), ctypes.byref(ws)) == 0
+    c64 = ctypes.c_int64()
+    assert lib.bcur_factors(h, p, p, p) == 8
+    assert lib.bcur_rank(h, ctypes.byref(c64), ctypes.byref(c64), None, None) == 8
+    assert lib.bcur_truncate(h, p, 4, p, p, p) == 8
+    assert lib.bcur_sample(h, None, p, p, p, p, p, None, None) == 1
+    lib.bcur_destroy(h)
+    assert lib.bcur_factors(None, p, p, p) == 1
+    assert lib.bcur_sync_status(None) == 1
+    # batch calls
+    arr = _lib_batch_items(lib, [_GOOD, _GOOD])
+    hb = ctypes.c_void_p()
+    wsb = ctypes.c_size_t()
+    assert lib.bcur_batch_plan(arr, 2, 2, None, ctypes.byref(hb), ctypes.byref(wsb)) == 0
+    cm, rm, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    assert lib.bcur_batch_dims(hb, 1, ctypes.byref(cm), ctypes.byref(rm), ctypes.byref(nl)) == 0
+    assert (cm.value, rm.value) == (_GOOD["g_col"] * _GOOD["block"], _GOOD["g_row"] * _GOOD["block"])
+    assert lib.bcur_batch_dims(hb, 2, None, None, None) == 1              # no item 2
+    assert lib.bcur_batch_set_workspace(hb, ctypes.c_void_p(0x1001), wsb.value) == 1  # misaligned
+    assert lib.bcur_batch_set_workspace(hb, ctypes.c_void_p(0x1000), wsb.value - 256) == 2
+    lab, ms = ctypes.c_char_p(), ctypes.c_double()
+    assert lib.bcur_batch_profile_count(hb) == 0
+    assert lib.bcur_batch_profile_entry(hb, 0, ctypes.byref(lab), ctypes.byref(ms)) == 1
+    lib.bcur_batch_destroy(hb)
+    assert lib.bcur_batch_dims(None, 0, None, None, None) == 1
+    assert lib.bcur_batch_set_stream(None, None) == 1
+    assert lib.bcur_batch_profile(None, 1) == 1
+    assert lib.bcur_batch_profile_count(None) == 0
+
+
+def _lib_batch_items(lib, items):
+    from paper_1703_06065_gb300 import _lib
+
+    arr = (_lib.BatchItem * max(1, len(items)))()
+    for i, it in enumerate(items):
+        a = arr[i]
+        a.m, a.n, a.lda = it["m"], it["n"], it.get("lda", it["n"])
+        a.k, a.p, a.block = it["k"], it["p"], it["block"]
+        a.g_col, a.g_row = it["g_col"], it["g_row"]
+    return arr
